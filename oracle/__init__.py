@@ -1,0 +1,19 @@
+"""FP64 CPU oracle for the preconditioned SPS hot path.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
+statement of what the GPU library computes: the Joseph projector (C, plain
+loops), the polyenergetic forward model and PWLS objective (Eqs. 1-2), the SPS
+update (Eqs. 3-9), the quadratic penalty (Eq. 13, Eqs. 18-19), the Fourier,
+modified-Fourier, Haar, per-ray/per-pixel block and cross-material Fourier
+preconditioners (Eqs. 11-24) and the preconditioned iteration (Sec. II-C).
+It shares no code with the CUDA path and never imports it; only the tests,
+the smoke check and the benchmark's CPU-baseline leg may use it.
+
+Parity pins: every function here is checked in ``tests/test_oracle_*.py``
+against closed forms, invariants and brute force (chord lengths, adjoint
+identity, finite differences, circulant/Haar/block exactness, 8x8 brute-force
+minimisers).  Whole-run iterate histories have no external pin beyond the
+per-step pins: parity unpinned for 50/100-iteration trajectories as such.
+"""
+from .projector import IdentityProjector, Projector, build as build_c  # noqa: F401
+from . import model, penalty, haar, precond, psps, build  # noqa: F401

@@ -1,0 +1,121 @@
+"""Oracle forward model, PWLS objective, gradient and SPS per-ray quantities.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+Notation: rays i, energies E, channels c, materials m.  l[m,i] are material
+line integrals (l = A x_m for the image problems, l = x for projection-domain
+decomposition), Q[E,m] mass attenuation per unit density, S[c,E] the channel
+sensitivity with the gain folded in (MBIR: one energy, one channel, Q = 1,
+S = I0).  Everything is FP64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def weights(y: np.ndarray) -> np.ndarray:
+    """Inverse data covariance: Sigma_y = diag(max(y, 1)), a plug-in Poisson
+    variance (the paper only says the covariance is known, Sec. II-A)."""
+    return 1.0 / np.maximum(y, 1.0)
+
+
+def transmission(Q: np.ndarray, l: np.ndarray) -> np.ndarray:
+    """t[E,i] = exp(-sum_m Q[E,m] l[m,i])  (the exp(-A x) of Eq. 1)."""
+    return np.exp(-(Q @ l))
+
+
+def forward_model(Q: np.ndarray, S: np.ndarray, l: np.ndarray) -> np.ndarray:
+    """Mean counts y_bar[c,i] = sum_E S[c,E] exp(-[Q l]_E,i)  (Eq. 1 with the
+    operator outside the exponential B -> S, inside A -> Q or QA)."""
+    return S @ transmission(Q, l)
+
+
+def data_objective(Q, S, l, y) -> float:
+    """L = 1/2 (y - y_bar)^T Sigma^-1 (y - y_bar)  (Eq. 2, second line)."""
+    r = forward_model(Q, S, l) - y
+    return 0.5 * float(np.sum(weights(y) * r * r))
+
+
+def data_grad_l(Q, S, l, y) -> np.ndarray:
+    """dL/dl[m,i] = -sum_E Q[E,m] t[E,i] sum_c S[c,E] w[c,i] (y_bar - y)[c,i]."""
+    t = transmission(Q, l)
+    r = S @ t - y
+    v = S.T @ (weights(y) * r)
+    return -(Q.T @ (t * v))
+
+
+def sps_curvature(Q, S, l, y) -> np.ndarray:
+    """Per (energy, ray) maximum curvature c of the separable surrogate.
+
+    The data term is majorised, for each ray and energy, by the 1-D function
+    h(z) = 1/2 eta e^{-2z} + rho e^{-z} of z = [Q l]_E (Sec. II-B, Eqs. 3-9),
+    with eta = B^T Sigma^-1 B 1 and rho = B^T Sigma^-1 B t^n - eta t^n
+    - B^T Sigma^-1 y (the paper's rho printed with x^n where the current
+    transmission t^n belongs).  h''(z) = 2 eta u^2 + rho u with u = e^{-z} is a
+    convex quadratic in u, so its maximum over z >= min(0, z^n) sits at an
+    end point: c = max(0, 2 eta u_hi^2 + rho u_hi), u_hi = max(1, t^n).  (The
+    cited maximum-curvature rule is not in the paper; this is its derivation
+    for this h.)
+    """
+    w = weights(y)
+    t = transmission(Q, l)
+    r = S @ t - y
+    sigma = S.sum(axis=1)                    # sum_E S[c,E]
+    eta = S.T @ (w * sigma[:, None])         # [E, i]
+    rho = S.T @ (w * r) - eta * t            # [E, i]
+    u_hi = np.maximum(1.0, t)
+    return np.maximum(0.0, 2.0 * eta * u_hi * u_hi + rho * u_hi)
+
+
+def curvature_numerator(Q, S, l, y, gamma_m: np.ndarray) -> np.ndarray:
+    """kappa[m,i] = sum_E Q[E,m] gamma[E,i] c[E,i] with gamma[E,i] =
+    sum_m Q[E,m] gamma_m[m,i]; the separable curvature is then
+    d = A^T kappa (Eq. 4: d = diag(A^T D{gamma} c) with A -> QA)."""
+    c = sps_curvature(Q, S, l, y)
+    gE = Q @ gamma_m
+    return Q.T @ (gE * c)
+
+
+def line_terms(Q, S, l, q, y, alpha: float):
+    """Data part of phi(alpha) = L(l + alpha q) and its first two derivatives
+    in alpha, summed over all rays."""
+    w = weights(y)
+    la = l + alpha * q
+    t = transmission(Q, la)
+    r = S @ t - y
+    dz = Q @ q
+    dyb = -(S @ (t * dz))
+    d2yb = S @ (t * dz * dz)
+    f = 0.5 * float(np.sum(w * r * r))
+    f1 = float(np.sum(w * r * dyb))
+    f2 = float(np.sum(w * (dyb * dyb + r * d2yb)))
+    return f, f1, f2
+
+
+def water_fit(Q, S, y, water: int = 0, n_newton: int = 10) -> np.ndarray:
+    """Per-ray single-material (water) line-integral estimate used to
+    approximate D = D{exp(-Q l_hat)} before reconstruction (Sec. II-D: assume
+    all attenuation is water).  Gauss-Newton on the per-ray PWLS misfit,
+    10 iterations from l = 0, clamped to l >= 0."""
+    w = weights(y)
+    qw = Q[:, water][:, None]                 # [E, 1]
+    lw = np.zeros(y.shape[1])
+    for _ in range(n_newton):
+        t = np.exp(-qw * lw[None, :])         # [E, i]
+        r = S @ t - y                         # [c, i]
+        J = -(S @ (qw * t))                   # d y_bar / d lw  [c, i]
+        g = np.sum(w * r * J, axis=0)
+        h = np.sum(w * J * J, axis=0)
+        step = np.where(h > 0, g / np.where(h > 0, h, 1.0), 0.0)
+        lw = np.maximum(lw - step, 0.0)
+    return lw
+
+
+def fisher_blocks(Q, S, y, t_hat: np.ndarray) -> np.ndarray:
+    """Per-ray F_i = Q^T D_i S^T Sigma_i^-1 S D_i Q  ([i, m, m']), the block of
+    the Fisher information in line-integral space (Sec. II-D/E Hessians with
+    B = I, G folded into S), with D_i = diag(t_hat[:, i])."""
+    w = weights(y)                            # [c, i]
+    J = S[:, :, None] * (t_hat[None, :, :])   # [c, E, i] : S_cE t_Ei
+    Jm = np.einsum("cei,em->cmi", J, Q)       # [c, m, i]
+    return np.einsum("cmi,ci,cni->imn", Jm, w, Jm)

@@ -1,0 +1,286 @@
+"""Oracle preconditioners x = M x' (Sec. II-C to II-E): builds and applies.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+Every preconditioner offers M v, M^T v and the elementwise-absolute |M| v,
+|M|^T v on arrays v[n_mat][*shape].  |M| (any elementwise upper bound of the
+absolute entries of M) is what makes the separable SPS curvature valid for a
+signed operator A M: d' = |M|^T A^T(gamma~ c) + |M|^T |R| |M| 1 with
+gamma~ = A |M| 1.
+
+Readings of the paper used here:
+* Eigenvalue estimate (Eq. 12): Lambda~ = D{U dx}^-1 D{U H dx}, evaluated as
+  written: the ratio of the two transforms.  For a shift-variant H the
+  phase-corrected Fourier ratio is complex and its real part goes negative at
+  some frequencies (a Joseph impulse response is not point-symmetric), which
+  the -1/2 power cannot take; the modulus |Lambda~| is used instead, and for
+  N_k x N_k blocks its matrix analogue, the Hermitian polar factor
+  (L^H L)^1/2, of which the real part is kept.  Both equal Lambda exactly when
+  H is circulant.
+* Haar test functions: Eq. 12 with the single test function U^T 1 (the
+  paper's choice) lets every coefficient's response overlap with all others;
+  on CT Hessians that gives estimates from -4x to 6x the true diagonal
+  u_k^T H u_k.  The same estimator is therefore applied with a family of test
+  functions U^T xi, each xi the indicator of one subband of one level
+  restricted to one class of a P x P lattice of positions (P = 3), so that the
+  coefficients excited together are well separated; the union covers every
+  coefficient once.  ``lattice=0`` selects the paper's single U^T 1.
+* Fourier: periodic unitary 2-D DFT per material on the image grid (no
+  padding); the test impulse sits at the centre pixel (ny//2, nx//2).
+* Eigenvalues are clamped to >= 1e-6 x the largest before the -1/2 power.
+* M0 = D{(F+R)1}^-1/2 (Eq. 15) or, with several materials, the per-pixel /
+  per-ray N_k x N_k blocks of (F+R)1_k (Eqs. 16, 21-22) raised to -1/2; a
+  block's eigenvalues are clamped to >= 1e-6 x its largest one, and pixels
+  whose block trace is <= 1e-12 x the largest trace get M0 = 0 (outside the
+  field of view).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import haar
+
+EIG_FLOOR = 1e-6
+ZERO_FLOOR = 1e-12
+
+
+def inv_sqrt_blocks(H: np.ndarray, floor: str = "block", zero_rule: bool = True) -> np.ndarray:
+    """Symmetric inverse square root of every N_k x N_k block in H[n, k, k]
+    (symmetrised first).  floor='block' clamps each block's eigenvalues to
+    >= EIG_FLOOR x its own largest; floor='global' to EIG_FLOOR x the largest
+    over all blocks."""
+    H = 0.5 * (H + np.swapaxes(H, -1, -2))
+    lam, V = np.linalg.eigh(H)
+    lmax = lam.max(axis=-1, keepdims=True)
+    if floor == "global":
+        lo = EIG_FLOOR * lam.max()
+    else:
+        lo = EIG_FLOOR * lmax
+    lam_c = np.maximum(lam, lo)
+    out = np.einsum("nij,nj,nkj->nik", V, 1.0 / np.sqrt(np.maximum(lam_c, 1e-300)), V)
+    if zero_rule:
+        tr = np.trace(H, axis1=-2, axis2=-1)
+        dead = tr <= ZERO_FLOOR * tr.max()
+        out[dead] = 0.0
+    return out
+
+
+# ---------------------------------------------------------------------------
+# block-diagonal M0 (per pixel / per ray)
+# ---------------------------------------------------------------------------
+
+class Block:
+    """M = blockdiag(M0_j); blocks B[n_pix, m, m] act on v[m][*shape]."""
+
+    def __init__(self, B: np.ndarray, shape):
+        self.B = np.asarray(B, dtype=np.float64)
+        self.shape = tuple(shape)
+        self.nm = self.B.shape[-1]
+
+    def _mul(self, B, v):
+        vf = v.reshape(self.nm, -1)
+        return np.einsum("nij,jn->in", B, vf).reshape((self.nm,) + self.shape)
+
+    def M(self, v):
+        return self._mul(self.B, v)
+
+    def MT(self, v):
+        return self._mul(np.swapaxes(self.B, 1, 2), v)
+
+    def absM(self, v):
+        return self._mul(np.abs(self.B), v)
+
+    def absMT(self, v):
+        return self._mul(np.swapaxes(np.abs(self.B), 1, 2), v)
+
+
+class Identity:
+    def M(self, v):
+        return v.copy()
+
+    MT = absM = absMT = M
+
+
+# ---------------------------------------------------------------------------
+# Fourier family
+# ---------------------------------------------------------------------------
+
+def centre_index(shape):
+    return tuple(n // 2 for n in shape)
+
+
+def fourier_eigenvalues(apply_H, shape, k: int = 0, nm: int = 1) -> np.ndarray:
+    """Lambda~ of Eq. (12) for one material: |DFT(H delta_j) / DFT(delta_j)|
+    with delta_j the unit impulse at the centre pixel."""
+    d = np.zeros((nm,) + tuple(shape))
+    d[(k,) + centre_index(shape)] = 1.0
+    r = apply_H(d)
+    lam = np.fft.fftn(r[k]) / np.fft.fftn(d[k])
+    return np.abs(lam)
+
+
+def clamp_eigs(lam: np.ndarray) -> np.ndarray:
+    return np.maximum(lam, EIG_FLOOR * lam.max())
+
+
+class Fourier:
+    """M = m0 U^H diag(lam^-1/2) U m0 (Eq. 14 with m0 = 1, Eq. 17 with the
+    zero-frequency normalisation m0 = M0 of Eq. 15).  One material.
+    |M| = m0 |C| m0 with |C| the circulant of the absolute kernel
+    |IDFT(lam^-1/2)|."""
+
+    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None):
+        self.s = 1.0 / np.sqrt(clamp_eigs(lam))
+        self.shape = lam.shape
+        self.m0 = np.ones(self.shape) if m0 is None else np.asarray(m0, dtype=np.float64).reshape(self.shape)
+        kern = np.fft.ifftn(self.s).real
+        self.s_abs = np.fft.fftn(np.abs(kern)).real
+
+    def _filt(self, spec, v):
+        out = np.empty_like(v, dtype=np.float64)
+        for k in range(v.shape[0]):
+            out[k] = self.m0 * np.fft.ifftn(spec * np.fft.fftn(self.m0 * v[k])).real
+        return out
+
+    def M(self, v):
+        return self._filt(self.s, v)
+
+    MT = M
+
+    def absM(self, v):
+        return self._filt(self.s_abs, v)
+
+    absMT = absM
+
+
+class CrossFourier:
+    """Cross-material Fourier preconditioner (Eq. 24):
+    M = M0^T U^H L^-1/2 U M0 with L block diagonal over spatial frequencies
+    (one N_k x N_k block per frequency), M0 the per-pixel blocks."""
+
+    def __init__(self, L: np.ndarray, M0: Block):
+        # L[f..., k', k] real symmetric blocks
+        self.shape = L.shape[:-2]
+        nm = L.shape[-1]
+        L = polar_real(L) if np.iscomplexobj(L) else L
+        flat = L.reshape(-1, nm, nm)
+        Li = inv_sqrt_blocks(flat, floor="global", zero_rule=False)
+        self.Li = Li.reshape(L.shape)
+        kern = np.fft.ifftn(self.Li, axes=tuple(range(len(self.shape)))).real
+        self.Li_abs = np.fft.fftn(np.abs(kern), axes=tuple(range(len(self.shape)))).real
+        self.M0 = M0
+
+    def _mid(self, W, v):
+        ax = tuple(range(1, v.ndim))
+        V = np.fft.fftn(v, axes=ax)
+        out = np.einsum("...ij,j...->i...", W, V)
+        return np.fft.ifftn(out, axes=ax).real
+
+    def M(self, v):
+        return self.M0.MT(self._mid(self.Li, self.M0.M(v)))
+
+    def MT(self, v):
+        return self.M0.MT(self._mid(np.swapaxes(self.Li, -1, -2), self.M0.M(v)))
+
+    def absM(self, v):
+        return self.M0.absMT(self._mid(self.Li_abs, self.M0.absM(v)))
+
+    def absMT(self, v):
+        return self.M0.absMT(self._mid(np.swapaxes(self.Li_abs, -1, -2), self.M0.absM(v)))
+
+
+def cross_fourier_blocks(apply_H, M0: Block, shape, nm: int) -> np.ndarray:
+    """L_k of Eq. (23) for every material k: DFT of the zero-frequency-
+    normalised response M0^T H M0 delta_jk divided by DFT(delta_jk), stacked as
+    L[f..., k', k] (complex; see ``polar_real``)."""
+    L = np.zeros(tuple(shape) + (nm, nm), dtype=complex)
+    ax = tuple(range(1, len(shape) + 1))
+    for k in range(nm):
+        d = np.zeros((nm,) + tuple(shape))
+        d[(k,) + centre_index(shape)] = 1.0
+        r = M0.MT(apply_H(M0.M(d)))
+        den = np.fft.fftn(d[k])
+        R = np.fft.fftn(r, axes=ax) / den[None]
+        L[..., :, k] = np.moveaxis(R, 0, -1)
+    return L
+
+
+def polar_real(L: np.ndarray) -> np.ndarray:
+    """Re((L^H L)^1/2), symmetrised, for every block L[..., k, k] (the block
+    analogue of |lambda|)."""
+    shp = L.shape
+    flat = L.reshape(-1, shp[-1], shp[-1])
+    G = np.einsum("nji,njk->nik", flat.conj(), flat)
+    lam, V = np.linalg.eigh(G)
+    P = np.einsum("nij,nj,nkj->nik", V, np.sqrt(np.maximum(lam, 0.0)), V.conj())
+    P = P.real
+    P = 0.5 * (P + np.swapaxes(P, -1, -2))
+    return P.reshape(shp)
+
+
+# ---------------------------------------------------------------------------
+# Haar wavelet
+# ---------------------------------------------------------------------------
+
+class Haar:
+    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT M0 (Eq. 20); |M| uses |U| and |M0|.
+    One material, 2-D images."""
+
+    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None):
+        self.s = 1.0 / np.sqrt(clamp_eigs(lam))
+        self.shape = lam.shape
+        self.m0 = np.ones(self.shape) if m0 is None else np.asarray(m0, dtype=np.float64).reshape(self.shape)
+
+    def _op(self, v, absolute):
+        out = np.empty_like(v, dtype=np.float64)
+        for k in range(v.shape[0]):
+            c = haar.forward(self.m0 * v[k], absolute)
+            out[k] = self.m0 * haar.transpose(self.s * c, absolute)
+        return out
+
+    def M(self, v):
+        return self._op(v, False)
+
+    MT = M
+
+    def absM(self, v):
+        return self._op(v, True)
+
+    absMT = absM
+
+
+def haar_test_sets(shape, lattice: int = 3):
+    """Coefficient sets (boolean masks in the Mallat layout) whose indicator
+    xi gives one test function U^T xi: per level, per detail subband (HL top
+    right, LH bottom left, HH bottom right) and per class (a, c) of the
+    position within the subband modulo ``lattice``; the final LL block is one
+    more set.  ``lattice=0`` returns the single all-ones set."""
+    if lattice == 0:
+        return [np.ones(shape, dtype=bool)]
+    sets = []
+    ii, jj = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
+    lv = haar._levels(*shape)
+    for h, w in lv:
+        h2, w2 = h // 2, w // 2
+        for (r0, c0) in ((0, w2), (h2, 0), (h2, w2)):
+            inband = (ii >= r0) & (ii < r0 + h2) & (jj >= c0) & (jj < c0 + w2)
+            for a in range(min(lattice, h2)):
+                for c in range(min(lattice, w2)):
+                    sel = inband & ((ii - r0) % lattice == a) & ((jj - c0) % lattice == c)
+                    if sel.any():
+                        sets.append(sel)
+    h, w = lv[-1] if lv else shape
+    sets.append((ii < h // 2 if lv else ii < h) & (jj < w // 2 if lv else jj < w))
+    return sets
+
+
+def haar_eigenvalues(apply_H, shape, lattice: int = 3) -> np.ndarray:
+    """Eq. (12) with wavelet test functions dx = U^T xi (Sec. II-D-3):
+    Lambda~_k = [U H dx]_k / [U dx]_k for the coefficients k that xi excites."""
+    lam = np.zeros(shape)
+    for sel in haar_test_sets(shape, lattice):
+        dx = haar.transpose(sel.astype(np.float64))
+        r = haar.forward(apply_H(dx[None])[0])
+        den = haar.forward(dx)
+        lam[sel] = r[sel] / den[sel]
+    return np.abs(lam)

@@ -1,0 +1,167 @@
+"""Pins for the oracle forward model, objective, gradient, SPS curvature,
+penalty and water fit (CPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from synth import FAN2D, PAR2D, Geometry
+
+
+def small_spectral(nm=2, ne=7, nc=3, seed=0):
+    rng = np.random.default_rng(seed)
+    Q = rng.uniform(0.01, 0.05, (ne, nm))
+    S = rng.uniform(10.0, 200.0, (nc, ne))
+    return Q, S
+
+
+def test_monoenergetic_reduces_to_beer_lambert(oracle_lib):
+    """One energy, one channel, Q = 1, S = I0: y_bar = I0 exp(-l)."""
+    from oracle import model
+    l = np.array([[0.0, 0.5, 2.0, -0.3]])
+    got = model.forward_model(np.ones((1, 1)), np.full((1, 1), 1e4), l)
+    assert np.allclose(got[0], 1e4 * np.array([1.0, math.exp(-0.5), math.exp(-2.0), math.exp(0.3)]),
+                       rtol=1e-15)
+
+
+def test_energy_independent_attenuation(oracle_lib):
+    """Q with identical rows: every channel sees exp(-q.l) times its total
+    sensitivity sum_E S[c,E] (non-square shapes catch transposes)."""
+    from oracle import model
+    rng = np.random.default_rng(1)
+    q = np.array([0.02, 0.07])
+    Q = np.tile(q, (5, 1))
+    S = rng.uniform(1, 10, (3, 5))
+    l = rng.uniform(0, 30, (2, 11))
+    got = model.forward_model(Q, S, l)
+    want = S.sum(1)[:, None] * np.exp(-(q @ l))[None, :]
+    assert np.allclose(got, want, rtol=1e-14)
+
+
+def _fd_check(f, grad, x, h_rel=1e-6, n_dir=6, seed=0):
+    rng = np.random.default_rng(seed)
+    for _ in range(n_dir):
+        v = rng.standard_normal(x.shape)
+        h = h_rel * max(1.0, np.abs(x).max())
+        fd = (f(x + h * v) - f(x - h * v)) / (2 * h)
+        an = float(np.sum(grad * v))
+        assert abs(fd - an) <= 1e-7 * max(abs(an), abs(fd), 1e-30) + 1e-9 * abs(f(x)), (fd, an)
+
+
+@pytest.mark.parametrize("spectral", [False, True])
+def test_gradient_finite_differences(oracle_lib, spectral):
+    from oracle import psps
+    g = Geometry(FAN2D, 10, 9, 1, 1.0, 1.0, 1.0, 15, 0.0, 2 * math.pi, 17, 1, 1.2, 1.0, 40.0, 80.0)
+    A = oracle_lib.Projector(g)
+    rng = np.random.default_rng(2)
+    if spectral:
+        Q, S = small_spectral()
+        beta = np.array([[3.0, 0.4], [0.4, 2.0]])
+        x = rng.uniform(0, 2.0, (2, 9, 10))
+    else:
+        Q, S = np.ones((1, 1)), np.full((1, 1), 1e3)
+        beta = np.array([[5.0]])
+        x = rng.uniform(0, 0.05, (1, 9, 10))
+    l = A.project(x)
+    from oracle import model
+    y = np.round(model.forward_model(Q, S, l) * rng.uniform(0.9, 1.1, (S.shape[0], g.n_rays)))
+    st = psps.Setup(A, Q, S, y, beta)
+    _fd_check(lambda z: st.objective(z), st.gradient(x), x)
+
+
+def test_sps_curvature_majorises():
+    """The parabola with curvature c touching h(z) = 1/2 eta e^{-2z} + rho
+    e^{-z} at z^n lies above h on z >= min(0, z^n) for every ray/energy; the
+    construction is exercised with eta, rho from random spectra and data."""
+    from oracle import model
+    rng = np.random.default_rng(4)
+    Q, S = small_spectral(nm=2, ne=6, nc=3, seed=5)
+    l = rng.uniform(-0.5, 40.0, (2, 400))
+    y = rng.poisson(model.forward_model(Q, S, rng.uniform(0, 40, (2, 400)))).astype(float)
+    w = model.weights(y)
+    t = model.transmission(Q, l)
+    r = S @ t - y
+    eta = S.T @ (w * S.sum(1)[:, None])
+    rho = S.T @ (w * r) - eta * t
+    c = model.sps_curvature(Q, S, l, y)
+    zn = Q @ l
+
+    def h(z):
+        return 0.5 * eta * np.exp(-2 * z) + rho * np.exp(-z)
+
+    def dh(z):
+        return -eta * np.exp(-2 * z) - rho * np.exp(-z)
+    for s in np.linspace(0, 1, 41):
+        lo = np.minimum(0.0, zn)
+        z = lo + s * (zn + 3.0 - lo)
+        surr = h(zn) + dh(zn) * (z - zn) + 0.5 * c * (z - zn) ** 2
+        assert np.all(surr >= h(z) - 1e-9 * (np.abs(h(z)) + 1))
+    # the surrogate's gradient at z^n is the true data gradient (paper's rho
+    # with t^n): -Q^T (eta t^2 + rho t) == dL/dl
+    gs = -(Q.T @ (eta * t * t + rho * t))
+    assert np.allclose(gs, model.data_grad_l(Q, S, l, y), rtol=1e-12, atol=1e-12 * np.abs(gs).max())
+
+
+def test_fisher_blocks_are_gauss_newton_hessian():
+    """At noiseless data the Hessian of L in l is J^T W J = F_i (FD check)."""
+    from oracle import model
+    rng = np.random.default_rng(6)
+    Q, S = small_spectral(nm=3, ne=8, nc=4, seed=7)
+    l = rng.uniform(0, 20, (3, 5))
+    y = model.forward_model(Q, S, l)
+    F = model.fisher_blocks(Q, S, y, model.transmission(Q, l))
+    h = 1e-5
+    for i in range(5):
+        H = np.zeros((3, 3))
+        for a in range(3):
+            e = np.zeros((3, 5))
+            e[a, i] = h
+            H[:, a] = (model.data_grad_l(Q, S, l + e, y)[:, i] - model.data_grad_l(Q, S, l - e, y)[:, i]) / (2 * h)
+        assert np.allclose(H, F[i], rtol=1e-6, atol=1e-8 * np.abs(F[i]).max())
+
+
+def test_water_fit_recovers_water():
+    from oracle import model
+    E = np.arange(20.0, 121.0)
+    Q = synth.material_Q(E, ["water", "bone"], np.random.default_rng(0))
+    S = np.stack([1e5 * synth.kramers(E, 80.0), 1e5 * synth.kramers(E, 120.0)])
+    lw = np.array([0.0, 10.0, 100.0, 250.0])
+    y = model.forward_model(Q, S, np.stack([lw, np.zeros(4)]))
+    assert np.allclose(model.water_fit(Q, S, y), lw, rtol=1e-7, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# penalty
+# ---------------------------------------------------------------------------
+
+def _pairs(shape):
+    idx = np.arange(int(np.prod(shape))).reshape(shape)
+    out = []
+    for ax in range(len(shape)):
+        a = np.moveaxis(idx, ax, 0)
+        out += list(zip(a[:-1].ravel(), a[1:].ravel()))
+    return out
+
+
+@pytest.mark.parametrize("shape", [(5, 7), (3, 4, 5)])
+def test_penalty_pairs_and_gradient(shape):
+    from oracle.penalty import Penalty, gamma_apply
+    rng = np.random.default_rng(8)
+    beta = np.array([[2.0, 0.3], [0.3, 1.5]])
+    x = rng.standard_normal((2,) + shape)
+    pen = Penalty(beta)
+    xf = x.reshape(2, -1)
+    want = 0.0
+    for j, k in _pairs(shape):
+        dj = xf[:, j] - xf[:, k]
+        want += 0.5 * float(dj @ beta @ dj)
+    assert abs(pen.value(x) - want) <= 1e-12 * abs(want)
+    assert np.allclose(gamma_apply(np.ones(shape)), 0.0)
+    _fd_check(pen.value, pen.apply(x), x)
+    # |Gamma| 1 = 2 |N_j|
+    nb = np.zeros(int(np.prod(shape)))
+    for j, k in _pairs(shape):
+        nb[j] += 1
+        nb[k] += 1
+    assert np.allclose(pen.abs_apply(np.ones((2,) + shape))[0].ravel(), 2 * nb * np.abs(beta[0]).sum())

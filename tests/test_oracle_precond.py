@@ -1,0 +1,162 @@
+"""Pins for the oracle Haar transform and preconditioners (CPU): exactness on
+Hessians that are diagonal in the assumed basis, orthonormality, closed-form
+block square roots and the elementwise bounds |M| that the separable
+curvature relies on."""
+import math
+
+import numpy as np
+import pytest
+
+from synth import Geometry, PAR2D
+
+
+def dense(op, shape, nm=1):
+    n = nm * int(np.prod(shape))
+    cols = []
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        cols.append(op(e.reshape((nm,) + tuple(shape))).ravel())
+    return np.stack(cols, 1)
+
+
+def even_positive(shape, rng, lo=0.5):
+    G = rng.uniform(lo, 3.0, shape)
+    Gr = G[tuple(np.meshgrid(*[(-np.arange(n)) % n for n in shape], indexing="ij"))]
+    return 0.5 * (G + Gr)
+
+
+def test_haar_orthonormal_and_abs():
+    from oracle import haar
+    shape = (8, 8)
+    U = dense(lambda v: haar.forward(v[0])[None], shape)
+    UT = dense(lambda v: haar.transpose(v[0])[None], shape)
+    assert np.allclose(U @ U.T, np.eye(64), atol=1e-14)
+    assert np.allclose(UT, U.T, atol=1e-15)
+    Ua = dense(lambda v: haar.forward(v[0], absolute=True)[None], shape)
+    UaT = dense(lambda v: haar.transpose(v[0], absolute=True)[None], shape)
+    assert np.array_equal(Ua, np.abs(U))
+    assert np.array_equal(UaT, np.abs(U).T)
+    # the coarsest coefficient of an N x N image is its sum / N
+    x = np.random.default_rng(0).random(shape)
+    assert abs(haar.forward(x)[0, 0] - x.sum() / 8) < 1e-13
+
+
+def test_inv_sqrt_2x2_closed_form():
+    from oracle.precond import inv_sqrt_blocks
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((50, 2, 2))
+    H = np.einsum("nij,nkj->nik", B, B) + 0.1 * np.eye(2)
+    got = inv_sqrt_blocks(H, zero_rule=False)
+    for h, g in zip(H, got):
+        s = math.sqrt(np.linalg.det(h))
+        t = math.sqrt(np.trace(h) + 2 * s)
+        sq = (h + s * np.eye(2)) / t          # closed-form principal square root
+        assert np.allclose(g, np.linalg.inv(sq), rtol=1e-12, atol=1e-13)
+
+
+def test_fourier_exact_on_circulant():
+    from oracle import precond
+    shape = (12, 10)
+    rng = np.random.default_rng(2)
+    lam = even_positive(shape, rng)
+
+    def apply_H(v):
+        return np.stack([np.fft.ifftn(lam * np.fft.fftn(v[k])).real for k in range(v.shape[0])])
+    est = precond.fourier_eigenvalues(apply_H, shape)
+    assert np.allclose(est, lam, rtol=1e-12)
+    P = precond.Fourier(est)
+    v = rng.standard_normal((1,) + shape)
+    assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-11, atol=1e-11)
+    # modified Fourier (Eq. 17): M = M0 U^H Lambda~^-1/2 U M0 with Lambda~ the
+    # spectrum of N = M0 H M0.  When N is circulant its estimate is exact and
+    # the two-sided form gives M^T H M = M0 N^-1/2 N N^-1/2 M0 = M0^2.
+    lamN = precond.fourier_eigenvalues(lambda z: 0.25 * apply_H(z), shape)
+    P2 = precond.Fourier(lamN, np.full(shape, 0.5))
+    assert np.allclose(P2.MT(apply_H(P2.M(v))), 0.25 * v, rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("lattice", [0, 3])
+def test_haar_exact_on_wavelet_diagonal(lattice):
+    from oracle import haar, precond
+    shape = (16, 16)
+    rng = np.random.default_rng(3)
+    lam = rng.uniform(0.2, 5.0, shape)
+
+    def apply_H(v):
+        return np.stack([haar.transpose(lam * haar.forward(v[k])) for k in range(v.shape[0])])
+    est = precond.haar_eigenvalues(apply_H, shape, lattice=lattice)
+    assert np.allclose(est, lam, rtol=1e-12)
+    P = precond.Haar(est)
+    v = rng.standard_normal((1,) + shape)
+    assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-11, atol=1e-11)
+
+
+def test_haar_test_sets_partition():
+    from oracle.precond import haar_test_sets
+    for shape in [(16, 16), (64, 64), (8, 8)]:
+        cnt = np.zeros(shape, int)
+        for s in haar_test_sets(shape, 3):
+            cnt += s
+        assert (cnt == 1).all()
+
+
+def test_block_exact_without_coupling(oracle_lib):
+    """A = I (projection domain), R = 0: the per-ray blocks are the whole
+    Hessian, so M0^T H M0 = I for every ray."""
+    from oracle import build, model, psps
+    rng = np.random.default_rng(4)
+    E = np.arange(20.0, 81.0)
+    import synth
+    Q = synth.material_Q(E, ["water", "bone"], rng)
+    S = np.stack([1e5 * synth.kramers(E, 60.0), 1e5 * synth.kramers(E, 80.0)])
+    l = np.stack([rng.uniform(0, 200, 30), rng.uniform(0, 20, 30)])
+    y = rng.poisson(model.forward_model(Q, S, l)).astype(float)
+    st = psps.Setup(oracle_lib.IdentityProjector(30), Q, S, y, None)
+    P = build.build(st, "block")
+    F = build.fisher(st)
+    for i in range(30):
+        B = P.B[i]
+        assert np.allclose(B.T @ F[i] @ B, np.eye(2), atol=1e-9)
+
+
+def test_cross_fourier_exact_on_block_circulant():
+    from oracle import precond
+    shape = (8, 6)
+    nm = 3
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal(shape + (nm, nm))
+    idx = tuple(np.meshgrid(*[(-np.arange(n)) % n for n in shape], indexing="ij"))
+    G = 0.5 * (G + G[idx])
+    Lb = np.einsum("...ij,...kj->...ik", G, G) + 0.5 * np.eye(nm)
+
+    def apply_H(v):
+        V = np.fft.fftn(v, axes=(1, 2))
+        return np.fft.ifftn(np.einsum("...ij,j...->i...", Lb, V), axes=(1, 2)).real
+    M0 = precond.Block(np.tile(np.eye(nm), (int(np.prod(shape)), 1, 1)), shape)
+    L = precond.cross_fourier_blocks(apply_H, M0, shape, nm)
+    assert np.allclose(L, Lb, rtol=1e-11, atol=1e-11)
+    P = precond.CrossFourier(L, M0)
+    v = rng.standard_normal((nm,) + shape)
+    assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-10, atol=1e-10)
+
+
+def test_abs_bounds_dominate(oracle_lib):
+    """|M| >= |M_ij| elementwise (dense, tiny grid) for every preconditioner
+    built on a real projector-based Hessian."""
+    import synth
+    from oracle import build, psps
+    g = Geometry(PAR2D, 8, 8, 1, 1.0, 1.0, 1.0, 12, 0.0, math.pi, 13, 1, 1.0, 1.0)
+    A = oracle_lib.Projector(g)
+    img = synth.render(g, [synth.Ellipse(0.5, -0.3, 2.5, 3.0, 0.2, 0.02)])
+    y = np.round(1e4 * np.exp(-A.project(img[None])))
+    st = psps.Setup(A, np.ones((1, 1)), np.full((1, 1), 1e4), y, np.array([[50.0]]))
+    for kind in ["fourier", "mod_fourier", "haar", "block"]:
+        P = build.build(st, kind)
+        Md = dense(P.M, st.shape)
+        MTd = dense(P.MT, st.shape)
+        Ad = dense(P.absM, st.shape)
+        ATd = dense(P.absMT, st.shape)
+        assert np.allclose(MTd, Md.T, atol=1e-12 * np.abs(Md).max())
+        assert (Ad >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all(), kind
+        assert np.allclose(ATd, Ad.T, atol=1e-12 * np.abs(Ad).max())
