@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark: preconditioned-SPS iterations/s on one GB300 for the 2-D fan-beam
+MBIR workload (512x512 at 0.5 mm, 720 views over 360 deg, 888 curved bins,
+SID 500 / SDD 1000 mm, water phantom with inserts, I0 = 1e5, beta = 1e4,
+Haar-wavelet preconditioner with the line search), plus wall time to a 1e-4
+relative objective gap for PSPS and for plain SPS on the same GPU.
+
+A step is one full preconditioned SPS iteration (model, backprojection,
+preconditioner applies, projection, line search, update) replayed as a CUDA
+graph.  L2 (129 MB) is flushed with a 256 MB write between timed steps; each
+step is timed with CUDA events on the launching stream.
+
+--impl reference times the FP64 CPU oracle's iteration on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "precond-SPS iters/s & time to 1e-4 rel objective gap vs plain SPS, one GB300"
+WORKLOAD = "c2_fan2d_512_haar"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.index = index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(prob, n_iter: int):
+    """The FP64 oracle's PSPS iteration on the same workload, timed; the Haar
+    eigenvalues are built with the paper's single test function (one
+    Hessian application) to keep the sample bounded -- the per-iteration
+    work does not depend on the eigenvalue values."""
+    import oracle
+    from oracle import build as obuild, model, precond, psps as opsps
+    st = opsps.Setup(oracle.Projector(prob.geom), prob.Q, prob.S, prob.y, prob.beta)
+    F = obuild.fisher(st)
+    aH = obuild.make_apply_H(st, F)
+    m0 = obuild.m0_blocks(st, F)[:, 0, 0].reshape(st.shape)
+    lam = precond.haar_eigenvalues(lambda v: m0[None] * aH(m0[None] * v), st.shape, lattice=0)
+    P = precond.Haar(lam, m0)
+    t0 = time.perf_counter()
+    opsps.run(st, P, n_iter, opsps.LineSearch())
+    dt = time.perf_counter() - t0
+    # run() adds one final exact projection + objective; count it as overhead
+    return n_iter / dt, dt
+
+
+def reference_arm(args, prob):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_c()
+    t_start = time.perf_counter()
+    rate_w, _ = oracle_sample(prob, 1)
+    per = 1.0 / rate_w
+    budget = 150.0
+    k = max(1, min(args.steps, int(budget / max(per, 1e-3))))
+    rate, dt = oracle_sample(prob, k)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": k, "warmup": 1, "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"kind": "oracle", "value": rate, "unit": "iter/s", "cores": 1,
+                             "sample": f"{k} FP64 oracle PSPS-Haar iterations of the full 512^2 / 720x888 "
+                                       f"fan-beam workload (single-threaded C projector + NumPy)"},
+            "e2e": {"value": rate, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line), flush=True)
+
+
+def gap_runs(p, plan, spec, yd, beta, pc, n_star: int, n_cmp: int):
+    """Objective histories for PSPS (Haar) and plain SPS (with and without the
+    line search); Phi* from a long PSPS run."""
+    st = p.State(plan, spec, pc, yd, beta, graph=True)
+    h_star = p.psps_step(st, n_star)
+    out = {}
+    for name, pcx, ls in [("psps_haar", pc, True), ("sps", None, False), ("sps_ls", None, True)]:
+        s = p.State(plan, spec, pcx, yd, beta, line_search=ls, graph=True)
+        out[name] = p.psps_step(s, n_cmp)
+    phi_star = min(float(np.min(h_star)), *[float(np.min(v)) for v in out.values()])
+    return phi_star, out
+
+
+def ours(args, prob):
+    import torch
+
+    import paper_2010_01371_gb300 as p
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    y_host = torch.as_tensor(prob.y.astype(np.float32)).pin_memory()
+    yd = y_host.to(dev)
+    t0 = time.perf_counter()
+    plan = p.Plan(prob.geom)
+    spec = p.Spectrum(prob.Q, prob.S)
+    pc = p.Precond(plan, spec, "haar", yd, prob.beta)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    st = p.State(plan, spec, pc, yd, prob.beta, line_search=True, graph=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(args.warmup):
+        p.psps_step(st, 1, history=False)
+    torch.cuda.synchronize()
+    p.psps_profile(st, True)
+    p.psps_step(st, 1, history=False)          # re-capture the graph with timers
+    p.psps_profile(st, True)                   # reset totals
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = p.psps_launch_count(st)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.psps_step(st, 1, history=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop()
+    launches = p.psps_launch_count(st) - launches0
+    prof = p.psps_profile_read(st)
+    p.psps_profile(st, False)
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    # end to end through the public API with host buffers: every step uploads
+    # the measured counts from pinned memory and reads back the objective.
+    st2 = p.State(plan, spec, pc, yd, prob.beta, line_search=True, graph=True)
+    p.psps_step(st2, 1, history=True)
+    y_stage = torch.empty_like(yd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y_stage.copy_(y_host, non_blocking=True)
+        p.psps_step(st2, 1, history=True)      # synchronises, copies Phi back
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # roofline of the dominant stage
+    n_pix, n_rays = plan.n_pix, plan.n_rays
+    stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    alg_bytes = {
+        "backproject": 2 * 4 * (n_rays + n_pix),   # 2 channels: sinograms in, images out
+        "project": 4 * (n_rays + n_pix),
+        "model": 4 * (2 * n_rays + 2 * n_rays + n_rays),   # l, gamma, y in; g, kappa out
+        "linesearch": 4 * 3 * n_rays * 8,                   # l, q, y per evaluation (3 + 8 halvings max)
+        "precond": 4 * n_pix * 16,
+        "update": 4 * 2 * (n_pix + n_rays) * 2,
+        "reproject": 4 * (n_rays + n_pix),
+    }[dom]
+    hbm, src = peaks()
+    achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9 if stage_ms[dom] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "image": "512x512@0.5mm", "sinogram": "720x888 fan curved",
+                       "precond": "haar(M0, lattice 3)", "line_search": True, "graph": True,
+                       "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3)},
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline,
+            "e2e": {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": int(yd.numel() * 4),
+                    "d2h_bytes_per_step": 16}}
+    if rank == 0 and not args.no_gap:
+        t0 = time.perf_counter()
+        phi_star, runs = gap_runs(p, plan, spec, yd, prob.beta, pc, args.gap_star, args.gap_iters)
+        # per-iteration times of each method from short timed runs
+        per_iter = {}
+        for name, pcx, ls in [("psps_haar", pc, True), ("sps", None, False), ("sps_ls", None, True)]:
+            s = p.State(plan, spec, pcx, yd, prob.beta, line_search=ls, graph=True)
+            p.psps_step(s, 3, history=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.psps_step(s, 20, history=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per_iter[name] = e0.elapsed_time(e1) / 20
+        gap = {"target": 1e-4, "phi_star": phi_star, "phi_star_iters": args.gap_star}
+        for name, h in runs.items():
+            g = (h - phi_star) / (h[0] - phi_star)
+            hit = np.nonzero(g <= 1e-4)[0]
+            it = int(hit[0]) if hit.size else None
+            gap[name] = {"iters": it, "ms_per_iter": per_iter[name],
+                         "ms_to_gap": (it * per_iter[name]) if it is not None else None,
+                         "gap_at_end": float(g[-1]), "iters_run": len(h) - 1}
+        gap["wall_s"] = time.perf_counter() - t0
+        line["time_to_gap"] = gap
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build_c()
+        rate, dt = oracle_sample(prob, args.cpu_iters)
+        line["cpu_baseline"] = {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_iters} FP64 oracle PSPS-Haar iterations of the same "
+                                          f"workload ({dt:.1f} s, single-threaded)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-gap", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--gap-iters", type=int, default=300)
+    ap.add_argument("--gap-star", type=int, default=1500)
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    args = ap.parse_args()
+    import synth
+    prob = synth.config2()
+    if args.impl == "reference":
+        reference_arm(args, prob)
+    else:
+        ours(args, prob)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * mbir.h -- C ABI of the GB300 preconditioned-SPS library (libpsps.so).
+ *
+ * The library evaluates one preconditioned separable-parabolic-surrogates
+ * (PSPS) iteration for penalized weighted least-squares CT reconstruction
+ * (MBIR), projection-domain material decomposition and one-step model-based
+ * material decomposition (MBMD), following Tivnan, Wang & Stayman,
+ * "A Preconditioned Algorithm for Model-Based Iterative CT Reconstruction and
+ * Material Decomposition from Spectral CT Data" (arXiv 2010.01371):
+ *   mean model            y_bar = B exp(-A x)                    (Sec. II-A, Eq. 1)
+ *   objective             1/2 (y - y_bar)^T Sigma^-1 (y - y_bar) + 1/2 x^T R x (Eq. 2)
+ *   SPS update            Sec. II-B, Eqs. 3-9
+ *   preconditioned SPS    x = M x', operator A -> A M            (Sec. II-C)
+ *   preconditioners       Fourier / modified Fourier / Haar wavelet (Sec. II-D),
+ *                         per-ray cross-material blocks (Sec. II-E),
+ *                         per-pixel blocks and cross-material Fourier (Sec. II-F)
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an mbir_status; on failure mbir_last_error()
+ *     returns a thread-local message.  Invalid arguments return
+ *     MBIR_ERR_ARG before anything is launched or written.
+ *   - Array pointers named x, l, y, grad, ... are DEVICE pointers owned by the
+ *     caller; they must stay valid until the work queued on `stream` is
+ *     done.  Calls are asynchronous on `stream` unless documented otherwise.
+ *   - Images are row-major [n_mat][nz][ny][nx] (2-D: [n_mat][ny][nx]) FP32;
+ *     sinograms are [n_chan or n_mat][n_views][n_v][n_u] (2-D: [..][n_views][n_u]).
+ *   - Handles (mbir_plan, mbmd_spectrum, psps_precond, psps_state) are owned by
+ *     the library: created by *_create, released by *_destroy.  A handle may
+ *     be used from one host thread at a time.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef MBIR_H
+#define MBIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mbir_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    MBIR_OK = 0,
+    MBIR_ERR_ARG = -1,            /* invalid argument or shape          */
+    MBIR_ERR_CUDA = -2,           /* a CUDA runtime call failed         */
+    MBIR_ERR_OOM = -3,            /* device allocation failed           */
+    MBIR_ERR_NONFINITE = -4,      /* a reduction produced NaN / Inf     */
+    MBIR_ERR_TIMEOUT = -5,        /* a bounded device wait gave up      */
+    MBIR_ERR_UNIMPLEMENTED = -6   /* option not available in this build */
+} mbir_status;
+
+enum { MBIR_PAR2D = 0, MBIR_FAN2D = 1, MBIR_CONE3D = 2 };
+
+/* Scan geometry (lengths in mm, angles in radians).
+ * Pixel (ix,iy,iz) is centred at ((ix-(nx-1)/2)dx, (iy-(ny-1)/2)dy, (iz-(nz-1)/2)dz).
+ * Views: angle_v = angle0 + v * angle_span / n_views.
+ *   MBIR_PAR2D : ray direction -(cos a, sin a); bin b crosses the centre line at
+ *                t_b = (b-(n_u-1)/2) du along (-sin a, cos a).
+ *   MBIR_FAN2D : curved detector; source at sid (cos a, sin a); fan angle
+ *                g_b = (b-(n_u-1)/2) du / sdd; direction -(cos(a-g_b), sin(a-g_b)).
+ *   MBIR_CONE3D: flat detector at distance sdd from the source (sid from the
+ *                centre), axes e_u = (-sin a, cos a, 0), e_v = (0, 0, 1); pixel
+ *                (iu,iv) at ((iu-(n_u-1)/2) du, (iv-(n_v-1)/2) dv).
+ * The projector is Joseph's method: the dominant direction axis drives the
+ * march, one (bi)linearly interpolated sample per driving-axis pixel, scaled by
+ * the pixel size over |u_axis|.  (The paper leaves A unspecified; Sec. II-D.) */
+typedef struct {
+    int kind;
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int n_views;
+    double angle0, angle_span;
+    int n_u, n_v;
+    double du, dv;
+    double sid, sdd;
+} mbir_geometry;
+
+typedef struct mbir_plan mbir_plan;
+typedef struct mbmd_spectrum mbmd_spectrum;
+typedef struct psps_precond psps_precond;
+typedef struct psps_state psps_state;
+
+/* ---------------------------------------------------------------- projector */
+
+/* Create a projector plan for one geometry: precomputes the per-ray Joseph
+ * set-up (FP64 on the device, stored FP32) and owns the projector's scratch.
+ * n_mat_max bounds the number of channels later calls may pass (1..8). */
+mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, mbir_plan **out);
+mbir_status mbir_plan_destroy(mbir_plan *plan);
+/* Number of rays (sinogram entries per channel) and pixels of a plan. */
+int64_t mbir_plan_n_rays(const mbir_plan *plan);
+int64_t mbir_plan_n_pix(const mbir_plan *plan);
+
+/* l[m] = A x[m] for m < n_mat (the operator A inside the exponential,
+ * Sec. II-D; for one-step MBMD, A is applied per basis material, Sec. II-F).
+ * x: [n_mat][image], l: [n_mat][n_rays] (overwritten). */
+mbir_status mbir_project(mbir_plan *plan, const float *x, float *l, int n_mat, mbir_stream stream);
+
+/* x[m] (+)= A^T s[m]: the exact transpose of mbir_project (same weights).
+ * accumulate = 0 overwrites x, 1 adds to it. */
+mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_mat, int accumulate,
+                             mbir_stream stream);
+
+/* ------------------------------------------------------- spectral model */
+
+/* Spectral model of Sec. II-E/F: Q[E][m] (mass attenuation of material m at
+ * energy E, per unit of x), S[c][E] (channel sensitivity with the gain folded
+ * in).  Standard CT (Sec. II-D) is n_mat = n_energy = n_chan = 1, Q = 1,
+ * S = I0.  Host FP64 arrays, copied; limits: n_mat <= 4, n_chan <= 8,
+ * n_energy <= 256. */
+mbir_status mbmd_spectrum_create(int n_mat, int n_energy, int n_chan, const double *Q, const double *S,
+                                 mbmd_spectrum **out);
+mbir_status mbmd_spectrum_destroy(mbmd_spectrum *spec);
+
+/* Mean counts y_bar[c][i] = sum_E S[c][E] exp(-sum_m Q[E][m] l[m][i]) (Eq. 1).
+ * l: [n_mat][n_rays], ybar: [n_chan][n_rays]. */
+mbir_status mbmd_forward_model(const mbmd_spectrum *spec, const float *l, float *ybar, int64_t n_rays,
+                               mbir_stream stream);
+
+/* PWLS data term L = 1/2 sum_{c,i} w (y - y_bar)^2 with w = 1/max(y, 1)
+ * (Eq. 2, Sigma_y = diag(max(y,1))).  plan != NULL: x_or_l is an image
+ * [n_mat][image] and l = A x is formed internally; plan == NULL: x_or_l is
+ * the line-integral array [n_mat][n_rays] (projection-domain decomposition).
+ * *objective is a DEVICE double written with the FP64-reduced value. */
+mbir_status mbmd_objective(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
+                           int64_t n_rays, double *objective, mbir_stream stream);
+
+/* Gradient of the data term with respect to x (plan != NULL: the adjoint
+ * A^T of the per-ray derivative, recomputing l = A x and exp(-Q l) instead of
+ * storing them) or l (plan == NULL).  grad has the shape of x_or_l
+ * (overwritten); objective (device, nullable) receives L. */
+mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
+                          int64_t n_rays, float *grad, double *objective, mbir_stream stream);
+
+/* ----------------------------------------------------- preconditioners */
+
+enum {
+    PSPS_PRECOND_NONE = 0,          /* M = I: plain SPS (Sec. II-B)                   */
+    PSPS_PRECOND_FOURIER = 1,       /* M = U^H Lambda^-1/2 U (Eq. 14)                 */
+    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U M0 (Eqs. 15-17)       */
+    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT M0 (Eq. 20)   */
+    PSPS_PRECOND_BLOCK = 4,         /* per-pixel / per-ray N_k x N_k M0 (Eqs. 16, 22) */
+    PSPS_PRECOND_BLOCK_FOURIER = 5  /* cross-material Fourier (Eqs. 23-24)            */
+};
+enum { PSPS_APPLY_M = 0, PSPS_APPLY_MT = 1, PSPS_APPLY_ABS_M = 2, PSPS_APPLY_ABS_MT = 3 };
+
+/* Build a preconditioner once, before iterating (Sec. II-C): the Hessian at
+ * the solution is approximated with D from the data (standard CT: y / I0;
+ * spectral: a per-ray water-only fit), M0 from (F+R)1_k, and the eigenvalues
+ * from Eq. 12 taken in modulus (the phase-corrected ratio is complex for a
+ * shift-variant Hessian), clamped to >= 1e-6 of the largest.  Haar
+ * eigenvalues use Eq. 12 with one test function per (level, subband, class of
+ * a P x P position lattice).
+ * y: device [n_chan][n_rays]; beta: host [n_mat][n_mat] penalty strengths
+ * (NULL = no penalty); haar_lattice: lattice size P of the Haar test
+ * functions (0 = the paper's single U^T 1; 3 is the default); plan == NULL
+ * selects projection-domain decomposition (only NONE and BLOCK).
+ * Synchronises `stream`. */
+mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spectrum *spec, int kind, const float *y,
+                                    int64_t n_rays, const double *beta, int haar_lattice, mbir_stream stream,
+                                    psps_precond **out);
+mbir_status psps_precondition_destroy(psps_precond *pc);
+
+/* out = op(M) in for op in PSPS_APPLY_*, arrays shaped like the unknowns
+ * ([n_mat][image] or [n_mat][n_rays]); in and out must not alias. */
+mbir_status psps_precondition(psps_precond *pc, int op, const float *in, float *out, mbir_stream stream);
+
+/* ------------------------------------------------------------ iteration */
+
+enum {
+    PSPS_FLAG_LINESEARCH = 1, /* safeguarded Newton line search on phi(alpha)  */
+    PSPS_FLAG_NONNEG = 2,     /* clamp x >= 0 after each step (plain SPS only) */
+    PSPS_FLAG_GRAPH = 4       /* replay each iteration as a captured CUDA graph */
+};
+
+/* Create an iteration state: copies y (device [n_chan][n_rays]), beta (host
+ * [n_mat][n_mat], NULL = 0) and x0 (device image, NULL = 0); pc == NULL runs
+ * plain SPS.  The state keeps x, l = A x (updated incrementally, recomputed
+ * exactly every `reproject_every` iterations), the precomputed
+ * gamma~ = A|M|1 and |M|^T|R||M|1, and the objective history on the device.
+ * Synchronises `stream`. */
+mbir_status psps_state_create(mbir_plan *plan, const mbmd_spectrum *spec, psps_precond *pc, const float *y,
+                              int64_t n_rays, const double *beta, const float *x0, int flags,
+                              int reproject_every, mbir_stream stream, psps_state **out);
+mbir_status psps_state_destroy(psps_state *st);
+
+/* Run n_iter iterations on `stream` (asynchronous).  If objective_history
+ * (HOST, length n_iter + 1) is non-NULL the call synchronises and writes
+ * Phi before each iteration and after the last one (after an exact
+ * re-projection).  Returns MBIR_ERR_NONFINITE if a reduction went non-finite. */
+mbir_status psps_step(psps_state *st, int n_iter, double *objective_history, mbir_stream stream);
+
+/* Copy the current image x (device, [n_mat][image]) / step lengths (host,
+ * the last n alphas of the most recent psps_step call; synchronises). */
+mbir_status psps_get_image(psps_state *st, float *x, mbir_stream stream);
+mbir_status psps_get_alphas(psps_state *st, double *alphas, int n, mbir_stream stream);
+
+/* Stage timers.  psps_profile(st, 1) resets and enables CUDA-event timers
+ * around the contiguous stages of an iteration (indices below); after every
+ * psps_step call the stages of its LAST iteration are synchronised and added
+ * to the totals that psps_profile_read returns (ms[k] summed milliseconds,
+ * count[k] number of timed stage runs).  Enabling or disabling re-captures the
+ * iteration graph. */
+enum {
+    PSPS_PROF_REPROJECT = 0,   /* exact re-projection l = A x            */
+    PSPS_PROF_MODEL = 1,       /* per-ray gradient/curvature numerators  */
+    PSPS_PROF_BACKPROJECT = 2, /* A^T of both numerators (2 n_mat ch.)   */
+    PSPS_PROF_PRECOND = 3,     /* penalty, M^T, |M|^T, direction, M      */
+    PSPS_PROF_PROJECT = 4,     /* q = A p                                */
+    PSPS_PROF_LINESEARCH = 5,  /* phi(alpha) evaluations and control    */
+    PSPS_PROF_UPDATE = 6,      /* x += alpha p, l += alpha q             */
+    PSPS_PROF_STAGES = 7
+};
+mbir_status psps_profile(psps_state *st, int enable);
+mbir_status psps_profile_read(psps_state *st, double *ms, int64_t *count);
+/* Number of this library's kernels launched so far by graph replays of the
+ * iteration (PSPS_FLAG_GRAPH), counted from the captured graphs' kernel nodes. */
+mbir_status psps_launch_count(psps_state *st, int64_t *count);
+
+/* Thread-local description of the last error (never NULL). */
+const char *mbir_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBIR_H */

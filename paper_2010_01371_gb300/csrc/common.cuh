@@ -1,0 +1,140 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/mbir.h"
+
+namespace psps {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+mbir_status fail(mbir_status code, const char *fmt, ...);
+
+#define PSPS_CUDA(call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            return ::psps::fail(e_ == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA, \
+                                "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+        }                                                                                     \
+    } while (0)
+
+#define PSPS_TRY(expr)                         \
+    do {                                       \
+        mbir_status s_ = (expr);               \
+        if (s_ != MBIR_OK) return s_;          \
+    } while (0)
+
+#define PSPS_LAUNCH_CHECK() PSPS_CUDA(cudaGetLastError())
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device buffer owned by a handle (freed in the destructor).
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    mbir_status alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(MBIR_ERR_OOM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+        }
+        n = count;
+        return MBIR_OK;
+    }
+    mbir_status zero(cudaStream_t s) {
+        cudaError_t e = cudaMemsetAsync(p, 0, n * sizeof(T), s);
+        if (e != cudaSuccess) return fail(MBIR_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+        return MBIR_OK;
+    }
+};
+
+// ------------------------------------------------------------- reductions
+// Block-level FP64 sum of up to 4 values per thread; thread 0 writes the
+// block's partial sums to out[k * gridDim.x + blockIdx.x].  blockDim.x must
+// be a multiple of 32 and <= 1024.
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double *out) {
+    __shared__ double sh[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double a = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[k][wid] = a;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = lane < nw ? sh[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) out[(size_t)k * gridDim.x + blockIdx.x] = a;
+        }
+    }
+}
+
+// Sum `n` partials (fixed order, one block) into dst[0..K) (dst += if add).
+mbir_status reduce_partials(const double *partials, int n, int K, double *dst, int add, cudaStream_t s);
+
+// ------------------------------------------------------------ handles
+struct RayTable2D {
+    // Per ray (2-D): interpolation coordinate at driving index 0, its
+    // increment per driving index, weight (pixel size / |u_axis|), driving
+    // axis (0 = x, 1 = y) and the conservative range of driving indices.
+    float *f0 = nullptr, *df = nullptr, *w = nullptr;
+    int *axis_lo_hi = nullptr;  // packed: axis | (lo << 1) | (hi << 16) [lo,hi < 32768]
+};
+
+}  // namespace psps
+
+struct mbir_plan {
+    mbir_geometry g;
+    int n_mat_max = 1;
+    int64_t n_rays = 0, n_pix = 0;
+    // 2-D per-ray Joseph set-up
+    psps::DBuf<float4> ray;       // (f0, df, w, bits(axis,lo,hi))
+    // 3-D per-view set-up (source, detector origin and axes) in FP64
+    psps::DBuf<double> view3d;
+    // scratch: packed / transposed image copies for the forward projector
+    psps::DBuf<float> xrow, xcol;
+    // scratch for reductions
+    psps::DBuf<double> partials;
+    int partials_cap = 0;
+};
+
+struct mbmd_spectrum {
+    int n_mat = 1, n_energy = 1, n_chan = 1;
+    psps::DBuf<float> qs;   // device: Q[E][m] then S[c][E] then sigma[c]
+    double *hQ = nullptr, *hS = nullptr;  // host FP64 copies
+    ~mbmd_spectrum() {
+        delete[] hQ;
+        delete[] hS;
+    }
+};
+
+namespace psps {
+// projector internals (projector.cu)
+mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s);
+mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s);
+}  // namespace psps

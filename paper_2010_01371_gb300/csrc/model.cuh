@@ -1,0 +1,37 @@
+// Per-ray spectral forward model, PWLS data term, SPS numerators and
+// line-search terms (model.cu).
+#pragma once
+#include "common.cuh"
+
+namespace psps {
+
+struct SpecDev {
+    int nm, ne, nc;
+    const float *qs;  // Q[ne][nm], S[nc][ne], sigma[nc] (sigma_c = sum_E S[c][E])
+};
+
+inline SpecDev spec_dev(const mbmd_spectrum *s) { return SpecDev{s->n_mat, s->n_energy, s->n_chan, s->qs.p}; }
+
+constexpr int kModelThreads = 256;
+constexpr int kModelMaxBlocks = 2048;  // grid-stride; partial sums per block
+
+inline int model_blocks(int64_t n) {
+    int64_t b = cdiv(n, kModelThreads);
+    return (int)(b < kModelMaxBlocks ? (b < 1 ? 1 : b) : kModelMaxBlocks);
+}
+
+// data term partials (1 per block); g, kappa optional ([nm][n_rays]).
+// gamma: per-ray gamma_m = [A |M| 1]_m ([nm][n_rays]) for kappa.
+mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
+                              float *g, float *kappa, double *partials, int nblocks, cudaStream_t s);
+// phi(alpha) data terms (f, f1, f2) partials (3 per block) at alpha = *alpha;
+// returns immediately when *skip != 0.
+mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y,
+                           const double *alpha, const int *skip, double *partials, int nblocks, cudaStream_t s);
+mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s);
+// Per-ray Fisher blocks F_i = Q^T D S^T W S D Q (upper triangle, packed
+// [nm(nm+1)/2][n_rays]) with D = y / I0 (one energy/channel) or the water fit.
+mbir_status launch_fisher_blocks(const mbmd_spectrum *spec, int64_t n_rays, const float *y, float *F,
+                                 cudaStream_t s);
+
+}  // namespace psps

@@ -1,0 +1,531 @@
+// Preconditioners x = M x' (Sec. II-C to II-F): one-time build on the GPU and
+// the per-iteration applies M, M^T, |M|, |M|^T.
+//
+// Build (Sec. II-C): the Hessian at the solution H = A^T F A + R is formed
+// with the per-ray Fisher blocks F_i of the data approximated from the
+// measurements (standard CT: D = y / I0; spectral: water-only fit), applied
+// matrix-free (project, per-ray block multiply, backproject, penalty).
+//  * M0 = blocks of (F+R)1_k raised to -1/2 (Eqs. 30, 42, 53-54): column k of
+//    every per-pixel (per-ray) block is the response to the all-ones image of
+//    material k; FP64 symmetric inverse square roots on the GPU with each
+//    block's eigenvalues clamped to >= 1e-6 of its largest and blocks whose
+//    trace is <= 1e-12 of the largest set to zero (outside the field of view).
+//  * Fourier (Eqs. 28-29, 32-33): Lambda~ = |DFT(N delta_c) / DFT(delta_c)| for
+//    the unit impulse at the centre pixel c (N = H, or M0 H M0); |DFT(delta)| =
+//    1, so Lambda~ is the modulus of the response's DFT.  The modulus replaces
+//    the real part: for a shift-variant H the phase-corrected ratio is complex
+//    and its real part can be negative.
+//  * Haar (Eqs. 18, 34): Lambda~_k = [U N U^T xi]_k / [U U^T xi]_k with xi
+//    the indicator of one subband of one level restricted to one class of a
+//    P x P position lattice (one test function per set; P = 0 is the single
+//    all-ones test function U^T 1).
+//  * Eigenvalues clamped to >= 1e-6 of the largest before the -1/2 power.
+// |M| for the separable curvature: Fourier uses the circulant of the absolute
+// kernel |IDFT(Lambda~^-1/2)|, Haar the all-positive taps |U|, blocks |M0|.
+#include <cmath>
+#include <vector>
+
+#include "haar.cuh"
+#include "model.cuh"
+#include "precond.cuh"
+
+namespace psps {
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned nblk(int64_t n) { return (unsigned)cdiv(n, kThreads); }
+
+__global__ void set_value_kernel(float *p, int64_t idx, float v) { p[idx] = v; }
+
+__global__ void fill_kernel(float *p, int64_t n, float v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// out[c][j] = a[c][j] * b[j]  (b broadcast over channels)
+__global__ void mul_bcast_kernel(const float *a, const float *b, float *out, int64_t n, int channels) {
+    const int64_t tot = n * channels;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] * b[i % n];
+}
+
+// u[p][m][i] = sum_k F_i[m][k] l[p][k][i]; F packed upper triangle [nm(nm+1)/2][n_rays]
+__global__ void fisher_mul_kernel(int nm, int nprobe, int64_t n_rays, const float *__restrict__ F,
+                                  const float *__restrict__ l, float *__restrict__ u) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rays) return;
+    float f[4][4];
+    int k = 0;
+    for (int a = 0; a < nm; ++a)
+        for (int b = a; b < nm; ++b, ++k) f[a][b] = f[b][a] = F[(int64_t)k * n_rays + i];
+    for (int p = 0; p < nprobe; ++p) {
+        float lv[4];
+        for (int m = 0; m < nm; ++m) lv[m] = l[((int64_t)p * nm + m) * n_rays + i];
+        for (int m = 0; m < nm; ++m) {
+            float acc = 0.f;
+            for (int kk = 0; kk < nm; ++kk) acc = fmaf(f[m][kk], lv[kk], acc);
+            u[((int64_t)p * nm + m) * n_rays + i] = acc;
+        }
+    }
+}
+
+__global__ void modulus_kernel(const float2 *Z, float *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = hypotf(Z[i].x, Z[i].y);
+}
+
+__global__ void real_part_kernel(const float2 *Z, float *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = Z[i].x;
+}
+
+__global__ void abs_kernel(float *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fabsf(p[i]);
+}
+
+// s = max(|lam|, floor)^-1/2 (FP64 arithmetic)
+__global__ void invsqrt_clamp_kernel(const float *lam, double floor_v, float *s, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = fabs((double)lam[i]);
+        if (v < floor_v) v = floor_v;
+        s[i] = (float)(1.0 / sqrt(v));
+    }
+}
+
+// Indicator of one Haar test set in the Mallat layout of an n x n image:
+// level block size h (n, n/2, ..., 2), band 0 = HL (top right), 1 = LH
+// (bottom left), 2 = HH (bottom right), 3 = final low-pass block; lattice
+// class (a, c) of the position inside the band modulo P (P = 0: all ones).
+__global__ void haar_mask_kernel(int n, int h, int band, int a, int c, int P, float *out) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        float v = 0.f;
+        if (P == 0) {
+            v = 1.f;
+        } else {
+            const int h2 = h / 2;
+            int r0 = 0, c0 = 0;
+            bool in;
+            if (band == 3) {
+                in = i < h2 && j < h2;
+            } else {
+                r0 = band == 0 ? 0 : h2;
+                c0 = band == 1 ? 0 : h2;
+                in = i >= r0 && i < r0 + h2 && j >= c0 && j < c0 + h2;
+                if (in) in = ((i - r0) % P == a) && ((j - c0) % P == c);
+            }
+            v = in ? 1.f : 0.f;
+        }
+        out[t] = v;
+    }
+}
+
+__global__ void masked_ratio_kernel(const float *mask, const float *r, const float *den, float *lam, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (mask[i] != 0.f) lam[i] = r[i] / den[i];
+}
+
+// Symmetric inverse square root of nm x nm blocks (FP64, cyclic Jacobi).
+// H[a][b][j] full (both triangles); writes B and |B| as [a][b][j].
+__global__ void block_invsqrt_kernel(int nm, int64_t n, const float *__restrict__ H, double max_trace,
+                                     float *__restrict__ Bout, float *__restrict__ Babs) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double A[4][4], V[4][4];
+    double tr = 0.0;
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            A[a][b] = 0.5 * ((double)H[((int64_t)a * nm + b) * n + j] + (double)H[((int64_t)b * nm + a) * n + j]);
+            V[a][b] = a == b ? 1.0 : 0.0;
+        }
+    for (int a = 0; a < nm; ++a) tr += A[a][a];
+    const bool dead = !(tr > 1e-12 * max_trace);
+    if (nm > 1 && !dead) {
+        for (int sweep = 0; sweep < 20; ++sweep) {
+            double off = 0.0;
+            for (int p = 0; p < nm; ++p)
+                for (int q = p + 1; q < nm; ++q) off += A[p][q] * A[p][q];
+            if (off < 1e-30 * tr * tr) break;
+            for (int p = 0; p < nm; ++p)
+                for (int q = p + 1; q < nm; ++q) {
+                    if (A[p][q] == 0.0) continue;
+                    const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                    const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                    for (int k = 0; k < nm; ++k) {
+                        const double akp = A[k][p], akq = A[k][q];
+                        A[k][p] = cs * akp - sn * akq;
+                        A[k][q] = sn * akp + cs * akq;
+                    }
+                    for (int k = 0; k < nm; ++k) {
+                        const double apk = A[p][k], aqk = A[q][k];
+                        A[p][k] = cs * apk - sn * aqk;
+                        A[q][k] = sn * apk + cs * aqk;
+                    }
+                    for (int k = 0; k < nm; ++k) {
+                        const double vkp = V[k][p], vkq = V[k][q];
+                        V[k][p] = cs * vkp - sn * vkq;
+                        V[k][q] = sn * vkp + cs * vkq;
+                    }
+                }
+        }
+    }
+    double lam[4], lmax = 0.0;
+    for (int a = 0; a < nm; ++a) {
+        lam[a] = A[a][a];
+        if (lam[a] > lmax) lmax = lam[a];
+    }
+    for (int a = 0; a < nm; ++a) {
+        double v = lam[a];
+        if (v < 1e-6 * lmax) v = 1e-6 * lmax;
+        lam[a] = v > 0 ? 1.0 / sqrt(v) : 0.0;
+    }
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            double v = 0.0;
+            if (!dead)
+                for (int k = 0; k < nm; ++k) v += V[a][k] * lam[k] * V[b][k];
+            Bout[((int64_t)a * nm + b) * n + j] = (float)v;
+            Babs[((int64_t)a * nm + b) * n + j] = (float)fabs(v);
+        }
+}
+
+// out[m][j] = sum_k B[m][k][j] in[k][j]   (transpose: B[k][m][j])
+__global__ void block_apply_kernel(int nm, int64_t n, const float *__restrict__ B, const float *__restrict__ in,
+                                   float *__restrict__ out, int transpose) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        float v[4];
+        for (int k = 0; k < nm; ++k) v[k] = in[(int64_t)k * n + j];
+        for (int m = 0; m < nm; ++m) {
+            float acc = 0.f;
+            for (int k = 0; k < nm; ++k) {
+                const int64_t bi = transpose ? ((int64_t)k * nm + m) : ((int64_t)m * nm + k);
+                acc = fmaf(B[bi * n + j], v[k], acc);
+            }
+            out[(int64_t)m * n + j] = acc;
+        }
+    }
+}
+
+unsigned gs(int64_t n) {
+    int64_t b = cdiv(n, kThreads);
+    return (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+// Matrix-free Hessian H v = A^T F A v + R v for nprobe stacked vectors of nm
+// materials (images), or F v per ray in the projection domain.
+struct HessOp {
+    mbir_plan *plan;
+    int nm;
+    int64_t n_rays, n;
+    const float *F;
+    PenaltyDev pd;
+    bool has_pen;
+    DBuf<float> l, u;
+    mbir_status init(int max_ch) {
+        if (plan) {
+            PSPS_TRY(l.alloc((size_t)max_ch * n_rays));
+            PSPS_TRY(u.alloc((size_t)max_ch * n_rays));
+        }
+        return MBIR_OK;
+    }
+    mbir_status apply(const float *v, float *out, int nprobe, cudaStream_t s) {
+        const int ch = nprobe * nm;
+        if (!plan) {
+            fisher_mul_kernel<<<nblk(n_rays), kThreads, 0, s>>>(nm, nprobe, n_rays, F, v, out);
+            PSPS_LAUNCH_CHECK();
+            return MBIR_OK;
+        }
+        PSPS_TRY(project(plan, v, l.p, ch, s));
+        fisher_mul_kernel<<<nblk(n_rays), kThreads, 0, s>>>(nm, nprobe, n_rays, F, l.p, u.p);
+        PSPS_LAUNCH_CHECK();
+        PSPS_TRY(backproject(plan, u.p, out, ch, 0, s));
+        if (has_pen)
+            for (int p = 0; p < nprobe; ++p)
+                PSPS_TRY(launch_penalty(pd, plan->g.nx, plan->g.ny, plan->g.nz, v + (int64_t)p * nm * n, nullptr,
+                                        out + (int64_t)p * nm * n, 1, 0, nullptr, penalty_blocks(n), s));
+        return MBIR_OK;
+    }
+};
+
+mbir_status host_max_abs(const float *d, int64_t n, double &mx, cudaStream_t s) {
+    std::vector<float> h(n);
+    PSPS_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    PSPS_CUDA(cudaStreamSynchronize(s));
+    mx = 0.0;
+    for (int64_t i = 0; i < n; ++i) mx = fmax(mx, fabs((double)h[i]));
+    return MBIR_OK;
+}
+
+// s = clamp(|lam|)^-1/2 in place of `s`; s_abs = Re DFT |IDFT(s)| (Fourier only)
+mbir_status finish_scalar(psps_precond *pc, float *lam, bool fourier, cudaStream_t s) {
+    double mx;
+    PSPS_TRY(host_max_abs(lam, pc->n, mx, s));
+    if (!(mx > 0) || !std::isfinite(mx)) return fail(MBIR_ERR_NONFINITE, "preconditioner eigenvalues are not positive");
+    invsqrt_clamp_kernel<<<gs(pc->n), kThreads, 0, s>>>(lam, 1e-6 * mx, pc->s.p, pc->n);
+    PSPS_LAUNCH_CHECK();
+    if (fourier) {
+        // kernel k = IDFT(s): filter the unit impulse at the origin
+        float *imp = pc->tmp.p, *k = pc->tmp.p + pc->n;
+        PSPS_CUDA(cudaMemsetAsync(imp, 0, sizeof(float) * pc->n, s));
+        set_value_kernel<<<1, 1, 0, s>>>(imp, 0, 1.f);
+        PSPS_TRY(pc->fft.filter(1, imp, pc->Z.p, k, nullptr, pc->s.p, s));
+        abs_kernel<<<gs(pc->n), kThreads, 0, s>>>(k, pc->n);
+        PSPS_TRY(pc->fft.forward(1, k, pc->Z.p, s));
+        real_part_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->Z.p, pc->s_abs.p, pc->n);
+        PSPS_LAUNCH_CHECK();
+    } else {
+        PSPS_CUDA(cudaMemcpyAsync(pc->s_abs.p, pc->s.p, sizeof(float) * pc->n, cudaMemcpyDeviceToDevice, s));
+    }
+    return MBIR_OK;
+}
+
+}  // namespace
+
+mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out, cudaStream_t s) {
+    const bool absm = (op == PSPS_APPLY_ABS_M || op == PSPS_APPLY_ABS_MT);
+    const bool tr = (op == PSPS_APPLY_MT || op == PSPS_APPLY_ABS_MT);
+    const int64_t tot = pc->n * pc->nm;
+    switch (pc->kind) {
+        case PSPS_PRECOND_NONE:
+            if (in != out) PSPS_CUDA(cudaMemcpyAsync(out, in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, s));
+            return MBIR_OK;
+        case PSPS_PRECOND_FOURIER:
+        case PSPS_PRECOND_MOD_FOURIER:
+            // symmetric: M^T = M, |M|^T = |M|
+            return pc->fft.filter(pc->nm, in, pc->Z.p, out, pc->kind == PSPS_PRECOND_MOD_FOURIER ? pc->m0.p : nullptr,
+                                  absm ? pc->s_abs.p : pc->s.p, s);
+        case PSPS_PRECOND_HAAR:
+            return haar_apply(pc->nx, pc->nm, in, pc->tmp.p, out, pc->m0.p, pc->s.p, absm ? 0xffffffffu : 0u, s);
+        case PSPS_PRECOND_BLOCK:
+            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Babs.p : pc->B.p, in, out,
+                                                              tr ? 1 : 0);
+            PSPS_LAUNCH_CHECK();
+            return MBIR_OK;
+        default:
+            return fail(MBIR_ERR_UNIMPLEMENTED, "preconditioner kind %d not built", pc->kind);
+    }
+}
+
+mbir_status precond_apply2(psps_precond *pc, int op0, const float *in0, float *out0, int op1, const float *in1,
+                           float *out1, cudaStream_t s) {
+    PSPS_TRY(precond_apply(pc, op0, in0, out0, s));
+    return precond_apply(pc, op1, in1, out1, s);
+}
+
+}  // namespace psps
+
+using namespace psps;
+
+namespace {
+
+mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, const float *y, int64_t n_rays,
+                       const double *beta, int haar_lattice, cudaStream_t s, psps_precond *pc) {
+    const int nm = spec->n_mat;
+    pc->kind = kind;
+    pc->nm = nm;
+    pc->image = plan != nullptr;
+    if (plan) {
+        pc->nx = plan->g.nx;
+        pc->ny = plan->g.ny * (plan->g.kind == MBIR_CONE3D ? plan->g.nz : 1);
+        pc->n = plan->n_pix;
+    } else {
+        pc->nx = (int)n_rays;
+        pc->ny = 1;
+        pc->n = n_rays;
+    }
+    if (kind == PSPS_PRECOND_NONE) return MBIR_OK;
+    if (!plan && kind != PSPS_PRECOND_BLOCK)
+        return fail(MBIR_ERR_ARG, "projection-domain decomposition supports NONE and BLOCK preconditioners");
+    if ((kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_HAAR) && nm != 1)
+        return fail(MBIR_ERR_ARG, "Fourier / modified Fourier / Haar preconditioners are single-material (n_mat = 1)");
+    if (kind == PSPS_PRECOND_BLOCK_FOURIER) return fail(MBIR_ERR_UNIMPLEMENTED, "cross-material Fourier not built");
+    if (plan && plan->g.kind == MBIR_CONE3D && kind != PSPS_PRECOND_BLOCK)
+        return fail(MBIR_ERR_UNIMPLEMENTED, "3-D volumes support the BLOCK preconditioner only");
+    if (kind == PSPS_PRECOND_HAAR && !haar_supported(pc->nx, plan->g.ny))
+        return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
+    if (kind == PSPS_PRECOND_HAAR && (haar_lattice < 0 || haar_lattice > 64))
+        return fail(MBIR_ERR_ARG, "haar_lattice must be 0..64");
+    if ((kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER)) PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+
+    const int64_t n = pc->n;
+    const int nF = nm * (nm + 1) / 2;
+    DBuf<float> F;
+    PSPS_TRY(F.alloc((size_t)nF * n_rays));
+    PSPS_TRY(launch_fisher_blocks(spec, n_rays, y, F.p, s));
+
+    HessOp H{plan, nm, n_rays, n, F.p, PenaltyDev{}, false};
+    H.pd.nm = nm;
+    for (int a = 0; a < 16; ++a) H.pd.beta[a] = 0.f;
+    if (beta && plan) {
+        for (int a = 0; a < nm; ++a)
+            for (int b = 0; b < nm; ++b) {
+                H.pd.beta[a * 4 + b] = (float)beta[a * nm + b];
+                if (beta[a * nm + b] != 0.0) H.has_pen = true;
+            }
+    }
+    const int max_ch = plan ? plan->n_mat_max : nm * nm;
+    PSPS_TRY(H.init(max_ch));
+    PSPS_TRY(pc->tmp.alloc((size_t)n * (nm * 2 > max_ch ? nm * 2 : max_ch) * 2));
+    PSPS_TRY(pc->Z.alloc((size_t)n * nm * 2));
+    PSPS_TRY(pc->s.alloc(n));
+    PSPS_TRY(pc->s_abs.alloc(n));
+
+    // ---- M0 blocks from (F+R) 1_k (Eqs. 30, 53-54): all nm probes at once
+    if (nm * nm > max_ch && plan) return fail(MBIR_ERR_ARG, "plan n_mat_max must be >= n_mat^2 for the block build");
+    {
+        DBuf<float> ones, Hcols;
+        PSPS_TRY(ones.alloc((size_t)nm * nm * n));
+        PSPS_TRY(Hcols.alloc((size_t)nm * nm * n));
+        PSPS_CUDA(cudaMemsetAsync(ones.p, 0, sizeof(float) * ones.n, s));
+        for (int k = 0; k < nm; ++k)
+            fill_kernel<<<gs(n), kThreads, 0, s>>>(ones.p + ((int64_t)k * nm + k) * n, n, 1.f);
+        PSPS_LAUNCH_CHECK();
+        PSPS_TRY(H.apply(ones.p, Hcols.p, nm, s));
+        // Hcols[k][m][j] = (H 1_k)_m(j) = block[m][k] -> reorder to [m][k][j]
+        DBuf<float> Hb;
+        PSPS_TRY(Hb.alloc((size_t)nm * nm * n));
+        for (int k = 0; k < nm; ++k)
+            for (int m = 0; m < nm; ++m)
+                PSPS_CUDA(cudaMemcpyAsync(Hb.p + ((int64_t)m * nm + k) * n, Hcols.p + ((int64_t)k * nm + m) * n,
+                                          sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        // largest trace (host)
+        std::vector<float> hb((size_t)nm * nm * n);
+        PSPS_CUDA(cudaMemcpyAsync(hb.data(), Hb.p, sizeof(float) * hb.size(), cudaMemcpyDeviceToHost, s));
+        PSPS_CUDA(cudaStreamSynchronize(s));
+        double mt = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double t = 0.0;
+            for (int a = 0; a < nm; ++a) t += hb[((size_t)a * nm + a) * n + j];
+            mt = fmax(mt, t);
+        }
+        if (!(mt > 0) || !std::isfinite(mt)) return fail(MBIR_ERR_NONFINITE, "zero-frequency response is not positive");
+        PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
+        PSPS_TRY(pc->Babs.alloc((size_t)nm * nm * n));
+        block_invsqrt_kernel<<<nblk(n), kThreads, 0, s>>>(nm, n, Hb.p, mt, pc->B.p, pc->Babs.p);
+        PSPS_LAUNCH_CHECK();
+        PSPS_CUDA(cudaStreamSynchronize(s));
+    }
+    if (kind == PSPS_PRECOND_BLOCK) return MBIR_OK;
+    // one material from here on: m0 = B
+    PSPS_TRY(pc->m0.alloc(n));
+    if (kind == PSPS_PRECOND_FOURIER) {
+        fill_kernel<<<gs(n), kThreads, 0, s>>>(pc->m0.p, n, 1.f);
+    } else {
+        PSPS_CUDA(cudaMemcpyAsync(pc->m0.p, pc->B.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    const float *m0 = pc->m0.p;
+    const int nx = pc->nx, ny = plan->g.ny;
+    // N v = m0 .* H (m0 .* v)
+    auto applyN = [&](const float *v, float *out, int nprobe) -> mbir_status {
+        float *w = pc->tmp.p;  // nprobe * n
+        mul_bcast_kernel<<<gs(n * nprobe), kThreads, 0, s>>>(v, m0, w, n, nprobe);
+        PSPS_LAUNCH_CHECK();
+        PSPS_TRY(H.apply(w, out, nprobe, s));
+        mul_bcast_kernel<<<gs(n * nprobe), kThreads, 0, s>>>(out, m0, out, n, nprobe);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    };
+    DBuf<float> lam;
+    PSPS_TRY(lam.alloc(n));
+    if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER) {
+        DBuf<float> d, r;
+        PSPS_TRY(d.alloc(n));
+        PSPS_TRY(r.alloc(n));
+        PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * n, s));
+        set_value_kernel<<<1, 1, 0, s>>>(d.p, (int64_t)(ny / 2) * nx + nx / 2, 1.f);
+        PSPS_TRY(applyN(d.p, r.p, 1));
+        PSPS_TRY(pc->fft.forward(1, r.p, pc->Z.p, s));
+        modulus_kernel<<<gs(n), kThreads, 0, s>>>(pc->Z.p, lam.p, n);
+        PSPS_LAUNCH_CHECK();
+        PSPS_TRY(finish_scalar(pc, lam.p, true, s));
+        PSPS_CUDA(cudaStreamSynchronize(s));
+        return MBIR_OK;
+    }
+    // ---- Haar
+    {
+        const int P = haar_lattice;
+        struct Set {
+            int h, band, a, c;
+        };
+        std::vector<Set> sets;
+        if (P == 0) {
+            sets.push_back({nx, 0, 0, 0});
+        } else {
+            for (int h = nx; h >= 2; h /= 2) {
+                const int h2 = h / 2;
+                for (int band = 0; band < 3; ++band)
+                    for (int a = 0; a < (P < h2 ? P : h2); ++a)
+                        for (int c = 0; c < (P < h2 ? P : h2); ++c) sets.push_back({h, band, a, c});
+            }
+            sets.push_back({2, 3, 0, 0});
+        }
+        const int batch = plan->n_mat_max;
+        DBuf<float> mask, dx, r, den, coef;
+        PSPS_TRY(mask.alloc((size_t)batch * n));
+        PSPS_TRY(dx.alloc((size_t)batch * n));
+        PSPS_TRY(r.alloc((size_t)batch * n));
+        PSPS_TRY(den.alloc((size_t)batch * n));
+        PSPS_TRY(coef.alloc((size_t)batch * n));
+        DBuf<float> tmp2;
+        PSPS_TRY(tmp2.alloc((size_t)batch * n));
+        PSPS_CUDA(cudaMemsetAsync(lam.p, 0, sizeof(float) * n, s));
+        for (size_t s0 = 0; s0 < sets.size(); s0 += batch) {
+            const int nb = (int)(sets.size() - s0 < (size_t)batch ? sets.size() - s0 : batch);
+            for (int b = 0; b < nb; ++b) {
+                const Set &st = sets[s0 + b];
+                haar_mask_kernel<<<gs(n), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.c, P, mask.p + (int64_t)b * n);
+            }
+            PSPS_LAUNCH_CHECK();
+            // dx = U^T xi  (haar_inverse uses its coefficient input as scratch)
+            PSPS_CUDA(cudaMemcpyAsync(coef.p, mask.p, sizeof(float) * nb * n, cudaMemcpyDeviceToDevice, s));
+            PSPS_TRY(haar_inverse(nx, nb, coef.p, dx.p, nullptr, 0u, s));
+            PSPS_TRY(applyN(dx.p, tmp2.p, nb));
+            PSPS_TRY(haar_forward(nx, nb, tmp2.p, r.p, nullptr, nullptr, 0u, s));
+            PSPS_TRY(haar_forward(nx, nb, dx.p, den.p, nullptr, nullptr, 0u, s));
+            for (int b = 0; b < nb; ++b)
+                masked_ratio_kernel<<<gs(n), kThreads, 0, s>>>(mask.p + (int64_t)b * n, r.p + (int64_t)b * n,
+                                                               den.p + (int64_t)b * n, lam.p, n);
+            PSPS_LAUNCH_CHECK();
+        }
+        PSPS_TRY(finish_scalar(pc, lam.p, false, s));
+        PSPS_CUDA(cudaStreamSynchronize(s));
+    }
+    return MBIR_OK;
+}
+
+}  // namespace
+
+extern "C" mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spectrum *spec, int kind, const float *y,
+                                               int64_t n_rays, const double *beta, int haar_lattice, mbir_stream stream,
+                                               psps_precond **out) {
+    if (!spec || !y || !out) return fail(MBIR_ERR_ARG, "psps_precondition_build: null argument");
+    *out = nullptr;
+    if (kind < PSPS_PRECOND_NONE || kind > PSPS_PRECOND_BLOCK_FOURIER)
+        return fail(MBIR_ERR_ARG, "psps_precondition_build: unknown kind %d", kind);
+    if (plan && n_rays != plan->n_rays) return fail(MBIR_ERR_ARG, "psps_precondition_build: n_rays does not match plan");
+    if (n_rays < 1) return fail(MBIR_ERR_ARG, "psps_precondition_build: n_rays must be >= 1");
+    if (plan && spec->n_mat > plan->n_mat_max) return fail(MBIR_ERR_ARG, "psps_precondition_build: n_mat > n_mat_max");
+    psps_precond *pc = new psps_precond();
+    mbir_status st = build_impl(plan, spec, kind, y, n_rays, beta, haar_lattice, (cudaStream_t)stream, pc);
+    if (st != MBIR_OK) {
+        delete pc;
+        return st;
+    }
+    *out = pc;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status psps_precondition_destroy(psps_precond *pc) {
+    delete pc;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status psps_precondition(psps_precond *pc, int op, const float *in, float *out, mbir_stream s) {
+    if (!pc || !in || !out) return fail(MBIR_ERR_ARG, "psps_precondition: null argument");
+    if (op < PSPS_APPLY_M || op > PSPS_APPLY_ABS_MT) return fail(MBIR_ERR_ARG, "psps_precondition: bad op %d", op);
+    if (in == out) return fail(MBIR_ERR_ARG, "psps_precondition: in and out must not alias");
+    return precond_apply(pc, op, in, out, (cudaStream_t)s);
+}

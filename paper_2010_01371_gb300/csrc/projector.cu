@@ -1,0 +1,376 @@
+// Joseph ray-driven projector A and its exact transpose A^T on the GPU.
+//
+// The paper leaves the system matrix A of the mean model (Eq. 1; A -> A for
+// standard CT, Eq. 20, and A -> QA for one-step MBMD, Eq. 44) unspecified;
+// this is Joseph's method on a pixel-centred grid.  For each ray the axis with
+// the largest |u| component drives the march; at every driving-axis pixel
+// index i the ray's coordinate along the other axis is interpolated linearly
+// (2-D) between the two neighbouring pixel centres (zero outside the grid)
+// and the samples are summed with weight (pixel size) / |u_axis|.
+//
+// Design (2-D):
+//  * set-up: one FP64 thread per ray computes the interpolation coordinate at
+//    i = 0, its increment per step, the weight and a conservative range of i
+//    (outside it every sample is zero); stored as one float4 per ray and
+//    shared by the forward and the transpose so both use identical weights;
+//  * forward: one thread per ray, neighbouring threads = neighbouring bins of
+//    one view, so a warp samples neighbouring rows of the same column.  The
+//    image is re-laid out per call into an x-driven copy [ix][iy][m] and a
+//    y-driven copy [iy][ix][m] (materials packed as float/float2/float4) so
+//    both ray families read contiguous addresses; Kahan-compensated FP32
+//    accumulation along the ray;
+//  * transpose: ray-driven scatter with FP32 atomics (red.global.add).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace psps {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void ray_2d(const mbir_geometry &g, int64_t ray, double &px, double &py, double &ux,
+                                       double &uy) {
+    const int view = (int)(ray / g.n_u);
+    const int iu = (int)(ray % g.n_u);
+    const double ang = g.angle0 + view * (g.angle_span / g.n_views);
+    double c, s;
+    sincos(ang, &s, &c);
+    if (g.kind == MBIR_PAR2D) {
+        const double t = (iu - 0.5 * (g.n_u - 1)) * g.du;
+        px = -s * t;
+        py = c * t;
+        ux = -c;
+        uy = -s;
+    } else {
+        const double ga = (iu - 0.5 * (g.n_u - 1)) * g.du / g.sdd;
+        px = g.sid * c;
+        py = g.sid * s;
+        double sg, cg;
+        sincos(ang - ga, &sg, &cg);
+        ux = -cg;
+        uy = -sg;
+    }
+}
+
+// Conservative range of driving indices i in [0, n_drive-1] for which the
+// interpolation coordinate f(i) = f0 + i*df lies in (-1, n_other).
+__device__ __forceinline__ void drive_range(double f0, double df, int n_drive, int n_other, int &lo, int &hi) {
+    double a, b;
+    if (df == 0.0) {
+        if (f0 > -1.0 && f0 < (double)n_other) {
+            lo = 0;
+            hi = n_drive - 1;
+        } else {
+            lo = 1;
+            hi = 0;
+        }
+        return;
+    }
+    a = (-1.0 - f0) / df;
+    b = ((double)n_other - f0) / df;
+    if (a > b) {
+        double t = a;
+        a = b;
+        b = t;
+    }
+    double l = floor(a) - 1.0, h = ceil(b) + 1.0;
+    if (l < 0) l = 0;
+    if (h > n_drive - 1) h = n_drive - 1;
+    if (l > h) {
+        lo = 1;
+        hi = 0;
+    } else {
+        lo = (int)l;
+        hi = (int)h;
+    }
+}
+
+__global__ void setup_2d_kernel(mbir_geometry g, int64_t n_rays, float4 *tab) {
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n_rays) return;
+    double px, py, ux, uy;
+    ray_2d(g, ray, px, py, ux, uy);
+    const double cx = 0.5 * (g.nx - 1), cy = 0.5 * (g.ny - 1);
+    int axis, lo, hi;
+    double f0, df, w;
+    if (fabs(ux) >= fabs(uy)) {
+        axis = 0;
+        // f(i) = (py + ((i - cx) dx - px) uy/ux) / dy + cy
+        df = g.dx * uy / ux / g.dy;
+        f0 = (py + ((0.0 - cx) * g.dx - px) * uy / ux) / g.dy + cy;
+        w = g.dx / fabs(ux);
+        drive_range(f0, df, g.nx, g.ny, lo, hi);
+    } else {
+        axis = 1;
+        df = g.dy * ux / uy / g.dx;
+        f0 = (px + ((0.0 - cy) * g.dy - py) * ux / uy) / g.dx + cx;
+        w = g.dy / fabs(uy);
+        drive_range(f0, df, g.ny, g.nx, lo, hi);
+    }
+    const int bits = axis | (lo << 1) | (hi << 16);
+    tab[ray] = make_float4((float)f0, (float)df, (float)w, __int_as_float(bits));
+}
+
+template <int NM>
+struct Pack;
+template <>
+struct Pack<1> {
+    using T = float;
+    static constexpr int P = 1;
+    __device__ static void get(const T &v, float (&o)[1]) { o[0] = v; }
+};
+template <>
+struct Pack<2> {
+    using T = float2;
+    static constexpr int P = 2;
+    __device__ static void get(const T &v, float (&o)[2]) {
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+};
+template <>
+struct Pack<3> {
+    using T = float4;
+    static constexpr int P = 4;
+    __device__ static void get(const T &v, float (&o)[3]) {
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+    }
+};
+template <>
+struct Pack<4> {
+    using T = float4;
+    static constexpr int P = 4;
+    __device__ static void get(const T &v, float (&o)[4]) {
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+};
+
+// x [m][ny][nx] -> xrow [iy][ix][P] and xcol [ix][iy][P] (P = packed stride).
+// 32x32 tiles through shared memory for the transposed copy.
+template <int NM>
+__global__ void pack_kernel(const float *__restrict__ x, int nx, int ny, float *__restrict__ xrow,
+                            float *__restrict__ xcol) {
+    constexpr int P = Pack<NM>::P;
+    __shared__ float tile[NM][32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int64_t npix = (int64_t)nx * ny;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int iy = by + r, ix = bx + threadIdx.x;
+        if (iy < ny && ix < nx) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const float v = x[m * npix + (int64_t)iy * nx + ix];
+                tile[m][r][threadIdx.x] = v;
+                if (xrow) xrow[((int64_t)iy * nx + ix) * P + m] = v;
+            }
+            if (xrow && P > NM) xrow[((int64_t)iy * nx + ix) * P + NM] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int ix = bx + r, iy = by + threadIdx.x;
+        if (iy < ny && ix < nx) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) xcol[((int64_t)ix * ny + iy) * P + m] = tile[m][threadIdx.x][r];
+            if (P > NM) xcol[((int64_t)ix * ny + iy) * P + NM] = 0.f;
+        }
+    }
+}
+
+__device__ __forceinline__ void decode(float4 r, int &axis, int &lo, int &hi) {
+    const int bits = __float_as_int(r.w);
+    axis = bits & 1;
+    lo = (bits >> 1) & 0x7fff;
+    hi = (bits >> 16) & 0x7fff;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restrict__ tab, int64_t n_rays, int nx,
+                                                          int ny, const typename Pack<NM>::T *__restrict__ xrow,
+                                                          const typename Pack<NM>::T *__restrict__ xcol,
+                                                          float *__restrict__ l) {
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n_rays) return;
+    const float4 r = tab[ray];
+    int axis, lo, hi;
+    decode(r, axis, lo, hi);
+    const typename Pack<NM>::T *src = axis == 0 ? xcol : xrow;
+    const int n_other = axis == 0 ? ny : nx;
+    float acc[NM], comp[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
+    for (int i = lo; i <= hi; ++i) {
+        const float fy = fmaf((float)i, r.y, r.x);
+        const float fl = floorf(fy);
+        const int i0 = (int)fl;
+        const float f = fy - fl;
+        const typename Pack<NM>::T *base = src + (int64_t)i * n_other;
+        float a[NM], b[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) a[m] = b[m] = 0.f;
+        if (i0 >= 0 && i0 < n_other) Pack<NM>::get(__ldg(base + i0), a);
+        if (i0 + 1 >= 0 && i0 + 1 < n_other) Pack<NM>::get(__ldg(base + i0 + 1), b);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const float v = __fadd_rn(__fmul_rn(1.f - f, a[m]), __fmul_rn(f, b[m]));
+            const float yk = __fsub_rn(v, comp[m]);
+            const float t = __fadd_rn(acc[m], yk);
+            comp[m] = __fsub_rn(__fsub_rn(t, acc[m]), yk);
+            acc[m] = t;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) l[(int64_t)m * n_rays + ray] = acc[m] * r.z;
+}
+
+__global__ void __launch_bounds__(kThreads) back_2d_kernel(const float4 *__restrict__ tab, int64_t n_rays, int nx,
+                                                           int ny, int n_mat, const float *__restrict__ sino,
+                                                           float *__restrict__ x) {
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n_rays) return;
+    const float4 r = tab[ray];
+    int axis, lo, hi;
+    decode(r, axis, lo, hi);
+    const int64_t npix = (int64_t)nx * ny;
+    for (int m = 0; m < n_mat; ++m) {
+        const float ws = r.z * sino[(int64_t)m * n_rays + ray];
+        if (ws == 0.f) continue;
+        float *img = x + m * npix;
+        const int n_other = axis == 0 ? ny : nx;
+        for (int i = lo; i <= hi; ++i) {
+            const float fy = fmaf((float)i, r.y, r.x);
+            const float fl = floorf(fy);
+            const int i0 = (int)fl;
+            const float f = fy - fl;
+            // pixel index of (driving i, other j)
+            if (i0 >= 0 && i0 < n_other) {
+                const int64_t idx = axis == 0 ? (int64_t)i0 * nx + i : (int64_t)i * nx + i0;
+                atomicAdd(img + idx, (1.f - f) * ws);
+            }
+            if (i0 + 1 >= 0 && i0 + 1 < n_other) {
+                const int64_t idx = axis == 0 ? (int64_t)(i0 + 1) * nx + i : (int64_t)i * nx + i0 + 1;
+                atomicAdd(img + idx, f * ws);
+            }
+        }
+    }
+}
+
+template <int NM>
+mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s) {
+    constexpr int P = Pack<NM>::P;
+    const int nx = p->g.nx, ny = p->g.ny;
+    float *xrow = (NM == 1) ? nullptr : p->xrow.p;
+    dim3 blk(32, 8), grd((unsigned)cdiv(nx, 32), (unsigned)cdiv(ny, 32));
+    pack_kernel<NM><<<grd, blk, 0, s>>>(x, nx, ny, xrow, p->xcol.p);
+    PSPS_LAUNCH_CHECK();
+    const typename Pack<NM>::T *row = (NM == 1) ? (const typename Pack<NM>::T *)x
+                                                : (const typename Pack<NM>::T *)p->xrow.p;
+    (void)P;
+    fwd_2d_kernel<NM><<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(
+        p->ray.p, p->n_rays, nx, ny, row, (const typename Pack<NM>::T *)p->xcol.p, l);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+}  // namespace
+
+mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s) {
+    if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
+    int done = 0;
+    for (int m0 = 0; m0 < n_mat; m0 += 4) {
+        const int nm = n_mat - m0 < 4 ? n_mat - m0 : 4;
+        const float *xm = x + (int64_t)m0 * p->n_pix;
+        float *lm = l + (int64_t)m0 * p->n_rays;
+        switch (nm) {
+            case 1: PSPS_TRY(project_2d_nm<1>(p, xm, lm, s)); break;
+            case 2: PSPS_TRY(project_2d_nm<2>(p, xm, lm, s)); break;
+            case 3: PSPS_TRY(project_2d_nm<3>(p, xm, lm, s)); break;
+            default: PSPS_TRY(project_2d_nm<4>(p, xm, lm, s)); break;
+        }
+        done += nm;
+    }
+    (void)done;
+    return MBIR_OK;
+}
+
+mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s) {
+    if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
+    if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
+    back_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->ray.p, p->n_rays, p->g.nx, p->g.ny,
+                                                                           n_mat, sino, x);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+}  // namespace psps
+
+using namespace psps;
+
+extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, mbir_plan **out) {
+    if (!g || !out) return fail(MBIR_ERR_ARG, "mbir_plan_create: null argument");
+    *out = nullptr;
+    if (g->kind != MBIR_PAR2D && g->kind != MBIR_FAN2D && g->kind != MBIR_CONE3D)
+        return fail(MBIR_ERR_ARG, "mbir_plan_create: unknown geometry kind %d", g->kind);
+    if (g->kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "mbir_plan_create: cone-beam not built");
+    if (g->nx < 1 || g->ny < 1 || g->nx > 16384 || g->ny > 16384 || g->n_views < 1 || g->n_u < 1)
+        return fail(MBIR_ERR_ARG, "mbir_plan_create: bad sizes nx=%d ny=%d views=%d n_u=%d (1..16384)", g->nx, g->ny,
+                    g->n_views, g->n_u);
+    if (!(g->dx > 0) || !(g->dy > 0) || !(g->du > 0) || !(g->angle_span != 0))
+        return fail(MBIR_ERR_ARG, "mbir_plan_create: pixel/bin sizes must be > 0 and angle_span != 0");
+    if (g->kind == MBIR_FAN2D) {
+        const double half = 0.5 * sqrt(g->nx * g->dx * g->nx * g->dx + g->ny * g->dy * g->ny * g->dy);
+        if (!(g->sdd > 0) || !(g->sid > half))
+            return fail(MBIR_ERR_ARG, "mbir_plan_create: fan beam needs sdd > 0 and the source outside the image");
+    }
+    if (n_mat_max < 1 || n_mat_max > 8) return fail(MBIR_ERR_ARG, "mbir_plan_create: n_mat_max must be 1..8");
+    mbir_plan *p = new mbir_plan();
+    p->g = *g;
+    if (g->kind != MBIR_CONE3D) p->g.nz = 1, p->g.n_v = 1;
+    p->n_mat_max = n_mat_max;
+    p->n_rays = (int64_t)g->n_views * g->n_u;
+    p->n_pix = (int64_t)g->nx * g->ny;
+    mbir_status st;
+    if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->xcol.alloc(p->n_pix * 4)) != MBIR_OK ||
+        (st = p->xrow.alloc(p->n_pix * 4)) != MBIR_OK || (st = p->partials.alloc(8 * 4096)) != MBIR_OK) {
+        delete p;
+        return st;
+    }
+    p->partials_cap = 4096;
+    setup_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads>>>(p->g, p->n_rays, p->ray.p);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(MBIR_ERR_CUDA, "mbir_plan_create: set-up kernel: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbir_plan_destroy(mbir_plan *p) {
+    delete p;
+    return MBIR_OK;
+}
+
+extern "C" int64_t mbir_plan_n_rays(const mbir_plan *p) { return p ? p->n_rays : -1; }
+extern "C" int64_t mbir_plan_n_pix(const mbir_plan *p) { return p ? p->n_pix : -1; }
+
+extern "C" mbir_status mbir_project(mbir_plan *p, const float *x, float *l, int n_mat, mbir_stream s) {
+    if (!p || !x || !l) return fail(MBIR_ERR_ARG, "mbir_project: null argument");
+    if (n_mat < 1 || n_mat > p->n_mat_max) return fail(MBIR_ERR_ARG, "mbir_project: n_mat %d not in 1..%d", n_mat, p->n_mat_max);
+    return project(p, x, l, n_mat, (cudaStream_t)s);
+}
+
+extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate,
+                                        mbir_stream s) {
+    if (!p || !x || !sino) return fail(MBIR_ERR_ARG, "mbir_backproject: null argument");
+    if (n_mat < 1 || n_mat > p->n_mat_max)
+        return fail(MBIR_ERR_ARG, "mbir_backproject: n_mat %d not in 1..%d", n_mat, p->n_mat_max);
+    return backproject(p, sino, x, n_mat, accumulate, (cudaStream_t)s);
+}

@@ -1,0 +1,103 @@
+"""GPU forward model, PWLS objective and adjoint gradient parity with the
+FP64 oracle (standard CT and spectral)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from _helpers import phantom, rel_l2, small_geoms, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def psps():
+    import paper_2010_01371_gb300 as p
+    p.lib()
+    return p
+
+
+def spectral(nm=2):
+    E = np.arange(20.0, 141.0)
+    names = ["water", "bone", "iodine"][:nm]
+    Q = synth.material_Q(E, names, np.random.default_rng(11))
+    S = np.stack([1e5 * synth.kramers(E, 80.0), 1e5 * synth.kramers(E, 140.0)])
+    return Q, S
+
+
+def test_forward_model_parity(psps, oracle_lib):
+    from oracle import model
+    Q, S = spectral(2)
+    rng = np.random.default_rng(1)
+    l = np.stack([rng.uniform(0, 300, 5003), rng.uniform(0, 30, 5003)])
+    spec = psps.Spectrum(Q, S)
+    got = to_host(psps.mbmd_forward_model(spec, to_dev(l)))
+    want = model.forward_model(Q, S, l)
+    assert rel_l2(got, want) < 1e-5
+
+
+@pytest.mark.parametrize("case", ["mbir", "spectral"])
+def test_objective_and_gradient_parity(psps, oracle_lib, case):
+    from oracle import model
+    g = small_geoms()["fan2d_ragged"]
+    A = oracle_lib.Projector(g)
+    if case == "mbir":
+        Q, S = np.ones((1, 1)), np.full((1, 1), 1e5)
+        x_true = phantom(g, seed=2, nm=1)
+        x = 0.5 * x_true
+    else:
+        Q, S = spectral(2)
+        x_true = 20 * phantom(g, seed=3, nm=2)
+        x = 0.6 * x_true
+    y = np.random.default_rng(4).poisson(model.forward_model(Q, S, A.project(x_true))).astype(float)
+    plan = psps.Plan(g)
+    spec = psps.Spectrum(Q, S)
+    obj = float(psps.mbmd_objective(plan, spec, to_dev(x), to_dev(y)).item())
+    want_obj = model.data_objective(Q, S, A.project(x), y)
+    assert abs(obj - want_obj) <= 1e-5 * abs(want_obj)
+    grad, obj2 = psps.mbmd_gradient(plan, spec, to_dev(x), to_dev(y))
+    want = A.backproject(model.data_grad_l(Q, S, A.project(x), y))
+    assert rel_l2(to_host(grad), want) < 1e-5, rel_l2(to_host(grad), want)
+    assert abs(float(obj2.item()) - want_obj) <= 1e-5 * abs(want_obj)
+
+
+def test_projection_domain_gradient(psps, oracle_lib):
+    from oracle import model
+    Q, S = spectral(2)
+    rng = np.random.default_rng(6)
+    lt = np.stack([rng.uniform(0, 300, 4099), rng.uniform(0, 30, 4099)])
+    y = rng.poisson(model.forward_model(Q, S, lt)).astype(float)
+    l = 0.8 * lt
+    spec = psps.Spectrum(Q, S)
+    grad, obj = psps.mbmd_gradient(None, spec, to_dev(l), to_dev(y))
+    assert rel_l2(to_host(grad), model.data_grad_l(Q, S, l, y)) < 1e-5
+    want = model.data_objective(Q, S, l, y)
+    assert abs(float(obj.item()) - want) <= 1e-5 * abs(want)
+
+
+def test_autograd_adjoint(psps, oracle_lib):
+    """MBMDData: backward (hand-written adjoint) equals the oracle gradient and
+    a central finite difference of the forward along a random direction."""
+    import torch
+    from oracle import model
+    g = small_geoms()["par2d_ragged"]
+    A = oracle_lib.Projector(g)
+    Q, S = np.ones((1, 1)), np.full((1, 1), 1e4)
+    xt = phantom(g, seed=7)
+    y = np.random.default_rng(8).poisson(1e4 * np.exp(-A.project(xt))).astype(float)
+    plan, spec = psps.Plan(g), psps.Spectrum(Q, S)
+    x = to_dev(0.5 * xt).requires_grad_(True)
+    yd = to_dev(y)
+    L = psps.MBMDData.apply(x, plan, spec, yd)
+    L.backward()
+    want = A.backproject(model.data_grad_l(Q, S, A.project(0.5 * xt), y))
+    assert rel_l2(to_host(x.grad), want) < 1e-5
+    v = np.random.default_rng(9).standard_normal(xt.shape)
+    h = 1e-3 * np.abs(xt).max()
+    with torch.no_grad():
+        fp = float(psps.MBMDData.apply(to_dev(0.5 * xt + h * v), plan, spec, yd))
+        fm = float(psps.MBMDData.apply(to_dev(0.5 * xt - h * v), plan, spec, yd))
+    fd = (fp - fm) / (2 * h)
+    an = float(np.sum(want * v))
+    assert abs(fd - an) <= 1e-3 * abs(an)

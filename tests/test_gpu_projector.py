@@ -1,0 +1,96 @@
+"""GPU Joseph projector / backprojector parity with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from _helpers import phantom, rel_l2, small_geoms, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5   # relative L2, projections and backprojections
+
+
+@pytest.fixture(scope="module")
+def psps():
+    import paper_2010_01371_gb300 as p
+    p.lib()
+    return p
+
+
+@pytest.mark.parametrize("name", list(small_geoms()))
+@pytest.mark.parametrize("nm", [1, 2])
+def test_project_parity(psps, oracle_lib, name, nm):
+    g = small_geoms()[name]
+    x = phantom(g, seed=1, nm=nm)
+    plan = psps.Plan(g)
+    got = to_host(psps.mbir_project(plan, to_dev(x)))
+    want = oracle_lib.Projector(g).project(x)
+    assert got.shape == want.shape
+    assert rel_l2(got, want) < TOL, rel_l2(got, want)
+
+
+@pytest.mark.parametrize("name", list(small_geoms()))
+def test_backproject_parity(psps, oracle_lib, name):
+    g = small_geoms()[name]
+    rng = np.random.default_rng(2)
+    s = rng.random((2, g.n_rays))
+    plan = psps.Plan(g)
+    got = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    want = oracle_lib.Projector(g).backproject(s)
+    assert rel_l2(got, want) < TOL, rel_l2(got, want)
+    # accumulate = 1 adds to the existing contents
+    base = to_dev(np.ones((2,) + g.image_shape))
+    psps.mbir_backproject(plan, to_dev(s), base, accumulate=True)
+    assert rel_l2(to_host(base), want + 1.0) < TOL
+
+
+@pytest.mark.parametrize("nm", [3, 4, 5])
+def test_material_packing(psps, oracle_lib, nm):
+    g = small_geoms()["fan2d_ragged"]
+    x = phantom(g, seed=3, nm=nm)
+    plan = psps.Plan(g)
+    got = to_host(psps.mbir_project(plan, to_dev(x)))
+    assert rel_l2(got, oracle_lib.Projector(g).project(x)) < TOL
+
+
+def test_adjoint_fp32(psps):
+    g = small_geoms()["fan2d_c2_128"]
+    rng = np.random.default_rng(4)
+    x = rng.random((1,) + g.image_shape)
+    y = rng.random((1, g.n_rays))
+    plan = psps.Plan(g)
+    Ax = to_host(psps.mbir_project(plan, to_dev(x)))
+    Aty = to_host(psps.mbir_backproject(plan, to_dev(y)))
+    lhs, rhs = float(np.sum(Ax * y)), float(np.sum(x * Aty))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+def test_full_size_sampled(psps, oracle_lib):
+    """Full 512^2 / 720 x 888 fan-beam geometry: every 97th ray (plus the
+    first and last) against the oracle ray by ray, and the adjoint identity
+    at full size."""
+    prob = synth.config2()
+    g = prob.geom
+    x = prob.truth
+    plan = psps.Plan(g)
+    got = to_host(psps.mbir_project(plan, to_dev(x)))[0]
+    rays = np.unique(np.concatenate([np.arange(0, g.n_rays, 97), [g.n_rays - 1]]))
+    want = oracle_lib.Projector(g).project_rays(x[0], rays)
+    assert rel_l2(got[rays], want) < TOL, rel_l2(got[rays], want)
+    rng = np.random.default_rng(5)
+    y = rng.random((1, g.n_rays))
+    Aty = to_host(psps.mbir_backproject(plan, to_dev(y)))
+    lhs, rhs = float(np.sum(got * y[0])), float(np.sum(x * Aty))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+def test_empty_and_errors(psps):
+    import torch
+    g = small_geoms()["par2d_ragged"]
+    plan = psps.Plan(g, n_mat_max=2)
+    x = torch.zeros((3,) + g.image_shape, device="cuda")
+    with pytest.raises(psps.MbirError):
+        psps.mbir_project(plan, x, n_mat=3)
+    # an all-zero image projects to zeros
+    z = psps.mbir_project(plan, torch.zeros((1,) + g.image_shape, device="cuda"))
+    assert float(z.abs().max()) == 0.0

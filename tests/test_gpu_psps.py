@@ -1,0 +1,84 @@
+"""GPU (preconditioned) SPS iterations against the FP64 oracle run of the
+same algorithm on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import synth
+from _helpers import rel_l2, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4      # relative L2 of the image after the run
+OBJ_TOL = 1e-5      # relative objective history
+
+
+@pytest.fixture(scope="module")
+def psps():
+    import paper_2010_01371_gb300 as p
+    p.lib()
+    return p
+
+
+def run_both(psps, oracle_lib, prob, kind, n_iter, line_search=True, nonneg=False, graph=False, proj=True):
+    from oracle import build, psps as opsps
+    A = oracle_lib.Projector(prob.geom) if proj else oracle_lib.IdentityProjector(prob.n_rays)
+    beta = prob.beta if proj else None
+    st = opsps.Setup(A, prob.Q, prob.S, prob.y, beta)
+    P = build.build(st, kind)
+    xo, ho, ao = opsps.run(st, P, n_iter, opsps.LineSearch() if line_search else None, nonneg=nonneg,
+                           return_alphas=True)
+    plan = psps.Plan(prob.geom) if proj else None
+    spec = psps.Spectrum(prob.Q, prob.S)
+    yd = to_dev(prob.y)
+    pc = psps.Precond(plan, spec, kind, yd, beta) if kind != "none" else None
+    state = psps.State(plan, spec, pc, yd, beta, line_search=line_search, nonneg=nonneg, graph=graph)
+    hg = psps.psps_step(state, n_iter)
+    xg = to_host(psps.psps_get_image(state))
+    ag = psps.psps_get_alphas(state, n_iter)
+    return xo, ho, ao, xg, hg, ag
+
+
+@pytest.mark.parametrize("kind,ls", [("none", False), ("none", True), ("fourier", True), ("mod_fourier", True),
+                                     ("haar", True), ("block", True)])
+def test_config1_50_iterations(psps, oracle_lib, kind, ls):
+    prob = synth.config1()
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, kind, 50, line_search=ls)
+    assert np.all(np.isfinite(hg))
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL, np.max(np.abs(hg - ho) / np.abs(ho))
+    assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
+    if ls:
+        assert np.all(np.diff(hg) <= 1e-7 * hg[0])
+
+
+def test_config2_reduced_haar(psps, oracle_lib):
+    prob = synth.config2(nx=128, n_views=180, n_u=222)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "haar", 20)
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL
+    assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
+
+
+def test_projection_domain_block(psps, oracle_lib):
+    prob = synth.config3(n_views=12, n_u=301)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "block", 50, proj=False)
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL
+    assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
+
+
+def test_nonneg_plain_sps_monotone(psps, oracle_lib):
+    prob = synth.config1()
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "none", 30, line_search=False, nonneg=True)
+    assert np.all(np.diff(hg) <= 1e-7 * hg[0])
+    assert (xg >= 0).all()
+    assert rel_l2(xg, xo) < IMG_TOL
+
+
+def test_graph_replay_matches(psps):
+    prob = synth.config1()
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    yd = to_dev(prob.y)
+    pc = psps.Precond(plan, spec, "mod_fourier", yd, prob.beta)
+    a = psps.State(plan, spec, pc, yd, prob.beta)
+    b = psps.State(plan, spec, pc, yd, prob.beta, graph=True)
+    ha, hb = psps.psps_step(a, 25), psps.psps_step(b, 25)
+    assert np.allclose(ha, hb, rtol=1e-6)
+    assert rel_l2(to_host(psps.psps_get_image(b)), to_host(psps.psps_get_image(a))) < 1e-5
