@@ -8,8 +8,8 @@
  * "A Preconditioned Algorithm for Model-Based Iterative CT Reconstruction and
  * Material Decomposition from Spectral CT Data" (arXiv 2010.01371):
  *   mean model            y_bar = B exp(-A x)                    (Sec. II-A, Eq. 1)
- *   objective             1/2 (y - y_bar)^T Sigma^-1 (y - y_bar) + 1/2 x^T R x (Eq. 2)
- *   SPS update            Sec. II-B, Eqs. 3-9
+ *   objective             1/2 (y - y_bar)^T Sigma^-1 (y - y_bar) + 1/2 x^T R x (Eqs. 2-3)
+ *   SPS update            Sec. II-B, Eqs. 4-11
  *   preconditioned SPS    x = M x', operator A -> A M            (Sec. II-C)
  *   preconditioners       Fourier / modified Fourier / Haar wavelet (Sec. II-D),
  *                         per-ray cross-material blocks (Sec. II-E),
@@ -119,7 +119,7 @@ mbir_status mbmd_forward_model(const mbmd_spectrum *spec, const float *l, float 
                                mbir_stream stream);
 
 /* PWLS data term L = 1/2 sum_{c,i} w (y - y_bar)^2 with w = 1/max(y, 1)
- * (Eq. 2, Sigma_y = diag(max(y,1))).  plan != NULL: x_or_l is an image
+ * (Eq. 3, Sigma_y = diag(max(y,1))).  plan != NULL: x_or_l is an image
  * [n_mat][image] and l = A x is formed internally; plan == NULL: x_or_l is
  * the line-integral array [n_mat][n_rays] (projection-domain decomposition).
  * *objective is a DEVICE double written with the FP64-reduced value. */
@@ -137,20 +137,20 @@ mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec, const floa
 
 enum {
     PSPS_PRECOND_NONE = 0,          /* M = I: plain SPS (Sec. II-B)                   */
-    PSPS_PRECOND_FOURIER = 1,       /* M = U^H Lambda^-1/2 U (Eq. 14)                 */
-    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U M0 (Eqs. 15-17)       */
-    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT M0 (Eq. 20)   */
-    PSPS_PRECOND_BLOCK = 4,         /* per-pixel / per-ray N_k x N_k M0 (Eqs. 16, 22) */
-    PSPS_PRECOND_BLOCK_FOURIER = 5  /* cross-material Fourier (Eqs. 23-24)            */
+    PSPS_PRECOND_FOURIER = 1,       /* M = U^H Lambda^-1/2 U (Eq. 29)                 */
+    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U M0 (Eqs. 30-33)       */
+    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT M0 (Eq. 34)   */
+    PSPS_PRECOND_BLOCK = 4,         /* per-pixel / per-ray N_k x N_k M0 (Eqs. 42, 54) */
+    PSPS_PRECOND_BLOCK_FOURIER = 5  /* cross-material Fourier (Eqs. 56-57)            */
 };
 enum { PSPS_APPLY_M = 0, PSPS_APPLY_MT = 1, PSPS_APPLY_ABS_M = 2, PSPS_APPLY_ABS_MT = 3 };
 
 /* Build a preconditioner once, before iterating (Sec. II-C): the Hessian at
  * the solution is approximated with D from the data (standard CT: y / I0;
  * spectral: a per-ray water-only fit), M0 from (F+R)1_k, and the eigenvalues
- * from Eq. 12 taken in modulus (the phase-corrected ratio is complex for a
+ * from Eq. 18 taken in modulus (the phase-corrected ratio is complex for a
  * shift-variant Hessian), clamped to >= 1e-6 of the largest.  Haar
- * eigenvalues use Eq. 12 with one test function per (level, subband, class of
+ * eigenvalues use Eq. 18 with one test function per (level, subband, class of
  * a P x P position lattice).
  * y: device [n_chan][n_rays]; beta: host [n_mat][n_mat] penalty strengths
  * (NULL = no penalty); haar_lattice: lattice size P of the Haar test
@@ -160,6 +160,19 @@ enum { PSPS_APPLY_M = 0, PSPS_APPLY_MT = 1, PSPS_APPLY_ABS_M = 2, PSPS_APPLY_ABS
 mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spectrum *spec, int kind, const float *y,
                                     int64_t n_rays, const double *beta, int haar_lattice, mbir_stream stream,
                                     psps_precond **out);
+/* Create a preconditioner from precomputed data instead of building it (to
+ * reuse one across reconstructions, or to load one):
+ *   FOURIER / MOD_FOURIER / HAAR (n_mat = 1, plan required): lam = the
+ *     eigenvalue estimates (device, n values: the [ny][nx] DFT spectrum, or the
+ *     Haar coefficients in the Mallat layout); m0 = the diagonal
+ *     zero-frequency normalisation (device, n values; NULL = 1; ignored for
+ *     FOURIER).  lam is taken in modulus, clamped to >= 1e-6 of its largest
+ *     and raised to -1/2 exactly as psps_precondition_build does.
+ *   BLOCK: blocks = the M0 blocks themselves (device [n_mat][n_mat][n]).
+ * n = pixels per material (plan) or rays (plan == NULL, BLOCK only).
+ * Synchronises `stream`. */
+mbir_status psps_precondition_create(mbir_plan *plan, int kind, int n_mat, int64_t n, const float *lam,
+                                     const float *m0, const float *blocks, mbir_stream stream, psps_precond **out);
 mbir_status psps_precondition_destroy(psps_precond *pc);
 
 /* out = op(M) in for op in PSPS_APPLY_*, arrays shaped like the unknowns

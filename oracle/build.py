@@ -38,7 +38,7 @@ def make_apply_H(st: Setup, F: np.ndarray):
 
 
 def m0_blocks(st: Setup, F: np.ndarray) -> np.ndarray:
-    """Blocks of (F+R)1_k (Eqs. 16/22): column k of every per-pixel block is
+    """Blocks of (F+R)1_k (Eqs. 42, 54): column k of every per-pixel block is
     the response to the all-ones image of material k."""
     nm = st.nm
     apply_H = make_apply_H(st, F)

@@ -3,8 +3,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file belongs to the oracle: a plain, slow,
  * obviously correct CPU statement of the ray-driven projector A that the
- * forward model y_bar = B exp(-A x) (Eq. 1; A -> A for standard CT, QA for
- * one-step MBMD) is built on.  Only tests, the smoke check and the CPU-baseline
+ * forward model y_bar = B exp(-A x) (Eq. 1; A -> A for standard CT, Eq. 20, QA for
+ * one-step MBMD, Eq. 44) is built on.  Only tests, the smoke check and the CPU-baseline
  * leg of the benchmark may load it.  It shares no code with the CUDA library.
  *
  * Definition (the paper fixes no projector; this is the textbook Joseph

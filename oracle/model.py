@@ -31,7 +31,7 @@ def forward_model(Q: np.ndarray, S: np.ndarray, l: np.ndarray) -> np.ndarray:
 
 
 def data_objective(Q, S, l, y) -> float:
-    """L = 1/2 (y - y_bar)^T Sigma^-1 (y - y_bar)  (Eq. 2, second line)."""
+    """L = 1/2 (y - y_bar)^T Sigma^-1 (y - y_bar)  (Eq. 3)."""
     r = forward_model(Q, S, l) - y
     return 0.5 * float(np.sum(weights(y) * r * r))
 
@@ -48,7 +48,7 @@ def sps_curvature(Q, S, l, y) -> np.ndarray:
     """Per (energy, ray) maximum curvature c of the separable surrogate.
 
     The data term is majorised, for each ray and energy, by the 1-D function
-    h(z) = 1/2 eta e^{-2z} + rho e^{-z} of z = [Q l]_E (Sec. II-B, Eqs. 3-9),
+    h(z) = 1/2 eta e^{-2z} + rho e^{-z} of z = [Q l]_E (Sec. II-B, Eqs. 4-11),
     with eta = B^T Sigma^-1 B 1 and rho = B^T Sigma^-1 B t^n - eta t^n
     - B^T Sigma^-1 y (the paper's rho printed with x^n where the current
     transmission t^n belongs).  h''(z) = 2 eta u^2 + rho u with u = e^{-z} is a
@@ -70,7 +70,7 @@ def sps_curvature(Q, S, l, y) -> np.ndarray:
 def curvature_numerator(Q, S, l, y, gamma_m: np.ndarray) -> np.ndarray:
     """kappa[m,i] = sum_E Q[E,m] gamma[E,i] c[E,i] with gamma[E,i] =
     sum_m Q[E,m] gamma_m[m,i]; the separable curvature is then
-    d = A^T kappa (Eq. 4: d = diag(A^T D{gamma} c) with A -> QA)."""
+    d = A^T kappa (Eq. 6: d = diag(A^T D{gamma} c) with A -> QA)."""
     c = sps_curvature(Q, S, l, y)
     gE = Q @ gamma_m
     return Q.T @ (gE * c)

@@ -2,11 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
 
-Gamma is the first-order smoothness kernel of Eq. (13)/(19): Gamma_jj = |N_j|,
+Gamma is the first-order smoothness kernel of Eqs. 26 and 52: Gamma_jj = |N_j|,
 Gamma_jj' = -1 for j' in N_j, with N_j the 4-neighbourhood (2-D) or
 6-neighbourhood (3-D) of pixel j inside the grid (no wrap-around; edge pixels
 have fewer neighbours).  beta is the symmetric n_mat x n_mat strength matrix
-(a 1x1 matrix for standard CT).  The paper's summation form (Eq. 18) counts
+(a 1x1 matrix for standard CT).  The paper's summation form (Eq. 49) counts
 every neighbour pair twice relative to its matrix form 1/2 x^T R x; the matrix
 form is the one used here, i.e. 1/2 sum_{k,k'} beta_kk' sum_{unordered pairs}
 (x_jk - x_j'k)(x_jk' - x_j'k').

@@ -9,7 +9,7 @@ signed operator A M: d' = |M|^T A^T(gamma~ c) + |M|^T |R| |M| 1 with
 gamma~ = A |M| 1.
 
 Readings of the paper used here:
-* Eigenvalue estimate (Eq. 12): Lambda~ = D{U dx}^-1 D{U H dx}, evaluated as
+* Eigenvalue estimate (Eq. 18): Lambda~ = D{U dx}^-1 D{U H dx}, evaluated as
   written: the ratio of the two transforms.  For a shift-variant H the
   phase-corrected Fourier ratio is complex and its real part goes negative at
   some frequencies (a Joseph impulse response is not point-symmetric), which
@@ -17,7 +17,7 @@ Readings of the paper used here:
   N_k x N_k blocks its matrix analogue, the Hermitian polar factor
   (L^H L)^1/2, of which the real part is kept.  Both equal Lambda exactly when
   H is circulant.
-* Haar test functions: Eq. 12 with the single test function U^T 1 (the
+* Haar test functions: Eq. 18 with the single test function U^T 1 (the
   paper's choice) lets every coefficient's response overlap with all others;
   on CT Hessians that gives estimates from -4x to 6x the true diagonal
   u_k^T H u_k.  The same estimator is therefore applied with a family of test
@@ -28,8 +28,8 @@ Readings of the paper used here:
 * Fourier: periodic unitary 2-D DFT per material on the image grid (no
   padding); the test impulse sits at the centre pixel (ny//2, nx//2).
 * Eigenvalues are clamped to >= 1e-6 x the largest before the -1/2 power.
-* M0 = D{(F+R)1}^-1/2 (Eq. 15) or, with several materials, the per-pixel /
-  per-ray N_k x N_k blocks of (F+R)1_k (Eqs. 16, 21-22) raised to -1/2; a
+* M0 = D{(F+R)1}^-1/2 (Eq. 30) or, with several materials, the per-pixel /
+  per-ray N_k x N_k blocks of (F+R)1_k (Eqs. 42, 53-54) raised to -1/2; a
   block's eigenvalues are clamped to >= 1e-6 x its largest one, and pixels
   whose block trace is <= 1e-12 x the largest trace get M0 = 0 (outside the
   field of view).
@@ -110,7 +110,7 @@ def centre_index(shape):
 
 
 def fourier_eigenvalues(apply_H, shape, k: int = 0, nm: int = 1) -> np.ndarray:
-    """Lambda~ of Eq. (12) for one material: |DFT(H delta_j) / DFT(delta_j)|
+    """Lambda~ of Eq. 18 (as Eq. 28 / 32) for one material: |DFT(H delta_j) / DFT(delta_j)|
     with delta_j the unit impulse at the centre pixel."""
     d = np.zeros((nm,) + tuple(shape))
     d[(k,) + centre_index(shape)] = 1.0
@@ -124,8 +124,8 @@ def clamp_eigs(lam: np.ndarray) -> np.ndarray:
 
 
 class Fourier:
-    """M = m0 U^H diag(lam^-1/2) U m0 (Eq. 14 with m0 = 1, Eq. 17 with the
-    zero-frequency normalisation m0 = M0 of Eq. 15).  One material.
+    """M = m0 U^H diag(lam^-1/2) U m0 (Eq. 29 with m0 = 1, Eq. 33 with the
+    zero-frequency normalisation m0 = M0 of Eq. 30).  One material.
     |M| = m0 |C| m0 with |C| the circulant of the absolute kernel
     |IDFT(lam^-1/2)|."""
 
@@ -154,7 +154,7 @@ class Fourier:
 
 
 class CrossFourier:
-    """Cross-material Fourier preconditioner (Eq. 24):
+    """Cross-material Fourier preconditioner (Eq. 57):
     M = M0^T U^H L^-1/2 U M0 with L block diagonal over spatial frequencies
     (one N_k x N_k block per frequency), M0 the per-pixel blocks."""
 
@@ -190,7 +190,7 @@ class CrossFourier:
 
 
 def cross_fourier_blocks(apply_H, M0: Block, shape, nm: int) -> np.ndarray:
-    """L_k of Eq. (23) for every material k: DFT of the zero-frequency-
+    """L_k of Eq. 56 for every material k: DFT of the zero-frequency-
     normalised response M0^T H M0 delta_jk divided by DFT(delta_jk), stacked as
     L[f..., k', k] (complex; see ``polar_real``)."""
     L = np.zeros(tuple(shape) + (nm, nm), dtype=complex)
@@ -223,7 +223,7 @@ def polar_real(L: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 class Haar:
-    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT M0 (Eq. 20); |M| uses |U| and |M0|.
+    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT M0 (Eq. 34); |M| uses |U| and |M0|.
     One material, 2-D images."""
 
     def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None):
@@ -275,7 +275,7 @@ def haar_test_sets(shape, lattice: int = 3):
 
 
 def haar_eigenvalues(apply_H, shape, lattice: int = 3) -> np.ndarray:
-    """Eq. (12) with wavelet test functions dx = U^T xi (Sec. II-D-3):
+    """Eq. 18 with wavelet test functions dx = U^T xi (Sec. II-D-3):
     Lambda~_k = [U H dx]_k / [U dx]_k for the coefficients k that xi excites."""
     lam = np.zeros(shape)
     for sel in haar_test_sets(shape, lattice):

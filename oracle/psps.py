@@ -11,17 +11,18 @@ One iteration in the preconditioned basis x = M x' (Sec. II-B, II-C):
   5. p' = -grad'/d' (zero where d' = 0), p = M p', q = A p;
   6. step length alpha: 1 (classic SPS) or the safeguarded line search below;
   7. x += alpha p, l += alpha q.
-With M = I this is the paper's plain SPS update (Eq. 6): the surrogate
+With M = I this is the paper's plain SPS update (Eq. 7): the surrogate
 gradient at x^n equals the true gradient, the curvature is A^T D{gamma} c
 plus the penalty's separable bound |R| 1.  ``gamma~ = A |M| 1`` generalises
-gamma = A 1 (Eq. 8) to the signed operator A M.
+gamma = A 1 (Eq. 9) to the signed operator A M.
 
 Line search (not in the paper; the step direction is the SPS step):
 evaluate phi(alpha) = Phi(x + alpha p), phi', phi'' at alpha_0 = 1 and take
 Newton steps alpha_{k+1} = clip(alpha_k - phi'/phi'', 0, alpha_max) (kept
-when phi'' <= 0) for ``n_ls`` evaluations in total; pick the evaluated alpha
-with the smallest phi (first on ties); if phi there exceeds phi(0), halve it up
-to ``n_halve`` times, else use alpha = 0.
+when phi'' <= 0) for ``n_ls`` evaluations in total; accept the last evaluated
+alpha if phi there does not exceed phi(0), else halve it up to ``n_halve``
+times, else use alpha = 0.  Only comparisons against phi(0) decide, never
+near-equal values of phi at two nearby alphas.
 """
 from __future__ import annotations
 
@@ -82,15 +83,11 @@ def line_search(st: Setup, x, p, l, q, phi0: float, ls: LineSearch):
         return f + R0 + a * pRx + 0.5 * a * a * pRp, f1 + pRx + a * pRp, f2 + pRp
 
     a = 1.0
-    best_a, best_f = None, None
     for k in range(ls.n_ls):
         f, f1, f2 = phi(a)
-        if best_f is None or f < best_f:
-            best_a, best_f = a, f
         if k + 1 < ls.n_ls:
             an = a - f1 / f2 if f2 > 0 else a
             a = min(max(an, 0.0), ls.alpha_max)
-    a, f = best_a, best_f
     if f <= phi0:
         return a, f
     for _ in range(ls.n_halve):

@@ -155,8 +155,21 @@ def mbmd_gradient(plan: Plan | None, spec: Spectrum, x_or_l, y, grad=None, with_
 class Precond:
     """One-time preconditioner build (``psps_precondition_build``)."""
 
-    def __init__(self, plan: Plan | None, spec: Spectrum, kind: str, y, beta=None, haar_lattice: int = 3):
+    def __init__(self, plan: Plan | None, spec: Spectrum, kind: str, y=None, beta=None, haar_lattice: int = 3,
+                 lam=None, m0=None, blocks=None):
+        """Build from data (``y``) or, when ``lam`` / ``blocks`` is given,
+        create from precomputed eigenvalues / blocks
+        (``psps_precondition_create``)."""
         self.kind = kind
+        self.plan, self.spec = plan, spec
+        if y is None:
+            n = plan.n_pix if plan else (blocks.shape[-1] if blocks is not None else 0)
+            h = ctypes.c_void_p()
+            _call(lib().psps_precondition_create, plan.h if plan else None, PSPS_PRECOND[kind], spec.n_mat, int(n),
+                  _dev(lam, "lam") if lam is not None else None, _dev(m0, "m0") if m0 is not None else None,
+                  _dev(blocks, "blocks") if blocks is not None else None, _stream(), ctypes.byref(h))
+            self.h = h
+            return
         n_rays = y.numel() // spec.n_chan
         b = None
         if beta is not None:
@@ -166,7 +179,6 @@ class Precond:
         _call(lib().psps_precondition_build, plan.h if plan else None, spec.h, PSPS_PRECOND[kind], _dev(y, "y"),
               int(n_rays), b, int(haar_lattice), _stream(), ctypes.byref(h))
         self.h = h
-        self.plan, self.spec = plan, spec
 
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:

@@ -43,6 +43,8 @@ SIGNATURES = [
     ("mbmd_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     ("psps_precondition_build", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int64, P(c_double), c_int,
                                         c_void_p, P(c_void_p)]),
+    ("psps_precondition_create", c_int, [c_void_p, c_int, c_int, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         P(c_void_p)]),
     ("psps_precondition_destroy", c_int, [c_void_p]),
     ("psps_precondition", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     ("psps_state_create", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, P(c_double), c_void_p, c_int,

@@ -79,6 +79,11 @@ __global__ void real_part_kernel(const float2 *Z, float *out, int64_t n) {
         out[i] = Z[i].x;
 }
 
+__global__ void abs_copy_kernel(const float *in, float *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fabsf(in[i]);
+}
+
 __global__ void abs_kernel(float *p, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = fabsf(p[i]);
@@ -283,6 +288,20 @@ mbir_status finish_scalar(psps_precond *pc, float *lam, bool fourier, cudaStream
 }
 
 }  // namespace
+
+mbir_status launch_abs_copy(const float *in, float *out, int64_t n, cudaStream_t s) {
+    abs_copy_kernel<<<gs(n), kThreads, 0, s>>>(in, out, n);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+mbir_status launch_fill(float *p, int64_t n, float v, cudaStream_t s) {
+    fill_kernel<<<gs(n), kThreads, 0, s>>>(p, n, v);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+mbir_status finish_scalar_pub(psps_precond *pc, float *lam, bool fourier, cudaStream_t s) {
+    return finish_scalar(pc, lam, fourier, s);
+}
 
 mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out, cudaStream_t s) {
     const bool absm = (op == PSPS_APPLY_ABS_M || op == PSPS_APPLY_ABS_MT);
@@ -510,6 +529,69 @@ extern "C" mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spect
     if (plan && spec->n_mat > plan->n_mat_max) return fail(MBIR_ERR_ARG, "psps_precondition_build: n_mat > n_mat_max");
     psps_precond *pc = new psps_precond();
     mbir_status st = build_impl(plan, spec, kind, y, n_rays, beta, haar_lattice, (cudaStream_t)stream, pc);
+    if (st != MBIR_OK) {
+        delete pc;
+        return st;
+    }
+    *out = pc;
+    return MBIR_OK;
+}
+
+namespace {
+mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const float *lam, const float *m0,
+                        const float *blocks, cudaStream_t s, psps_precond *pc) {
+    pc->kind = kind;
+    pc->nm = nm;
+    pc->image = plan != nullptr;
+    pc->n = n;
+    pc->nx = plan ? plan->g.nx : (int)n;
+    pc->ny = plan ? (int)(n / plan->g.nx) : 1;
+    if (kind == PSPS_PRECOND_NONE) return MBIR_OK;
+    if (kind == PSPS_PRECOND_BLOCK) {
+        if (!blocks) return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK needs blocks");
+        PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
+        PSPS_TRY(pc->Babs.alloc((size_t)nm * nm * n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->B.p, blocks, sizeof(float) * pc->B.n, cudaMemcpyDeviceToDevice, s));
+        PSPS_TRY(launch_abs_copy(blocks, pc->Babs.p, (int64_t)pc->B.n, s));
+        PSPS_CUDA(cudaStreamSynchronize(s));
+        return MBIR_OK;
+    }
+    if (!plan || nm != 1 || !lam)
+        return fail(MBIR_ERR_ARG, "psps_precondition_create: Fourier/Haar kinds need a plan, n_mat = 1 and lam");
+    if (kind == PSPS_PRECOND_HAAR && !haar_supported(plan->g.nx, plan->g.ny))
+        return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
+    if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER) PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+    if (kind == PSPS_PRECOND_BLOCK_FOURIER) return fail(MBIR_ERR_UNIMPLEMENTED, "cross-material Fourier not built");
+    PSPS_TRY(pc->tmp.alloc((size_t)n * 4));
+    PSPS_TRY(pc->Z.alloc((size_t)n * 2));
+    PSPS_TRY(pc->s.alloc(n));
+    PSPS_TRY(pc->s_abs.alloc(n));
+    PSPS_TRY(pc->m0.alloc(n));
+    if (m0 && kind != PSPS_PRECOND_FOURIER)
+        PSPS_CUDA(cudaMemcpyAsync(pc->m0.p, m0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    else
+        PSPS_TRY(launch_fill(pc->m0.p, n, 1.f, s));
+    DBuf<float> l2;
+    PSPS_TRY(l2.alloc(n));
+    PSPS_CUDA(cudaMemcpyAsync(l2.p, lam, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    PSPS_TRY(finish_scalar_pub(pc, l2.p, kind != PSPS_PRECOND_HAAR, s));
+    PSPS_CUDA(cudaStreamSynchronize(s));
+    return MBIR_OK;
+}
+}  // namespace
+
+extern "C" mbir_status psps_precondition_create(mbir_plan *plan, int kind, int n_mat, int64_t n, const float *lam,
+                                                const float *m0, const float *blocks, mbir_stream stream,
+                                                psps_precond **out) {
+    if (!out) return fail(MBIR_ERR_ARG, "psps_precondition_create: null out");
+    *out = nullptr;
+    if (kind < PSPS_PRECOND_NONE || kind > PSPS_PRECOND_BLOCK_FOURIER)
+        return fail(MBIR_ERR_ARG, "psps_precondition_create: unknown kind %d", kind);
+    if (n_mat < 1 || n_mat > 4) return fail(MBIR_ERR_ARG, "psps_precondition_create: n_mat must be 1..4");
+    if (plan && n != plan->n_pix) return fail(MBIR_ERR_ARG, "psps_precondition_create: n must equal the plan's pixels");
+    if (n < 1) return fail(MBIR_ERR_ARG, "psps_precondition_create: n must be >= 1");
+    psps_precond *pc = new psps_precond();
+    mbir_status st = create_impl(plan, kind, n_mat, n, lam, m0, blocks, (cudaStream_t)stream, pc);
     if (st != MBIR_OK) {
         delete pc;
         return st;

@@ -9,7 +9,7 @@
 //   p' = -grad'/d' (0 where d' = 0),  p = M p',  q = A p
 //   step length: 1 (classic SPS), or safeguarded Newton on
 //     phi(alpha) = Phi(x + alpha p) from alpha = 1 (n_ls evaluations; the
-//     best evaluated alpha, halved up to n_halve times until phi <= phi(0),
+//     last evaluated alpha, halved up to n_halve times until phi <= phi(0),
 //     else 0), with per-ray exact phi, phi', phi'' and the penalty's exact
 //     quadratic in alpha; scalar control runs in one-thread kernels that read
 //     the FP64 partial sums, so nothing returns to the host
@@ -92,21 +92,19 @@ __global__ void ctrl_newton_kernel(DevLS *ls, const double *part, int nb, int la
     const double f1 = f1d + ls->pRx + a * ls->pRp;
     const double f2 = f2d + ls->pRp;
     if (!isfinite(f) || !isfinite(f1) || !isfinite(f2)) ls->nonfinite = 1;
-    if (f < ls->best_f) {
-        ls->best_f = f;
-        ls->best_a = a;
-    }
     if (!last) {
         double an = f2 > 0 ? a - f1 / f2 : a;
         if (!(an >= 0)) an = 0.0;  // also catches NaN
         if (an > cfg.alpha_max) an = cfg.alpha_max;
         ls->alpha = an;
     } else {
-        if (ls->best_f <= ls->phi0) {
-            ls->alpha = ls->best_a;
+        // accept the last evaluated alpha unless phi rose above phi(0)
+        ls->best_a = a;
+        ls->best_f = f;
+        if (f <= ls->phi0) {
             ls->done = 1;
         } else {
-            ls->alpha = 0.5 * ls->best_a;
+            ls->alpha = 0.5 * a;
             if (cfg.n_halve == 0) {
                 ls->alpha = 0.0;
                 ls->done = 1;
@@ -195,6 +193,7 @@ struct psps_state {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [0] plain, [1] with re-projection
     // optional stage timers (events around contiguous regions of one iteration)
     int64_t graph_kernels[2] = {0, 0};  // kernel nodes per captured iteration
+    bool graph_marks[2][PSPS_PROF_STAGES] = {};  // stages timed inside each graph
     int64_t launches = 0;                // kernels launched through graph replays
     bool prof = false;
     cudaEvent_t ev[PSPS_PROF_STAGES][2] = {};
@@ -218,9 +217,16 @@ struct psps_state {
 
 namespace {
 
+// Stage timer: during graph capture the record must be an external event
+// node (a plain record in a capturing stream only expresses a dependency).
 inline void mark(psps_state *st, int stage, int end, cudaStream_t s) {
     if (!st->prof) return;
-    cudaEventRecord(st->ev[stage][end], s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(st->ev[stage][end], s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(st->ev[stage][end], s);
     if (end) st->recorded[stage] = true;
 }
 
@@ -343,7 +349,12 @@ mbir_status ensure_graph(psps_state *st, int which, cudaStream_t s) {
         cudaStreamDestroy(cs);
         return fail(MBIR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
     }
+    for (int k = 0; k < PSPS_PROF_STAGES; ++k) st->recorded[k] = false;
     mbir_status st_ = iterate(st, which == 1, cs);
+    for (int k = 0; k < PSPS_PROF_STAGES; ++k) {
+        st->graph_marks[which][k] = st->recorded[k];
+        st->recorded[k] = false;
+    }
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     if (st_ != MBIR_OK) return st_;
@@ -487,6 +498,8 @@ extern "C" mbir_status psps_step(psps_state *st, int n_iter, double *objective_h
             PSPS_TRY(ensure_graph(st, rp ? 1 : 0, s));
             PSPS_CUDA(cudaGraphLaunch(st->graph[rp ? 1 : 0], s));
             st->launches += st->graph_kernels[rp ? 1 : 0];
+            if (st->prof)
+                for (int k = 0; k < PSPS_PROF_STAGES; ++k) st->recorded[k] = st->graph_marks[rp ? 1 : 0][k];
         } else {
             PSPS_TRY(iterate(st, rp, s));
         }

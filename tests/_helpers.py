@@ -43,3 +43,40 @@ def phantom(geom, seed=0, nm=1):
                                        vmin=0.01, vmax=0.03)
         out.append(synth.render(geom, shapes, supersample=2) + 0.002 * rng.random(geom.image_shape))
     return np.stack(out)
+
+
+def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True):
+    """Oracle preconditioner for a problem plus the data that defines it
+    (eigenvalues, m0, blocks in the library's [m][k][n] layout)."""
+    from oracle import build, precond, psps as opsps
+    A = oracle_lib.Projector(prob.geom) if proj else oracle_lib.IdentityProjector(prob.n_rays)
+    st = opsps.Setup(A, prob.Q, prob.S, prob.y, prob.beta if proj else None)
+    if kind == "none":
+        return st, precond.Identity(), {}
+    F = build.fisher(st)
+    aH = build.make_apply_H(st, F)
+    if kind == "fourier":
+        lam = precond.fourier_eigenvalues(aH, st.shape)
+        return st, precond.Fourier(lam), {"lam": lam}
+    B = build.m0_blocks(st, F)
+    if kind == "block":
+        return st, precond.Block(B, st.shape), {"blocks": np.ascontiguousarray(np.transpose(B, (1, 2, 0)))}
+    m0 = B[:, 0, 0].reshape(st.shape)
+
+    def aN(v):
+        return m0[None] * aH(m0[None] * v)
+    if kind == "mod_fourier":
+        lam = precond.fourier_eigenvalues(aN, st.shape)
+        return st, precond.Fourier(lam, m0), {"lam": lam, "m0": m0}
+    if kind == "haar":
+        lam = precond.haar_eigenvalues(aN, st.shape, lattice=lattice)
+        return st, precond.Haar(lam, m0), {"lam": lam, "m0": m0}
+    raise ValueError(kind)
+
+
+def gpu_precond_from(psps, plan, spec, kind, data):
+    """The library's preconditioner created from the oracle's data."""
+    if kind == "none":
+        return None
+    kw = {k: to_dev(v) for k, v in data.items()}
+    return psps.Precond(plan, spec, kind, **kw)

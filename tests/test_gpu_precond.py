@@ -1,13 +1,22 @@
-"""GPU preconditioner builds and applies against the oracle's builds."""
+"""GPU preconditioner applies and builds against the oracle.
+
+Applies are checked with the preconditioner created from the oracle's own
+eigenvalues / blocks (tolerance 1e-5: the FP32 FFT and Haar kernels).  The
+GPU build itself runs in FP32 (impulse responses through the FP32 projector,
+FP32 FFT) and is checked against the FP64 build at 1e-3: the eigenvalues at
+the smallest frequencies are differences of large responses, where FP32
+rounding of ~1e-7 of the largest response becomes ~1e-4 of the smallest.
+"""
 import numpy as np
 import pytest
 
 import synth
-from _helpers import rel_l2, to_dev, to_host
+from _helpers import gpu_precond_from, oracle_precond, rel_l2, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-4   # FP32 build (impulse responses, FFT) against the FP64 one
+APPLY_TOL = 1e-5
+BUILD_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -21,47 +30,53 @@ def problems():
     return {"c1": synth.config1(), "c2_64": synth.config2(nx=64, n_views=90, n_u=111)}
 
 
+OPS = ["M", "MT", "absM", "absMT"]
+
+
+def check_ops(psps, pc, P, shape, tol, seed=3):
+    v = np.random.default_rng(seed).standard_normal(shape)
+    for op in OPS:
+        got = to_host(psps.psps_precondition(pc, op, to_dev(v)))
+        want = getattr(P, op)(v)
+        assert rel_l2(got, want) < tol, (op, rel_l2(got, want))
+
+
 @pytest.mark.parametrize("pname", ["c1", "c2_64"])
 @pytest.mark.parametrize("kind", ["fourier", "mod_fourier", "haar", "block"])
 def test_apply_parity(psps, oracle_lib, pname, kind):
-    from oracle import build, psps as opsps
     prob = problems()[pname]
-    st = opsps.Setup(oracle_lib.Projector(prob.geom), prob.Q, prob.S, prob.y, prob.beta)
-    P = build.build(st, kind)
-    plan = psps.Plan(prob.geom)
-    spec = psps.Spectrum(prob.Q, prob.S)
+    st, P, data = oracle_precond(oracle_lib, prob, kind)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    pc = gpu_precond_from(psps, plan, spec, kind, data)
+    check_ops(psps, pc, P, (1,) + prob.geom.image_shape, APPLY_TOL)
+
+
+@pytest.mark.parametrize("pname", ["c1", "c2_64"])
+@pytest.mark.parametrize("kind", ["fourier", "mod_fourier", "haar", "block"])
+def test_build_parity(psps, oracle_lib, pname, kind):
+    prob = problems()[pname]
+    st, P, _ = oracle_precond(oracle_lib, prob, kind)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     pc = psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta)
-    rng = np.random.default_rng(3)
-    v = rng.standard_normal((1,) + prob.geom.image_shape)
-    for op, fn in [("M", P.M), ("MT", P.MT), ("absM", P.absM), ("absMT", P.absMT)]:
-        got = to_host(psps.psps_precondition(pc, op, to_dev(v)))
-        want = fn(v)
-        assert rel_l2(got, want) < TOL, (op, rel_l2(got, want))
+    check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOL)
 
 
 def test_projection_domain_block(psps, oracle_lib):
-    from oracle import build, psps as opsps
     prob = synth.config3(n_views=10, n_u=333)
-    st = opsps.Setup(oracle_lib.IdentityProjector(prob.n_rays), prob.Q, prob.S, prob.y, None)
-    P = build.build(st, "block")
+    st, P, data = oracle_precond(oracle_lib, prob, "block", proj=False)
     spec = psps.Spectrum(prob.Q, prob.S)
-    pc = psps.Precond(None, spec, "block", to_dev(prob.y))
-    v = np.random.default_rng(4).standard_normal((2, prob.n_rays))
-    for op, fn in [("M", P.M), ("MT", P.MT), ("absM", P.absM)]:
-        assert rel_l2(to_host(psps.psps_precondition(pc, op, to_dev(v))), fn(v)) < 1e-5
+    shape = (2, prob.n_rays)
+    check_ops(psps, gpu_precond_from(psps, None, spec, "block", data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(None, spec, "block", to_dev(prob.y)), P, shape, APPLY_TOL)
 
 
 def test_paper_single_test_function(psps, oracle_lib):
-    """haar_lattice = 0 is Eq. 18 with the single test function U^T 1."""
-    from oracle import build, precond, psps as opsps
+    """haar_lattice = 0 is Eq. 18 with the single test function U^T 1.  Its
+    estimate is a sum of responses that nearly cancel, so the FP32 build
+    carries ~1e-3 relative error; checked at 1e-2."""
     prob = problems()["c1"]
-    st = opsps.Setup(oracle_lib.Projector(prob.geom), prob.Q, prob.S, prob.y, prob.beta)
-    F = build.fisher(st)
-    aH = build.make_apply_H(st, F)
-    m0 = build.m0_blocks(st, F)[:, 0, 0].reshape(st.shape)
-    lam = precond.haar_eigenvalues(lambda v: m0[None] * aH(m0[None] * v), st.shape, lattice=0)
-    P = precond.Haar(lam, m0)
+    st, P, data = oracle_precond(oracle_lib, prob, "haar", lattice=0)
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    check_ops(psps, gpu_precond_from(psps, plan, spec, "haar", data), P, (1, 64, 64), APPLY_TOL)
     pc = psps.Precond(plan, spec, "haar", to_dev(prob.y), prob.beta, haar_lattice=0)
-    v = np.random.default_rng(5).standard_normal((1,) + prob.geom.image_shape)
-    assert rel_l2(to_host(psps.psps_precondition(pc, "M", to_dev(v))), P.M(v)) < TOL
+    check_ops(psps, pc, P, (1, 64, 64), 1e-2)

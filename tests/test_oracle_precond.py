@@ -68,7 +68,7 @@ def test_fourier_exact_on_circulant():
     P = precond.Fourier(est)
     v = rng.standard_normal((1,) + shape)
     assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-11, atol=1e-11)
-    # modified Fourier (Eq. 17): M = M0 U^H Lambda~^-1/2 U M0 with Lambda~ the
+    # modified Fourier (Eq. 33): M = M0 U^H Lambda~^-1/2 U M0 with Lambda~ the
     # spectrum of N = M0 H M0.  When N is circulant its estimate is exact and
     # the two-sided form gives M^T H M = M0 N^-1/2 N N^-1/2 M0 = M0^2.
     lamN = precond.fourier_eigenvalues(lambda z: 0.25 * apply_H(z), shape)

@@ -131,7 +131,7 @@ def test_converges_to_bruteforce_minimiser(oracle_lib):
 
 def test_ideal_preconditioner_is_fast(oracle_lib):
     """With the ideal M = H^-1/2 (dense eigendecomposition at the minimiser,
-    Eq. 11) PSPS closes the objective gap far faster than plain SPS.  (It is
+    Eq. 17) PSPS closes the objective gap far faster than plain SPS.  (It is
     not a one-step Newton method: the separable curvature of the surrogate
     for the signed operator A M is not uniform across x'.)"""
     from oracle import psps
