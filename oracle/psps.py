@@ -17,12 +17,15 @@ plus the penalty's separable bound |R| 1.  ``gamma~ = A |M| 1`` generalises
 gamma = A 1 (Eq. 9) to the signed operator A M.
 
 Line search (not in the paper; the step direction is the SPS step):
-evaluate phi(alpha) = Phi(x + alpha p), phi', phi'' at alpha_0 = 1 and take
-Newton steps alpha_{k+1} = clip(alpha_k - phi'/phi'', 0, alpha_max) (kept
-when phi'' <= 0) for ``n_ls`` evaluations in total; accept the last evaluated
-alpha if phi there does not exceed phi(0), else halve it up to ``n_halve``
-times, else use alpha = 0.  Only comparisons against phi(0) decide, never
-near-equal values of phi at two nearby alphas.
+evaluate phi(alpha) = Phi(x + alpha p), phi', phi'' starting from the step
+length accepted in the previous iteration (1 at the first), and take Newton
+steps alpha_{k+1} = alpha_k - phi'/phi'' kept inside [alpha_k/8, 8 alpha_k]
+and below alpha_max (alpha kept when phi'' <= 0, divided by 8 when phi is not
+finite or z = Q(l + alpha q) leaves z >= z_min there) for ``n_ls``
+evaluations in total; accept the last evaluated alpha if phi there does not
+exceed phi(0), else halve it up to ``n_halve`` times, else use alpha = 0 (the
+next iteration then starts below the last halving).  Only comparisons
+against phi(0) decide, never near-equal values of phi at two nearby alphas.
 """
 from __future__ import annotations
 
@@ -39,6 +42,9 @@ class LineSearch:
     n_ls: int = 3
     n_halve: int = 8
     alpha_max: float = 1e6
+    trust: float = 8.0
+    z_min: float = -20.0
+    warm: bool = True
 
 
 class Setup:
@@ -70,7 +76,8 @@ class Setup:
         return self.proj.backproject(model.data_grad_l(self.Q, self.S, l, self.y)) + self.pen.apply(x)
 
 
-def line_search(st: Setup, x, p, l, q, phi0: float, ls: LineSearch):
+def line_search(st: Setup, x, p, l, q, phi0: float, ls: LineSearch, a0: float = 1.0):
+    """Returns (alpha, phi(alpha), next starting alpha)."""
     pen = st.pen
     Rx = pen.apply(x)
     Rp = pen.apply(p)
@@ -79,23 +86,34 @@ def line_search(st: Setup, x, p, l, q, phi0: float, ls: LineSearch):
     pRp = float(np.sum(p * Rp))
 
     def phi(a):
+        # points outside the domain z = Q (l + a q) >= z_min are rejected
+        if np.min(st.Q @ (l + a * q)) < ls.z_min:
+            return np.inf, np.nan, np.nan
         f, f1, f2 = model.line_terms(st.Q, st.S, l, q, st.y, a)
         return f + R0 + a * pRx + 0.5 * a * a * pRp, f1 + pRx + a * pRp, f2 + pRp
 
-    a = 1.0
+    a = a0
     for k in range(ls.n_ls):
-        f, f1, f2 = phi(a)
+        with np.errstate(over="ignore", invalid="ignore"):
+            f, f1, f2 = phi(a)
         if k + 1 < ls.n_ls:
-            an = a - f1 / f2 if f2 > 0 else a
-            a = min(max(an, 0.0), ls.alpha_max)
-    if f <= phi0:
-        return a, f
+            if not (np.isfinite(f) and np.isfinite(f1) and np.isfinite(f2)):
+                an = a / ls.trust
+            elif f2 > 0:
+                an = min(max(a - f1 / f2, a / ls.trust), a * ls.trust)
+            else:
+                an = a
+            a = min(an, ls.alpha_max)
+    if np.isfinite(f) and f <= phi0:
+        return a, f, a
+    cand = a
     for _ in range(ls.n_halve):
         a = 0.5 * a
-        f = phi(a)[0]
-        if f <= phi0:
-            return a, f
-    return 0.0, phi0
+        with np.errstate(over="ignore", invalid="ignore"):
+            f = phi(a)[0]
+        if np.isfinite(f) and f <= phi0:
+            return a, f, a
+    return 0.0, phi0, cand / 2.0 ** (ls.n_halve + 1)
 
 
 def run(st: Setup, precond, n_iter: int, line_search_cfg: LineSearch | None = None,
@@ -109,6 +127,7 @@ def run(st: Setup, precond, n_iter: int, line_search_cfg: LineSearch | None = No
     gamma_m = A.project(absM1)
     dR = precond.absMT(st.pen.abs_apply(absM1))
     hist, alphas = [], []
+    a_prev = 1.0
     for n in range(n_iter):
         if n > 0 and reproject_every and n % reproject_every == 0:
             l = A.project(x)
@@ -124,7 +143,9 @@ def run(st: Setup, precond, n_iter: int, line_search_cfg: LineSearch | None = No
         p = precond.M(pp)
         q = A.project(p)
         if line_search_cfg is not None:
-            alpha, _ = line_search(st, x, p, l, q, phi0, line_search_cfg)
+            alpha, _, a_next = line_search(st, x, p, l, q, phi0, line_search_cfg,
+                                           a_prev if line_search_cfg.warm else 1.0)
+            a_prev = a_next
         else:
             alpha = 1.0
         alphas.append(alpha)

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(kModelThreads)
 template <int NM>
 __global__ void __launch_bounds__(kModelThreads)
     ls_eval_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
-                   const float *__restrict__ y, const double *alpha_p, const int *skip, double *__restrict__ partials) {
+                   const float *__restrict__ y, const double *alpha_p, const int *skip, float z_min,
+                   double *__restrict__ partials) {
     if (skip && *skip) return;
     extern __shared__ float sh[];
     load_spec(sp, sh);
@@ -120,9 +121,10 @@ __global__ void __launch_bounds__(kModelThreads)
     const float *S = sh + sp.ne * NM;
     const int nc = sp.nc, ne = sp.ne;
     const float alpha = (float)*alpha_p;
-    double f = 0.0, f1 = 0.0, f2 = 0.0;
+    double f = 0.0, f1 = 0.0, f2 = 0.0, bad = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
         float la[NM], qm[NM];
+        float zlo = 3.0e38f;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             qm[m] = q[(int64_t)m * n_rays + i];
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(kModelThreads)
                 z = fmaf(Q[e * NM + m], la[m], z);
                 dz = fmaf(Q[e * NM + m], qm[m], dz);
             }
+            zlo = fminf(zlo, z);
             const float t = expf(-z);
             const float tdz = t * dz;
             for (int c = 0; c < nc; ++c) {
@@ -154,9 +157,10 @@ __global__ void __launch_bounds__(kModelThreads)
             f1 += w * r * d1[c];
             f2 += w * ((double)d1[c] * d1[c] + r * d2[c]);
         }
+        if (!(zlo >= z_min)) bad += 1.0;
     }
-    double v[3] = {f, f1, f2};
-    block_sum_store<3>(v, partials);
+    double v[4] = {f, f1, f2, bad};
+    block_sum_store<4>(v, partials);
 }
 
 __global__ void forward_model_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, float *__restrict__ ybar) {
@@ -256,13 +260,14 @@ mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const 
 }
 
 mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y,
-                           const double *alpha, const int *skip, double *partials, int nblocks, cudaStream_t s) {
+                           const double *alpha, const int *skip, float z_min, double *partials, int nblocks,
+                           cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     switch (sp.nm) {
-        case 1: ls_eval_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, partials); break;
-        case 2: ls_eval_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, partials); break;
-        case 3: ls_eval_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, partials); break;
-        case 4: ls_eval_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, partials); break;
+        case 1: ls_eval_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
+        case 2: ls_eval_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
+        case 3: ls_eval_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
+        case 4: ls_eval_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
         default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
     }
     PSPS_LAUNCH_CHECK();

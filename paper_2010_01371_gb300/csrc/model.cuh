@@ -24,10 +24,12 @@ inline int model_blocks(int64_t n) {
 // gamma: per-ray gamma_m = [A |M| 1]_m ([nm][n_rays]) for kappa.
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
                               float *g, float *kappa, double *partials, int nblocks, cudaStream_t s);
-// phi(alpha) data terms (f, f1, f2) partials (3 per block) at alpha = *alpha;
-// returns immediately when *skip != 0.
+// phi(alpha) data terms (f, f1, f2) and the number of rays with some
+// z = Q (l + alpha q) below z_min, as partials (4 per block) at
+// alpha = *alpha; returns immediately when *skip != 0.
 mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y,
-                           const double *alpha, const int *skip, double *partials, int nblocks, cudaStream_t s);
+                           const double *alpha, const int *skip, float z_min, double *partials, int nblocks,
+                           cudaStream_t s);
 mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s);
 // Per-ray Fisher blocks F_i = Q^T D S^T W S D Q (upper triangle, packed
 // [nm(nm+1)/2][n_rays]) with D = y / I0 (one energy/channel) or the water fit.

@@ -8,9 +8,10 @@
 //   grad' = M^T grad,   d' = |M|^T G_kappa + |M|^T |R| |M| 1
 //   p' = -grad'/d' (0 where d' = 0),  p = M p',  q = A p
 //   step length: 1 (classic SPS), or safeguarded Newton on
-//     phi(alpha) = Phi(x + alpha p) from alpha = 1 (n_ls evaluations; the
-//     last evaluated alpha, halved up to n_halve times until phi <= phi(0),
-//     else 0), with per-ray exact phi, phi', phi'' and the penalty's exact
+//     phi(alpha) = Phi(x + alpha p) from the previous iteration's step length
+//     (steps kept within a factor 8; n_ls evaluations; the last evaluated
+//     alpha, halved up to n_halve times until phi <= phi(0), else 0), with
+//     per-ray exact phi, phi', phi'' and the penalty's exact
 //     quadratic in alpha; scalar control runs in one-thread kernels that read
 //     the FP64 partial sums, so nothing returns to the host
 //   x += alpha p,  l += alpha q
@@ -32,12 +33,14 @@ constexpr int kThreads = 256;
 struct DevLS {
     double phi0, R0, pRx, pRp;
     double alpha, best_a, best_f;
+    double a_prev;  // step length accepted in the previous iteration
     int done, nonfinite, it, pad;
 };
 
 struct LsCfg {
     int n_ls, n_halve;
-    double alpha_max;
+    double alpha_max, trust;
+    float z_min;
 };
 
 // Block-wide fixed-order sum of n partials (one block of kThreads threads).
@@ -75,7 +78,7 @@ __global__ void ctrl_ls_init_kernel(DevLS *ls, const double *ppen, int npen) {
     if (threadIdx.x == 0) {
         ls->pRx = pRx;
         ls->pRp = pRp;
-        ls->alpha = 1.0;
+        ls->alpha = ls->a_prev > 0 ? ls->a_prev : 1.0;
         ls->best_a = 0.0;
         ls->best_f = INFINITY;
         ls->done = 0;
@@ -86,22 +89,31 @@ __global__ void ctrl_newton_kernel(DevLS *ls, const double *part, int nb, int la
     const double fd = block_sum(part, nb);
     const double f1d = block_sum(part + nb, nb);
     const double f2d = block_sum(part + 2 * nb, nb);
+    const double bad = block_sum(part + 3 * nb, nb);
     if (threadIdx.x != 0) return;
     const double a = ls->alpha;
-    const double f = fd + ls->R0 + a * ls->pRx + 0.5 * a * a * ls->pRp;
+    const double f = bad > 0 ? INFINITY : fd + ls->R0 + a * ls->pRx + 0.5 * a * a * ls->pRp;
     const double f1 = f1d + ls->pRx + a * ls->pRp;
     const double f2 = f2d + ls->pRp;
-    if (!isfinite(f) || !isfinite(f1) || !isfinite(f2)) ls->nonfinite = 1;
+    const bool finite = isfinite(f) && isfinite(f1) && isfinite(f2);
     if (!last) {
-        double an = f2 > 0 ? a - f1 / f2 : a;
-        if (!(an >= 0)) an = 0.0;  // also catches NaN
+        double an;
+        if (!finite) {
+            an = a / cfg.trust;
+        } else if (f2 > 0) {
+            an = a - f1 / f2;
+            if (an < a / cfg.trust) an = a / cfg.trust;
+            if (an > a * cfg.trust) an = a * cfg.trust;
+        } else {
+            an = a;
+        }
         if (an > cfg.alpha_max) an = cfg.alpha_max;
         ls->alpha = an;
     } else {
         // accept the last evaluated alpha unless phi rose above phi(0)
         ls->best_a = a;
         ls->best_f = f;
-        if (f <= ls->phi0) {
+        if (isfinite(f) && f <= ls->phi0) {
             ls->done = 1;
         } else {
             ls->alpha = 0.5 * a;
@@ -116,10 +128,11 @@ __global__ void ctrl_newton_kernel(DevLS *ls, const double *part, int nb, int la
 __global__ void ctrl_halve_kernel(DevLS *ls, const double *part, int nb, int last) {
     if (ls->done) return;  // uniform across the block
     const double fd = block_sum(part, nb);
+    const double bad = block_sum(part + 3 * nb, nb);
     if (threadIdx.x != 0) return;
     const double a = ls->alpha;
-    const double f = fd + ls->R0 + a * ls->pRx + 0.5 * a * a * ls->pRp;
-    if (f <= ls->phi0) {
+    const double f = bad > 0 ? INFINITY : fd + ls->R0 + a * ls->pRx + 0.5 * a * a * ls->pRp;
+    if (isfinite(f) && f <= ls->phi0) {
         ls->done = 1;
     } else if (last) {
         ls->alpha = 0.0;
@@ -156,8 +169,11 @@ __global__ void update_kernel(DevLS *ls, float *__restrict__ x, const float *__r
     }
 }
 
-__global__ void finish_iter_kernel(DevLS *ls, double *alphas) {
+// Records alpha; the next line search starts from it, or below the last
+// halving after a failed search.
+__global__ void finish_iter_kernel(DevLS *ls, double *alphas, int n_halve) {
     alphas[ls->it] = ls->alpha;
+    ls->a_prev = ls->alpha > 0 ? ls->alpha : ls->best_a / (double)(2 << n_halve);
     ls->it += 1;
 }
 
@@ -184,7 +200,7 @@ struct psps_state {
     int64_t n = 0, n_rays = 0;
     bool has_pen = false;
     PenaltyDev pd{};
-    LsCfg cfg{3, 8, 1e6};
+    LsCfg cfg{3, 8, 1e6, 8.0, -20.0f};
     DBuf<float> x, l, y, gamma, dR, gk, G, gp, dp, pp, p, q;
     DBuf<double> part_obj, part_pen, part_ls, history, alphas;
     DBuf<DevLS> ls;
@@ -301,13 +317,14 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
         PSPS_LAUNCH_CHECK();
         const int nb = st->nb_model;
         for (int k = 0; k < st->cfg.n_ls; ++k) {
-            PSPS_TRY(launch_ls_eval(sp, nr, st->l.p, st->q.p, st->y.p, &st->ls.p->alpha, nullptr, st->part_ls.p, nb, s));
+            PSPS_TRY(launch_ls_eval(sp, nr, st->l.p, st->q.p, st->y.p, &st->ls.p->alpha, nullptr, st->cfg.z_min,
+                                    st->part_ls.p, nb, s));
             ctrl_newton_kernel<<<1, kThreads, 0, s>>>(st->ls.p, st->part_ls.p, nb, k + 1 == st->cfg.n_ls, st->cfg);
             PSPS_LAUNCH_CHECK();
         }
         for (int h = 0; h < st->cfg.n_halve; ++h) {
             PSPS_TRY(launch_ls_eval(sp, nr, st->l.p, st->q.p, st->y.p, &st->ls.p->alpha, &st->ls.p->done,
-                                    st->part_ls.p, nb, s));
+                                    st->cfg.z_min, st->part_ls.p, nb, s));
             ctrl_halve_kernel<<<1, kThreads, 0, s>>>(st->ls.p, st->part_ls.p, nb, h + 1 == st->cfg.n_halve);
             PSPS_LAUNCH_CHECK();
         }
@@ -321,7 +338,7 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
         st->ls.p, st->x.p, st->p.p, nm * n, nonneg ? nullptr : st->l.p, st->q.p, nm * nr, nonneg ? 1 : 0,
         st->alphas.p);
     PSPS_LAUNCH_CHECK();
-    finish_iter_kernel<<<1, 1, 0, s>>>(st->ls.p, st->alphas.p);
+    finish_iter_kernel<<<1, 1, 0, s>>>(st->ls.p, st->alphas.p, st->cfg.n_halve);
     PSPS_LAUNCH_CHECK();
     if (nonneg) PSPS_TRY(project_or_copy(st, st->x.p, st->l.p, s));
     mark(st, PSPS_PROF_UPDATE, 1, s);
@@ -433,7 +450,7 @@ extern "C" mbir_status psps_state_create(mbir_plan *plan, const mbmd_spectrum *s
     A(st->q, nm * nr);
     if (e == MBIR_OK) e = st->part_obj.alloc(st->nb_model);
     if (e == MBIR_OK) e = st->part_pen.alloc(3 * st->nb_pen);
-    if (e == MBIR_OK) e = st->part_ls.alloc(3 * st->nb_model);
+    if (e == MBIR_OK) e = st->part_ls.alloc(4 * st->nb_model);
     if (e == MBIR_OK) e = st->ls.alloc(1);
     if (e != MBIR_OK) {
         delete st;
