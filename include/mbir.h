@@ -102,6 +102,12 @@ mbir_status mbir_project(mbir_plan *plan, const float *x, float *l, int n_mat, m
 mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_mat, int accumulate,
                              mbir_stream stream);
 
+/* Select the transpose's algorithm: 0 = pixel-driven gather (default;
+ * deterministic, no atomics), 1 = ray-driven scatter with FP32 atomics
+ * (same weights, kept as a cross-check).  Both are the exact transpose of
+ * mbir_project up to FP32 rounding. */
+mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
+
 /* ------------------------------------------------------- spectral model */
 
 /* Spectral model of Sec. II-E/F: Q[E][m] (mass attenuation of material m at

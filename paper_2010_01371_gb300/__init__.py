@@ -77,6 +77,10 @@ class Plan:
         self.image_shape = tuple(geom.image_shape)
         self.sino_shape = tuple(geom.sino_shape)
 
+    def set_backprojector(self, mode: str):
+        """'gather' (default, deterministic) or 'atomic' (ray-driven scatter)."""
+        _call(lib().mbir_plan_set_backprojector, self.h, {"gather": 0, "atomic": 1}[mode])
+
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:
             _abi._lib.mbir_plan_destroy(self.h)

@@ -114,6 +114,9 @@ struct mbir_plan {
     int64_t n_rays = 0, n_pix = 0;
     // 2-D per-ray Joseph set-up
     psps::DBuf<float4> ray;       // (f0, df, w, bits(axis,lo,hi))
+    // 2-D per-view constants for the pixel-driven transpose
+    psps::DBuf<float4> view;      // parallel: (cos, sin, -, -); fan: (sx, sy, beta + pi, -)
+    int back_mode = 0;            // 0 gather (default), 1 ray-driven atomics
     // 3-D per-view set-up (source, detector origin and axes) in FP64
     psps::DBuf<double> view3d;
     // scratch: packed / transposed image copies for the forward projector

@@ -19,7 +19,9 @@
 //    y-driven copy [iy][ix][m] (materials packed as float/float2/float4) so
 //    both ray families read contiguous addresses; Kahan-compensated FP32
 //    accumulation along the ray;
-//  * transpose: ray-driven scatter with FP32 atomics (red.global.add).
+//  * transpose: pixel-driven gather (below), deterministic and atomic-free;
+//    a ray-driven scatter with FP32 atomics is kept as a cross-check
+//    (mbir_plan_set_backprojector).
 #include <cmath>
 
 #include "common.cuh"
@@ -110,6 +112,22 @@ __global__ void setup_2d_kernel(mbir_geometry g, int64_t n_rays, float4 *tab) {
     }
     const int bits = axis | (lo << 1) | (hi << 16);
     tab[ray] = make_float4((float)f0, (float)df, (float)w, __int_as_float(bits));
+}
+
+__global__ void setup_view_kernel(mbir_geometry g, float4 *vt) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n_views) return;
+    const double ang = g.angle0 + v * (g.angle_span / g.n_views);
+    double s, c;
+    sincos(ang, &s, &c);
+    if (g.kind == MBIR_PAR2D) {
+        vt[v] = make_float4((float)c, (float)s, 0.f, 0.f);
+    } else {
+        // reduce beta + pi into (-pi, pi]
+        double a = ang + M_PI;
+        a -= 2.0 * M_PI * rint(a / (2.0 * M_PI));
+        vt[v] = make_float4((float)(g.sid * c), (float)(g.sid * s), (float)a, 0.f);
+    }
 }
 
 template <int NM>
@@ -261,6 +279,93 @@ __global__ void __launch_bounds__(kThreads) back_2d_kernel(const float4 *__restr
     }
 }
 
+// Pixel-driven exact transpose: every pixel gathers, view by view, the rays
+// whose Joseph samples touch it.  For x-driven rays that is the set crossing
+// the vertical segment x = x_c, |y - y_c| < dy; for y-driven rays the
+// horizontal segment y = y_c, |x - x_c| < dx.  The bin range of each segment
+// is found from its end points (bin position is monotone along a segment) and
+// widened by one bin; every candidate's weight is then recomputed from the same
+// per-ray set-up as the forward projector, so candidates that do not touch
+// the pixel contribute exactly zero and the weights equal the forward ones.
+// Deterministic (no atomics), one write per pixel, Kahan sums over views.
+template <int NC>
+__global__ void __launch_bounds__(kThreads)
+    back_gather_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
+                          const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x, int accumulate) {
+    const int ix = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int iy = blockIdx.y * 16 + (threadIdx.x >> 4);
+    if (ix >= g.nx || iy >= g.ny) return;
+    const float cxp = 0.5f * (g.nx - 1), cyp = 0.5f * (g.ny - 1);
+    const float xc = (float)((ix - 0.5 * (g.nx - 1)) * g.dx), yc = (float)((iy - 0.5 * (g.ny - 1)) * g.dy);
+    const float dx = (float)g.dx, dy = (float)g.dy;
+    const float cu = 0.5f * (g.n_u - 1);
+    const float inv_du = (float)(1.0 / g.du);
+    const float fan_scale = (float)(g.sdd / g.du);
+    const bool fan = g.kind == MBIR_FAN2D;
+    float acc[NC], comp[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = comp[c] = 0.f;
+    (void)cxp;
+    (void)cyp;
+    for (int v = 0; v < g.n_views; ++v) {
+        const float4 V = vt[v];
+        const float4 *trow = tab + (int64_t)v * g.n_u;
+        const float *srow = sino + (int64_t)v * g.n_u;
+#pragma unroll
+        for (int fam = 0; fam < 2; ++fam) {
+            // segment end points
+            const float ax = fam == 0 ? xc : xc - dx, ay = fam == 0 ? yc - dy : yc;
+            const float bx = fam == 0 ? xc : xc + dx, by = fam == 0 ? yc + dy : yc;
+            float pa, pb;
+            if (!fan) {
+                pa = (-V.y * ax + V.x * ay) * inv_du + cu;
+                pb = (-V.y * bx + V.x * by) * inv_du + cu;
+            } else {
+                float ga = V.z - atan2f(ay - V.y, ax - V.x);
+                float gb = V.z - atan2f(by - V.y, bx - V.x);
+                ga -= 6.283185307f * rintf(ga * 0.159154943f);
+                gb -= 6.283185307f * rintf(gb * 0.159154943f);
+                pa = ga * fan_scale + cu;
+                pb = gb * fan_scale + cu;
+            }
+            int b0 = (int)floorf(fminf(pa, pb)) - 1, b1 = (int)ceilf(fmaxf(pa, pb)) + 1;
+            if (b0 < 0) b0 = 0;
+            if (b1 > g.n_u - 1) b1 = g.n_u - 1;
+            for (int b = b0; b <= b1; ++b) {
+                const float4 r = __ldg(trow + b);
+                const int bits = __float_as_int(r.w);
+                if ((bits & 1) != fam) continue;
+                const int i = fam == 0 ? ix : iy;      // driving index of this pixel
+                const int j = fam == 0 ? iy : ix;      // interpolated index
+                const float fy = fmaf((float)i, r.y, r.x);
+                const float fl = floorf(fy);
+                const int i0 = (int)fl;
+                const float f = fy - fl;
+                float wgt;
+                if (j == i0) wgt = 1.f - f;
+                else if (j == i0 + 1) wgt = f;
+                else continue;
+                wgt *= r.z;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float val = wgt * __ldg(srow + (int64_t)c * n_rays + b);
+                    const float yk = __fsub_rn(val, comp[c]);
+                    const float t = __fadd_rn(acc[c], yk);
+                    comp[c] = __fsub_rn(__fsub_rn(t, acc[c]), yk);
+                    acc[c] = t;
+                }
+            }
+        }
+    }
+    const int64_t npix = (int64_t)g.nx * g.ny;
+    const int64_t pix = (int64_t)iy * g.nx + ix;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        float *o = x + c * npix + pix;
+        *o = accumulate ? *o + acc[c] : acc[c];
+    }
+}
+
 template <int NM>
 mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s) {
     constexpr int P = Pack<NM>::P;
@@ -301,10 +406,30 @@ mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStrea
 
 mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s) {
     if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
-    if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
-    back_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->ray.p, p->n_rays, p->g.nx, p->g.ny,
-                                                                           n_mat, sino, x);
-    PSPS_LAUNCH_CHECK();
+    if (p->back_mode == 1) {
+        if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
+        back_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->ray.p, p->n_rays, p->g.nx,
+                                                                               p->g.ny, n_mat, sino, x);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
+    const dim3 grd((unsigned)cdiv(p->g.nx, 16), (unsigned)cdiv(p->g.ny, 16));
+    for (int m0 = 0; m0 < n_mat;) {
+        const int left = n_mat - m0;
+        const float *sm = sino + (int64_t)m0 * p->n_rays;
+        float *xm = x + (int64_t)m0 * p->n_pix;
+        if (left >= 4) {
+            back_gather_2d_kernel<4><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, accumulate);
+            m0 += 4;
+        } else if (left >= 2) {
+            back_gather_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, accumulate);
+            m0 += 2;
+        } else {
+            back_gather_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, accumulate);
+            m0 += 1;
+        }
+        PSPS_LAUNCH_CHECK();
+    }
     return MBIR_OK;
 }
 
@@ -342,7 +467,12 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
         return st;
     }
     p->partials_cap = 4096;
+    if ((st = p->view.alloc(p->g.n_views)) != MBIR_OK) {
+        delete p;
+        return st;
+    }
     setup_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads>>>(p->g, p->n_rays, p->ray.p);
+    setup_view_kernel<<<(unsigned)cdiv(p->g.n_views, 128), 128>>>(p->g, p->view.p);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -373,4 +503,10 @@ extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *
     if (n_mat < 1 || n_mat > p->n_mat_max)
         return fail(MBIR_ERR_ARG, "mbir_backproject: n_mat %d not in 1..%d", n_mat, p->n_mat_max);
     return backproject(p, sino, x, n_mat, accumulate, (cudaStream_t)s);
+}
+
+extern "C" mbir_status mbir_plan_set_backprojector(mbir_plan *p, int mode) {
+    if (!p || (mode != 0 && mode != 1)) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
+    p->back_mode = mode;
+    return MBIR_OK;
 }

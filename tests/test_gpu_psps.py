@@ -1,5 +1,18 @@
 """GPU (preconditioned) SPS iterations against the FP64 oracle run of the
-same algorithm on the same seeded inputs."""
+same algorithm on the same seeded inputs.
+
+* Without the line search (the paper's update, Eq. 7, on the operator A M)
+  the iteration is a majorise-minimise contraction and whole 50-iteration
+  runs are compared: objective history to 1e-5, image to 1e-4.
+* With the line search the iterates of a descent method with a
+  data-dependent step amplify rounding differences from one iteration to the
+  next (measured: relative differences grow 2-3x per iteration on the plain
+  Fourier preconditioner), so FP32 and FP64 runs part after a few dozen
+  iterations.  There the check is per step: from oracle iterates x_k the GPU
+  runs one iteration (line search from alpha = 1) and x_{k+1}, Phi and alpha
+  are compared with the oracle's one step from the same x_k; whole runs are
+  checked for monotone descent.
+"""
 import numpy as np
 import pytest
 
@@ -19,63 +32,107 @@ def psps():
     return p
 
 
+def gpu_state(psps, prob, kind, data, proj=True, line_search=True, nonneg=False, graph=False, x0=None,
+              gpu_build=False):
+    plan = psps.Plan(prob.geom) if proj else None
+    spec = psps.Spectrum(prob.Q, prob.S)
+    yd = to_dev(prob.y)
+    beta = prob.beta if proj else None
+    if gpu_build:
+        pc = psps.Precond(plan, spec, kind, yd, beta) if kind != "none" else None
+    else:
+        pc = gpu_precond_from(psps, plan, spec, kind, data)
+    return psps.State(plan, spec, pc, yd, beta, x0=to_dev(x0) if x0 is not None else None,
+                      line_search=line_search, nonneg=nonneg, graph=graph), (plan, spec, pc)
+
+
 def run_both(psps, oracle_lib, prob, kind, n_iter, line_search=True, nonneg=False, graph=False, proj=True,
              gpu_build=False):
     """Oracle and GPU runs of the same iteration.  The GPU preconditioner is
     created from the oracle's eigenvalues/blocks (so the comparison isolates
     the iteration), or built on the GPU when gpu_build is set."""
     from oracle import psps as opsps
-    beta = prob.beta if proj else None
     st, P, data = oracle_precond(oracle_lib, prob, kind, proj=proj)
     xo, ho, ao = opsps.run(st, P, n_iter, opsps.LineSearch() if line_search else None, nonneg=nonneg,
                            return_alphas=True)
-    plan = psps.Plan(prob.geom) if proj else None
-    spec = psps.Spectrum(prob.Q, prob.S)
-    yd = to_dev(prob.y)
-    if gpu_build:
-        pc = psps.Precond(plan, spec, kind, yd, beta) if kind != "none" else None
-    else:
-        pc = gpu_precond_from(psps, plan, spec, kind, data)
-    state = psps.State(plan, spec, pc, yd, beta, line_search=line_search, nonneg=nonneg, graph=graph)
+    state, keep = gpu_state(psps, prob, kind, data, proj, line_search, nonneg, graph, gpu_build=gpu_build)
     hg = psps.psps_step(state, n_iter)
     xg = to_host(psps.psps_get_image(state))
     ag = psps.psps_get_alphas(state, n_iter)
     return xo, ho, ao, xg, hg, ag
 
 
-@pytest.mark.parametrize("kind,ls", [("none", False), ("none", True), ("fourier", True), ("mod_fourier", True),
-                                     ("haar", True), ("block", True)])
-def test_config1_50_iterations(psps, oracle_lib, kind, ls):
+@pytest.mark.parametrize("kind", ["none", "fourier", "mod_fourier", "haar", "block"])
+def test_config1_50_iterations(psps, oracle_lib, kind):
     prob = synth.config1()
-    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, kind, 50, line_search=ls)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, kind, 50, line_search=False)
     assert np.all(np.isfinite(hg))
     assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL, np.max(np.abs(hg - ho) / np.abs(ho))
     assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
-    if ls:
-        assert np.all(np.diff(hg) <= 1e-7 * hg[0])
 
 
-@pytest.mark.parametrize("kind", ["mod_fourier", "haar"])
-def test_config1_gpu_built(psps, oracle_lib, kind):
-    """Whole pipeline: GPU-built preconditioner (FP32 build, ~1e-4 from the
-    FP64 one) and 50 iterations.  The build difference enters the iterates
-    once and is carried along: checked at 1e-3 (objective) / 1e-2 (image)."""
-    prob = synth.config1()
-    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, kind, 50, gpu_build=True)
-    assert np.max(np.abs(hg - ho) / np.abs(ho)) < 1e-3
-    assert rel_l2(xg, xo) < 1e-2, rel_l2(xg, xo)
-
-
-def test_config2_reduced_haar(psps, oracle_lib):
+def test_config2_reduced_haar_no_ls(psps, oracle_lib):
     prob = synth.config2(nx=128, n_views=180, n_u=222)
-    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "haar", 20)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "haar", 20, line_search=False)
     assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL
     assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
 
 
-def test_projection_domain_block(psps, oracle_lib):
+def step_cases():
+    c1 = synth.config1
+    c2 = lambda: synth.config2(nx=128, n_views=180, n_u=222)   # noqa: E731
+    c3 = lambda: synth.config3(n_views=12, n_u=301)            # noqa: E731
+    return {"c1-none": (c1, "none", True), "c1-fourier": (c1, "fourier", True),
+            "c1-mod_fourier": (c1, "mod_fourier", True), "c1-haar": (c1, "haar", True),
+            "c1-block": (c1, "block", True), "c2-haar": (c2, "haar", True), "c2-none": (c2, "none", True),
+            "c3-block": (c3, "block", False)}
+
+
+@pytest.mark.parametrize("case", list(step_cases()))
+def test_line_search_step_parity(psps, oracle_lib, case):
+    from oracle import psps as opsps
+    mk, kind, proj = step_cases()[case]
+    prob = mk()
+    st, P, data = oracle_precond(oracle_lib, prob, kind, proj=proj)
+    for k in [0, 4, 15]:
+        xk, _ = opsps.run(st, P, k, opsps.LineSearch()) if k else (st.zeros(), None)
+        x1o, h1o, a1o = opsps.run(st, P, 1, opsps.LineSearch(), x0=xk, return_alphas=True)
+        state, keep = gpu_state(psps, prob, kind, data, proj, x0=xk)
+        h1g = psps.psps_step(state, 1)
+        a1g = psps.psps_get_alphas(state, 1)
+        x1g = to_host(psps.psps_get_image(state))
+        assert abs(h1g[0] - h1o[0]) <= OBJ_TOL * abs(h1o[0]), (k, h1g, h1o)
+        assert abs(h1g[1] - h1o[1]) <= OBJ_TOL * abs(h1o[1]), (k, h1g, h1o)
+        assert abs(a1g[0] - a1o[0]) <= 1e-4 * abs(a1o[0]), (k, a1g, a1o)
+        assert rel_l2(x1g, x1o) < IMG_TOL, (k, rel_l2(x1g, x1o))
+
+
+@pytest.mark.parametrize("case", ["c1-haar", "c1-mod_fourier", "c2-haar", "c3-block"])
+def test_line_search_runs_descend(psps, oracle_lib, case):
+    mk, kind, proj = step_cases()[case]
+    prob = mk()
+    st, P, data = oracle_precond(oracle_lib, prob, kind, proj=proj)
+    state, keep = gpu_state(psps, prob, kind, data, proj)
+    h = psps.psps_step(state, 40)
+    assert np.all(np.isfinite(h))
+    assert np.all(np.diff(h) <= 1e-7 * h[0])
+    assert h[-1] < 0.05 * h[0]
+
+
+@pytest.mark.parametrize("kind", ["mod_fourier", "haar"])
+def test_config1_gpu_built(psps, oracle_lib, kind):
+    """Whole pipeline without the line search: GPU-built preconditioner (FP32
+    build, ~1e-4 from the FP64 one) and 50 iterations; the build difference
+    is carried along: checked at 1e-3 (objective) / 1e-2 (image)."""
+    prob = synth.config1()
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, kind, 50, line_search=False, gpu_build=True)
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < 1e-3
+    assert rel_l2(xg, xo) < 1e-2, rel_l2(xg, xo)
+
+
+def test_projection_domain_block_no_ls(psps, oracle_lib):
     prob = synth.config3(n_views=12, n_u=301)
-    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "block", 50, proj=False)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "block", 50, proj=False, line_search=False)
     assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL
     assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
 
@@ -93,9 +150,12 @@ def test_graph_replay_matches(psps):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     yd = to_dev(prob.y)
     pc = psps.Precond(plan, spec, "mod_fourier", yd, prob.beta)
-    a = psps.State(plan, spec, pc, yd, prob.beta)
-    b = psps.State(plan, spec, pc, yd, prob.beta, graph=True)
+    a = psps.State(plan, spec, pc, yd, prob.beta, line_search=False)
+    b = psps.State(plan, spec, pc, yd, prob.beta, line_search=False, graph=True)
     ha, hb = psps.psps_step(a, 25), psps.psps_step(b, 25)
-    # the backprojection's FP32 atomics make runs differ at rounding level
-    assert np.allclose(ha, hb, rtol=1e-5)
+    assert np.allclose(ha, hb, rtol=1e-6)
     assert rel_l2(to_host(psps.psps_get_image(b)), to_host(psps.psps_get_image(a))) < 1e-5
+    c = psps.State(plan, spec, pc, yd, prob.beta, graph=True)
+    hc = psps.psps_step(c, 10)
+    assert np.all(np.diff(hc) <= 1e-7 * hc[0])
+    assert psps.psps_launch_count(c) > 0
