@@ -102,9 +102,10 @@ mbir_status mbir_project(mbir_plan *plan, const float *x, float *l, int n_mat, m
 mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_mat, int accumulate,
                              mbir_stream stream);
 
-/* Select the transpose's algorithm: 0 = pixel-driven gather (default;
- * deterministic, no atomics), 1 = ray-driven scatter with FP32 atomics
- * (same weights, kept as a cross-check).  Both are the exact transpose of
+/* Select the transpose's algorithm: 0 = tile scatter through shared memory
+ * (default), 1 = pixel-driven gather (deterministic: no atomics, bitwise
+ * reproducible), 2 = ray-driven scatter with global FP32 atomics.  All use the
+ * forward projector's per-ray weights and are the exact transpose of
  * mbir_project up to FP32 rounding. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 

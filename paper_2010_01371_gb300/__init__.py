@@ -78,8 +78,9 @@ class Plan:
         self.sino_shape = tuple(geom.sino_shape)
 
     def set_backprojector(self, mode: str):
-        """'gather' (default, deterministic) or 'atomic' (ray-driven scatter)."""
-        _call(lib().mbir_plan_set_backprojector, self.h, {"gather": 0, "atomic": 1}[mode])
+        """'tile' (default), 'gather' (deterministic) or 'atomic' (ray-driven
+        scatter with global atomics)."""
+        _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2}[mode])
 
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:

@@ -116,7 +116,7 @@ struct mbir_plan {
     psps::DBuf<float4> ray;       // (f0, df, w, bits(axis,lo,hi))
     // 2-D per-view constants for the pixel-driven transpose
     psps::DBuf<float4> view;      // parallel: (cos, sin, -, -); fan: (sx, sy, beta + pi, -)
-    int back_mode = 0;            // 0 gather (default), 1 ray-driven atomics
+    int back_mode = 0;            // 0 tile scatter (default), 1 pixel gather, 2 ray-driven atomics
     // 3-D per-view set-up (source, detector origin and axes) in FP64
     psps::DBuf<double> view3d;
     // scratch: packed / transposed image copies for the forward projector

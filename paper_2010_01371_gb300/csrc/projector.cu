@@ -19,8 +19,9 @@
 //    y-driven copy [iy][ix][m] (materials packed as float/float2/float4) so
 //    both ray families read contiguous addresses; Kahan-compensated FP32
 //    accumulation along the ray;
-//  * transpose: pixel-driven gather (below), deterministic and atomic-free;
-//    a ray-driven scatter with FP32 atomics is kept as a cross-check
+//  * transpose: tile scatter into shared memory (default), a pixel-driven
+//    gather (deterministic, no atomics) and a ray-driven scatter with global
+//    FP32 atomics, all with the forward's per-ray weights
 //    (mbir_plan_set_backprojector).
 #include <cmath>
 
@@ -366,6 +367,129 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Tile scatter transpose (the default).  One CTA owns a kBT x kBT image tile
+// (one accumulator per channel in shared memory) and a range of views; it
+// finds the bins whose rays can touch the tile in each view (fan angle / offset
+// of the tile corners, widened by two bins), walks every such ray over the
+// driving indices of the tile with the forward projector's own per-ray
+// set-up, and adds both interpolation weights times the ray's sinogram values
+// into shared memory.  Each (ray, sample, pixel) term is added by exactly
+// the CTA whose tile holds the pixel, so the result is the transpose of the
+// forward weights; the tile is then added to the image with one global
+// atomic per pixel and channel per CTA.
+constexpr int kBT = 32;          // tile side (pixels)
+constexpr int kBV = 8;           // views processed together by a CTA
+constexpr int kBVsplit = 180;    // views per CTA
+
+template <int NC>
+__global__ void __launch_bounds__(kThreads)
+    back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
+                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x) {
+    __shared__ float acc[NC][kBT][kBT + 1];
+    __shared__ int brange[kBV][2];
+    const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
+    const int v_begin = blockIdx.z * kBVsplit;
+    const int v_end = min(g.n_views, v_begin + kBVsplit);
+    for (int k = threadIdx.x; k < NC * kBT * (kBT + 1); k += blockDim.x) (&acc[0][0][0])[k] = 0.f;
+    const bool fan = g.kind == MBIR_FAN2D;
+    const float cu = 0.5f * (g.n_u - 1);
+    const float inv_du = (float)(1.0 / g.du), fan_scale = (float)(g.sdd / g.du);
+    // tile corners (pixel-centre coordinates widened by one pixel)
+    const float x_lo = (float)((c0 - 1 - 0.5 * (g.nx - 1)) * g.dx), x_hi = (float)((c0 + kBT - 0.5 * (g.nx - 1)) * g.dx);
+    const float y_lo = (float)((r0 - 1 - 0.5 * (g.ny - 1)) * g.dy), y_hi = (float)((r0 + kBT - 0.5 * (g.ny - 1)) * g.dy);
+    for (int vb = v_begin; vb < v_end; vb += kBV) {
+        const int nvb = min(kBV, v_end - vb);
+        __syncthreads();
+        if (threadIdx.x < nvb) {
+            const float4 V = vt[vb + threadIdx.x];
+            float bmin = 3e38f, bmax = -3e38f;
+            for (int k = 0; k < 4; ++k) {
+                const float px = (k & 1) ? x_hi : x_lo, py = (k & 2) ? y_hi : y_lo;
+                float b;
+                if (!fan) {
+                    b = (-V.y * px + V.x * py) * inv_du + cu;
+                } else {
+                    float ga = V.z - atan2f(py - V.y, px - V.x);
+                    ga -= 6.283185307f * rintf(ga * 0.159154943f);
+                    b = ga * fan_scale + cu;
+                }
+                bmin = fminf(bmin, b);
+                bmax = fmaxf(bmax, b);
+            }
+            int b0 = (int)floorf(bmin) - 2, b1 = (int)ceilf(bmax) + 2;
+            b0 = max(b0, 0);
+            b1 = min(b1, g.n_u - 1);
+            brange[threadIdx.x][0] = b0;
+            brange[threadIdx.x][1] = max(0, b1 - b0 + 1);   // bin count
+        }
+        __syncthreads();
+        // flatten the (view, bin) work of this view block
+        int total = 0;
+        for (int k = 0; k < nvb; ++k) total += brange[k][1];
+        for (int item = threadIdx.x; item < total; item += blockDim.x) {
+            int k = 0, rem = item;
+            while (rem >= brange[k][1]) {
+                rem -= brange[k][1];
+                ++k;
+            }
+            const int v = vb + k, b = brange[k][0] + rem;
+            const int64_t ray = (int64_t)v * g.n_u + b;
+            const float4 r = __ldg(tab + ray);
+            const int bits = __float_as_int(r.w);
+            const int axis = bits & 1;
+            const int lo = (bits >> 1) & 0x7fff, hi = (bits >> 16) & 0x7fff;
+            // driving index range inside the tile, and where the interpolated
+            // coordinate can touch rows/columns [o0, o0 + kBT)
+            const int d0 = axis == 0 ? c0 : r0, o0 = axis == 0 ? r0 : c0;
+            int ia = max(lo, d0), ib = min(hi, d0 + kBT - 1);
+            if (r.y != 0.f) {
+                float ta = ((float)o0 - 1.f - r.x) / r.y, tb = ((float)(o0 + kBT) - r.x) / r.y;
+                if (ta > tb) {
+                    const float t = ta;
+                    ta = tb;
+                    tb = t;
+                }
+                ia = max(ia, (int)floorf(ta) - 1);
+                ib = min(ib, (int)ceilf(tb) + 1);
+            }
+            if (ia > ib) continue;
+            float ws[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ws[c] = r.z * __ldg(sino + (int64_t)c * n_rays + ray);
+            for (int i = ia; i <= ib; ++i) {
+                const float fy = fmaf((float)i, r.y, r.x);
+                const float fl = floorf(fy);
+                const int j0 = (int)fl - o0;
+                const float f = fy - fl;
+                const int li = i - d0;
+                if (j0 >= 0 && j0 < kBT) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        float *a = axis == 0 ? &acc[c][j0][li] : &acc[c][li][j0];
+                        atomicAdd(a, (1.f - f) * ws[c]);
+                    }
+                }
+                if (j0 + 1 >= 0 && j0 + 1 < kBT) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        float *a = axis == 0 ? &acc[c][j0 + 1][li] : &acc[c][li][j0 + 1];
+                        atomicAdd(a, f * ws[c]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int64_t npix = (int64_t)g.nx * g.ny;
+    for (int k = threadIdx.x; k < kBT * kBT; k += blockDim.x) {
+        const int rr = k / kBT, cc = k % kBT;
+        const int iy = r0 + rr, ix = c0 + cc;
+        if (iy >= g.ny || ix >= g.nx) continue;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, acc[c][rr][cc]);
+    }
+}
+
 template <int NM>
 mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s) {
     constexpr int P = Pack<NM>::P;
@@ -406,11 +530,29 @@ mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStrea
 
 mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s) {
     if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
-    if (p->back_mode == 1) {
+    if (p->back_mode == 2) {
         if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
         back_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->ray.p, p->n_rays, p->g.nx,
                                                                                p->g.ny, n_mat, sino, x);
         PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
+    if (p->back_mode == 0) {
+        if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
+        const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT), (unsigned)cdiv(p->g.n_views, kBVsplit));
+        for (int m0 = 0; m0 < n_mat;) {
+            const int left = n_mat - m0;
+            const float *sm = sino + (int64_t)m0 * p->n_rays;
+            float *xm = x + (int64_t)m0 * p->n_pix;
+            if (left >= 2) {
+                back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                m0 += 2;
+            } else {
+                back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                m0 += 1;
+            }
+            PSPS_LAUNCH_CHECK();
+        }
         return MBIR_OK;
     }
     const dim3 grd((unsigned)cdiv(p->g.nx, 16), (unsigned)cdiv(p->g.ny, 16));
@@ -506,7 +648,7 @@ extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *
 }
 
 extern "C" mbir_status mbir_plan_set_backprojector(mbir_plan *p, int mode) {
-    if (!p || (mode != 0 && mode != 1)) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
+    if (!p || mode < 0 || mode > 2) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
     p->back_mode = mode;
     return MBIR_OK;
 }

@@ -30,7 +30,7 @@ def test_project_parity(psps, oracle_lib, name, nm):
 
 
 @pytest.mark.parametrize("name", list(small_geoms()))
-@pytest.mark.parametrize("mode", ["gather", "atomic"])
+@pytest.mark.parametrize("mode", ["tile", "gather", "atomic"])
 def test_backproject_parity(psps, oracle_lib, name, mode):
     g = small_geoms()[name]
     rng = np.random.default_rng(2)
@@ -56,23 +56,32 @@ def test_material_packing(psps, oracle_lib, nm):
 
 
 @pytest.mark.parametrize("nch", [1, 2, 3, 4, 5])
-def test_gather_channels(psps, oracle_lib, nch):
-    """The gather transpose handles 1..5 channels (groups of 4, 2, 1)."""
-    g = small_geoms()["par2d_ragged"]
-    s = np.random.default_rng(7).random((nch, g.n_rays))
-    got = to_host(psps.mbir_backproject(psps.Plan(g), to_dev(s)))
-    assert rel_l2(got, oracle_lib.Projector(g).backproject(s)) < TOL
+@pytest.mark.parametrize("mode", ["tile", "gather"])
+def test_transpose_channels(psps, oracle_lib, nch, mode):
+    """The transposes handle 1..5 channels (groups of 4 / 2 / 1)."""
+    for name in ["par2d_ragged", "fan2d_ragged"]:
+        g = small_geoms()[name]
+        s = np.random.default_rng(7).random((nch, g.n_rays))
+        plan = psps.Plan(g)
+        plan.set_backprojector(mode)
+        got = to_host(psps.mbir_backproject(plan, to_dev(s)))
+        assert rel_l2(got, oracle_lib.Projector(g).backproject(s)) < TOL
 
 
-def test_gather_equals_atomic(psps):
-    g = small_geoms()["fan2d_c2_128"]
+def test_transposes_agree(psps):
+    g = synth.config2().geom
     s = to_dev(np.random.default_rng(8).random((2, g.n_rays)))
-    pa, pb = psps.Plan(g), psps.Plan(g)
-    pb.set_backprojector("atomic")
-    a, b = to_host(psps.mbir_backproject(pa, s)), to_host(psps.mbir_backproject(pb, s))
-    assert rel_l2(a, b) < 1e-6
+    out = {}
+    for mode in ["tile", "gather", "atomic"]:
+        p = psps.Plan(g)
+        p.set_backprojector(mode)
+        out[mode] = to_host(psps.mbir_backproject(p, s))
+    assert rel_l2(out["tile"], out["gather"]) < 1e-6
+    assert rel_l2(out["atomic"], out["gather"]) < 1e-6
     # the gather is deterministic: bitwise equal on a second run
-    assert np.array_equal(a, to_host(psps.mbir_backproject(pa, s)))
+    p = psps.Plan(g)
+    p.set_backprojector("gather")
+    assert np.array_equal(out["gather"], to_host(psps.mbir_backproject(p, s)))
 
 
 def test_adjoint_fp32(psps):
