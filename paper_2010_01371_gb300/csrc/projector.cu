@@ -449,6 +449,10 @@ __global__ void __launch_bounds__(kThreads)
                     ta = tb;
                     tb = t;
                 }
+                // nearly axis-aligned rays give huge |ta|, |tb|: clamp before
+                // converting so that the integer bounds cannot overflow
+                ta = fminf(fmaxf(ta, -1.0e8f), 1.0e8f);
+                tb = fminf(fmaxf(tb, -1.0e8f), 1.0e8f);
                 ia = max(ia, (int)floorf(ta) - 1);
                 ib = min(ib, (int)ceilf(tb) + 1);
             }
