@@ -140,6 +140,26 @@ mbir_status mbmd_objective(mbir_plan *plan, const mbmd_spectrum *spec, const flo
 mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
                           int64_t n_rays, float *grad, double *objective, mbir_stream stream);
 
+/* mbmd_objective for projection-domain line integrals (the plan == NULL
+ * case) that allocates no device memory.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory: code
+ * inside a host framework whose device memory belongs to another allocator,
+ * deployments held to a fixed memory budget, and loops that must not call
+ * cudaMalloc / cudaFree (they can block or synchronise the device).
+ * Arguments: Q[n_energy][n_mat] and S[n_chan][n_energy] are HOST FP64 arrays
+ * (as for mbmd_spectrum_create), l [n_mat][n_rays] and y [n_chan][n_rays] are
+ * device arrays, *objective is a device double that receives
+ * L = 1/2 sum w (y - y_bar)^2 (overwritten, not accumulated).
+ * Scratch: a static 28,928-byte device array per GPU, held until the process
+ * exits; limits n_mat <= 4, n_energy <= 256, n_chan <= 8 (larger sizes return
+ * MBIR_ERR_ARG with a message); n_rays is not limited.  The first call on
+ * each device looks up the array's address (make it before any stream
+ * capture).  Every call shares the array: calls that overlap on the GPU race
+ * and must be ordered by the caller (one stream, or events). */
+mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_chan, const double *Q, const double *S,
+                                   const float *l, const float *y, int64_t n_rays, double *objective,
+                                   mbir_stream stream);
+
 /* ----------------------------------------------------- preconditioners */
 
 enum {

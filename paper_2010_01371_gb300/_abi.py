@@ -42,6 +42,8 @@ SIGNATURES = [
     ("mbmd_forward_model", c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     ("mbmd_objective", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("mbmd_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    ("mbmd_objective_noalloc", c_int, [c_int, c_int, c_int, P(c_double), P(c_double), c_void_p, c_void_p, c_int64,
+                                       c_void_p, c_void_p]),
     ("psps_precondition_build", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int64, P(c_double), c_int,
                                         c_void_p, P(c_void_p)]),
     ("psps_precondition_create", c_int, [c_void_p, c_int, c_int, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
