@@ -186,6 +186,7 @@ def ours(args, prob):
     torch.cuda.synchronize()
     launches0 = p.psps_launch_count(st)
     times = []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -194,6 +195,7 @@ def ours(args, prob):
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = float(np.sum(times))
     if world > 1:
@@ -286,6 +288,43 @@ def ours(args, prob):
         torch.distributed.destroy_process_group()
 
 
+def kernel_bench(args, prob):
+    """Times the projector and transpose variants alone on the workload's
+    geometry (CUDA events, L2 flushed between launches)."""
+    import torch
+
+    import paper_2010_01371_gb300 as p
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    plan = p.Plan(prob.geom)
+    rng = np.random.default_rng(0)
+    x1 = torch.as_tensor(prob.truth.astype(np.float32), device=dev)
+    s2 = torch.as_tensor(rng.random((2, plan.n_rays)).astype(np.float32), device=dev)
+    out = {}
+
+    def timeit(fn, reps=20):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+    l1 = torch.empty((1, plan.n_rays), device=dev)
+    g2 = torch.empty((2,) + plan.image_shape, device=dev)
+    for mode in ["tile", "ray"]:
+        plan.set_projector(mode)
+        out[f"project_{mode}_1ch_ms"] = timeit(lambda: p.mbir_project(plan, x1, l1))
+    for mode in ["tile", "gather", "atomic"]:
+        plan.set_backprojector(mode)
+        out[f"backproject_{mode}_2ch_ms"] = timeit(lambda: p.mbir_backproject(plan, s2, g2))
+    print(json.dumps({"kernels": out, "workload": WORKLOAD}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,9 +336,13 @@ def main():
     ap.add_argument("--gap-iters", type=int, default=300)
     ap.add_argument("--gap-star", type=int, default=1500)
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--kernels", action="store_true", help="time the projector variants alone")
     args = ap.parse_args()
     import synth
     prob = synth.config2()
+    if args.kernels:
+        kernel_bench(args, prob)
+        return
     if args.impl == "reference":
         reference_arm(args, prob)
     else:

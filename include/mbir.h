@@ -108,6 +108,11 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
  * forward projector's per-ray weights and are the exact transpose of
  * mbir_project up to FP32 rounding. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
+/* Select the forward projector's algorithm: 0 = per-tile partial sums through
+ * shared memory, combined with one FP32 atomic per (tile, ray) (default);
+ * 1 = one thread per ray with Kahan-compensated sums (deterministic).  Same
+ * Joseph weights. */
+mbir_status mbir_plan_set_projector(mbir_plan *plan, int mode);
 
 /* ------------------------------------------------------- spectral model */
 

@@ -82,6 +82,10 @@ class Plan:
         scatter with global atomics)."""
         _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2}[mode])
 
+    def set_projector(self, mode: str):
+        """'tile' (default) or 'ray' (one thread per ray, deterministic)."""
+        _call(lib().mbir_plan_set_projector, self.h, {"tile": 0, "ray": 1}[mode])
+
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:
             _abi._lib.mbir_plan_destroy(self.h)

@@ -13,12 +13,12 @@
 //    i = 0, its increment per step, the weight and a conservative range of i
 //    (outside it every sample is zero); stored as one float4 per ray and
 //    shared by the forward and the transpose so both use identical weights;
-//  * forward: one thread per ray, neighbouring threads = neighbouring bins of
-//    one view, so a warp samples neighbouring rows of the same column.  The
-//    image is re-laid out per call into an x-driven copy [ix][iy][m] and a
-//    y-driven copy [iy][ix][m] (materials packed as float/float2/float4) so
-//    both ray families read contiguous addresses; Kahan-compensated FP32
-//    accumulation along the ray;
+//  * forward: tile sums through shared memory (default, see the tile
+//    decomposition below), or one thread per ray (neighbouring threads =
+//    neighbouring bins of one view) reading an x-driven copy [ix][iy][m] and a
+//    y-driven copy [iy][ix][m] of the image (materials packed as
+//    float/float2/float4) with Kahan-compensated FP32 accumulation along the
+//    ray (mbir_plan_set_projector);
 //  * transpose: tile scatter into shared memory (default), a pixel-driven
 //    gather (deterministic, no atomics) and a ray-driven scatter with global
 //    FP32 atomics, all with the forward's per-ray weights
@@ -367,130 +367,218 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Tile scatter transpose (the default).  One CTA owns a kBT x kBT image tile
-// (one accumulator per channel in shared memory) and a range of views; it
-// finds the bins whose rays can touch the tile in each view (fan angle / offset
-// of the tile corners, widened by two bins), walks every such ray over the
-// driving indices of the tile with the forward projector's own per-ray
-// set-up, and adds both interpolation weights times the ray's sinogram values
-// into shared memory.  Each (ray, sample, pixel) term is added by exactly
-// the CTA whose tile holds the pixel, so the result is the transpose of the
-// forward weights; the tile is then added to the image with one global
-// atomic per pixel and channel per CTA.
+// ---------------------------------------------------------------------------
+// Tile decomposition shared by the forward projector and the transpose.
+//
+// One CTA owns a kBT x kBT image tile and a chunk of kBVsplit views.  A
+// prologue finds, for every view, the bins whose rays can touch the tile (fan
+// angle / offset of the tile corners widened by one pixel, plus two bins) and
+// prefix-sums their counts; the threads then stride over the flattened
+// (view, bin) items with no further barriers.  For one item the driving
+// indices inside the tile where the interpolated coordinate can reach the
+// tile are solved from the ray's own set-up (f0, df), and each Joseph sample
+// is split into its two pixel terms; a CTA handles exactly the terms whose
+// pixel lies in its tile, so every term is counted once over all CTAs:
+//   forward:   partial sums over the tile's terms, one global atomic per
+//              (tile, ray, channel) into l;
+//   transpose: terms added into shared-memory accumulators (one per channel),
+//              one global atomic per (pixel, channel) per CTA into x.
+// Both use the same per-ray weights as the one-ray-per-thread forward, so the
+// pair is an exact transpose up to FP32 rounding.
 constexpr int kBT = 32;          // tile side (pixels)
-constexpr int kBV = 8;           // views processed together by a CTA
 constexpr int kBVsplit = 180;    // views per CTA
 
-template <int NC>
-__global__ void __launch_bounds__(kThreads)
-    back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
-                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x) {
-    __shared__ float acc[NC][kBT][kBT + 1];
-    __shared__ int brange[kBV][2];
-    const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
-    const int v_begin = blockIdx.z * kBVsplit;
-    const int v_end = min(g.n_views, v_begin + kBVsplit);
-    for (int k = threadIdx.x; k < NC * kBT * (kBT + 1); k += blockDim.x) (&acc[0][0][0])[k] = 0.f;
+struct TileItems {
+    int nv;                      // views in this chunk
+    int v_begin;
+    int b0[kBVsplit];
+    int prefix[kBVsplit + 1];
+};
+
+// Prologue: bin ranges of all views of the chunk (all threads), prefix sum.
+__device__ __forceinline__ void tile_items(TileItems &ti, const float4 *__restrict__ vt, const mbir_geometry &g,
+                                           int c0, int r0) {
     const bool fan = g.kind == MBIR_FAN2D;
     const float cu = 0.5f * (g.n_u - 1);
     const float inv_du = (float)(1.0 / g.du), fan_scale = (float)(g.sdd / g.du);
-    // tile corners (pixel-centre coordinates widened by one pixel)
     const float x_lo = (float)((c0 - 1 - 0.5 * (g.nx - 1)) * g.dx), x_hi = (float)((c0 + kBT - 0.5 * (g.nx - 1)) * g.dx);
     const float y_lo = (float)((r0 - 1 - 0.5 * (g.ny - 1)) * g.dy), y_hi = (float)((r0 + kBT - 0.5 * (g.ny - 1)) * g.dy);
-    for (int vb = v_begin; vb < v_end; vb += kBV) {
-        const int nvb = min(kBV, v_end - vb);
-        __syncthreads();
-        if (threadIdx.x < nvb) {
-            const float4 V = vt[vb + threadIdx.x];
-            float bmin = 3e38f, bmax = -3e38f;
-            for (int k = 0; k < 4; ++k) {
-                const float px = (k & 1) ? x_hi : x_lo, py = (k & 2) ? y_hi : y_lo;
-                float b;
-                if (!fan) {
-                    b = (-V.y * px + V.x * py) * inv_du + cu;
-                } else {
-                    float ga = V.z - atan2f(py - V.y, px - V.x);
-                    ga -= 6.283185307f * rintf(ga * 0.159154943f);
-                    b = ga * fan_scale + cu;
-                }
-                bmin = fminf(bmin, b);
-                bmax = fmaxf(bmax, b);
+    for (int k = threadIdx.x; k < ti.nv; k += blockDim.x) {
+        const float4 V = vt[ti.v_begin + k];
+        float bmin = 3e38f, bmax = -3e38f;
+        for (int q = 0; q < 4; ++q) {
+            const float px = (q & 1) ? x_hi : x_lo, py = (q & 2) ? y_hi : y_lo;
+            float b;
+            if (!fan) {
+                b = (-V.y * px + V.x * py) * inv_du + cu;
+            } else {
+                float ga = V.z - atan2f(py - V.y, px - V.x);
+                ga -= 6.283185307f * rintf(ga * 0.159154943f);
+                b = ga * fan_scale + cu;
             }
-            int b0 = (int)floorf(bmin) - 2, b1 = (int)ceilf(bmax) + 2;
-            b0 = max(b0, 0);
-            b1 = min(b1, g.n_u - 1);
-            brange[threadIdx.x][0] = b0;
-            brange[threadIdx.x][1] = max(0, b1 - b0 + 1);   // bin count
+            bmin = fminf(bmin, b);
+            bmax = fmaxf(bmax, b);
         }
-        __syncthreads();
-        // flatten the (view, bin) work of this view block
-        int total = 0;
-        for (int k = 0; k < nvb; ++k) total += brange[k][1];
-        for (int item = threadIdx.x; item < total; item += blockDim.x) {
-            int k = 0, rem = item;
-            while (rem >= brange[k][1]) {
-                rem -= brange[k][1];
-                ++k;
+        const int b0 = max((int)floorf(bmin) - 2, 0), b1 = min((int)ceilf(bmax) + 2, g.n_u - 1);
+        ti.b0[k] = b0;
+        ti.prefix[k + 1] = max(0, b1 - b0 + 1);   // count, turned into a prefix below
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // warp-level inclusive scan over the counts, 32 views at a time
+        int carry = 0;
+        for (int base = 0; base < ti.nv; base += 32) {
+            const int k = base + threadIdx.x;
+            int v = k < ti.nv ? ti.prefix[k + 1] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (threadIdx.x >= o) v += t;
             }
-            const int v = vb + k, b = brange[k][0] + rem;
-            const int64_t ray = (int64_t)v * g.n_u + b;
-            const float4 r = __ldg(tab + ray);
-            const int bits = __float_as_int(r.w);
-            const int axis = bits & 1;
-            const int lo = (bits >> 1) & 0x7fff, hi = (bits >> 16) & 0x7fff;
-            // driving index range inside the tile, and where the interpolated
-            // coordinate can touch rows/columns [o0, o0 + kBT)
-            const int d0 = axis == 0 ? c0 : r0, o0 = axis == 0 ? r0 : c0;
-            int ia = max(lo, d0), ib = min(hi, d0 + kBT - 1);
-            if (r.y != 0.f) {
-                float ta = ((float)o0 - 1.f - r.x) / r.y, tb = ((float)(o0 + kBT) - r.x) / r.y;
-                if (ta > tb) {
-                    const float t = ta;
-                    ta = tb;
-                    tb = t;
-                }
-                // nearly axis-aligned rays give huge |ta|, |tb|: clamp before
-                // converting so that the integer bounds cannot overflow
-                ta = fminf(fmaxf(ta, -1.0e8f), 1.0e8f);
-                tb = fminf(fmaxf(tb, -1.0e8f), 1.0e8f);
-                ia = max(ia, (int)floorf(ta) - 1);
-                ib = min(ib, (int)ceilf(tb) + 1);
+            if (k < ti.nv) ti.prefix[k + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (threadIdx.x == 0) ti.prefix[0] = 0;
+    }
+    __syncthreads();
+}
+
+// Driving-index range [ia, ib] of one ray inside the tile (empty: ia > ib);
+// axis / d0 / o0: the ray's driving axis, the tile's first driving index and
+// the tile's first interpolated index.
+__device__ __forceinline__ void tile_ray_range(const float4 &r, int c0, int r0, int &axis, int &d0, int &o0, int &ia,
+                                               int &ib) {
+    const int bits = __float_as_int(r.w);
+    axis = bits & 1;
+    const int lo = (bits >> 1) & 0x7fff, hi = (bits >> 16) & 0x7fff;
+    d0 = axis == 0 ? c0 : r0;
+    o0 = axis == 0 ? r0 : c0;
+    ia = max(lo, d0);
+    ib = min(hi, d0 + kBT - 1);
+    if (r.y != 0.f) {
+        float ta = ((float)o0 - 1.f - r.x) / r.y, tb = ((float)(o0 + kBT) - r.x) / r.y;
+        if (ta > tb) {
+            const float t = ta;
+            ta = tb;
+            tb = t;
+        }
+        // nearly axis-aligned rays give huge |ta|, |tb|: clamp before
+        // converting so that the integer bounds cannot overflow
+        ta = fminf(fmaxf(ta, -1.0e8f), 1.0e8f);
+        tb = fminf(fmaxf(tb, -1.0e8f), 1.0e8f);
+        ia = max(ia, (int)floorf(ta) - 1);
+        ib = min(ib, (int)ceilf(tb) + 1);
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kThreads, 6)
+    back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
+                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x) {
+    __shared__ float acc[NC][kBT][kBT + 1];
+    __shared__ TileItems ti;
+    const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
+    if (threadIdx.x == 0) {
+        ti.v_begin = blockIdx.z * kBVsplit;
+        ti.nv = min(g.n_views - ti.v_begin, kBVsplit);
+    }
+    for (int k = threadIdx.x; k < NC * kBT * (kBT + 1); k += blockDim.x) (&acc[0][0][0])[k] = 0.f;
+    __syncthreads();
+    tile_items(ti, vt, g, c0, r0);
+    const int total = ti.prefix[ti.nv];
+    int k = 0;
+    for (int item = threadIdx.x; item < total; item += blockDim.x) {
+        while (item >= ti.prefix[k + 1]) ++k;
+        const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
+        const float4 r = __ldg(tab + ray);
+        int axis, d0, o0, ia, ib;
+        tile_ray_range(r, c0, r0, axis, d0, o0, ia, ib);
+        if (ia > ib) continue;
+        float ws[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ws[c] = r.z * __ldg(sino + (int64_t)c * n_rays + ray);
+        for (int i = ia; i <= ib; ++i) {
+            const float fy = fmaf((float)i, r.y, r.x);
+            const float fl = floorf(fy);
+            const int j0 = (int)fl - o0;
+            const float f = fy - fl;
+            const int li = i - d0;
+            if (j0 >= 0 && j0 < kBT) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) atomicAdd(axis == 0 ? &acc[c][j0][li] : &acc[c][li][j0], (1.f - f) * ws[c]);
             }
-            if (ia > ib) continue;
-            float ws[NC];
+            if (j0 + 1 >= 0 && j0 + 1 < kBT) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) ws[c] = r.z * __ldg(sino + (int64_t)c * n_rays + ray);
-            for (int i = ia; i <= ib; ++i) {
-                const float fy = fmaf((float)i, r.y, r.x);
-                const float fl = floorf(fy);
-                const int j0 = (int)fl - o0;
-                const float f = fy - fl;
-                const int li = i - d0;
-                if (j0 >= 0 && j0 < kBT) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        float *a = axis == 0 ? &acc[c][j0][li] : &acc[c][li][j0];
-                        atomicAdd(a, (1.f - f) * ws[c]);
-                    }
-                }
-                if (j0 + 1 >= 0 && j0 + 1 < kBT) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        float *a = axis == 0 ? &acc[c][j0 + 1][li] : &acc[c][li][j0 + 1];
-                        atomicAdd(a, f * ws[c]);
-                    }
-                }
+                for (int c = 0; c < NC; ++c) atomicAdd(axis == 0 ? &acc[c][j0 + 1][li] : &acc[c][li][j0 + 1], f * ws[c]);
             }
         }
     }
     __syncthreads();
     const int64_t npix = (int64_t)g.nx * g.ny;
-    for (int k = threadIdx.x; k < kBT * kBT; k += blockDim.x) {
-        const int rr = k / kBT, cc = k % kBT;
+    for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+        const int rr = q / kBT, cc = q % kBT;
         const int iy = r0 + rr, ix = c0 + cc;
         if (iy >= g.ny || ix >= g.nx) continue;
 #pragma unroll
         for (int c = 0; c < NC; ++c) atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, acc[c][rr][cc]);
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kThreads, 8)
+    fwd_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
+                       const float *__restrict__ x, int64_t n_rays, float *__restrict__ l) {
+    __shared__ float img[NC][kBT][kBT + 1];
+    __shared__ TileItems ti;
+    const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
+    if (threadIdx.x == 0) {
+        ti.v_begin = blockIdx.z * kBVsplit;
+        ti.nv = min(g.n_views - ti.v_begin, kBVsplit);
+    }
+    const int64_t npix = (int64_t)g.nx * g.ny;
+    for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+        const int rr = q / kBT, cc = q % kBT;
+        const int iy = r0 + rr, ix = c0 + cc;
+        const bool in = iy < g.ny && ix < g.nx;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) img[c][rr][cc] = in ? x[c * npix + (int64_t)iy * g.nx + ix] : 0.f;
+    }
+    __syncthreads();
+    tile_items(ti, vt, g, c0, r0);
+    const int total = ti.prefix[ti.nv];
+    int k = 0;
+    for (int item = threadIdx.x; item < total; item += blockDim.x) {
+        while (item >= ti.prefix[k + 1]) ++k;
+        const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
+        const float4 r = __ldg(tab + ray);
+        int axis, d0, o0, ia, ib;
+        tile_ray_range(r, c0, r0, axis, d0, o0, ia, ib);
+        if (ia > ib) continue;
+        float sum[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sum[c] = 0.f;
+        bool any = false;
+        for (int i = ia; i <= ib; ++i) {
+            const float fy = fmaf((float)i, r.y, r.x);
+            const float fl = floorf(fy);
+            const int j0 = (int)fl - o0;
+            const float f = fy - fl;
+            const int li = i - d0;
+            if (j0 >= 0 && j0 < kBT) {
+                any = true;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sum[c] = fmaf(1.f - f, axis == 0 ? img[c][j0][li] : img[c][li][j0], sum[c]);
+            }
+            if (j0 + 1 >= 0 && j0 + 1 < kBT) {
+                any = true;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sum[c] = fmaf(f, axis == 0 ? img[c][j0 + 1][li] : img[c][li][j0 + 1], sum[c]);
+            }
+        }
+        if (any) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (sum[c] != 0.f) atomicAdd(l + (int64_t)c * n_rays + ray, sum[c] * r.z);
+        }
     }
 }
 
@@ -515,6 +603,25 @@ mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s
 
 mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s) {
     if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
+    if (p->fwd_mode == 0) {
+        PSPS_CUDA(cudaMemsetAsync(l, 0, sizeof(float) * (size_t)n_mat * p->n_rays, s));
+        const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT),
+                       (unsigned)cdiv(p->g.n_views, kBVsplit));
+        for (int m0 = 0; m0 < n_mat;) {
+            const int left = n_mat - m0;
+            const float *xm = x + (int64_t)m0 * p->n_pix;
+            float *lm = l + (int64_t)m0 * p->n_rays;
+            if (left >= 2) {
+                fwd_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, xm, p->n_rays, lm);
+                m0 += 2;
+            } else {
+                fwd_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, xm, p->n_rays, lm);
+                m0 += 1;
+            }
+            PSPS_LAUNCH_CHECK();
+        }
+        return MBIR_OK;
+    }
     int done = 0;
     for (int m0 = 0; m0 < n_mat; m0 += 4) {
         const int nm = n_mat - m0 < 4 ? n_mat - m0 : 4;
@@ -543,7 +650,8 @@ mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, in
     }
     if (p->back_mode == 0) {
         if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
-        const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT), (unsigned)cdiv(p->g.n_views, kBVsplit));
+        const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT),
+                       (unsigned)cdiv(p->g.n_views, kBVsplit));
         for (int m0 = 0; m0 < n_mat;) {
             const int left = n_mat - m0;
             const float *sm = sino + (int64_t)m0 * p->n_rays;
@@ -654,5 +762,11 @@ extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *
 extern "C" mbir_status mbir_plan_set_backprojector(mbir_plan *p, int mode) {
     if (!p || mode < 0 || mode > 2) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
     p->back_mode = mode;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbir_plan_set_projector(mbir_plan *p, int mode) {
+    if (!p || mode < 0 || mode > 1) return fail(MBIR_ERR_ARG, "mbir_plan_set_projector: bad argument");
+    p->fwd_mode = mode;
     return MBIR_OK;
 }

@@ -19,10 +19,12 @@ def psps():
 
 @pytest.mark.parametrize("name", list(small_geoms()))
 @pytest.mark.parametrize("nm", [1, 2])
-def test_project_parity(psps, oracle_lib, name, nm):
+@pytest.mark.parametrize("mode", ["tile", "ray"])
+def test_project_parity(psps, oracle_lib, name, nm, mode):
     g = small_geoms()[name]
     x = phantom(g, seed=1, nm=nm)
     plan = psps.Plan(g)
+    plan.set_projector(mode)
     got = to_host(psps.mbir_project(plan, to_dev(x)))
     want = oracle_lib.Projector(g).project(x)
     assert got.shape == want.shape
@@ -47,10 +49,12 @@ def test_backproject_parity(psps, oracle_lib, name, mode):
 
 
 @pytest.mark.parametrize("nm", [3, 4, 5])
-def test_material_packing(psps, oracle_lib, nm):
+@pytest.mark.parametrize("mode", ["tile", "ray"])
+def test_material_packing(psps, oracle_lib, nm, mode):
     g = small_geoms()["fan2d_ragged"]
     x = phantom(g, seed=3, nm=nm)
     plan = psps.Plan(g)
+    plan.set_projector(mode)
     got = to_host(psps.mbir_project(plan, to_dev(x)))
     assert rel_l2(got, oracle_lib.Projector(g).project(x)) < TOL
 
@@ -96,7 +100,8 @@ def test_adjoint_fp32(psps):
     assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
 
 
-def test_full_size_sampled(psps, oracle_lib):
+@pytest.mark.parametrize("mode", ["tile", "ray"])
+def test_full_size_sampled(psps, oracle_lib, mode):
     """Full 512^2 / 720 x 888 fan-beam geometry: every 97th ray (plus the
     first and last) against the oracle ray by ray, and the adjoint identity
     at full size."""
@@ -104,6 +109,7 @@ def test_full_size_sampled(psps, oracle_lib):
     g = prob.geom
     x = prob.truth
     plan = psps.Plan(g)
+    plan.set_projector(mode)
     got = to_host(psps.mbir_project(plan, to_dev(x)))[0]
     rays = np.unique(np.concatenate([np.arange(0, g.n_rays, 97), [g.n_rays - 1]]))
     want = oracle_lib.Projector(g).project_rays(x[0], rays)
