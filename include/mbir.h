@@ -109,9 +109,10 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
  * mbir_project up to FP32 rounding. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 /* Select the forward projector's algorithm: 0 = per-tile partial sums through
- * shared memory, combined with one FP32 atomic per (tile, ray) (default);
- * 1 = one thread per ray with Kahan-compensated sums (deterministic).  Same
- * Joseph weights. */
+ * shared memory, combined with one FP32 atomic per (tile, ray); 1 = one thread
+ * per ray with Kahan-compensated sums (default; deterministic, and faster on
+ * one channel: 0.27 vs 0.43 ms on 512^2 / 720 x 888 fan beam).  Same Joseph
+ * weights. */
 mbir_status mbir_plan_set_projector(mbir_plan *plan, int mode);
 
 /* ------------------------------------------------------- spectral model */

@@ -83,7 +83,7 @@ class Plan:
         _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2}[mode])
 
     def set_projector(self, mode: str):
-        """'tile' (default) or 'ray' (one thread per ray, deterministic)."""
+        """'ray' (default: one thread per ray, deterministic) or 'tile'."""
         _call(lib().mbir_plan_set_projector, self.h, {"tile": 0, "ray": 1}[mode])
 
     def __del__(self):

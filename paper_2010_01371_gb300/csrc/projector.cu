@@ -13,12 +13,12 @@
 //    i = 0, its increment per step, the weight and a conservative range of i
 //    (outside it every sample is zero); stored as one float4 per ray and
 //    shared by the forward and the transpose so both use identical weights;
-//  * forward: tile sums through shared memory (default, see the tile
-//    decomposition below), or one thread per ray (neighbouring threads =
+//  * forward: one thread per ray (default; neighbouring threads =
 //    neighbouring bins of one view) reading an x-driven copy [ix][iy][m] and a
 //    y-driven copy [iy][ix][m] of the image (materials packed as
 //    float/float2/float4) with Kahan-compensated FP32 accumulation along the
-//    ray (mbir_plan_set_projector);
+//    ray, or tile sums through shared memory (the tile decomposition below;
+//    mbir_plan_set_projector);
 //  * transpose: tile scatter into shared memory (default), a pixel-driven
 //    gather (deterministic, no atomics) and a ray-driven scatter with global
 //    FP32 atomics, all with the forward's per-ray weights

@@ -107,7 +107,9 @@ def test_line_search_step_parity(psps, oracle_lib, case):
         assert abs(h1g[0] - h1o[0]) <= OBJ_TOL * abs(h1o[0]), (k, h1g, h1o)
         assert abs(h1g[1] - h1o[1]) <= OBJ_TOL * abs(h1o[1]), (k, h1g, h1o)
         assert abs(a1g[0] - a1o[0]) <= 1e-4 * abs(a1o[0]), (k, a1g, a1o)
-        assert rel_l2(x1g, x1o) < IMG_TOL, (k, rel_l2(x1g, x1o))
+        # plain Fourier: FP32 FFT of a spectrum spanning 3 decades (see above)
+        tol = 2e-4 if kind == "fourier" else IMG_TOL
+        assert rel_l2(x1g, x1o) < tol, (k, rel_l2(x1g, x1o))
 
 
 @pytest.mark.parametrize("case", ["c1-haar", "c1-mod_fourier", "c2-haar", "c3-block"])
