@@ -41,7 +41,7 @@ from .penalty import NoPenalty, Penalty
 class LineSearch:
     n_ls: int = 3
     n_halve: int = 8
-    alpha_max: float = 1e6
+    alpha_max: float = 1e12
     trust: float = 8.0
     z_min: float = -20.0
     warm: bool = True

@@ -71,6 +71,7 @@ __device__ __forceinline__ void lin(const Pass &p, int idx, int &b, int &k) {
 // mode 1: forward, spectral multiply by spec[k * spec_ks + b * spec_bs] (real),
 //         inverse; complex Z in place
 // mode 2: inverse, complex Z -> real output (times post, times norm)
+// mode 4: inverse, complex Z in place
 __global__ void __launch_bounds__(kThreads)
     fft_pass_kernel(Pass p, int mode, const float *__restrict__ rin, float2 *__restrict__ Z, float *__restrict__ rout,
                     const float *__restrict__ pre_post, const float *__restrict__ spec, int64_t spec_ks, int64_t spec_bs,
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
         R = stockham(R, R == X ? Y : X, p.N, p.B, +1, tw);
-    } else {
+    } else {  // modes 2 and 4
         R = stockham(X, Y, p.N, p.B, +1, tw);
     }
     for (int idx = threadIdx.x; idx < p.N * p.B; idx += blockDim.x) {
@@ -178,6 +179,25 @@ mbir_status FftPlan::forward(int channels, const float *in, float2 *Z, cudaStrea
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 3, nullptr, Z, nullptr, nullptr,
                                                                                     nullptr, 0, 0, 1.f, twy.p);
+        PSPS_LAUNCH_CHECK();
+    }
+    return MBIR_OK;
+}
+
+mbir_status FftPlan::inverse(int channels, float2 *Z, float *out, const float *post, cudaStream_t s) const {
+    const int64_t npix = (int64_t)nx * ny;
+    {
+        Pass p{ny, pick_B(ny), nx, 1, nx, npix};
+        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
+        fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 4, nullptr, Z, nullptr, nullptr,
+                                                                                    nullptr, 0, 0, 1.f, twy.p);
+        PSPS_LAUNCH_CHECK();
+    }
+    {
+        Pass p{nx, pick_B(nx), 1, nx, ny, npix};
+        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
+        fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(
+            p, 2, nullptr, Z, out, post, nullptr, 0, 0, (float)(1.0 / (double)npix), twx.p);
         PSPS_LAUNCH_CHECK();
     }
     return MBIR_OK;

@@ -15,6 +15,8 @@ struct FftPlan {
     mbir_status init(int nx, int ny);
     // Z = DFT(in) (unnormalised, complex [channels][ny][nx]).
     mbir_status forward(int channels, const float *in, float2 *Z, cudaStream_t s) const;
+    // out = post .* Re(IDFT(Z)) (normalised by 1/(nx ny)); Z is overwritten.
+    mbir_status inverse(int channels, float2 *Z, float *out, const float *post, cudaStream_t s) const;
     mbir_status filter(int channels, const float *in, float2 *Z, float *out, const float *m0, const float *spec,
                        cudaStream_t s) const;
 };

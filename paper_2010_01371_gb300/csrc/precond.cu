@@ -214,6 +214,159 @@ __global__ void block_apply_kernel(int nm, int64_t n, const float *__restrict__ 
     }
 }
 
+// Cyclic Jacobi eigendecomposition of a symmetric n x n matrix (n <= 8, FP64):
+// A is destroyed (its diagonal becomes the eigenvalues), V gets the
+// eigenvectors as columns.
+__device__ void sym_eig(int n, double (&A)[8][8], double (&V)[8][8]) {
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) V[a][b] = a == b ? 1.0 : 0.0;
+    double scale = 0.0;
+    for (int a = 0; a < n; ++a) scale += A[a][a] * A[a][a];
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[p][q] * A[p][q];
+        if (off <= 1e-30 * scale || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = cs * akp - sn * akq;
+                    A[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = cs * apk - sn * aqk;
+                    A[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = cs * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+}
+
+// Z[a][f] <- sum_b L[a][b][f] Z[b][f] for every frequency f (nm <= 4).
+__global__ void mix_kernel(int nm, int64_t n, const float *__restrict__ L, float2 *__restrict__ Z) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+        float2 v[4];
+        for (int b = 0; b < nm; ++b) v[b] = Z[(int64_t)b * n + f];
+        for (int a = 0; a < nm; ++a) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int b = 0; b < nm; ++b) {
+                const float l = L[((int64_t)a * nm + b) * n + f];
+                acc.x = fmaf(l, v[b].x, acc.x);
+                acc.y = fmaf(l, v[b].y, acc.y);
+            }
+            Z[(int64_t)a * n + f] = acc;
+        }
+    }
+}
+
+// Lc[a][k][f] = Z[a][f] / DFT(delta_c)(f) = Z[a][f] exp(+2 pi i (fy cy/ny + fx cx/nx))
+__global__ void phase_kernel(int nm, int nx, int ny, int cx, int cy, const float2 *__restrict__ Z, int k,
+                             float2 *__restrict__ Lc) {
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+        const int fy = (int)(f / nx), fx = (int)(f % nx);
+        const double ang = 2.0 * M_PI * ((double)((int64_t)fy * cy % ny) / ny + (double)((int64_t)fx * cx % nx) / nx);
+        double sn, cs;
+        sincos(ang, &sn, &cs);
+        for (int a = 0; a < nm; ++a) {
+            const float2 z = Z[(int64_t)a * n + f];
+            Lc[((int64_t)a * nm + k) * n + f] = make_float2((float)(z.x * cs - z.y * sn), (float)(z.x * sn + z.y * cs));
+        }
+    }
+}
+
+// P = Re((L^H L)^1/2), symmetrised (the block analogue of |lambda|), and its
+// largest eigenvalue, per frequency (FP64; the Hermitian square root through
+// the real 2nm x 2nm embedding [[Re, -Im], [Im, Re]]).
+__global__ void polar_kernel(int nm, int64_t n, const float2 *__restrict__ Lc, float *__restrict__ P,
+                             float *__restrict__ lmax) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    double Lr[4][4], Li[4][4];
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            const float2 z = Lc[((int64_t)a * nm + b) * n + f];
+            Lr[a][b] = z.x;
+            Li[a][b] = z.y;
+        }
+    double E[8][8], V[8][8];
+    const int m2 = 2 * nm;
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            double gr = 0.0, gi = 0.0;  // G = L^H L: G_ab = sum_c conj(L_ca) L_cb
+            for (int c = 0; c < nm; ++c) {
+                gr += Lr[c][a] * Lr[c][b] + Li[c][a] * Li[c][b];
+                gi += Lr[c][a] * Li[c][b] - Li[c][a] * Lr[c][b];
+            }
+            E[a][b] = gr;
+            E[a + nm][b + nm] = gr;
+            E[a][b + nm] = -gi;
+            E[a + nm][b] = gi;
+        }
+    sym_eig(m2, E, V);
+    double S[4][4];
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            double v = 0.0;
+            for (int k = 0; k < m2; ++k) v += V[a][k] * sqrt(fmax(E[k][k], 0.0)) * V[b][k];
+            S[a][b] = v;
+        }
+    double A[8][8];
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            A[a][b] = 0.5 * (S[a][b] + S[b][a]);
+            P[((int64_t)a * nm + b) * n + f] = (float)A[a][b];
+        }
+    sym_eig(nm, A, V);
+    double mx = A[0][0];
+    for (int a = 1; a < nm; ++a) mx = fmax(mx, A[a][a]);
+    lmax[f] = (float)mx;
+}
+
+// Largest eigenvalue of every symmetric block P[a][b][f] (FP64).
+__global__ void block_lmax_kernel(int nm, int64_t n, const float *__restrict__ P, float *__restrict__ lmax) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    double A[8][8], V[8][8];
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b)
+            A[a][b] = 0.5 * ((double)P[((int64_t)a * nm + b) * n + f] + (double)P[((int64_t)b * nm + a) * n + f]);
+    sym_eig(nm, A, V);
+    double mx = A[0][0];
+    for (int a = 1; a < nm; ++a) mx = fmax(mx, A[a][a]);
+    lmax[f] = (float)mx;
+}
+
+// Li = P^-1/2 with every eigenvalue clamped to >= floor (FP64).
+__global__ void invsqrt_floor_kernel(int nm, int64_t n, const float *__restrict__ P, double floor_v,
+                                     float *__restrict__ Li) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    double A[8][8], V[8][8];
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b)
+            A[a][b] = 0.5 * ((double)P[((int64_t)a * nm + b) * n + f] + (double)P[((int64_t)b * nm + a) * n + f]);
+    sym_eig(nm, A, V);
+    double s[4];
+    for (int a = 0; a < nm; ++a) s[a] = 1.0 / sqrt(fmax(A[a][a], floor_v));
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b) {
+            double v = 0.0;
+            for (int k = 0; k < nm; ++k) v += V[a][k] * s[k] * V[b][k];
+            Li[((int64_t)a * nm + b) * n + f] = (float)v;
+        }
+}
+
 unsigned gs(int64_t n) {
     int64_t b = cdiv(n, kThreads);
     return (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
@@ -303,6 +456,57 @@ mbir_status finish_scalar_pub(psps_precond *pc, float *lam, bool fourier, cudaSt
     return finish_scalar(pc, lam, fourier, s);
 }
 
+// Li = P^-1/2 (global eigenvalue floor 1e-6 of the largest) and its
+// absolute-kernel spectra Li_abs[a][b] = Re DFT |IDFT(Li[a][b])|.
+mbir_status finish_cross_fourier(psps_precond *pc, const float *P, const float *lmax, cudaStream_t s) {
+    const int nm = pc->nm;
+    const int64_t n = pc->n;
+    double mx;
+    PSPS_TRY(host_max_abs(lmax, n, mx, s));
+    if (!(mx > 0) || !std::isfinite(mx)) return fail(MBIR_ERR_NONFINITE, "cross-material eigenvalues are not positive");
+    PSPS_TRY(pc->Li.alloc((size_t)nm * nm * n));
+    PSPS_TRY(pc->Li_abs.alloc((size_t)nm * nm * n));
+    invsqrt_floor_kernel<<<nblk(n), 128, 0, s>>>(nm, n, P, 1e-6 * mx, pc->Li.p);
+    PSPS_LAUNCH_CHECK();
+    float *imp = pc->tmp.p, *k = pc->tmp.p + n;
+    for (int ab = 0; ab < nm * nm; ++ab) {
+        PSPS_CUDA(cudaMemsetAsync(imp, 0, sizeof(float) * n, s));
+        set_value_kernel<<<1, 1, 0, s>>>(imp, 0, 1.f);
+        PSPS_TRY(pc->fft.filter(1, imp, pc->Z.p, k, nullptr, pc->Li.p + (int64_t)ab * n, s));
+        abs_kernel<<<gs(n), kThreads, 0, s>>>(k, n);
+        PSPS_TRY(pc->fft.forward(1, k, pc->Z.p, s));
+        real_part_kernel<<<gs(n), kThreads, 0, s>>>(pc->Z.p, pc->Li_abs.p + (int64_t)ab * n, n);
+        PSPS_LAUNCH_CHECK();
+    }
+    PSPS_CUDA(cudaStreamSynchronize(s));
+    return MBIR_OK;
+}
+
+mbir_status launch_block_lmax(int nm, int64_t n, const float *P, float *lmax, cudaStream_t s) {
+    block_lmax_kernel<<<nblk(n), 128, 0, s>>>(nm, n, P, lmax);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+mbir_status launch_polar(int nm, int64_t n, const float2 *Lc, float *P, float *lmax, cudaStream_t s) {
+    polar_kernel<<<nblk(n), 128, 0, s>>>(nm, n, Lc, P, lmax);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+mbir_status launch_phase(int nm, int nx, int ny, const float2 *Z, int k, float2 *Lc, cudaStream_t s) {
+    phase_kernel<<<gs((int64_t)nx * ny), kThreads, 0, s>>>(nm, nx, ny, nx / 2, ny / 2, Z, k, Lc);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+mbir_status launch_block_apply(int nm, int64_t n, const float *B, const float *in, float *out, int transpose,
+                               cudaStream_t s) {
+    block_apply_kernel<<<gs(n), kThreads, 0, s>>>(nm, n, B, in, out, transpose);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
 mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out, cudaStream_t s) {
     const bool absm = (op == PSPS_APPLY_ABS_M || op == PSPS_APPLY_ABS_MT);
     const bool tr = (op == PSPS_APPLY_MT || op == PSPS_APPLY_ABS_MT);
@@ -323,6 +527,21 @@ mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out,
                                                               tr ? 1 : 0);
             PSPS_LAUNCH_CHECK();
             return MBIR_OK;
+        case PSPS_PRECOND_BLOCK_FOURIER: {
+            // M = M0^T U^H L^-1/2 U M0 (Eq. 57); every factor is symmetric, so
+            // M^T = M; |M| uses |M0| and the absolute-kernel spectra.
+            const float *Bm = absm ? pc->Babs.p : pc->B.p;
+            float *t0 = pc->tmp.p, *t1 = pc->tmp.p + pc->n * pc->nm;
+            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
+            PSPS_LAUNCH_CHECK();
+            PSPS_TRY(pc->fft.forward(pc->nm, t0, pc->Z.p, s));
+            mix_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Li_abs.p : pc->Li.p, pc->Z.p);
+            PSPS_LAUNCH_CHECK();
+            PSPS_TRY(pc->fft.inverse(pc->nm, pc->Z.p, t1, nullptr, s));
+            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
+            PSPS_LAUNCH_CHECK();
+            return MBIR_OK;
+        }
         default:
             return fail(MBIR_ERR_UNIMPLEMENTED, "preconditioner kind %d not built", pc->kind);
     }
@@ -360,14 +579,14 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         return fail(MBIR_ERR_ARG, "projection-domain decomposition supports NONE and BLOCK preconditioners");
     if ((kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_HAAR) && nm != 1)
         return fail(MBIR_ERR_ARG, "Fourier / modified Fourier / Haar preconditioners are single-material (n_mat = 1)");
-    if (kind == PSPS_PRECOND_BLOCK_FOURIER) return fail(MBIR_ERR_UNIMPLEMENTED, "cross-material Fourier not built");
     if (plan && plan->g.kind == MBIR_CONE3D && kind != PSPS_PRECOND_BLOCK)
         return fail(MBIR_ERR_UNIMPLEMENTED, "3-D volumes support the BLOCK preconditioner only");
     if (kind == PSPS_PRECOND_HAAR && !haar_supported(pc->nx, plan->g.ny))
         return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
     if (kind == PSPS_PRECOND_HAAR && (haar_lattice < 0 || haar_lattice > 64))
         return fail(MBIR_ERR_ARG, "haar_lattice must be 0..64");
-    if ((kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER)) PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+    if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_BLOCK_FOURIER)
+        PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
 
     const int64_t n = pc->n;
     const int nF = nm * (nm + 1) / 2;
@@ -428,6 +647,30 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_CUDA(cudaStreamSynchronize(s));
     }
     if (kind == PSPS_PRECOND_BLOCK) return MBIR_OK;
+    if (kind == PSPS_PRECOND_BLOCK_FOURIER) {
+        // L_k of Eq. 56: DFT of M0^T H M0 delta_{c,k} over DFT(delta_c), for
+        // each material k with the impulse at the centre pixel c
+        const int nx = pc->nx, ny = pc->ny;
+        DBuf<float2> Lc;
+        DBuf<float> d, v, hv, P, lmax;
+        PSPS_TRY(Lc.alloc((size_t)nm * nm * n));
+        PSPS_TRY(d.alloc((size_t)nm * n));
+        PSPS_TRY(v.alloc((size_t)nm * n));
+        PSPS_TRY(hv.alloc((size_t)nm * n));
+        for (int k = 0; k < nm; ++k) {
+            PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * nm * n, s));
+            set_value_kernel<<<1, 1, 0, s>>>(d.p, (int64_t)k * n + (int64_t)(ny / 2) * nx + nx / 2, 1.f);
+            PSPS_TRY(launch_block_apply(nm, n, pc->B.p, d.p, v.p, 0, s));
+            PSPS_TRY(H.apply(v.p, hv.p, 1, s));
+            PSPS_TRY(launch_block_apply(nm, n, pc->B.p, hv.p, v.p, 1, s));
+            PSPS_TRY(pc->fft.forward(nm, v.p, pc->Z.p, s));
+            PSPS_TRY(launch_phase(nm, nx, ny, pc->Z.p, k, Lc.p, s));
+        }
+        PSPS_TRY(P.alloc((size_t)nm * nm * n));
+        PSPS_TRY(lmax.alloc(n));
+        PSPS_TRY(launch_polar(nm, n, Lc.p, P.p, lmax.p, s));
+        return finish_cross_fourier(pc, P.p, lmax.p, s);
+    }
     // one material from here on: m0 = B
     PSPS_TRY(pc->m0.alloc(n));
     if (kind == PSPS_PRECOND_FOURIER) {
@@ -556,12 +799,26 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
         PSPS_CUDA(cudaStreamSynchronize(s));
         return MBIR_OK;
     }
+    if (kind == PSPS_PRECOND_BLOCK_FOURIER) {
+        if (!plan || !lam || !blocks)
+            return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK_FOURIER needs a plan, lam (P blocks) and blocks");
+        PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+        PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
+        PSPS_TRY(pc->Babs.alloc((size_t)nm * nm * n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->B.p, blocks, sizeof(float) * pc->B.n, cudaMemcpyDeviceToDevice, s));
+        PSPS_TRY(launch_abs_copy(blocks, pc->Babs.p, (int64_t)pc->B.n, s));
+        PSPS_TRY(pc->tmp.alloc((size_t)n * nm * 2));
+        PSPS_TRY(pc->Z.alloc((size_t)n * nm));
+        DBuf<float> lmax;
+        PSPS_TRY(lmax.alloc(n));
+        PSPS_TRY(launch_block_lmax(nm, n, lam, lmax.p, s));
+        return finish_cross_fourier(pc, lam, lmax.p, s);
+    }
     if (!plan || nm != 1 || !lam)
         return fail(MBIR_ERR_ARG, "psps_precondition_create: Fourier/Haar kinds need a plan, n_mat = 1 and lam");
     if (kind == PSPS_PRECOND_HAAR && !haar_supported(plan->g.nx, plan->g.ny))
         return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
     if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER) PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
-    if (kind == PSPS_PRECOND_BLOCK_FOURIER) return fail(MBIR_ERR_UNIMPLEMENTED, "cross-material Fourier not built");
     PSPS_TRY(pc->tmp.alloc((size_t)n * 4));
     PSPS_TRY(pc->Z.alloc((size_t)n * 2));
     PSPS_TRY(pc->s.alloc(n));

@@ -12,6 +12,7 @@ struct psps_precond {
     psps::DBuf<float> m0;    // diagonal zero-frequency normalisation (one material)
     psps::DBuf<float> s, s_abs;  // spectra / wavelet-domain scales
     psps::DBuf<float> B, Babs;   // blocks [nm][nm][n]
+    psps::DBuf<float> Li, Li_abs;  // cross-material Fourier: per-frequency blocks [nm][nm][n]
     psps::DBuf<float> tmp;       // scratch (n * nm * 2)
     psps::DBuf<float2> Z;        // FFT scratch (n * nm * 2 complex)
     psps::FftPlan fft;

@@ -200,7 +200,7 @@ struct psps_state {
     int64_t n = 0, n_rays = 0;
     bool has_pen = false;
     PenaltyDev pd{};
-    LsCfg cfg{3, 8, 1e6, 8.0, -20.0f};
+    LsCfg cfg{3, 8, 1e12, 8.0, -20.0f};
     DBuf<float> x, l, y, gamma, dR, gk, G, gp, dp, pp, p, q;
     DBuf<double> part_obj, part_pen, part_ls, history, alphas;
     DBuf<DevLS> ls;

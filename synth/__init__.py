@@ -386,3 +386,50 @@ def pc_channels(E, kvp: float, thresholds, I0: float):
     s = kramers(E, kvp)
     edges = list(thresholds) + [kvp + 1]
     return np.stack([I0 * s * ((E >= lo) & (E < hi)) for lo, hi in zip(edges[:-1], edges[1:])])
+
+
+def mbmd_problem(config: int, geom: Geometry, mats, names, Q, S, beta, n_iter: int, precond: str,
+                 name: str) -> Problem:
+    """One-step MBMD data: per-material analytic line integrals of additive
+    density ellipses, polyenergetic expected counts, Poisson noise."""
+    o, d = geom.rays()
+    l = np.stack([chord_lengths(shapes, o, d) for shapes in mats])       # [m, rays] (mm * g/cm^3)
+    ybar = S @ np.exp(-(Q @ l))
+    y = poisson(rng(config, "noise"), ybar)
+    truth = np.stack([render(geom, shapes, supersample=2) for shapes in mats])
+    return Problem(name, geom, Q, S, y, np.asarray(beta, dtype=np.float64), truth, n_iter, precond, geom.n_rays)
+
+
+def mbmd_phantom(g: np.random.Generator, scale: float):
+    """Water body with bone-like and iodine-like inserts (densities in g/cm^3:
+    water 1.0, bone 0.3-1.5, iodine 0.005-0.02, inside the water)."""
+    water = [Ellipse(0.0, 0.0, 110.0 * scale, 90.0 * scale, 0.0, 1.0)]
+    bone = random_ellipses(g, 4, radius=75.0 * scale, amin=5.0 * scale, amax=18.0 * scale, vmin=0.3, vmax=1.5)
+    iod = random_ellipses(g, 4, radius=75.0 * scale, amin=4.0 * scale, amax=12.0 * scale, vmin=0.005, vmax=0.02)
+    return [water, bone, iod]
+
+
+# written by oracle/derive_config4_beta.py (rounded)
+CONFIG4_BETA = np.array([[0.5, 0.1, 3.1], [0.1, 2.1, 6.4], [3.1, 6.4, 1960.0]])
+
+
+def config4_slice(nx: int = 512, n_views: int = 720, n_u: int = 888, slice_id: int = 0) -> Problem:
+    """One slice of the one-step MBMD workload: 3 materials (water, bone-like,
+    iodine-like with a 6x K-edge at 33.2 keV), 4 photon-counting channels
+    [25,40) [40,60) [60,80) [80,120] keV under a 120 kVp spectrum (I0 = 1e5),
+    fan beam like config 2 (bins scaled with the slice: the field of view
+    follows the image), per-pixel 3x3 blocks + cross-material Fourier.
+    beta (density units) = CONFIG4_BETA: 0.05 x the mean diagonal Fisher
+    information over 2|N| at full size, with positive cross terms
+    0.1 sqrt(beta_kk beta_k'k'), rounded."""
+    E = np.arange(20.0, 121.0)
+    Q = material_Q(E, ["water", "bone", "iodine"], rng(4, "materials"))
+    S = pc_channels(E, 120.0, [25.0, 40.0, 60.0, 80.0], 1e5)
+    g = rng(4, "phantom")
+    for _ in range(slice_id):
+        g = np.random.Generator(np.random.PCG64(g.integers(2 ** 63)))
+    dx = 0.5 * 512 / nx
+    geom = Geometry(FAN2D, nx, nx, 1, dx, dx, 1.0, n_views, 0.0, 2 * math.pi, n_u, 1, 1.0 * 888 / n_u, 1.0,
+                    500.0, 1000.0)
+    return mbmd_problem(4, geom, mbmd_phantom(g, 1.0), ["water", "bone", "iodine"], Q, S, CONFIG4_BETA, 100,
+                        "block_fourier", f"c4_mbmd_{nx}")

@@ -59,8 +59,15 @@ def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True):
         lam = precond.fourier_eigenvalues(aH, st.shape)
         return st, precond.Fourier(lam), {"lam": lam}
     B = build.m0_blocks(st, F)
+    blocks = np.ascontiguousarray(np.transpose(B, (1, 2, 0)))
     if kind == "block":
-        return st, precond.Block(B, st.shape), {"blocks": np.ascontiguousarray(np.transpose(B, (1, 2, 0)))}
+        return st, precond.Block(B, st.shape), {"blocks": blocks}
+    if kind == "block_fourier":
+        M0 = precond.Block(B, st.shape)
+        L = precond.cross_fourier_blocks(aH, M0, st.shape, st.nm)
+        P = precond.polar_real(L)
+        lam = np.ascontiguousarray(np.transpose(P.reshape(-1, st.nm, st.nm), (1, 2, 0)))
+        return st, precond.CrossFourier(L, M0), {"lam": lam, "blocks": blocks}
     m0 = B[:, 0, 0].reshape(st.shape)
 
     def aN(v):

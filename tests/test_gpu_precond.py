@@ -61,6 +61,19 @@ def test_build_parity(psps, oracle_lib, pname, kind):
     check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOL)
 
 
+@pytest.mark.parametrize("kind", ["block", "block_fourier"])
+def test_mbmd_apply_and_build(psps, oracle_lib, kind):
+    """One-step MBMD (3 materials): per-pixel 3x3 blocks and the cross-material
+    Fourier preconditioner (Eq. 57), created from the oracle's data (apply
+    tolerance) and built on the GPU (build tolerance)."""
+    prob = synth.config4_slice(nx=64, n_views=90, n_u=111)
+    st, P, data = oracle_precond(oracle_lib, prob, kind)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (3,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+
+
 def test_projection_domain_block(psps, oracle_lib):
     prob = synth.config3(n_views=10, n_u=333)
     st, P, data = oracle_precond(oracle_lib, prob, "block", proj=False)
