@@ -466,7 +466,7 @@ mbir_status finish_cross_fourier(psps_precond *pc, const float *P, const float *
     if (!(mx > 0) || !std::isfinite(mx)) return fail(MBIR_ERR_NONFINITE, "cross-material eigenvalues are not positive");
     PSPS_TRY(pc->Li.alloc((size_t)nm * nm * n));
     PSPS_TRY(pc->Li_abs.alloc((size_t)nm * nm * n));
-    invsqrt_floor_kernel<<<nblk(n), 128, 0, s>>>(nm, n, P, 1e-6 * mx, pc->Li.p);
+    invsqrt_floor_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(nm, n, P, 1e-6 * mx, pc->Li.p);
     PSPS_LAUNCH_CHECK();
     float *imp = pc->tmp.p, *k = pc->tmp.p + n;
     for (int ab = 0; ab < nm * nm; ++ab) {
@@ -483,13 +483,13 @@ mbir_status finish_cross_fourier(psps_precond *pc, const float *P, const float *
 }
 
 mbir_status launch_block_lmax(int nm, int64_t n, const float *P, float *lmax, cudaStream_t s) {
-    block_lmax_kernel<<<nblk(n), 128, 0, s>>>(nm, n, P, lmax);
+    block_lmax_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(nm, n, P, lmax);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
 }
 
 mbir_status launch_polar(int nm, int64_t n, const float2 *Lc, float *P, float *lmax, cudaStream_t s) {
-    polar_kernel<<<nblk(n), 128, 0, s>>>(nm, n, Lc, P, lmax);
+    polar_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(nm, n, Lc, P, lmax);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
 }
@@ -612,7 +612,6 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     PSPS_TRY(pc->s_abs.alloc(n));
 
     // ---- M0 blocks from (F+R) 1_k (Eqs. 30, 53-54): all nm probes at once
-    if (nm * nm > max_ch && plan) return fail(MBIR_ERR_ARG, "plan n_mat_max must be >= n_mat^2 for the block build");
     {
         DBuf<float> ones, Hcols;
         PSPS_TRY(ones.alloc((size_t)nm * nm * n));
@@ -621,7 +620,13 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         for (int k = 0; k < nm; ++k)
             fill_kernel<<<gs(n), kThreads, 0, s>>>(ones.p + ((int64_t)k * nm + k) * n, n, 1.f);
         PSPS_LAUNCH_CHECK();
-        PSPS_TRY(H.apply(ones.p, Hcols.p, nm, s));
+        // all nm probes at once when the plan has the channels, else one by one
+        if (!plan || nm * nm <= max_ch) {
+            PSPS_TRY(H.apply(ones.p, Hcols.p, nm, s));
+        } else {
+            for (int k = 0; k < nm; ++k)
+                PSPS_TRY(H.apply(ones.p + (int64_t)k * nm * n, Hcols.p + (int64_t)k * nm * n, 1, s));
+        }
         // Hcols[k][m][j] = (H 1_k)_m(j) = block[m][k] -> reorder to [m][k][j]
         DBuf<float> Hb;
         PSPS_TRY(Hb.alloc((size_t)nm * nm * n));
