@@ -121,7 +121,8 @@ struct mbir_plan {
     // 3-D per-view set-up (source, detector origin and axes) in FP64
     psps::DBuf<double> view3d;
     // scratch: packed / transposed image copies for the forward projector
-    psps::DBuf<float> xrow, xcol;
+    // (3-D: one copy per driving axis)
+    psps::DBuf<float> xrow, xcol, xcol3;
     // scratch for reductions
     psps::DBuf<double> partials;
     int partials_cap = 0;
@@ -141,4 +142,8 @@ namespace psps {
 // projector internals (projector.cu)
 mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s);
 mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s);
+// cone-beam (cone.cu)
+mbir_status cone_setup(mbir_plan *p);
+mbir_status project_cone(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s);
+mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s);
 }  // namespace psps

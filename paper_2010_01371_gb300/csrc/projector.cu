@@ -602,7 +602,7 @@ mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s
 }  // namespace
 
 mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s) {
-    if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
+    if (p->g.kind == MBIR_CONE3D) return project_cone(p, x, l, n_mat, s);
     if (p->fwd_mode == 0) {
         PSPS_CUDA(cudaMemsetAsync(l, 0, sizeof(float) * (size_t)n_mat * p->n_rays, s));
         const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT),
@@ -640,7 +640,7 @@ mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStrea
 }
 
 mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s) {
-    if (p->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "cone-beam projector not built");
+    if (p->g.kind == MBIR_CONE3D) return backproject_cone(p, sino, x, n_mat, accumulate, s);
     if (p->back_mode == 2) {
         if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
         back_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->ray.p, p->n_rays, p->g.nx,
@@ -696,32 +696,44 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
     *out = nullptr;
     if (g->kind != MBIR_PAR2D && g->kind != MBIR_FAN2D && g->kind != MBIR_CONE3D)
         return fail(MBIR_ERR_ARG, "mbir_plan_create: unknown geometry kind %d", g->kind);
-    if (g->kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "mbir_plan_create: cone-beam not built");
-    if (g->nx < 1 || g->ny < 1 || g->nx > 16384 || g->ny > 16384 || g->n_views < 1 || g->n_u < 1)
-        return fail(MBIR_ERR_ARG, "mbir_plan_create: bad sizes nx=%d ny=%d views=%d n_u=%d (1..16384)", g->nx, g->ny,
-                    g->n_views, g->n_u);
-    if (!(g->dx > 0) || !(g->dy > 0) || !(g->du > 0) || !(g->angle_span != 0))
+    const bool cone = g->kind == MBIR_CONE3D;
+    if (g->nx < 1 || g->ny < 1 || g->nx > 16384 || g->ny > 16384 || g->n_views < 1 || g->n_u < 1 ||
+        (cone && (g->nz < 1 || g->nz > 16384 || g->n_v < 1)))
+        return fail(MBIR_ERR_ARG, "mbir_plan_create: bad sizes nx=%d ny=%d nz=%d views=%d n_u=%d n_v=%d", g->nx, g->ny,
+                    g->nz, g->n_views, g->n_u, g->n_v);
+    if (!(g->dx > 0) || !(g->dy > 0) || !(g->du > 0) || !(g->angle_span != 0) || (cone && (!(g->dz > 0) || !(g->dv > 0))))
         return fail(MBIR_ERR_ARG, "mbir_plan_create: pixel/bin sizes must be > 0 and angle_span != 0");
-    if (g->kind == MBIR_FAN2D) {
+    if (g->kind == MBIR_FAN2D || cone) {
         const double half = 0.5 * sqrt(g->nx * g->dx * g->nx * g->dx + g->ny * g->dy * g->ny * g->dy);
         if (!(g->sdd > 0) || !(g->sid > half))
-            return fail(MBIR_ERR_ARG, "mbir_plan_create: fan beam needs sdd > 0 and the source outside the image");
+            return fail(MBIR_ERR_ARG, "mbir_plan_create: divergent beams need sdd > 0 and the source outside the image");
     }
     if (n_mat_max < 1 || n_mat_max > 8) return fail(MBIR_ERR_ARG, "mbir_plan_create: n_mat_max must be 1..8");
     mbir_plan *p = new mbir_plan();
     p->g = *g;
-    if (g->kind != MBIR_CONE3D) p->g.nz = 1, p->g.n_v = 1;
+    if (!cone) p->g.nz = 1, p->g.n_v = 1;
     p->n_mat_max = n_mat_max;
-    p->n_rays = (int64_t)g->n_views * g->n_u;
-    p->n_pix = (int64_t)g->nx * g->ny;
+    p->n_rays = (int64_t)p->g.n_views * p->g.n_u * p->g.n_v;
+    p->n_pix = (int64_t)p->g.nx * p->g.ny * p->g.nz;
     mbir_status st;
-    if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->xcol.alloc(p->n_pix * 4)) != MBIR_OK ||
-        (st = p->xrow.alloc(p->n_pix * 4)) != MBIR_OK || (st = p->partials.alloc(8 * 4096)) != MBIR_OK) {
+    if ((st = p->xcol.alloc(p->n_pix * 4)) != MBIR_OK || (st = p->xrow.alloc(p->n_pix * 4)) != MBIR_OK ||
+        (st = p->partials.alloc(8 * 4096)) != MBIR_OK || (cone && (st = p->xcol3.alloc(p->n_pix * 4)) != MBIR_OK)) {
         delete p;
         return st;
     }
     p->partials_cap = 4096;
-    if ((st = p->view.alloc(p->g.n_views)) != MBIR_OK) {
+    if (cone) {
+        st = cone_setup(p);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (st == MBIR_OK && e != cudaSuccess) st = fail(MBIR_ERR_CUDA, "mbir_plan_create: %s", cudaGetErrorString(e));
+        if (st != MBIR_OK) {
+            delete p;
+            return st;
+        }
+        *out = p;
+        return MBIR_OK;
+    }
+    if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->view.alloc(p->g.n_views)) != MBIR_OK) {
         delete p;
         return st;
     }

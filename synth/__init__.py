@@ -433,3 +433,40 @@ def config4_slice(nx: int = 512, n_views: int = 720, n_u: int = 888, slice_id: i
                     500.0, 1000.0)
     return mbmd_problem(4, geom, mbmd_phantom(g, 1.0), ["water", "bone", "iodine"], Q, S, CONFIG4_BETA, 100,
                         "block_fourier", f"c4_mbmd_{nx}")
+
+
+CONFIG5_BETA = np.array([[0.5, 3.0], [3.0, 2000.0]])
+
+
+def config5(n: int = 256, n_views: int = 360, n_u: int = 512, n_v: int = 384, rays: bool = True) -> Problem:
+    """3-D cone-beam one-step MBMD: 2 materials (water, iodine-like), 80/140 kVp
+    dual-energy channels (each normalised to I0 = 5e4), 256^3 at 0.5 mm, 360
+    views over 360 deg onto a 512 x 384 flat detector of 0.8 mm pixels, SID 600,
+    SDD 1200; seeded ellipsoid phantom; per-voxel 2x2 blocks.  Smaller n /
+    views / detector scale the same scan down (same field of view).  beta in
+    density units: the water and iodine strengths of CONFIG4_BETA (rounded)
+    with the cross term 0.1 sqrt(beta_11 beta_22)."""
+    E = np.arange(20.0, 141.0)
+    Q = material_Q(E, ["water", "iodine"], rng(5, "materials"))
+    I0 = 5e4
+    S = np.stack([I0 * kramers(E, 80.0), I0 * kramers(E, 140.0)])
+    scale = 256.0 / n
+    geom = Geometry(CONE3D, n, n, n, 0.5 * scale, 0.5 * scale, 0.5 * scale, n_views, 0.0, 2 * math.pi, n_u, n_v,
+                    0.8 * 512 / n_u, 0.8 * 384 / n_v, 600.0, 1200.0)
+    g = rng(5, "phantom")
+    water = [Ellipsoid(0.0, 0.0, 0.0, 55.0, 45.0, 50.0, 0.0, 1.0)]
+    iod = []
+    for _ in range(5):
+        r = g.uniform(4.0, 10.0)
+        th = g.uniform(0, 2 * math.pi)
+        rho = g.uniform(0, 30.0)
+        iod.append(Ellipsoid(rho * math.cos(th), rho * math.sin(th), g.uniform(-25, 25), r, r * g.uniform(0.7, 1.3),
+                             r * g.uniform(0.7, 1.3), g.uniform(0, math.pi), g.uniform(0.005, 0.02)))
+    mats = [water, iod]
+    truth = np.stack([render(geom, shapes, supersample=2) for shapes in mats])
+    if not rays:
+        return Problem("c5_cone3d", geom, Q, S, np.zeros((2, 0)), CONFIG5_BETA, truth, 50, "block", geom.n_rays)
+    o, d = geom.rays()
+    l = np.stack([chord_lengths(shapes, o, d) for shapes in mats])
+    y = poisson(rng(5, "noise"), S @ np.exp(-(Q @ l)))
+    return Problem("c5_cone3d", geom, Q, S, y, CONFIG5_BETA, truth, 50, "block", geom.n_rays)

@@ -23,6 +23,14 @@ def to_host(t):
     return t.detach().double().cpu().numpy()
 
 
+def cone_geoms():
+    return {
+        "cone_small": synth.config5(n=32, n_views=24, n_u=64, n_v=48, rays=False).geom,
+        "cone_ragged": Geometry(synth.CONE3D, 21, 18, 13, 0.9, 1.0, 1.2, 17, 0.3, 2 * math.pi, 37, 23, 1.1, 1.3,
+                                 60.0, 130.0),
+    }
+
+
 def small_geoms():
     """Several tiles' worth of rays with ragged sizes (non-multiples of the
     block sizes), parallel and fan."""
@@ -37,6 +45,12 @@ def small_geoms():
 def phantom(geom, seed=0, nm=1):
     rng = np.random.default_rng(seed)
     out = []
+    if geom.kind == synth.CONE3D:
+        for m in range(nm):
+            shapes = [synth.Ellipsoid(*rng.uniform(-3, 3, 3), *rng.uniform(3, 8, 3), rng.uniform(0, 3),
+                                      rng.uniform(0.01, 0.03)) for _ in range(3)]
+            out.append(synth.render(geom, shapes, supersample=2) + 0.002 * rng.random(geom.image_shape))
+        return np.stack(out)
     for m in range(nm):
         shapes = synth.random_ellipses(rng, 4, radius=0.4 * min(geom.nx * geom.dx, geom.ny * geom.dy),
                                        amin=0.05 * geom.nx * geom.dx, amax=0.15 * geom.nx * geom.dx,

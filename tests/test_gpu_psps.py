@@ -90,16 +90,27 @@ def test_config4_slice_no_ls(psps, oracle_lib, kind):
     assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
 
 
+@pytest.mark.parametrize("kind", ["none", "block"])
+def test_config5_reduced_no_ls(psps, oracle_lib, kind):
+    """3-D cone-beam one-step MBMD (2 materials, dual energy), 32^3 reduction."""
+    prob = synth.config5(n=32, n_views=24, n_u=64, n_v=48)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, kind, 20, line_search=False)
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL, np.max(np.abs(hg - ho) / np.abs(ho))
+    assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
+
+
 def step_cases():
     c1 = synth.config1
     c2 = lambda: synth.config2(nx=128, n_views=180, n_u=222)   # noqa: E731
     c3 = lambda: synth.config3(n_views=12, n_u=301)            # noqa: E731
     c4 = lambda: synth.config4_slice(nx=64, n_views=90, n_u=111)   # noqa: E731
+    c5 = lambda: synth.config5(n=32, n_views=24, n_u=64, n_v=48)   # noqa: E731
     return {"c1-none": (c1, "none", True), "c1-fourier": (c1, "fourier", True),
             "c1-mod_fourier": (c1, "mod_fourier", True), "c1-haar": (c1, "haar", True),
             "c1-block": (c1, "block", True), "c2-haar": (c2, "haar", True), "c2-none": (c2, "none", True),
             "c3-block": (c3, "block", False),
-            "c4-block": (c4, "block", True), "c4-block_fourier": (c4, "block_fourier", True)}
+            "c4-block": (c4, "block", True), "c4-block_fourier": (c4, "block_fourier", True),
+            "c5-block": (c5, "block", True)}
 
 
 @pytest.mark.parametrize("case", list(step_cases()))
