@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kModelThreads)
             const float yc = y[(int64_t)c * n_rays + i];
             const float w = 1.f / fmaxf(yc, 1.f);
             const float r = yb[c] - yc;
-            obj += 0.5 * (double)w * (double)r * (double)r;
             wr[c] = w * r;
+            obj += (double)(0.5f * wr[c] * r);
             ws[c] = w * sig[c];
         }
         if (g || kappa) {
@@ -161,6 +161,126 @@ __global__ void __launch_bounds__(kModelThreads)
     }
     double v[4] = {f, f1, f2, bad};
     block_sum_store<4>(v, partials);
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kModelThreads)
+    ls_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
+                    const float *__restrict__ y, DevLS *ls, LsCfg cfg, int mode, int last,
+                    double *__restrict__ partials) {
+    if (mode == 1 && ls->done) return;  // same value for every block
+    extern __shared__ float sh[];
+    load_spec(sp, sh);
+    const float *Q = sh;
+    const float *S = sh + sp.ne * NM;
+    const int nc = sp.nc, ne = sp.ne;
+    const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
+    double acc[2 * kMaxHalve];
+#pragma unroll
+    for (int k = 0; k < 2 * kMaxHalve; ++k) acc[k] = 0.0;
+    if (mode == 0) {
+        const float alpha = (float)ls->alpha;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            float la[NM], qm[NM];
+            float zlo = 3.0e38f;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                qm[m] = q[(int64_t)m * n_rays + i];
+                la[m] = fmaf(alpha, qm[m], l[(int64_t)m * n_rays + i]);
+            }
+            float yb[kMaxC], d1[kMaxC], d2[kMaxC];
+            for (int c = 0; c < nc; ++c) yb[c] = d1[c] = d2[c] = 0.f;
+            for (int e = 0; e < ne; ++e) {
+                float z = 0.f, dz = 0.f;
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    z = fmaf(Q[e * NM + m], la[m], z);
+                    dz = fmaf(Q[e * NM + m], qm[m], dz);
+                }
+                zlo = fminf(zlo, z);
+                const float t = expf(-z);
+                const float tdz = t * dz;
+                for (int c = 0; c < nc; ++c) {
+                    const float s = S[c * ne + e];
+                    yb[c] = fmaf(s, t, yb[c]);
+                    d1[c] = fmaf(-s, tdz, d1[c]);
+                    d2[c] = fmaf(s, tdz * dz, d2[c]);
+                }
+            }
+            float f = 0.f, f1 = 0.f, f2 = 0.f;
+            for (int c = 0; c < nc; ++c) {
+                const float yc = y[(int64_t)c * n_rays + i];
+                const float w = 1.f / fmaxf(yc, 1.f);
+                const float r = yb[c] - yc;
+                f = fmaf(0.5f * w * r, r, f);
+                f1 = fmaf(w * r, d1[c], f1);
+                f2 = fmaf(w, fmaf(d1[c], d1[c], r * d2[c]), f2);
+            }
+            acc[0] += (double)f;
+            acc[1] += (double)f1;
+            acc[2] += (double)f2;
+            if (!(zlo >= cfg.z_min)) acc[3] += 1.0;
+        }
+        double v[4] = {acc[0], acc[1], acc[2], acc[3]};
+        block_sum_store<4>(v, partials);
+    } else {
+        const double a0 = ls->best_a;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            float lm[NM], qm[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                qm[m] = q[(int64_t)m * n_rays + i];
+                lm[m] = l[(int64_t)m * n_rays + i];
+            }
+            double ak = a0;
+            for (int k = 0; k < nh; ++k) {
+                ak *= 0.5;
+                const float alpha = (float)ak;
+                float yb[kMaxC];
+                for (int c = 0; c < nc; ++c) yb[c] = 0.f;
+                float zlo = 3.0e38f;
+                for (int e = 0; e < ne; ++e) {
+                    float z = 0.f;
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alpha, qm[m], lm[m]), z);
+                    zlo = fminf(zlo, z);
+                    const float t = expf(-z);
+                    for (int c = 0; c < nc; ++c) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
+                }
+                float f = 0.f;
+                for (int c = 0; c < nc; ++c) {
+                    const float yc = y[(int64_t)c * n_rays + i];
+                    const float r = yb[c] - yc;
+                    f = fmaf(0.5f * r / fmaxf(yc, 1.f), r, f);
+                }
+                acc[k] += (double)f;
+                if (!(zlo >= cfg.z_min)) acc[kMaxHalve + k] += 1.0;
+            }
+        }
+        block_sum_store<2 * kMaxHalve>(acc, partials);
+    }
+    if (!last_block_arrive(&ls->ticket)) return;
+    const int nb = gridDim.x;
+    if (mode == 0) {
+        const double fd = block_sum_all(partials, nb), f1d = block_sum_all(partials + nb, nb);
+        const double f2d = block_sum_all(partials + 2 * nb, nb), bad = block_sum_all(partials + 3 * nb, nb);
+        if (threadIdx.x == 0) {
+            ls_newton_control(ls, fd, f1d, f2d, bad, last, cfg);
+            ls->ticket = 0;
+        }
+    } else {
+        double fk[kMaxHalve], bk[kMaxHalve];
+        for (int k = 0; k < nh; ++k) {
+            fk[k] = block_sum_all(partials + (int64_t)k * nb, nb);
+            bk[k] = block_sum_all(partials + (int64_t)(kMaxHalve + k) * nb, nb);
+        }
+        if (threadIdx.x == 0) {
+            ls_halve_control(ls, fk, bk, nh);
+            ls->ticket = 0;
+        }
+    }
 }
 
 __global__ void forward_model_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, float *__restrict__ ybar) {
@@ -268,6 +388,20 @@ mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const flo
         case 2: ls_eval_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
         case 3: ls_eval_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
         case 4: ls_eval_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
+        default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
+    }
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
+                            LsCfg cfg, int mode, int last, double *partials, int nblocks, cudaStream_t s) {
+    const size_t smem = spec_smem(sp);
+    switch (sp.nm) {
+        case 1: ls_fused_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
+        case 2: ls_fused_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
+        case 3: ls_fused_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
+        case 4: ls_fused_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
         default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
     }
     PSPS_LAUNCH_CHECK();

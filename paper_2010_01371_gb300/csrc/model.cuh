@@ -2,6 +2,7 @@
 // line-search terms (model.cu).
 #pragma once
 #include "common.cuh"
+#include "ls.cuh"
 
 namespace psps {
 
@@ -30,6 +31,12 @@ mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const 
 mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y,
                            const double *alpha, const int *skip, float z_min, double *partials, int nblocks,
                            cudaStream_t s);
+// Fused line-search evaluation: mode 0 evaluates phi, phi', phi'' at
+// ls->alpha and its last block runs the Newton control; mode 1 (skipped when
+// the search is done) evaluates the n_halve halving candidates at once and
+// its last block picks the step.  partials: 2 kMaxHalve doubles per block.
+mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
+                            LsCfg cfg, int mode, int last, double *partials, int nblocks, cudaStream_t s);
 mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s);
 // Per-ray Fisher blocks F_i = Q^T D S^T W S D Q (upper triangle, packed
 // [nm(nm+1)/2][n_rays]) with D = y / I0 (one energy/channel) or the water fit.

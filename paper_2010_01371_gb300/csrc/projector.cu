@@ -202,6 +202,30 @@ __global__ void pack_kernel(const float *__restrict__ x, int nx, int ny, float *
     }
 }
 
+// Neighbour pairs for the one-channel forward: pairs[i][j + 1] =
+// (x(i, j), x(i, j + 1)) along the interpolated axis, j = -1 .. n_other - 1,
+// zero outside the image, so every sample is one aligned 8-byte load.
+// family 0: i = column, j = row; family 1: i = row, j = column.
+__global__ void pair_pack_kernel(const float *__restrict__ x, int nx, int ny, float2 *__restrict__ pc,
+                                 float2 *__restrict__ pr) {
+    const int64_t ncol = (int64_t)nx * (ny + 1), nrow = (int64_t)ny * (nx + 1);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncol + nrow;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < ncol) {
+            const int i = (int)(t / (ny + 1)), j = (int)(t % (ny + 1)) - 1;   // column i, rows j, j+1
+            const float a = j >= 0 ? x[(int64_t)j * nx + i] : 0.f;
+            const float b = j + 1 < ny ? x[(int64_t)(j + 1) * nx + i] : 0.f;
+            pc[t] = make_float2(a, b);
+        } else {
+            const int64_t u = t - ncol;
+            const int i = (int)(u / (nx + 1)), j = (int)(u % (nx + 1)) - 1;   // row i, columns j, j+1
+            const float a = j >= 0 ? x[(int64_t)i * nx + j] : 0.f;
+            const float b = j + 1 < nx ? x[(int64_t)i * nx + j + 1] : 0.f;
+            pr[u] = make_float2(a, b);
+        }
+    }
+}
+
 __device__ __forceinline__ void decode(float4 r, int &axis, int &lo, int &hi) {
     const int bits = __float_as_int(r.w);
     axis = bits & 1;
@@ -246,6 +270,34 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restri
     }
 #pragma unroll
     for (int m = 0; m < NM; ++m) l[(int64_t)m * n_rays + ray] = acc[m] * r.z;
+}
+
+__global__ void __launch_bounds__(kThreads) fwd_2d_pair_kernel(const float4 *__restrict__ tab, int64_t n_rays, int nx,
+                                                               int ny, const float2 *__restrict__ pc,
+                                                               const float2 *__restrict__ pr, float *__restrict__ l) {
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n_rays) return;
+    const float4 r = tab[ray];
+    int axis, lo, hi;
+    decode(r, axis, lo, hi);
+    const float2 *src = axis == 0 ? pc : pr;
+    const int n_other = axis == 0 ? ny : nx;
+    const int64_t stride = n_other + 1;
+    float acc = 0.f, comp = 0.f;
+    for (int i = lo; i <= hi; ++i) {
+        const float fy = fmaf((float)i, r.y, r.x);
+        const float fl = floorf(fy);
+        const int i0 = (int)fl;
+        const float f = fy - fl;
+        if (i0 < -1 || i0 >= n_other) continue;
+        const float2 ab = __ldg(src + (int64_t)i * stride + i0 + 1);
+        const float v = __fadd_rn(__fmul_rn(1.f - f, ab.x), __fmul_rn(f, ab.y));
+        const float yk = __fsub_rn(v, comp);
+        const float t = __fadd_rn(acc, yk);
+        comp = __fsub_rn(__fsub_rn(t, acc), yk);
+        acc = t;
+    }
+    l[ray] = acc * r.z;
 }
 
 __global__ void __launch_bounds__(kThreads) back_2d_kernel(const float4 *__restrict__ tab, int64_t n_rays, int nx,
@@ -470,6 +522,12 @@ __device__ __forceinline__ void tile_ray_range(const float4 &r, int c0, int r0, 
     }
 }
 
+// Shared-memory reduction without a return value (red.shared.add.f32).
+__device__ __forceinline__ void red_shared_add(float *addr, float v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kThreads, 6)
     back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
@@ -504,11 +562,13 @@ __global__ void __launch_bounds__(kThreads, 6)
             const int li = i - d0;
             if (j0 >= 0 && j0 < kBT) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) atomicAdd(axis == 0 ? &acc[c][j0][li] : &acc[c][li][j0], (1.f - f) * ws[c]);
+                for (int c = 0; c < NC; ++c)
+                    red_shared_add(axis == 0 ? &acc[c][j0][li] : &acc[c][li][j0], (1.f - f) * ws[c]);
             }
             if (j0 + 1 >= 0 && j0 + 1 < kBT) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) atomicAdd(axis == 0 ? &acc[c][j0 + 1][li] : &acc[c][li][j0 + 1], f * ws[c]);
+                for (int c = 0; c < NC; ++c)
+                    red_shared_add(axis == 0 ? &acc[c][j0 + 1][li] : &acc[c][li][j0 + 1], f * ws[c]);
             }
         }
     }
@@ -585,6 +645,18 @@ __global__ void __launch_bounds__(kThreads, 8)
 template <int NM>
 mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s) {
     constexpr int P = Pack<NM>::P;
+    if (NM == 1) {
+        const int nx = p->g.nx, ny = p->g.ny;
+        float2 *pc = (float2 *)p->xcol.p, *pr = (float2 *)p->xrow.p;
+        const int64_t tot = (int64_t)nx * (ny + 1) + (int64_t)ny * (nx + 1);
+        const int64_t gb = cdiv(tot, kThreads) < 8192 ? cdiv(tot, kThreads) : 8192;
+        pair_pack_kernel<<<(unsigned)gb, kThreads, 0, s>>>(x, nx, ny, pc, pr);
+        PSPS_LAUNCH_CHECK();
+        fwd_2d_pair_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->ray.p, p->n_rays, nx, ny, pc,
+                                                                                   pr, l);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
     const int nx = p->g.nx, ny = p->g.ny;
     float *xrow = (NM == 1) ? nullptr : p->xrow.p;
     dim3 blk(32, 8), grd((unsigned)cdiv(nx, 32), (unsigned)cdiv(ny, 32));

@@ -30,19 +30,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-struct DevLS {
-    double phi0, R0, pRx, pRp;
-    double alpha, best_a, best_f;
-    double a_prev;  // step length accepted in the previous iteration
-    int done, nonfinite, it, pad;
-};
-
-struct LsCfg {
-    int n_ls, n_halve;
-    double alpha_max, trust;
-    float z_min;
-};
-
 // Block-wide fixed-order sum of n partials (one block of kThreads threads).
 __device__ double block_sum(const double *p, int n) {
     __shared__ double sh[32];
@@ -82,63 +69,6 @@ __global__ void ctrl_ls_init_kernel(DevLS *ls, const double *ppen, int npen) {
         ls->best_a = 0.0;
         ls->best_f = INFINITY;
         ls->done = 0;
-    }
-}
-
-__global__ void ctrl_newton_kernel(DevLS *ls, const double *part, int nb, int last, LsCfg cfg) {
-    const double fd = block_sum(part, nb);
-    const double f1d = block_sum(part + nb, nb);
-    const double f2d = block_sum(part + 2 * nb, nb);
-    const double bad = block_sum(part + 3 * nb, nb);
-    if (threadIdx.x != 0) return;
-    const double a = ls->alpha;
-    const double f = bad > 0 ? INFINITY : fd + ls->R0 + a * ls->pRx + 0.5 * a * a * ls->pRp;
-    const double f1 = f1d + ls->pRx + a * ls->pRp;
-    const double f2 = f2d + ls->pRp;
-    const bool finite = isfinite(f) && isfinite(f1) && isfinite(f2);
-    if (!last) {
-        double an;
-        if (!finite) {
-            an = a / cfg.trust;
-        } else if (f2 > 0) {
-            an = a - f1 / f2;
-            if (an < a / cfg.trust) an = a / cfg.trust;
-            if (an > a * cfg.trust) an = a * cfg.trust;
-        } else {
-            an = a;
-        }
-        if (an > cfg.alpha_max) an = cfg.alpha_max;
-        ls->alpha = an;
-    } else {
-        // accept the last evaluated alpha unless phi rose above phi(0)
-        ls->best_a = a;
-        ls->best_f = f;
-        if (isfinite(f) && f <= ls->phi0) {
-            ls->done = 1;
-        } else {
-            ls->alpha = 0.5 * a;
-            if (cfg.n_halve == 0) {
-                ls->alpha = 0.0;
-                ls->done = 1;
-            }
-        }
-    }
-}
-
-__global__ void ctrl_halve_kernel(DevLS *ls, const double *part, int nb, int last) {
-    if (ls->done) return;  // uniform across the block
-    const double fd = block_sum(part, nb);
-    const double bad = block_sum(part + 3 * nb, nb);
-    if (threadIdx.x != 0) return;
-    const double a = ls->alpha;
-    const double f = bad > 0 ? INFINITY : fd + ls->R0 + a * ls->pRx + 0.5 * a * a * ls->pRp;
-    if (isfinite(f) && f <= ls->phi0) {
-        ls->done = 1;
-    } else if (last) {
-        ls->alpha = 0.0;
-        ls->done = 1;
-    } else {
-        ls->alpha = 0.5 * a;
     }
 }
 
@@ -316,18 +246,11 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
         ctrl_ls_init_kernel<<<1, kThreads, 0, s>>>(st->ls.p, st->has_pen ? st->part_pen.p : nullptr, st->nb_pen);
         PSPS_LAUNCH_CHECK();
         const int nb = st->nb_model;
-        for (int k = 0; k < st->cfg.n_ls; ++k) {
-            PSPS_TRY(launch_ls_eval(sp, nr, st->l.p, st->q.p, st->y.p, &st->ls.p->alpha, nullptr, st->cfg.z_min,
-                                    st->part_ls.p, nb, s));
-            ctrl_newton_kernel<<<1, kThreads, 0, s>>>(st->ls.p, st->part_ls.p, nb, k + 1 == st->cfg.n_ls, st->cfg);
-            PSPS_LAUNCH_CHECK();
-        }
-        for (int h = 0; h < st->cfg.n_halve; ++h) {
-            PSPS_TRY(launch_ls_eval(sp, nr, st->l.p, st->q.p, st->y.p, &st->ls.p->alpha, &st->ls.p->done,
-                                    st->cfg.z_min, st->part_ls.p, nb, s));
-            ctrl_halve_kernel<<<1, kThreads, 0, s>>>(st->ls.p, st->part_ls.p, nb, h + 1 == st->cfg.n_halve);
-            PSPS_LAUNCH_CHECK();
-        }
+        for (int k = 0; k < st->cfg.n_ls; ++k)
+            PSPS_TRY(launch_ls_fused(sp, nr, st->l.p, st->q.p, st->y.p, st->ls.p, st->cfg, 0, k + 1 == st->cfg.n_ls,
+                                     st->part_ls.p, nb, s));
+        if (st->cfg.n_halve > 0)
+            PSPS_TRY(launch_ls_fused(sp, nr, st->l.p, st->q.p, st->y.p, st->ls.p, st->cfg, 1, 1, st->part_ls.p, nb, s));
     } else {
         set_alpha_one_kernel<<<1, 1, 0, s>>>(st->ls.p);
         PSPS_LAUNCH_CHECK();
@@ -450,7 +373,7 @@ extern "C" mbir_status psps_state_create(mbir_plan *plan, const mbmd_spectrum *s
     A(st->q, nm * nr);
     if (e == MBIR_OK) e = st->part_obj.alloc(st->nb_model);
     if (e == MBIR_OK) e = st->part_pen.alloc(3 * st->nb_pen);
-    if (e == MBIR_OK) e = st->part_ls.alloc(4 * st->nb_model);
+    if (e == MBIR_OK) e = st->part_ls.alloc(2 * kMaxHalve * st->nb_model);
     if (e == MBIR_OK) e = st->ls.alloc(1);
     if (e != MBIR_OK) {
         delete st;
