@@ -30,6 +30,19 @@ sys.path.insert(0, ROOT)
 METRIC = "precond-SPS iters/s & time to 1e-4 rel objective gap vs plain SPS, one GB300"
 WORKLOAD = "c2_fan2d_512_haar"
 
+# other workloads (python bench.py --workload NAME): problem builder,
+# preconditioner, description
+WORKLOADS = {
+    "c2_fan2d_512_haar": ("config2", "haar", "512x512@0.5mm, 720x888 fan curved, Haar(M0, lattice 3)"),
+    "c1_par2d_64_modfourier": ("config1", "mod_fourier", "64x64@1mm, 90x96 parallel, modified Fourier"),
+    "c3_projdomain_block": ("config3", "block", "720x888 rays, 2 materials x 2 kVp channels, per-ray 2x2 blocks"),
+    "c4_mbmd_512_blockfourier": ("config4_slice", "block_fourier",
+                                 "512x512@0.5mm, 3 materials x 4 PC channels (101 energies), 3x3 blocks + "
+                                 "cross-material Fourier"),
+    "c5_cone3d_256_block": ("config5", "block", "256^3@0.5mm, 360x384x512 cone flat, 2 materials x 2 kVp, 2x2 "
+                                                "per-voxel blocks"),
+}
+
 
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -139,19 +152,19 @@ def reference_arm(args, prob):
 
 
 def gap_runs(p, plan, spec, yd, beta, pc, n_star: int, n_cmp: int):
-    """Objective histories for PSPS (Haar) and plain SPS (with and without the
-    line search); Phi* from a long PSPS run."""
+    """Objective histories for PSPS and plain SPS (with and without the line
+    search); Phi* from a long PSPS run."""
     st = p.State(plan, spec, pc, yd, beta, graph=True)
     h_star = p.psps_step(st, n_star)
     out = {}
-    for name, pcx, ls in [("psps_haar", pc, True), ("sps", None, False), ("sps_ls", None, True)]:
+    for name, pcx, ls in [("psps", pc, True), ("sps", None, False), ("sps_ls", None, True)]:
         s = p.State(plan, spec, pcx, yd, beta, line_search=ls, graph=True)
         out[name] = p.psps_step(s, n_cmp)
     phi_star = min(float(np.min(h_star)), *[float(np.min(v)) for v in out.values()])
     return phi_star, out
 
 
-def ours(args, prob):
+def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
     import torch
 
     import paper_2010_01371_gb300 as p
@@ -166,12 +179,13 @@ def ours(args, prob):
     y_host = torch.as_tensor(prob.y.astype(np.float32)).pin_memory()
     yd = y_host.to(dev)
     t0 = time.perf_counter()
-    plan = p.Plan(prob.geom)
+    plan = p.Plan(prob.geom) if prob.geom is not None else None
     spec = p.Spectrum(prob.Q, prob.S)
-    pc = p.Precond(plan, spec, "haar", yd, prob.beta)
+    beta = prob.beta if plan is not None else None
+    pc = p.Precond(plan, spec, kind, yd, beta)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    st = p.State(plan, spec, pc, yd, prob.beta, line_search=True, graph=True)
+    st = p.State(plan, spec, pc, yd, beta, line_search=True, graph=True)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     for _ in range(args.warmup):
         p.psps_step(st, 1, history=False)
@@ -211,7 +225,7 @@ def ours(args, prob):
 
     # end to end through the public API with host buffers: every step uploads
     # the measured counts from pinned memory and reads back the objective.
-    st2 = p.State(plan, spec, pc, yd, prob.beta, line_search=True, graph=True)
+    st2 = p.State(plan, spec, pc, yd, beta, line_search=True, graph=True)
     p.psps_step(st2, 1, history=True)
     y_stage = torch.empty_like(yd)
     torch.cuda.synchronize()
@@ -223,17 +237,19 @@ def ours(args, prob):
     e2e_s = time.perf_counter() - t0
 
     # roofline of the dominant stage
-    n_pix, n_rays = plan.n_pix, plan.n_rays
+    n_rays = int(prob.n_rays)
+    n_pix = plan.n_pix if plan is not None else n_rays
     stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
     dom = max(stage_ms, key=stage_ms.get)
+    nm, nc = prob.Q.shape[1], prob.S.shape[0]
     alg_bytes = {
-        "backproject": 2 * 4 * (n_rays + n_pix),   # 2 channels: sinograms in, images out
-        "project": 4 * (n_rays + n_pix),
-        "model": 4 * (2 * n_rays + 2 * n_rays + n_rays),   # l, gamma, y in; g, kappa out
-        "linesearch": 4 * 3 * n_rays * 8,                   # l, q, y per evaluation (3 + 8 halvings max)
-        "precond": 4 * n_pix * 16,
-        "update": 4 * 2 * (n_pix + n_rays) * 2,
-        "reproject": 4 * (n_rays + n_pix),
+        "backproject": 2 * nm * 4 * (n_rays + n_pix),     # 2 n_mat channels: sinograms in, images out
+        "project": nm * 4 * (n_rays + n_pix),
+        "model": 4 * n_rays * (nm + nc + nm + 2 * nm),     # l, y, gamma in; g, kappa out
+        "linesearch": 4 * n_rays * (2 * nm + nc) * 4,      # l, q, y per evaluation, 3 Newton + 1 halving pass
+        "precond": 4 * n_pix * nm * 16,
+        "update": 4 * 2 * nm * (n_pix + n_rays),
+        "reproject": nm * 4 * (n_rays + n_pix),
     }[dom]
     hbm, src = peaks()
     achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9 if stage_ms[dom] > 0 else 0.0
@@ -244,19 +260,19 @@ def ours(args, prob):
     line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "image": "512x512@0.5mm", "sinogram": "720x888 fan curved",
-                       "precond": "haar(M0, lattice 3)", "line_search": True, "graph": True,
+            "config": {"workload": workload, "problem": desc or WORKLOADS[workload][2], "precond": kind,
+                       "line_search": True, "graph": True,
                        "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3)},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline,
             "e2e": {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": int(yd.numel() * 4),
                     "d2h_bytes_per_step": 16}}
     if rank == 0 and not args.no_gap:
         t0 = time.perf_counter()
-        phi_star, runs = gap_runs(p, plan, spec, yd, prob.beta, pc, args.gap_star, args.gap_iters)
+        phi_star, runs = gap_runs(p, plan, spec, yd, beta, pc, args.gap_star, args.gap_iters)
         # per-iteration times of each method from short timed runs
         per_iter = {}
-        for name, pcx, ls in [("psps_haar", pc, True), ("sps", None, False), ("sps_ls", None, True)]:
-            s = p.State(plan, spec, pcx, yd, prob.beta, line_search=ls, graph=True)
+        for name, pcx, ls in [("psps", pc, True), ("sps", None, False), ("sps_ls", None, True)]:
+            s = p.State(plan, spec, pcx, yd, beta, line_search=ls, graph=True)
             p.psps_step(s, 3, history=False)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -275,7 +291,7 @@ def ours(args, prob):
                          "gap_at_end": float(g[-1]), "iters_run": len(h) - 1}
         gap["wall_s"] = time.perf_counter() - t0
         line["time_to_gap"] = gap
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and workload == WORKLOAD:
         import oracle
         oracle.build_c()
         rate, dt = oracle_sample(prob, args.cpu_iters)
@@ -337,16 +353,20 @@ def main():
     ap.add_argument("--gap-star", type=int, default=1500)
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--kernels", action="store_true", help="time the projector variants alone")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     args = ap.parse_args()
     import synth
-    prob = synth.config2()
     if args.kernels:
-        kernel_bench(args, prob)
+        kernel_bench(args, synth.config2())
         return
     if args.impl == "reference":
-        reference_arm(args, prob)
-    else:
-        ours(args, prob)
+        reference_arm(args, synth.config2())
+        return
+    builder, kind, desc = WORKLOADS[args.workload]
+    prob = getattr(synth, builder)()
+    if args.workload != WORKLOAD:
+        args.no_cpu = True
+    ours(args, prob, args.workload, kind, desc)
 
 
 if __name__ == "__main__":

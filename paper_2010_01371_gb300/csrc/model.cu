@@ -163,11 +163,11 @@ __global__ void __launch_bounds__(kModelThreads)
     block_sum_store<4>(v, partials);
 }
 
-template <int NM>
+template <int NM, int MODE>
 __global__ void __launch_bounds__(kModelThreads)
     ls_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
-                    const float *__restrict__ y, DevLS *ls, LsCfg cfg, int mode, int last,
-                    double *__restrict__ partials) {
+                    const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, double *__restrict__ partials) {
+    constexpr int mode = MODE;
     if (mode == 1 && ls->done) return;  // same value for every block
     extern __shared__ float sh[];
     load_spec(sp, sh);
@@ -175,10 +175,11 @@ __global__ void __launch_bounds__(kModelThreads)
     const float *S = sh + sp.ne * NM;
     const int nc = sp.nc, ne = sp.ne;
     const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
-    double acc[2 * kMaxHalve];
+    constexpr int NACC = MODE == 0 ? 4 : 2 * kMaxHalve;
+    double acc[NACC];
 #pragma unroll
-    for (int k = 0; k < 2 * kMaxHalve; ++k) acc[k] = 0.0;
-    if (mode == 0) {
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+    if constexpr (MODE == 0) {
         const float alpha = (float)ls->alpha;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
              i += (int64_t)gridDim.x * blockDim.x) {
@@ -222,8 +223,7 @@ __global__ void __launch_bounds__(kModelThreads)
             acc[2] += (double)f2;
             if (!(zlo >= cfg.z_min)) acc[3] += 1.0;
         }
-        double v[4] = {acc[0], acc[1], acc[2], acc[3]};
-        block_sum_store<4>(v, partials);
+        block_sum_store<4>(acc, partials);
     } else {
         const double a0 = ls->best_a;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
@@ -259,11 +259,11 @@ __global__ void __launch_bounds__(kModelThreads)
                 if (!(zlo >= cfg.z_min)) acc[kMaxHalve + k] += 1.0;
             }
         }
-        block_sum_store<2 * kMaxHalve>(acc, partials);
+        block_sum_store<NACC>(acc, partials);
     }
     if (!last_block_arrive(&ls->ticket)) return;
     const int nb = gridDim.x;
-    if (mode == 0) {
+    if constexpr (MODE == 0) {
         const double fd = block_sum_all(partials, nb), f1d = block_sum_all(partials + nb, nb);
         const double f2d = block_sum_all(partials + 2 * nb, nb), bad = block_sum_all(partials + 3 * nb, nb);
         if (threadIdx.x == 0) {
@@ -394,14 +394,23 @@ mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const flo
     return MBIR_OK;
 }
 
+template <int NM>
+void ls_fused_launch(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls, LsCfg cfg,
+                     int mode, int last, double *partials, int nblocks, size_t smem, cudaStream_t s) {
+    if (mode == 0)
+        ls_fused_kernel<NM, 0><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
+    else
+        ls_fused_kernel<NM, 1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
+}
+
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
                             LsCfg cfg, int mode, int last, double *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     switch (sp.nm) {
-        case 1: ls_fused_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
-        case 2: ls_fused_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
-        case 3: ls_fused_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
-        case 4: ls_fused_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials); break;
+        case 1: ls_fused_launch<1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 2: ls_fused_launch<2>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 3: ls_fused_launch<3>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 4: ls_fused_launch<4>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
         default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
     }
     PSPS_LAUNCH_CHECK();
