@@ -335,7 +335,7 @@ def kernel_bench(args, prob):
     for mode in ["tile", "ray"]:
         plan.set_projector(mode)
         out[f"project_{mode}_1ch_ms"] = timeit(lambda: p.mbir_project(plan, x1, l1))
-    for mode in ["tile", "gather", "atomic"]:
+    for mode in ["tile", "tilewarp", "gather", "atomic"]:
         plan.set_backprojector(mode)
         out[f"backproject_{mode}_2ch_ms"] = timeit(lambda: p.mbir_backproject(plan, s2, g2))
     print(json.dumps({"kernels": out, "workload": WORKLOAD}), flush=True)

@@ -102,11 +102,12 @@ mbir_status mbir_project(mbir_plan *plan, const float *x, float *l, int n_mat, m
 mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_mat, int accumulate,
                              mbir_stream stream);
 
-/* Select the transpose's algorithm: 0 = tile scatter through shared memory
- * (default), 1 = pixel-driven gather (deterministic: no atomics, bitwise
- * reproducible), 2 = ray-driven scatter with global FP32 atomics.  All use the
- * forward projector's per-ray weights and are the exact transpose of
- * mbir_project up to FP32 rounding. */
+/* Select the transpose's algorithm (2-D): 0 = tile scatter through shared
+ * memory, one thread per ray (default), 1 = pixel-driven gather
+ * (deterministic: no atomics, bitwise reproducible), 2 = ray-driven scatter
+ * with global FP32 atomics, 3 = tile scatter with one warp per ray (lane =
+ * driving index).  All use the forward projector's per-ray weights and are the
+ * exact transpose of mbir_project up to FP32 rounding. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 /* Select the forward projector's algorithm: 0 = per-tile partial sums through
  * shared memory, combined with one FP32 atomic per (tile, ray); 1 = one thread

@@ -583,6 +583,68 @@ __global__ void __launch_bounds__(kThreads, 6)
     }
 }
 
+// Warp-per-ray variant of the tile transpose: the warps of a CTA stride over
+// the (view, bin) items and the 32 lanes take the 32 driving indices of the
+// tile, so a ray costs one pass of the warp with no loop and no divergence;
+// lanes whose sample misses the tile rows add nothing.
+template <int NC>
+__global__ void __launch_bounds__(kThreads, 6)
+    back_tile_warp_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
+                             const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x) {
+    static_assert(kBT == 32, "one lane per driving index of the tile");
+    __shared__ float acc[NC][kBT][kBT + 1];
+    __shared__ TileItems ti;
+    const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
+    if (threadIdx.x == 0) {
+        ti.v_begin = blockIdx.z * kBVsplit;
+        ti.nv = min(g.n_views - ti.v_begin, kBVsplit);
+    }
+    for (int k = threadIdx.x; k < NC * kBT * (kBT + 1); k += blockDim.x) (&acc[0][0][0])[k] = 0.f;
+    __syncthreads();
+    tile_items(ti, vt, g, c0, r0);
+    const int total = ti.prefix[ti.nv];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int k = 0;
+    for (int item = warp; item < total; item += nwarps) {
+        while (item >= ti.prefix[k + 1]) ++k;
+        const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
+        const float4 r = __ldg(tab + ray);
+        const int bits = __float_as_int(r.w);
+        const int axis = bits & 1;
+        const int lo = (bits >> 1) & 0x7fff, hi = (bits >> 16) & 0x7fff;
+        const int d0 = axis == 0 ? c0 : r0, o0 = axis == 0 ? r0 : c0;
+        const int i = d0 + lane;
+        if (i < lo || i > hi) continue;
+        const float fy = fmaf((float)i, r.y, r.x);
+        const float fl = floorf(fy);
+        const int j0 = (int)fl - o0;
+        if (j0 < -1 || j0 >= kBT) continue;
+        const float f = fy - fl;
+        float ws[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ws[c] = r.z * __ldg(sino + (int64_t)c * n_rays + ray);
+        if (j0 >= 0) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                red_shared_add(axis == 0 ? &acc[c][j0][lane] : &acc[c][lane][j0], (1.f - f) * ws[c]);
+        }
+        if (j0 + 1 < kBT) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                red_shared_add(axis == 0 ? &acc[c][j0 + 1][lane] : &acc[c][lane][j0 + 1], f * ws[c]);
+        }
+    }
+    __syncthreads();
+    const int64_t npix = (int64_t)g.nx * g.ny;
+    for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+        const int rr = q / kBT, cc = q % kBT;
+        const int iy = r0 + rr, ix = c0 + cc;
+        if (iy >= g.ny || ix >= g.nx) continue;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, acc[c][rr][cc]);
+    }
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kThreads, 8)
     fwd_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
@@ -720,19 +782,26 @@ mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, in
         PSPS_LAUNCH_CHECK();
         return MBIR_OK;
     }
-    if (p->back_mode == 0) {
+    if (p->back_mode == 0 || p->back_mode == 3) {
         if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
         const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT),
                        (unsigned)cdiv(p->g.n_views, kBVsplit));
+        const bool warp = p->back_mode == 3;
         for (int m0 = 0; m0 < n_mat;) {
             const int left = n_mat - m0;
             const float *sm = sino + (int64_t)m0 * p->n_rays;
             float *xm = x + (int64_t)m0 * p->n_pix;
             if (left >= 2) {
-                back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                if (warp)
+                    back_tile_warp_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                else
+                    back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
                 m0 += 2;
             } else {
-                back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                if (warp)
+                    back_tile_warp_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                else
+                    back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
                 m0 += 1;
             }
             PSPS_LAUNCH_CHECK();
@@ -844,7 +913,7 @@ extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *
 }
 
 extern "C" mbir_status mbir_plan_set_backprojector(mbir_plan *p, int mode) {
-    if (!p || mode < 0 || mode > 2) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
+    if (!p || mode < 0 || mode > 3) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
     p->back_mode = mode;
     return MBIR_OK;
 }

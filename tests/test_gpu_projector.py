@@ -32,7 +32,7 @@ def test_project_parity(psps, oracle_lib, name, nm, mode):
 
 
 @pytest.mark.parametrize("name", list(small_geoms()))
-@pytest.mark.parametrize("mode", ["tile", "gather", "atomic"])
+@pytest.mark.parametrize("mode", ["tile", "tilewarp", "gather", "atomic"])
 def test_backproject_parity(psps, oracle_lib, name, mode):
     g = small_geoms()[name]
     rng = np.random.default_rng(2)
@@ -60,7 +60,7 @@ def test_material_packing(psps, oracle_lib, nm, mode):
 
 
 @pytest.mark.parametrize("nch", [1, 2, 3, 4, 5])
-@pytest.mark.parametrize("mode", ["tile", "gather"])
+@pytest.mark.parametrize("mode", ["tile", "tilewarp", "gather"])
 def test_transpose_channels(psps, oracle_lib, nch, mode):
     """The transposes handle 1..5 channels (groups of 4 / 2 / 1)."""
     for name in ["par2d_ragged", "fan2d_ragged"]:
@@ -76,11 +76,12 @@ def test_transposes_agree(psps):
     g = synth.config2().geom
     s = to_dev(np.random.default_rng(8).random((2, g.n_rays)))
     out = {}
-    for mode in ["tile", "gather", "atomic"]:
+    for mode in ["tile", "tilewarp", "gather", "atomic"]:
         p = psps.Plan(g)
         p.set_backprojector(mode)
         out[mode] = to_host(psps.mbir_backproject(p, s))
     assert rel_l2(out["tile"], out["gather"]) < 1e-6
+    assert rel_l2(out["tilewarp"], out["gather"]) < 1e-6
     assert rel_l2(out["atomic"], out["gather"]) < 1e-6
     # the gather is deterministic: bitwise equal on a second run
     p = psps.Plan(g)
