@@ -335,9 +335,15 @@ def kernel_bench(args, prob):
     for mode in ["tile", "ray"]:
         plan.set_projector(mode)
         out[f"project_{mode}_1ch_ms"] = timeit(lambda: p.mbir_project(plan, x1, l1))
-    for mode in ["tile", "tilewarp", "gather", "atomic"]:
+    for mode in ["tile", "gather", "atomic"]:
         plan.set_backprojector(mode)
         out[f"backproject_{mode}_2ch_ms"] = timeit(lambda: p.mbir_backproject(plan, s2, g2))
+    plan.set_backprojector("tile")
+    for vs in [30, 45, 60, 90, 120, 180]:
+        plan.set_tiling(vs)
+        out[f"backproject_tile{vs}_2ch_ms"] = timeit(lambda: p.mbir_backproject(plan, s2, g2))
+        out[f"backproject_tile{vs}_1ch_ms"] = timeit(lambda: p.mbir_backproject(plan, s2[:1], g2[:1]))
+    plan.set_tiling(60)
     print(json.dumps({"kernels": out, "workload": WORKLOAD}), flush=True)
 
 

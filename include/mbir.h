@@ -103,12 +103,17 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
                              mbir_stream stream);
 
 /* Select the transpose's algorithm (2-D): 0 = tile scatter through shared
- * memory, one thread per ray (default), 1 = pixel-driven gather
- * (deterministic: no atomics, bitwise reproducible), 2 = ray-driven scatter
- * with global FP32 atomics, 3 = tile scatter with one warp per ray (lane =
- * driving index).  All use the forward projector's per-ray weights and are the
- * exact transpose of mbir_project up to FP32 rounding. */
+ * memory (default; lanes of a warp on consecutive driving indices of one ray),
+ * 1 = pixel-driven gather (deterministic: no atomics, bitwise reproducible),
+ * 2 = ray-driven scatter with global FP32 atomics.  All use the forward
+ * projector's per-ray weights and are the exact transpose of mbir_project up
+ * to FP32 rounding.  MBIR_ERR_ARG for another mode. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
+/* Views handled by one CTA of the tile transpose (mode 0), 1..180: the
+ * grid is (image tiles) x ceil(n_views / views_per_cta) CTAs.  Only changes
+ * the work split (and the FP32 summation order), not the result's definition.
+ * MBIR_ERR_ARG outside 1..180. */
+mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
 /* Select the forward projector's algorithm: 0 = per-tile partial sums through
  * shared memory, combined with one FP32 atomic per (tile, ray); 1 = one thread
  * per ray with Kahan-compensated sums (default; deterministic, and faster on

@@ -78,10 +78,13 @@ class Plan:
         self.sino_shape = tuple(geom.sino_shape)
 
     def set_backprojector(self, mode: str):
-        """'tile' (default), 'gather' (deterministic), 'atomic' (ray-driven
-        scatter with global atomics) or 'tilewarp' (tile scatter, one warp per
-        ray)."""
-        _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2, "tilewarp": 3}[mode])
+        """'tile' (default), 'gather' (deterministic) or 'atomic' (ray-driven
+        scatter with global atomics)."""
+        _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2}[mode])
+
+    def set_tiling(self, views_per_cta: int):
+        """Views per CTA of the 'tile' transpose (1..180)."""
+        _call(lib().mbir_plan_set_tiling, self.h, int(views_per_cta))
 
     def set_projector(self, mode: str):
         """'ray' (default: one thread per ray, deterministic) or 'tile'."""

@@ -35,6 +35,7 @@ SIGNATURES = [
     ("mbir_plan_n_rays", c_int64, [c_void_p]),
     ("mbir_plan_n_pix", c_int64, [c_void_p]),
     ("mbir_plan_set_backprojector", c_int, [c_void_p, c_int]),
+    ("mbir_plan_set_tiling", c_int, [c_void_p, c_int]),
     ("mbir_plan_set_projector", c_int, [c_void_p, c_int]),
     ("mbir_project", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("mbir_backproject", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),

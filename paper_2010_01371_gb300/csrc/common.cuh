@@ -117,6 +117,7 @@ struct mbir_plan {
     // 2-D per-view constants for the pixel-driven transpose
     psps::DBuf<float4> view;      // parallel: (cos, sin, -, -); fan: (sx, sy, beta + pi, -)
     int back_mode = 0;            // 0 tile scatter (default), 1 pixel gather, 2 ray-driven atomics
+    int back_views = 60;          // views per CTA of the tile transpose
     int fwd_mode = 1;             // 0 tile sums, 1 one thread per ray (default)
     // 3-D per-view set-up (source, detector origin and axes) in FP64
     psps::DBuf<double> view3d;

@@ -522,117 +522,135 @@ __device__ __forceinline__ void tile_ray_range(const float4 &r, int c0, int r0, 
     }
 }
 
-// Shared-memory reduction without a return value (red.shared.add.f32).
-__device__ __forceinline__ void red_shared_add(float *addr, float v) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+// tile_ray_range with one approximate reciprocal instead of two divisions:
+// the range only has to contain every driving index whose sample reaches the
+// tile, and the one-index margins on both sides absorb the few-ulp error of
+// the approximate reciprocal wherever the bound falls inside the tile.
+__device__ __forceinline__ void tile_ray_range_approx(const float4 &r, int c0, int r0, int &axis, int &d0, int &o0,
+                                                      int &ia, int &ib) {
+    const int bits = __float_as_int(r.w);
+    axis = bits & 1;
+    const int lo = (bits >> 1) & 0x7fff, hi = (bits >> 16) & 0x7fff;
+    d0 = axis == 0 ? c0 : r0;
+    o0 = axis == 0 ? r0 : c0;
+    ia = max(lo, d0);
+    ib = min(hi, d0 + kBT - 1);
+    if (r.y != 0.f) {
+        const float inv = __fdividef(1.f, r.y);
+        float ta = ((float)o0 - 1.f - r.x) * inv, tb = ((float)(o0 + kBT) - r.x) * inv;
+        const float t0 = fminf(ta, tb), t1 = fmaxf(ta, tb);
+        ia = max(ia, (int)floorf(fminf(fmaxf(t0, -1.0e8f), 1.0e8f)) - 1);
+        ib = min(ib, (int)ceilf(fminf(fmaxf(t1, -1.0e8f), 1.0e8f)) + 1);
+    }
 }
 
+
+// Tile transpose, lanes on driving indices.  Each warp takes 32 (view, bin)
+// items at a time, keeps those whose ray crosses the tile (ballot +
+// compaction into a per-warp staging area, x-driven rays from the front,
+// y-driven rays from the back), then walks the kept rays one by one with lane
+// l on driving index d0 + l.  The accumulators of both driving axes are
+// stored with the driving index fastest ([axis][c][interpolated row -1..kBT]
+// [driving index]), so the 32 lanes of one red.shared always hit 32 distinct
+// banks whatever the ray's slope; rows -1 and kBT are padding for samples
+// that straddle the tile edge (their other half belongs to the neighbouring
+// tile, which handles the same sample).
+//
+// No per-lane range test is needed besides the row test: driving indices
+// outside the ray's [lo, hi] only give samples whose interpolation pixels are
+// both off the grid (the range is widened by one index on each side), and
+// those, like lanes past the grid's edge, land in rows or columns that the
+// epilogue drops.
+//
+// The interpolation index is split without conversion instructions: with
+// h = fy - 1/2 and |h| < 2^22, h + 1.5 * 2^23 rounds to the integer nearest h,
+// which is floor(fy) except for integer fy, where it may give floor(fy) - 1
+// with fraction 1 — the same two weights on the same pixel, because the
+// linear interpolation is continuous there.
+__device__ __forceinline__ void red_shared_pair(unsigned addr, float lo, float hi) {
+    asm volatile(
+        "red.shared.add.f32 [%0], %1;\n\t"
+        "red.shared.add.f32 [%0+128], %2;" ::"r"(addr),
+        "f"(lo), "f"(hi)
+        : "memory");
+}
+
+// Kept rays [j0, j1) of one driving axis: fi = this lane's driving index,
+// rowbase = bits of (1.5 * 2^23 + first interpolated index - 1), addr = byte
+// address of this lane's column in the axis' first accumulator plane.
 template <int NC>
-__global__ void __launch_bounds__(kThreads, 6)
-    back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
-                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x) {
-    __shared__ float acc[NC][kBT][kBT + 1];
-    __shared__ TileItems ti;
-    const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
-    if (threadIdx.x == 0) {
-        ti.v_begin = blockIdx.z * kBVsplit;
-        ti.nv = min(g.n_views - ti.v_begin, kBVsplit);
-    }
-    for (int k = threadIdx.x; k < NC * kBT * (kBT + 1); k += blockDim.x) (&acc[0][0][0])[k] = 0.f;
-    __syncthreads();
-    tile_items(ti, vt, g, c0, r0);
-    const int total = ti.prefix[ti.nv];
-    int k = 0;
-    for (int item = threadIdx.x; item < total; item += blockDim.x) {
-        while (item >= ti.prefix[k + 1]) ++k;
-        const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
-        const float4 r = __ldg(tab + ray);
-        int axis, d0, o0, ia, ib;
-        tile_ray_range(r, c0, r0, axis, d0, o0, ia, ib);
-        if (ia > ib) continue;
-        float ws[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ws[c] = r.z * __ldg(sino + (int64_t)c * n_rays + ray);
-        for (int i = ia; i <= ib; ++i) {
-            const float fy = fmaf((float)i, r.y, r.x);
-            const float fl = floorf(fy);
-            const int j0 = (int)fl - o0;
-            const float f = fy - fl;
-            const int li = i - d0;
-            if (j0 >= 0 && j0 < kBT) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    red_shared_add(axis == 0 ? &acc[c][j0][li] : &acc[c][li][j0], (1.f - f) * ws[c]);
-            }
-            if (j0 + 1 >= 0 && j0 + 1 < kBT) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    red_shared_add(axis == 0 ? &acc[c][j0 + 1][li] : &acc[c][li][j0 + 1], f * ws[c]);
+__device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, int j0, int j1, float fi, int rowbase,
+                                               unsigned addr) {
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr unsigned kPlaneBytes = 4u * (kBT + 2) * kBT;
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+        const float4 a = ws[j];                      // f0 - 1/2, df, w * sino[0], w * sino[1]
+        const float h = fmaf(fi, a.y, a.x);          // fy - 1/2
+        const float rn = h + kMagic;                 // nearest integer to h, in the low mantissa bits
+        const int jr = __float_as_int(rn) - rowbase; // interpolated index - (first index - 1)
+        if ((unsigned)jr <= (unsigned)kBT) {
+            const float f = (h - (rn - kMagic)) + 0.5f;  // weight of the upper pixel
+            const unsigned q = addr + (unsigned)jr * (4u * kBT);
+            const float u0 = f * a.z;
+            red_shared_pair(q, a.z - u0, u0);
+            if (NC == 2) {
+                const float u1 = f * a.w;
+                red_shared_pair(q + kPlaneBytes, a.w - u1, u1);
             }
         }
     }
-    __syncthreads();
-    const int64_t npix = (int64_t)g.nx * g.ny;
-    for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
-        const int rr = q / kBT, cc = q % kBT;
-        const int iy = r0 + rr, ix = c0 + cc;
-        if (iy >= g.ny || ix >= g.nx) continue;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, acc[c][rr][cc]);
-    }
 }
 
-// Warp-per-ray variant of the tile transpose: the warps of a CTA stride over
-// the (view, bin) items and the 32 lanes take the 32 driving indices of the
-// tile, so a ray costs one pass of the warp with no loop and no divergence;
-// lanes whose sample misses the tile rows add nothing.
 template <int NC>
-__global__ void __launch_bounds__(kThreads, 6)
-    back_tile_warp_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
-                             const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x) {
+__global__ void __launch_bounds__(kThreads, 5)
+    back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
+                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x, int vs) {
     static_assert(kBT == 32, "one lane per driving index of the tile");
-    __shared__ float acc[NC][kBT][kBT + 1];
+    static_assert(NC == 1 || NC == 2, "one or two channels");
+    constexpr int kRows = kBT + 2;
+    constexpr int kPlane = kRows * kBT;
+    __shared__ float acc[2 * NC * kPlane];
     __shared__ TileItems ti;
+    __shared__ float4 stage[kThreads];
     const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
     if (threadIdx.x == 0) {
-        ti.v_begin = blockIdx.z * kBVsplit;
-        ti.nv = min(g.n_views - ti.v_begin, kBVsplit);
+        ti.v_begin = blockIdx.z * vs;
+        ti.nv = min(g.n_views - ti.v_begin, vs);
     }
-    for (int k = threadIdx.x; k < NC * kBT * (kBT + 1); k += blockDim.x) (&acc[0][0][0])[k] = 0.f;
+    for (int k = threadIdx.x; k < 2 * NC * kPlane; k += blockDim.x) acc[k] = 0.f;
     __syncthreads();
     tile_items(ti, vt, g, c0, r0);
     const int total = ti.prefix[ti.nv];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const int magic_bits = __float_as_int(12582912.0f);
+    const unsigned col = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
+    float4 *ws = stage + warp * 32;
     int k = 0;
-    for (int item = warp; item < total; item += nwarps) {
-        while (item >= ti.prefix[k + 1]) ++k;
-        const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
-        const float4 r = __ldg(tab + ray);
-        const int bits = __float_as_int(r.w);
-        const int axis = bits & 1;
-        const int lo = (bits >> 1) & 0x7fff, hi = (bits >> 16) & 0x7fff;
-        const int d0 = axis == 0 ? c0 : r0, o0 = axis == 0 ? r0 : c0;
-        const int i = d0 + lane;
-        if (i < lo || i > hi) continue;
-        const float fy = fmaf((float)i, r.y, r.x);
-        const float fl = floorf(fy);
-        const int j0 = (int)fl - o0;
-        if (j0 < -1 || j0 >= kBT) continue;
-        const float f = fy - fl;
-        float ws[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ws[c] = r.z * __ldg(sino + (int64_t)c * n_rays + ray);
-        if (j0 >= 0) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                red_shared_add(axis == 0 ? &acc[c][j0][lane] : &acc[c][lane][j0], (1.f - f) * ws[c]);
+    for (int base = warp * 32; base < total; base += nwarps * 32) {
+        const int item = base + lane;
+        bool keep = false;
+        int axis = 0;
+        float4 lr;
+        if (item < total) {
+            while (item >= ti.prefix[k + 1]) ++k;
+            const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
+            const float4 r = __ldg(tab + ray);
+            const float s0 = __ldg(sino + ray), s1 = NC == 2 ? __ldg(sino + n_rays + ray) : 0.f;
+            int d0, o0, ia, ib;
+            tile_ray_range_approx(r, c0, r0, axis, d0, o0, ia, ib);
+            keep = ia <= ib;
+            lr = make_float4(r.x - 0.5f, r.y, r.z * s0, r.z * s1);
         }
-        if (j0 + 1 < kBT) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                red_shared_add(axis == 0 ? &acc[c][j0 + 1][lane] : &acc[c][lane][j0 + 1], f * ws[c]);
-        }
+        const unsigned kx = __ballot_sync(0xffffffffu, keep && axis == 0);
+        const unsigned ky = __ballot_sync(0xffffffffu, keep && axis == 1);
+        if (keep) ws[axis == 0 ? __popc(kx & below) : 31 - __popc(ky & below)] = lr;
+        __syncwarp();
+        tile_lane_pass<NC>(ws, 0, __popc(kx), (float)(c0 + lane), magic_bits + r0 - 1, col);
+        tile_lane_pass<NC>(ws, 32 - __popc(ky), 32, (float)(r0 + lane), magic_bits + c0 - 1,
+                           col + 4u * NC * kPlane);
+        __syncwarp();
     }
     __syncthreads();
     const int64_t npix = (int64_t)g.nx * g.ny;
@@ -641,7 +659,11 @@ __global__ void __launch_bounds__(kThreads, 6)
         const int iy = r0 + rr, ix = c0 + cc;
         if (iy >= g.ny || ix >= g.nx) continue;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, acc[c][rr][cc]);
+        for (int c = 0; c < NC; ++c) {
+            // x-driven rays: [row][column]; y-driven rays: [column][row]
+            const float v = acc[c * kPlane + (rr + 1) * kBT + cc] + acc[(NC + c) * kPlane + (cc + 1) * kBT + rr];
+            atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, v);
+        }
     }
 }
 
@@ -782,26 +804,19 @@ mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, in
         PSPS_LAUNCH_CHECK();
         return MBIR_OK;
     }
-    if (p->back_mode == 0 || p->back_mode == 3) {
+    if (p->back_mode == 0) {
         if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
-        const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT),
-                       (unsigned)cdiv(p->g.n_views, kBVsplit));
-        const bool warp = p->back_mode == 3;
+        const int vs = p->back_views;
+        const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT), (unsigned)cdiv(p->g.n_views, vs));
         for (int m0 = 0; m0 < n_mat;) {
             const int left = n_mat - m0;
             const float *sm = sino + (int64_t)m0 * p->n_rays;
             float *xm = x + (int64_t)m0 * p->n_pix;
             if (left >= 2) {
-                if (warp)
-                    back_tile_warp_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
-                else
-                    back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs);
                 m0 += 2;
             } else {
-                if (warp)
-                    back_tile_warp_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
-                else
-                    back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm);
+                back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs);
                 m0 += 1;
             }
             PSPS_LAUNCH_CHECK();
@@ -913,8 +928,15 @@ extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *
 }
 
 extern "C" mbir_status mbir_plan_set_backprojector(mbir_plan *p, int mode) {
-    if (!p || mode < 0 || mode > 3) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
+    if (!p || mode < 0 || mode > 2) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
     p->back_mode = mode;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbir_plan_set_tiling(mbir_plan *p, int views_per_cta) {
+    if (!p || views_per_cta < 1 || views_per_cta > kBVsplit)
+        return fail(MBIR_ERR_ARG, "mbir_plan_set_tiling: views_per_cta must be 1..%d", kBVsplit);
+    p->back_views = views_per_cta;
     return MBIR_OK;
 }
 
