@@ -1,4 +1,4 @@
-// Error reporting and the fixed-order FP64 reduction shared by all kernels.
+// Error reporting and the fixed-order reduction of partial sums.
 #include <cstdarg>
 #include <cstring>
 
@@ -22,25 +22,15 @@ mbir_status fail(mbir_status code, const char *fmt, ...) {
 
 namespace {
 // One block sums n partials of each of K streams in a fixed order.
-__global__ void reduce_partials_kernel(const double *__restrict__ partials, int n, int K, double *dst, int add) {
-    __shared__ double sh[32];
+__global__ void reduce_partials_kernel(const dfloat *__restrict__ partials, int n, int K, double *dst, int add) {
     for (int k = 0; k < K; ++k) {
-        double a = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a += partials[(size_t)k * n + i];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            a = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (threadIdx.x == 0) dst[k] = add ? dst[k] + a : a;
-        }
-        __syncthreads();
+        const double a = block_sum_partials(partials + (size_t)k * n, n);
+        if (threadIdx.x == 0) dst[k] = add ? dst[k] + a : a;
     }
 }
 }  // namespace
 
-mbir_status reduce_partials(const double *partials, int n, int K, double *dst, int add, cudaStream_t s) {
+mbir_status reduce_partials(const dfloat *partials, int n, int K, double *dst, int add, cudaStream_t s) {
     reduce_partials_kernel<<<1, 256, 0, s>>>(partials, n, K, dst, add);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;

@@ -67,18 +67,46 @@ struct DBuf {
 };
 
 // ------------------------------------------------------------- reductions
-// Block-level FP64 sum of up to 4 values per thread; thread 0 writes the
-// block's partial sums to out[k * gridDim.x + blockIdx.x].  blockDim.x must
-// be a multiple of 32 and <= 1024.
+// Sums over rays and pixels are accumulated as double-floats: an unevaluated
+// pair hi + lo of FP32 numbers updated with Knuth's TwoSum error-free
+// transformation, which carries about twice FP32's precision with FP32
+// additions only (FP64 arithmetic runs at a small fraction of the FP32 rate
+// on this GPU).  Only the final few sums are converted to double.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(dfloat &a, float v) {
+    const float s = a.hi + v;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (v - bp);  // exact rounding error of a.hi + v
+    a.hi = s;
+    a.lo += e;
+}
+
+__device__ __forceinline__ void df_merge(dfloat &a, const dfloat &b) {
+    df_add(a, b.hi);
+    a.lo += b.lo;
+}
+
+__host__ __device__ inline double df_value(const dfloat &a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dfloat df_shfl_down(const dfloat &a, int o) {
+    return dfloat{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// Block-level sum of K double-floats per thread (fixed order); thread 0
+// writes the block's partial sums to out[k * gridDim.x + blockIdx.x].
+// blockDim.x must be a multiple of 32 and <= 1024.
 template <int K>
-__device__ __forceinline__ void block_sum_store(double (&v)[K], double *out) {
-    __shared__ double sh[K][32];
+__device__ __forceinline__ void block_sum_store(dfloat (&v)[K], dfloat *out) {
+    __shared__ dfloat sh[K][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double a = v[k];
+        dfloat a = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        for (int o = 16; o > 0; o >>= 1) df_merge(a, df_shfl_down(a, o));
         if (lane == 0) sh[k][wid] = a;
     }
     __syncthreads();
@@ -86,16 +114,40 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double *out) {
         const int nw = blockDim.x >> 5;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double a = lane < nw ? sh[k][lane] : 0.0;
+            dfloat a = lane < nw ? sh[k][lane] : dfloat{0.f, 0.f};
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            for (int o = 16; o > 0; o >>= 1) df_merge(a, df_shfl_down(a, o));
             if (lane == 0) out[(size_t)k * gridDim.x + blockIdx.x] = a;
         }
     }
 }
 
+// Fixed-order sum of n double-float partials by one whole block (ld.cg: the
+// partials may come from other blocks of the same kernel); the result is
+// valid in thread 0.
+__device__ inline double block_sum_partials(const dfloat *p, int n) {
+    __shared__ dfloat sh[32];
+    dfloat a{0.f, 0.f};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 v = __ldcg(reinterpret_cast<const float2 *>(p + i));
+        df_merge(a, dfloat{v.x, v.y});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) df_merge(a, df_shfl_down(a, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        dfloat t{0.f, 0.f};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_merge(t, sh[w]);
+        r = df_value(t);
+    }
+    __syncthreads();
+    return r;
+}
+
 // Sum `n` partials (fixed order, one block) into dst[0..K) (dst += if add).
-mbir_status reduce_partials(const double *partials, int n, int K, double *dst, int add, cudaStream_t s);
+mbir_status reduce_partials(const dfloat *partials, int n, int K, double *dst, int add, cudaStream_t s);
 
 // ------------------------------------------------------------ handles
 struct RayTable2D {
@@ -124,9 +176,6 @@ struct mbir_plan {
     // scratch: packed / transposed image copies for the forward projector
     // (3-D: one copy per driving axis)
     psps::DBuf<float> xrow, xcol, xcol3;
-    // scratch for reductions
-    psps::DBuf<double> partials;
-    int partials_cap = 0;
 };
 
 struct mbmd_spectrum {

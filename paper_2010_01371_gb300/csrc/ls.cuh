@@ -22,22 +22,6 @@ struct LsCfg {
 
 constexpr int kMaxHalve = 8;
 
-// Fixed-order block-wide sum of n doubles written by other blocks of the same
-// kernel (read past L1); the result is valid in thread 0.
-__device__ inline double block_sum_all(const double *p, int n) {
-    __shared__ double sh[32];
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a += __ldcg(p + i);
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
-    __syncthreads();
-    return r;
-}
-
 // Last-block arrival: thread 0 of every block makes its partial sums visible
 // and takes a ticket; the block that draws the last ticket gets true (no
 // waiting anywhere).

@@ -5,7 +5,7 @@
 // Per ray i with material line integrals l_m:
 //   z_E = sum_m Q[E][m] l_m,  t_E = exp(-z_E),  y_bar_c = sum_E S[c][E] t_E
 //   r_c = y_bar_c - y_c,  w_c = 1/max(y_c, 1)
-//   data term        1/2 sum_c w_c r_c^2                       (FP64 reduce)
+//   data term        1/2 sum_c w_c r_c^2                       (double-float sum)
 //   gradient num.    g_m = -sum_E Q[E][m] t_E v_E,  v_E = sum_c S[c][E] w_c r_c
 //   curvature        eta_E = sum_c S[c][E] w_c sigma_c (sigma_c = sum_E S[c][E]),
 //                    rho_E = v_E - eta_E t_E   (Eq. 10 with the current t where
@@ -13,8 +13,8 @@
 //                    c_E = max(0, 2 eta_E u^2 + rho_E u): the largest second
 //                    derivative of 1/2 eta e^{-2z} + rho e^{-z} on z >= min(0, z^n)
 //   curvature num.   kappa_m = sum_E Q[E][m] gamma_E c_E,  gamma_E = sum_m Q[E][m] gamma_m
-// Exponentials and sums run in FP32 (expf, correctly-rounded-ish library
-// call); the objective and line-search sums are reduced in FP64.
+// Exponentials and per-ray sums run in FP32 (expf); the objective and
+// line-search sums over rays are double-float reductions.
 #include <cmath>
 #include <vector>
 
@@ -35,14 +35,14 @@ template <int NM>
 __global__ void __launch_bounds__(kModelThreads)
     model_grad_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
                       const float *__restrict__ gamma, float *__restrict__ g, float *__restrict__ kappa,
-                      double *__restrict__ partials) {
+                      dfloat *__restrict__ partials) {
     extern __shared__ float sh[];
     load_spec(sp, sh);
     const float *Q = sh;
     const float *S = sh + sp.ne * NM;
     const float *sig = S + sp.nc * sp.ne;
     const int nc = sp.nc, ne = sp.ne;
-    double obj = 0.0;
+    dfloat obj{0.f, 0.f};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
         float lm[NM];
 #pragma unroll
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kModelThreads)
             const float w = 1.f / fmaxf(yc, 1.f);
             const float r = yb[c] - yc;
             wr[c] = w * r;
-            obj += (double)(0.5f * wr[c] * r);
+            df_add(obj, 0.5f * wr[c] * r);
             ws[c] = w * sig[c];
         }
         if (g || kappa) {
@@ -105,68 +105,14 @@ __global__ void __launch_bounds__(kModelThreads)
             }
         }
     }
-    double v[1] = {obj};
+    dfloat v[1] = {obj};
     block_sum_store<1>(v, partials);
-}
-
-template <int NM>
-__global__ void __launch_bounds__(kModelThreads)
-    ls_eval_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
-                   const float *__restrict__ y, const double *alpha_p, const int *skip, float z_min,
-                   double *__restrict__ partials) {
-    if (skip && *skip) return;
-    extern __shared__ float sh[];
-    load_spec(sp, sh);
-    const float *Q = sh;
-    const float *S = sh + sp.ne * NM;
-    const int nc = sp.nc, ne = sp.ne;
-    const float alpha = (float)*alpha_p;
-    double f = 0.0, f1 = 0.0, f2 = 0.0, bad = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
-        float la[NM], qm[NM];
-        float zlo = 3.0e38f;
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            qm[m] = q[(int64_t)m * n_rays + i];
-            la[m] = fmaf(alpha, qm[m], l[(int64_t)m * n_rays + i]);
-        }
-        float yb[kMaxC], d1[kMaxC], d2[kMaxC];
-        for (int c = 0; c < nc; ++c) yb[c] = d1[c] = d2[c] = 0.f;
-        for (int e = 0; e < ne; ++e) {
-            float z = 0.f, dz = 0.f;
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                z = fmaf(Q[e * NM + m], la[m], z);
-                dz = fmaf(Q[e * NM + m], qm[m], dz);
-            }
-            zlo = fminf(zlo, z);
-            const float t = expf(-z);
-            const float tdz = t * dz;
-            for (int c = 0; c < nc; ++c) {
-                const float s = S[c * ne + e];
-                yb[c] = fmaf(s, t, yb[c]);
-                d1[c] = fmaf(-s, tdz, d1[c]);
-                d2[c] = fmaf(s, tdz * dz, d2[c]);
-            }
-        }
-        for (int c = 0; c < nc; ++c) {
-            const float yc = y[(int64_t)c * n_rays + i];
-            const double w = 1.0 / fmax((double)yc, 1.0);
-            const double r = (double)yb[c] - (double)yc;
-            f += 0.5 * w * r * r;
-            f1 += w * r * d1[c];
-            f2 += w * ((double)d1[c] * d1[c] + r * d2[c]);
-        }
-        if (!(zlo >= z_min)) bad += 1.0;
-    }
-    double v[4] = {f, f1, f2, bad};
-    block_sum_store<4>(v, partials);
 }
 
 template <int NM, int MODE>
 __global__ void __launch_bounds__(kModelThreads)
     ls_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
-                    const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, double *__restrict__ partials) {
+                    const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
     constexpr int mode = MODE;
     if (mode == 1 && ls->done) return;  // same value for every block
     extern __shared__ float sh[];
@@ -176,9 +122,9 @@ __global__ void __launch_bounds__(kModelThreads)
     const int nc = sp.nc, ne = sp.ne;
     const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
     constexpr int NACC = MODE == 0 ? 4 : 2 * kMaxHalve;
-    double acc[NACC];
+    dfloat acc[NACC];
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NACC; ++k) acc[k] = dfloat{0.f, 0.f};
     if constexpr (MODE == 0) {
         const float alpha = (float)ls->alpha;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
@@ -218,10 +164,10 @@ __global__ void __launch_bounds__(kModelThreads)
                 f1 = fmaf(w * r, d1[c], f1);
                 f2 = fmaf(w, fmaf(d1[c], d1[c], r * d2[c]), f2);
             }
-            acc[0] += (double)f;
-            acc[1] += (double)f1;
-            acc[2] += (double)f2;
-            if (!(zlo >= cfg.z_min)) acc[3] += 1.0;
+            df_add(acc[0], f);
+            df_add(acc[1], f1);
+            df_add(acc[2], f2);
+            if (!(zlo >= cfg.z_min)) df_add(acc[3], 1.f);
         }
         block_sum_store<4>(acc, partials);
     } else {
@@ -255,8 +201,8 @@ __global__ void __launch_bounds__(kModelThreads)
                     const float r = yb[c] - yc;
                     f = fmaf(0.5f * r / fmaxf(yc, 1.f), r, f);
                 }
-                acc[k] += (double)f;
-                if (!(zlo >= cfg.z_min)) acc[kMaxHalve + k] += 1.0;
+                df_add(acc[k], f);
+                if (!(zlo >= cfg.z_min)) df_add(acc[kMaxHalve + k], 1.f);
             }
         }
         block_sum_store<NACC>(acc, partials);
@@ -264,8 +210,8 @@ __global__ void __launch_bounds__(kModelThreads)
     if (!last_block_arrive(&ls->ticket)) return;
     const int nb = gridDim.x;
     if constexpr (MODE == 0) {
-        const double fd = block_sum_all(partials, nb), f1d = block_sum_all(partials + nb, nb);
-        const double f2d = block_sum_all(partials + 2 * nb, nb), bad = block_sum_all(partials + 3 * nb, nb);
+        const double fd = block_sum_partials(partials, nb), f1d = block_sum_partials(partials + nb, nb);
+        const double f2d = block_sum_partials(partials + 2 * nb, nb), bad = block_sum_partials(partials + 3 * nb, nb);
         if (threadIdx.x == 0) {
             ls_newton_control(ls, fd, f1d, f2d, bad, last, cfg);
             ls->ticket = 0;
@@ -273,8 +219,8 @@ __global__ void __launch_bounds__(kModelThreads)
     } else {
         double fk[kMaxHalve], bk[kMaxHalve];
         for (int k = 0; k < nh; ++k) {
-            fk[k] = block_sum_all(partials + (int64_t)k * nb, nb);
-            bk[k] = block_sum_all(partials + (int64_t)(kMaxHalve + k) * nb, nb);
+            fk[k] = block_sum_partials(partials + (int64_t)k * nb, nb);
+            bk[k] = block_sum_partials(partials + (int64_t)(kMaxHalve + k) * nb, nb);
         }
         if (threadIdx.x == 0) {
             ls_halve_control(ls, fk, bk, nh);
@@ -366,7 +312,7 @@ size_t spec_smem(SpecDev sp) { return sizeof(float) * (size_t)(sp.ne * sp.nm + s
 }  // namespace
 
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
-                              float *g, float *kappa, double *partials, int nblocks, cudaStream_t s) {
+                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     switch (sp.nm) {
         case 1: model_grad_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, y, gamma, g, kappa, partials); break;
@@ -379,24 +325,9 @@ mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const 
     return MBIR_OK;
 }
 
-mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y,
-                           const double *alpha, const int *skip, float z_min, double *partials, int nblocks,
-                           cudaStream_t s) {
-    const size_t smem = spec_smem(sp);
-    switch (sp.nm) {
-        case 1: ls_eval_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
-        case 2: ls_eval_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
-        case 3: ls_eval_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
-        case 4: ls_eval_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, alpha, skip, z_min, partials); break;
-        default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
-    }
-    PSPS_LAUNCH_CHECK();
-    return MBIR_OK;
-}
-
 template <int NM>
 void ls_fused_launch(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls, LsCfg cfg,
-                     int mode, int last, double *partials, int nblocks, size_t smem, cudaStream_t s) {
+                     int mode, int last, dfloat *partials, int nblocks, size_t smem, cudaStream_t s) {
     if (mode == 0)
         ls_fused_kernel<NM, 0><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
     else
@@ -404,7 +335,7 @@ void ls_fused_launch(SpecDev sp, int64_t n_rays, const float *l, const float *q,
 }
 
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
-                            LsCfg cfg, int mode, int last, double *partials, int nblocks, cudaStream_t s) {
+                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     switch (sp.nm) {
         case 1: ls_fused_launch<1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
@@ -501,7 +432,7 @@ namespace {
 // Scratch for the stateless model calls: l and g sinograms plus partials.
 struct ModelScratch {
     DBuf<float> l, g;
-    DBuf<double> part;
+    DBuf<dfloat> part;
 };
 
 mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y, int64_t n_rays,

@@ -16,27 +16,22 @@ inline SpecDev spec_dev(const mbmd_spectrum *s) { return SpecDev{s->n_mat, s->n_
 constexpr int kModelThreads = 256;
 constexpr int kModelMaxBlocks = 2048;  // grid-stride; partial sums per block
 
+// About two rays per thread, at most kModelMaxBlocks blocks.
 inline int model_blocks(int64_t n) {
-    int64_t b = cdiv(n, kModelThreads);
+    int64_t b = cdiv(n, 2 * kModelThreads);
     return (int)(b < kModelMaxBlocks ? (b < 1 ? 1 : b) : kModelMaxBlocks);
 }
 
 // data term partials (1 per block); g, kappa optional ([nm][n_rays]).
 // gamma: per-ray gamma_m = [A |M| 1]_m ([nm][n_rays]) for kappa.
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
-                              float *g, float *kappa, double *partials, int nblocks, cudaStream_t s);
-// phi(alpha) data terms (f, f1, f2) and the number of rays with some
-// z = Q (l + alpha q) below z_min, as partials (4 per block) at
-// alpha = *alpha; returns immediately when *skip != 0.
-mbir_status launch_ls_eval(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y,
-                           const double *alpha, const int *skip, float z_min, double *partials, int nblocks,
-                           cudaStream_t s);
+                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s);
 // Fused line-search evaluation: mode 0 evaluates phi, phi', phi'' at
 // ls->alpha and its last block runs the Newton control; mode 1 (skipped when
 // the search is done) evaluates the n_halve halving candidates at once and
-// its last block picks the step.  partials: 2 kMaxHalve doubles per block.
+// its last block picks the step.  partials: 2 kMaxHalve per block.
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
-                            LsCfg cfg, int mode, int last, double *partials, int nblocks, cudaStream_t s);
+                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s);
 mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s);
 // Per-ray Fisher blocks F_i = Q^T D S^T W S D Q (upper triangle, packed
 // [nm(nm+1)/2][n_rays]) with D = y / I0 (one energy/channel) or the water fit.

@@ -6,8 +6,8 @@
 // must not call cudaMalloc / cudaFree because those can block or implicitly
 // synchronise the whole device.
 //
-// Its scratch (the FP32 copy of the spectral table and the per-block FP64
-// partial sums) lives in the file-scope array below, 28,928 bytes, which
+// Its scratch (the FP32 copy of the spectral table and the per-block
+// double-float partial sums) lives in the file-scope array below, 28,928 bytes, which
 // every GPU that loads this library holds until the process exits.  In host
 // code the array's name only stands in for the symbol and is never used as a
 // pointer: the device address is looked up with cudaGetSymbolAddress on the
@@ -24,7 +24,7 @@ namespace {
 
 constexpr size_t kTableFloats = 256 * 4 + 8 * 256 + 8;  // Q[E][m], S[c][E], sigma[c] at the limits
 constexpr size_t kTableBytes = ((kTableFloats * sizeof(float) + 255) / 256) * 256;
-constexpr size_t kPartialBytes = sizeof(double) * kModelMaxBlocks;
+constexpr size_t kPartialBytes = sizeof(dfloat) * kModelMaxBlocks;
 constexpr size_t kScratchBytes = kTableBytes + kPartialBytes;  // 28,928 bytes
 
 static_assert(kScratchBytes == 28928, "keep the documented scratch size in step");
@@ -82,7 +82,7 @@ extern "C" mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_cha
     void *base = nullptr;
     PSPS_TRY(scratch_address(&base));
     float *qs = (float *)base;
-    double *partials = (double *)((unsigned char *)base + kTableBytes);
+    dfloat *partials = (dfloat *)((unsigned char *)base + kTableBytes);
     cudaStream_t s = (cudaStream_t)stream;
     // pageable source: the copy is staged before the call returns, so the
     // stack table may go out of scope afterwards

@@ -24,18 +24,22 @@ __device__ __forceinline__ float gamma_at(const float *__restrict__ v, int64_t j
     return (float)cnt * c + sign * acc;
 }
 
-// Writes Rx (if rx_out) and reduces sum x.Rx, p.Rx, p.Rp (FP64 partials).
+// Writes Rx (if rx_out) and reduces sum x.Rx, p.Rx, p.Rp (double-float
+// partials).
 // abs_mode: |R| v instead (positive taps, |beta|), no reductions.
 __global__ void __launch_bounds__(kThreads)
     penalty_kernel(PenaltyDev pd, int nx, int ny, int nz, const float *__restrict__ x, const float *__restrict__ p,
-                   float *__restrict__ rx_out, int accumulate, int abs_mode, double *__restrict__ partials) {
+                   float *__restrict__ rx_out, int accumulate, int abs_mode, dfloat *__restrict__ partials) {
     const int64_t npix = (int64_t)nx * ny * nz;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    dfloat s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
     const float sign = abs_mode ? 1.f : -1.f;
+    const int64_t plane = (int64_t)nx * ny;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < npix; j += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(j % nx);
-        const int iy = (int)((j / nx) % ny);
-        const int iz = (int)(j / ((int64_t)nx * ny));
+        // one 64-bit division per pixel; the in-plane split is 32-bit
+        const int iz = (int)(j / plane);
+        const int jp = (int)(j - (int64_t)iz * plane);
+        const int iy = jp / nx;
+        const int ix = jp - iy * nx;
         float gx[4] = {0, 0, 0, 0}, gp[4] = {0, 0, 0, 0};
         for (int k = 0; k < pd.nm; ++k) {
             if (x) gx[k] = gamma_at(x + k * npix, j, ix, iy, iz, nx, ny, nz, sign);
@@ -53,16 +57,16 @@ __global__ void __launch_bounds__(kThreads)
                 *o = accumulate ? *o + rx : rx;
             }
             if (partials) {
-                const double xv = x ? (double)x[k * npix + j] : 0.0;
-                const double pv = p ? (double)p[k * npix + j] : 0.0;
-                s0 += xv * rx;
-                s1 += pv * rx;
-                s2 += pv * rp;
+                const float xv = x ? x[k * npix + j] : 0.f;
+                const float pv = p ? p[k * npix + j] : 0.f;
+                df_add(s0, xv * rx);
+                df_add(s1, pv * rx);
+                df_add(s2, pv * rp);
             }
         }
     }
     if (partials) {
-        double v[3] = {s0, s1, s2};
+        dfloat v[3] = {s0, s1, s2};
         block_sum_store<3>(v, partials);
     }
 }
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(kThreads)
 }  // namespace
 
 mbir_status launch_penalty(const PenaltyDev &pd, int nx, int ny, int nz, const float *x, const float *p, float *rx_out,
-                           int accumulate, int abs_mode, double *partials, int nblocks, cudaStream_t s) {
+                           int accumulate, int abs_mode, dfloat *partials, int nblocks, cudaStream_t s) {
     penalty_kernel<<<nblocks, kThreads, 0, s>>>(pd, nx, ny, nz, x, p, rx_out, accumulate, abs_mode, partials);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;

@@ -12,6 +12,6 @@ int penalty_blocks(int64_t npix);
 // rx_out (+)= R x (or |R| x with abs_mode); partials (3 per block, nullable):
 // sum x.Rx, sum p.Rx, sum p.Rp.  x or p may be null (their terms are zero).
 mbir_status launch_penalty(const PenaltyDev &pd, int nx, int ny, int nz, const float *x, const float *p, float *rx_out,
-                           int accumulate, int abs_mode, double *partials, int nblocks, cudaStream_t s);
+                           int accumulate, int abs_mode, dfloat *partials, int nblocks, cudaStream_t s);
 
 }  // namespace psps

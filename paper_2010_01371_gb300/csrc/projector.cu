@@ -873,11 +873,10 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
     p->n_pix = (int64_t)p->g.nx * p->g.ny * p->g.nz;
     mbir_status st;
     if ((st = p->xcol.alloc(p->n_pix * 4)) != MBIR_OK || (st = p->xrow.alloc(p->n_pix * 4)) != MBIR_OK ||
-        (st = p->partials.alloc(8 * 4096)) != MBIR_OK || (cone && (st = p->xcol3.alloc(p->n_pix * 4)) != MBIR_OK)) {
+        (cone && (st = p->xcol3.alloc(p->n_pix * 4)) != MBIR_OK)) {
         delete p;
         return st;
     }
-    p->partials_cap = 4096;
     if (cone) {
         st = cone_setup(p);
         cudaError_t e = cudaDeviceSynchronize();

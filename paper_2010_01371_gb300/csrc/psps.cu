@@ -30,26 +30,11 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Block-wide fixed-order sum of n partials (one block of kThreads threads).
-__device__ double block_sum(const double *p, int n) {
-    __shared__ double sh[32];
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a += p[i];
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
-    __syncthreads();
-    return r;  // valid in thread 0
-}
-
 // phi0 = data + 1/2 x.Rx; records the objective history.
-__global__ void ctrl_begin_kernel(DevLS *ls, const double *pobj, int nobj, const double *ppen, int npen,
+__global__ void ctrl_begin_kernel(DevLS *ls, const dfloat *pobj, int nobj, const dfloat *ppen, int npen,
                                   double *history) {
-    const double d = block_sum(pobj, nobj);
-    const double xRx = ppen ? block_sum(ppen, npen) : 0.0;
+    const double d = block_sum_partials(pobj, nobj);
+    const double xRx = ppen ? block_sum_partials(ppen, npen) : 0.0;
     if (threadIdx.x == 0) {
         ls->R0 = 0.5 * xRx;
         ls->phi0 = d + 0.5 * xRx;
@@ -59,9 +44,9 @@ __global__ void ctrl_begin_kernel(DevLS *ls, const double *pobj, int nobj, const
 }
 
 // penalty terms along p: partials are (x.Rx, p.Rx, p.Rp) blocks
-__global__ void ctrl_ls_init_kernel(DevLS *ls, const double *ppen, int npen) {
-    const double pRx = ppen ? block_sum(ppen + npen, npen) : 0.0;
-    const double pRp = ppen ? block_sum(ppen + 2 * npen, npen) : 0.0;
+__global__ void ctrl_ls_init_kernel(DevLS *ls, const dfloat *ppen, int npen) {
+    const double pRx = ppen ? block_sum_partials(ppen + npen, npen) : 0.0;
+    const double pRp = ppen ? block_sum_partials(ppen + 2 * npen, npen) : 0.0;
     if (threadIdx.x == 0) {
         ls->pRx = pRx;
         ls->pRp = pRp;
@@ -132,7 +117,8 @@ struct psps_state {
     PenaltyDev pd{};
     LsCfg cfg{3, 8, 1e12, 8.0, -20.0f};
     DBuf<float> x, l, y, gamma, dR, gk, G, gp, dp, pp, p, q;
-    DBuf<double> part_obj, part_pen, part_ls, history, alphas;
+    DBuf<dfloat> part_obj, part_pen, part_ls;
+    DBuf<double> history, alphas;
     DBuf<DevLS> ls;
     int nb_model = 1, nb_pen = 1;
     int hist_cap = 0;
@@ -198,7 +184,7 @@ mbir_status apply_M(psps_state *st, int op, const float *in, float *out, cudaStr
 }
 
 mbir_status penalty_call(psps_state *st, const float *x, const float *p, float *rx_out, int acc, int abs_mode,
-                         double *part, cudaStream_t s) {
+                         dfloat *part, cudaStream_t s) {
     const mbir_geometry &g = st->plan->g;
     return launch_penalty(st->pd, g.nx, g.ny, g.kind == MBIR_CONE3D ? g.nz : 1, x, p, rx_out, acc, abs_mode, part,
                           st->nb_pen, s);
