@@ -233,6 +233,21 @@ __device__ __forceinline__ void decode(float4 r, int &axis, int &lo, int &hi) {
     hi = (bits >> 16) & 0x7fff;
 }
 
+// Joseph sample split shared by the forward projector and the tile transpose
+// (identical arithmetic on both sides, so the pair is an exact transpose up
+// to the summation order): with h = fy - 1/2 = i * df + (f0 - 1/2) and
+// |h| < 2^22, h + 1.5 * 2^23 rounds to the integer nearest h, which is
+// floor(fy) except at integer fy, where it may give floor(fy) - 1 with
+// fraction 1 — the same two weights on the same pixel, since the linear
+// interpolation is continuous there.  No conversion instructions are used.
+constexpr float kSplitMagic = 12582912.0f;  // 1.5 * 2^23
+
+__device__ __forceinline__ int joseph_split(float h, float &f) {
+    const float rn = h + kSplitMagic;
+    f = (h - (rn - kSplitMagic)) + 0.5f;
+    return __float_as_int(rn) - __float_as_int(kSplitMagic);
+}
+
 template <int NM>
 __global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restrict__ tab, int64_t n_rays, int nx,
                                                           int ny, const typename Pack<NM>::T *__restrict__ xrow,
@@ -245,14 +260,13 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restri
     decode(r, axis, lo, hi);
     const typename Pack<NM>::T *src = axis == 0 ? xcol : xrow;
     const int n_other = axis == 0 ? ny : nx;
+    const float f0h = r.x - 0.5f;
     float acc[NM], comp[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
     for (int i = lo; i <= hi; ++i) {
-        const float fy = fmaf((float)i, r.y, r.x);
-        const float fl = floorf(fy);
-        const int i0 = (int)fl;
-        const float f = fy - fl;
+        float f;
+        const int i0 = joseph_split(fmaf((float)i, r.y, f0h), f);
         const typename Pack<NM>::T *base = src + (int64_t)i * n_other;
         float a[NM], b[NM];
 #pragma unroll
@@ -280,18 +294,21 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_pair_kernel(const float4 *__r
     const float4 r = tab[ray];
     int axis, lo, hi;
     decode(r, axis, lo, hi);
-    const float2 *src = axis == 0 ? pc : pr;
     const int n_other = axis == 0 ? ny : nx;
-    const int64_t stride = n_other + 1;
-    float acc = 0.f, comp = 0.f;
-    for (int i = lo; i <= hi; ++i) {
-        const float fy = fmaf((float)i, r.y, r.x);
-        const float fl = floorf(fy);
-        const int i0 = (int)fl;
-        const float f = fy - fl;
-        if (i0 < -1 || i0 >= n_other) continue;
-        const float2 ab = __ldg(src + (int64_t)i * stride + i0 + 1);
-        const float v = __fadd_rn(__fmul_rn(1.f - f, ab.x), __fmul_rn(f, ab.y));
+    const int stride = n_other + 1;
+    const float f0h = r.x - 0.5f;
+    // joseph_split inlined, returning i0 + 1 (the pair index) directly
+    const int rel = __float_as_int(kSplitMagic) - 1;
+    const float2 *row = (axis == 0 ? pc : pr) + (int64_t)lo * stride;
+    float acc = 0.f, comp = 0.f, fi = (float)lo;
+    for (int i = lo; i <= hi; ++i, fi += 1.f, row += stride) {
+        const float h = fmaf(fi, r.y, f0h);
+        const float rn = h + kSplitMagic;
+        const int k = __float_as_int(rn) - rel;
+        if ((unsigned)k > (unsigned)n_other) continue;  // both pixels off the grid
+        const float f = (h - (rn - kSplitMagic)) + 0.5f;
+        const float2 ab = __ldg(row + k);
+        const float v = fmaf(f, ab.y - ab.x, ab.x);
         const float yk = __fsub_rn(v, comp);
         const float t = __fadd_rn(acc, yk);
         comp = __fsub_rn(__fsub_rn(t, acc), yk);
@@ -562,11 +579,7 @@ __device__ __forceinline__ void tile_ray_range_approx(const float4 &r, int c0, i
 // those, like lanes past the grid's edge, land in rows or columns that the
 // epilogue drops.
 //
-// The interpolation index is split without conversion instructions: with
-// h = fy - 1/2 and |h| < 2^22, h + 1.5 * 2^23 rounds to the integer nearest h,
-// which is floor(fy) except for integer fy, where it may give floor(fy) - 1
-// with fraction 1 — the same two weights on the same pixel, because the
-// linear interpolation is continuous there.
+// Samples are split with joseph_split, like the forward projector's.
 __device__ __forceinline__ void red_shared_pair(unsigned addr, float lo, float hi) {
     asm volatile(
         "red.shared.add.f32 [%0], %1;\n\t"
@@ -576,21 +589,18 @@ __device__ __forceinline__ void red_shared_pair(unsigned addr, float lo, float h
 }
 
 // Kept rays [j0, j1) of one driving axis: fi = this lane's driving index,
-// rowbase = bits of (1.5 * 2^23 + first interpolated index - 1), addr = byte
-// address of this lane's column in the axis' first accumulator plane.
+// rowbase = the tile's first interpolated index - 1, addr = byte address of
+// this lane's column in the axis' first accumulator plane.
 template <int NC>
 __device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, int j0, int j1, float fi, int rowbase,
                                                unsigned addr) {
-    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
     constexpr unsigned kPlaneBytes = 4u * (kBT + 2) * kBT;
 #pragma unroll 2
     for (int j = j0; j < j1; ++j) {
-        const float4 a = ws[j];                      // f0 - 1/2, df, w * sino[0], w * sino[1]
-        const float h = fmaf(fi, a.y, a.x);          // fy - 1/2
-        const float rn = h + kMagic;                 // nearest integer to h, in the low mantissa bits
-        const int jr = __float_as_int(rn) - rowbase; // interpolated index - (first index - 1)
+        const float4 a = ws[j];  // f0 - 1/2, df, w * sino[0], w * sino[1]
+        float f;                 // weight of the upper pixel
+        const int jr = joseph_split(fmaf(fi, a.y, a.x), f) - rowbase;  // interpolated index - (first index - 1)
         if ((unsigned)jr <= (unsigned)kBT) {
-            const float f = (h - (rn - kMagic)) + 0.5f;  // weight of the upper pixel
             const unsigned q = addr + (unsigned)jr * (4u * kBT);
             const float u0 = f * a.z;
             red_shared_pair(q, a.z - u0, u0);
@@ -624,7 +634,6 @@ __global__ void __launch_bounds__(kThreads, 5)
     const int total = ti.prefix[ti.nv];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int magic_bits = __float_as_int(12582912.0f);
     const unsigned col = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
     float4 *ws = stage + warp * 32;
     int k = 0;
@@ -647,9 +656,8 @@ __global__ void __launch_bounds__(kThreads, 5)
         const unsigned ky = __ballot_sync(0xffffffffu, keep && axis == 1);
         if (keep) ws[axis == 0 ? __popc(kx & below) : 31 - __popc(ky & below)] = lr;
         __syncwarp();
-        tile_lane_pass<NC>(ws, 0, __popc(kx), (float)(c0 + lane), magic_bits + r0 - 1, col);
-        tile_lane_pass<NC>(ws, 32 - __popc(ky), 32, (float)(r0 + lane), magic_bits + c0 - 1,
-                           col + 4u * NC * kPlane);
+        tile_lane_pass<NC>(ws, 0, __popc(kx), (float)(c0 + lane), r0 - 1, col);
+        tile_lane_pass<NC>(ws, 32 - __popc(ky), 32, (float)(r0 + lane), c0 - 1, col + 4u * NC * kPlane);
         __syncwarp();
     }
     __syncthreads();
