@@ -146,6 +146,39 @@ __device__ inline double block_sum_partials(const dfloat *p, int n) {
     return r;
 }
 
+// K such sums in one pass (stream k at p + k * n), so that the block pays
+// the load latency once; the results are valid in thread 0.
+template <int K>
+__device__ inline void block_sum_partials_k(const dfloat *p, int n, double (&out)[K]) {
+    __shared__ dfloat sh[K][32];
+    dfloat a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = dfloat{0.f, 0.f};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float2 v = __ldcg(reinterpret_cast<const float2 *>(p + (size_t)k * n + i));
+            df_merge(a[k], dfloat{v.x, v.y});
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) df_merge(a[k], df_shfl_down(a[k], o));
+        if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = a[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dfloat t{0.f, 0.f};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_merge(t, sh[k][w]);
+            out[k] = df_value(t);
+        }
+    }
+    __syncthreads();
+}
+
 // Sum `n` partials (fixed order, one block) into dst[0..K) (dst += if add).
 mbir_status reduce_partials(const dfloat *partials, int n, int K, double *dst, int add, cudaStream_t s);
 

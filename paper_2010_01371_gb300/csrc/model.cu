@@ -31,7 +31,10 @@ __device__ __forceinline__ void load_spec(const SpecDev &sp, float *sh) {
     __syncthreads();
 }
 
-template <int NM>
+// Channel counts are compile-time upper bounds CM (1, 2, 4, 8) with the
+// actual count nc <= CM tested inside fully unrolled loops, so the per-channel
+// accumulators stay in registers.
+template <int NM, int CM>
 __global__ void __launch_bounds__(kModelThreads)
     model_grad_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
                       const float *__restrict__ gamma, float *__restrict__ g, float *__restrict__ kappa,
@@ -47,23 +50,30 @@ __global__ void __launch_bounds__(kModelThreads)
         float lm[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) lm[m] = l[(int64_t)m * n_rays + i];
-        float yb[kMaxC];
-        for (int c = 0; c < nc; ++c) yb[c] = 0.f;
+        float yb[CM];
+#pragma unroll
+        for (int c = 0; c < CM; ++c) yb[c] = 0.f;
         for (int e = 0; e < ne; ++e) {
             float z = 0.f;
 #pragma unroll
             for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], lm[m], z);
             const float t = expf(-z);
-            for (int c = 0; c < nc; ++c) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
         }
-        float wr[kMaxC], ws[kMaxC];
-        for (int c = 0; c < nc; ++c) {
-            const float yc = y[(int64_t)c * n_rays + i];
-            const float w = 1.f / fmaxf(yc, 1.f);
-            const float r = yb[c] - yc;
-            wr[c] = w * r;
-            df_add(obj, 0.5f * wr[c] * r);
-            ws[c] = w * sig[c];
+        float wr[CM], ws[CM];
+#pragma unroll
+        for (int c = 0; c < CM; ++c) {
+            wr[c] = ws[c] = 0.f;
+            if (c < nc) {
+                const float yc = y[(int64_t)c * n_rays + i];
+                const float w = 1.f / fmaxf(yc, 1.f);
+                const float r = yb[c] - yc;
+                wr[c] = w * r;
+                df_add(obj, 0.5f * wr[c] * r);
+                ws[c] = w * sig[c];
+            }
         }
         if (g || kappa) {
             float gm[NM], km[NM], gam[NM];
@@ -81,10 +91,12 @@ __global__ void __launch_bounds__(kModelThreads)
                 }
                 const float t = expf(-z);
                 float v = 0.f, eta = 0.f;
-                for (int c = 0; c < nc; ++c) {
-                    v = fmaf(S[c * ne + e], wr[c], v);
-                    eta = fmaf(S[c * ne + e], ws[c], eta);
-                }
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) {
+                        v = fmaf(S[c * ne + e], wr[c], v);
+                        eta = fmaf(S[c * ne + e], ws[c], eta);
+                    }
                 const float tv = t * v;
                 float cE = 0.f;
                 if (kappa) {
@@ -109,12 +121,11 @@ __global__ void __launch_bounds__(kModelThreads)
     block_sum_store<1>(v, partials);
 }
 
-template <int NM, int MODE>
+template <int NM, int CM, int MODE>
 __global__ void __launch_bounds__(kModelThreads)
     ls_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
                     const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
-    constexpr int mode = MODE;
-    if (mode == 1 && ls->done) return;  // same value for every block
+    if (MODE == 1 && ls->done) return;  // same value for every block
     extern __shared__ float sh[];
     load_spec(sp, sh);
     const float *Q = sh;
@@ -136,8 +147,9 @@ __global__ void __launch_bounds__(kModelThreads)
                 qm[m] = q[(int64_t)m * n_rays + i];
                 la[m] = fmaf(alpha, qm[m], l[(int64_t)m * n_rays + i]);
             }
-            float yb[kMaxC], d1[kMaxC], d2[kMaxC];
-            for (int c = 0; c < nc; ++c) yb[c] = d1[c] = d2[c] = 0.f;
+            float yb[CM], d1[CM], d2[CM];
+#pragma unroll
+            for (int c = 0; c < CM; ++c) yb[c] = d1[c] = d2[c] = 0.f;
             for (int e = 0; e < ne; ++e) {
                 float z = 0.f, dz = 0.f;
 #pragma unroll
@@ -148,22 +160,26 @@ __global__ void __launch_bounds__(kModelThreads)
                 zlo = fminf(zlo, z);
                 const float t = expf(-z);
                 const float tdz = t * dz;
-                for (int c = 0; c < nc; ++c) {
-                    const float s = S[c * ne + e];
-                    yb[c] = fmaf(s, t, yb[c]);
-                    d1[c] = fmaf(-s, tdz, d1[c]);
-                    d2[c] = fmaf(s, tdz * dz, d2[c]);
-                }
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) {
+                        const float s = S[c * ne + e];
+                        yb[c] = fmaf(s, t, yb[c]);
+                        d1[c] = fmaf(-s, tdz, d1[c]);
+                        d2[c] = fmaf(s, tdz * dz, d2[c]);
+                    }
             }
             float f = 0.f, f1 = 0.f, f2 = 0.f;
-            for (int c = 0; c < nc; ++c) {
-                const float yc = y[(int64_t)c * n_rays + i];
-                const float w = 1.f / fmaxf(yc, 1.f);
-                const float r = yb[c] - yc;
-                f = fmaf(0.5f * w * r, r, f);
-                f1 = fmaf(w * r, d1[c], f1);
-                f2 = fmaf(w, fmaf(d1[c], d1[c], r * d2[c]), f2);
-            }
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) {
+                    const float yc = y[(int64_t)c * n_rays + i];
+                    const float w = 1.f / fmaxf(yc, 1.f);
+                    const float r = yb[c] - yc;
+                    f = fmaf(0.5f * w * r, r, f);
+                    f1 = fmaf(w * r, d1[c], f1);
+                    f2 = fmaf(w, fmaf(d1[c], d1[c], r * d2[c]), f2);
+                }
             df_add(acc[0], f);
             df_add(acc[1], f1);
             df_add(acc[2], f2);
@@ -172,35 +188,50 @@ __global__ void __launch_bounds__(kModelThreads)
         block_sum_store<4>(acc, partials);
     } else {
         const double a0 = ls->best_a;
+        float alphas[kMaxHalve];
+        double ak = a0;
+#pragma unroll
+        for (int k = 0; k < kMaxHalve; ++k) {
+            ak *= 0.5;
+            alphas[k] = (float)ak;
+        }
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
              i += (int64_t)gridDim.x * blockDim.x) {
-            float lm[NM], qm[NM];
+            float lm[NM], qm[NM], yc[CM], wh[CM];
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 qm[m] = q[(int64_t)m * n_rays + i];
                 lm[m] = l[(int64_t)m * n_rays + i];
             }
-            double ak = a0;
-            for (int k = 0; k < nh; ++k) {
-                ak *= 0.5;
-                const float alpha = (float)ak;
-                float yb[kMaxC];
-                for (int c = 0; c < nc; ++c) yb[c] = 0.f;
+#pragma unroll
+            for (int c = 0; c < CM; ++c) {
+                yc[c] = c < nc ? y[(int64_t)c * n_rays + i] : 0.f;
+                wh[c] = 0.5f / fmaxf(yc[c], 1.f);
+            }
+#pragma unroll
+            for (int k = 0; k < kMaxHalve; ++k) {
+                if (k >= nh) break;
+                float yb[CM];
+#pragma unroll
+                for (int c = 0; c < CM; ++c) yb[c] = 0.f;
                 float zlo = 3.0e38f;
                 for (int e = 0; e < ne; ++e) {
                     float z = 0.f;
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alpha, qm[m], lm[m]), z);
+                    for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alphas[k], qm[m], lm[m]), z);
                     zlo = fminf(zlo, z);
                     const float t = expf(-z);
-                    for (int c = 0; c < nc; ++c) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
+#pragma unroll
+                    for (int c = 0; c < CM; ++c)
+                        if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
                 }
                 float f = 0.f;
-                for (int c = 0; c < nc; ++c) {
-                    const float yc = y[(int64_t)c * n_rays + i];
-                    const float r = yb[c] - yc;
-                    f = fmaf(0.5f * r / fmaxf(yc, 1.f), r, f);
-                }
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) {
+                        const float r = yb[c] - yc[c];
+                        f = fmaf(wh[c] * r, r, f);
+                    }
                 df_add(acc[k], f);
                 if (!(zlo >= cfg.z_min)) df_add(acc[kMaxHalve + k], 1.f);
             }
@@ -210,20 +241,17 @@ __global__ void __launch_bounds__(kModelThreads)
     if (!last_block_arrive(&ls->ticket)) return;
     const int nb = gridDim.x;
     if constexpr (MODE == 0) {
-        const double fd = block_sum_partials(partials, nb), f1d = block_sum_partials(partials + nb, nb);
-        const double f2d = block_sum_partials(partials + 2 * nb, nb), bad = block_sum_partials(partials + 3 * nb, nb);
+        double sums[4];
+        block_sum_partials_k<4>(partials, nb, sums);
         if (threadIdx.x == 0) {
-            ls_newton_control(ls, fd, f1d, f2d, bad, last, cfg);
+            ls_newton_control(ls, sums[0], sums[1], sums[2], sums[3], last, cfg);
             ls->ticket = 0;
         }
     } else {
-        double fk[kMaxHalve], bk[kMaxHalve];
-        for (int k = 0; k < nh; ++k) {
-            fk[k] = block_sum_partials(partials + (int64_t)k * nb, nb);
-            bk[k] = block_sum_partials(partials + (int64_t)(kMaxHalve + k) * nb, nb);
-        }
+        double sums[2 * kMaxHalve];
+        block_sum_partials_k<2 * kMaxHalve>(partials, nb, sums);
         if (threadIdx.x == 0) {
-            ls_halve_control(ls, fk, bk, nh);
+            ls_halve_control(ls, sums, sums + kMaxHalve, nh);
             ls->ticket = 0;
         }
     }
@@ -311,37 +339,68 @@ size_t spec_smem(SpecDev sp) { return sizeof(float) * (size_t)(sp.ne * sp.nm + s
 
 }  // namespace
 
+// Smallest channel bound CM in {1, 2, 4, 8} with nc <= CM.
+inline int channel_bound(int nc) { return nc <= 1 ? 1 : nc <= 2 ? 2 : nc <= 4 ? 4 : 8; }
+
+template <int NM, int CM>
+void model_grad_launch(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma, float *g,
+                       float *kappa, dfloat *partials, int nblocks, size_t smem, cudaStream_t s) {
+    model_grad_kernel<NM, CM><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, y, gamma, g, kappa, partials);
+}
+
+template <int NM>
+void model_grad_launch_nm(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma, float *g,
+                          float *kappa, dfloat *partials, int nblocks, size_t smem, cudaStream_t s) {
+    switch (channel_bound(sp.nc)) {
+        case 1: model_grad_launch<NM, 1>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+        case 2: model_grad_launch<NM, 2>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+        case 4: model_grad_launch<NM, 4>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+        default: model_grad_launch<NM, 8>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+    }
+}
+
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
                               float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     switch (sp.nm) {
-        case 1: model_grad_kernel<1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, y, gamma, g, kappa, partials); break;
-        case 2: model_grad_kernel<2><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, y, gamma, g, kappa, partials); break;
-        case 3: model_grad_kernel<3><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, y, gamma, g, kappa, partials); break;
-        case 4: model_grad_kernel<4><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, y, gamma, g, kappa, partials); break;
+        case 1: model_grad_launch_nm<1>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+        case 2: model_grad_launch_nm<2>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+        case 3: model_grad_launch_nm<3>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
+        case 4: model_grad_launch_nm<4>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
         default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
     }
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
 }
 
-template <int NM>
+template <int NM, int CM>
 void ls_fused_launch(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls, LsCfg cfg,
                      int mode, int last, dfloat *partials, int nblocks, size_t smem, cudaStream_t s) {
     if (mode == 0)
-        ls_fused_kernel<NM, 0><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
+        ls_fused_kernel<NM, CM, 0><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
     else
-        ls_fused_kernel<NM, 1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
+        ls_fused_kernel<NM, CM, 1><<<nblocks, kModelThreads, smem, s>>>(sp, n_rays, l, q, y, ls, cfg, last, partials);
+}
+
+template <int NM>
+void ls_fused_launch_nm(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
+                        LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, size_t smem, cudaStream_t s) {
+    switch (channel_bound(sp.nc)) {
+        case 1: ls_fused_launch<NM, 1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 2: ls_fused_launch<NM, 2>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 4: ls_fused_launch<NM, 4>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        default: ls_fused_launch<NM, 8>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+    }
 }
 
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
                             LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     switch (sp.nm) {
-        case 1: ls_fused_launch<1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
-        case 2: ls_fused_launch<2>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
-        case 3: ls_fused_launch<3>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
-        case 4: ls_fused_launch<4>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 1: ls_fused_launch_nm<1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 2: ls_fused_launch_nm<2>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 3: ls_fused_launch_nm<3>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
+        case 4: ls_fused_launch_nm<4>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
         default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
     }
     PSPS_LAUNCH_CHECK();

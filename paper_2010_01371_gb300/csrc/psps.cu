@@ -45,11 +45,11 @@ __global__ void ctrl_begin_kernel(DevLS *ls, const dfloat *pobj, int nobj, const
 
 // penalty terms along p: partials are (x.Rx, p.Rx, p.Rp) blocks
 __global__ void ctrl_ls_init_kernel(DevLS *ls, const dfloat *ppen, int npen) {
-    const double pRx = ppen ? block_sum_partials(ppen + npen, npen) : 0.0;
-    const double pRp = ppen ? block_sum_partials(ppen + 2 * npen, npen) : 0.0;
+    double pen[2] = {0.0, 0.0};
+    if (ppen) block_sum_partials_k<2>(ppen + npen, npen, pen);
     if (threadIdx.x == 0) {
-        ls->pRx = pRx;
-        ls->pRp = pRp;
+        ls->pRx = pen[0];
+        ls->pRp = pen[1];
         ls->alpha = ls->a_prev > 0 ? ls->a_prev : 1.0;
         ls->best_a = 0.0;
         ls->best_f = INFINITY;
