@@ -32,6 +32,21 @@ WORKLOAD = "c2_fan2d_512_haar"
 
 # other workloads (python bench.py --workload NAME): problem builder,
 # preconditioner, description
+# Bytes per step copied back by psps_step with a host history: the history
+# (2 doubles for one iteration) plus the device line-search record.
+DEVLS_BYTES = 80
+
+# Counters of the dominant kernel from one ncu capture of the same kernel and
+# workload (summaries under profiles/): DRAM bytes read + written per launch,
+# and the unit that binds it.  Remove an entry when its kernel changes.
+NCU_CAPTURES = {
+    ("c2_fan2d_512_haar", "backproject"): {
+        "traffic": 14.02e6,
+        "binding": {"unit": "SM shared-memory pipe (wavefronts)", "frac_of_peak": 0.772,
+                    "source": "profiles/back_tile_2d_c2_fan512.md"},
+    },
+}
+
 WORKLOADS = {
     "c2_fan2d_512_haar": ("config2", "haar", "512x512@0.5mm, 720x888 fan curved, Haar(M0, lattice 3)"),
     "c1_par2d_64_modfourier": ("config1", "mod_fourier", "64x64@1mm, 90x96 parallel, modified Fourier"),
@@ -39,6 +54,9 @@ WORKLOADS = {
     "c4_mbmd_512_blockfourier": ("config4_slice", "block_fourier",
                                  "512x512@0.5mm, 3 materials x 4 PC channels (101 energies), 3x3 blocks + "
                                  "cross-material Fourier"),
+    "c4_mbmd_16slices_blockfourier": ("config4", "block_fourier",
+                                      "16 slices 256^2..512^2 @0.5mm (seeded sizes), 720 views, 3 materials x 4 PC "
+                                      "channels, 3x3 blocks + cross-material Fourier, one graph per batch iteration"),
     "c5_cone3d_256_block": ("config5", "block", "256^3@0.5mm, 360x384x512 cone flat, 2 materials x 2 kVp, 2x2 "
                                                 "per-voxel blocks"),
 }
@@ -224,15 +242,16 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
     value = world * args.steps / (ms / 1000.0)
 
     # end to end through the public API with host buffers: every step uploads
-    # the measured counts from pinned memory and reads back the objective.
+    # the measured counts from pinned host memory into the state
+    # (psps_state_set_data) and reads back the objective history and the
+    # line-search record (psps_step with a host history synchronises).
     st2 = p.State(plan, spec, pc, yd, beta, line_search=True, graph=True)
     p.psps_step(st2, 1, history=True)
-    y_stage = torch.empty_like(yd)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        y_stage.copy_(y_host, non_blocking=True)
-        p.psps_step(st2, 1, history=True)      # synchronises, copies Phi back
+        p.psps_state_set_data(st2, y_host)
+        p.psps_step(st2, 1, history=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
 
@@ -253,9 +272,12 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
     }[dom]
     hbm, src = peaks()
     achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9 if stage_ms[dom] > 0 else 0.0
+    cap = NCU_CAPTURES.get((workload, dom))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "frac": achieved / hbm, "traffic": cap["traffic"] if cap else None, "peak_source": src,
                 "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
+    if cap:
+        roofline["binding"] = cap["binding"]
 
     line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -264,8 +286,8 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
                        "line_search": True, "graph": True,
                        "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3)},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline,
-            "e2e": {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": int(yd.numel() * 4),
-                    "d2h_bytes_per_step": 16}}
+            "e2e": {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": int(y_host.numel() * 4),
+                    "d2h_bytes_per_step": 2 * 8 + DEVLS_BYTES}}
     if rank == 0 and not args.no_gap:
         t0 = time.perf_counter()
         phi_star, runs = gap_runs(p, plan, spec, yd, beta, pc, args.gap_star, args.gap_iters)
@@ -302,6 +324,112 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def ours_batch(args, probs, workload, kind, desc):
+    """The batched workload: every slice has its own plan (autotuned view
+    split), spectrum handle, preconditioner and state; one psps_batch_step
+    iteration advances all slices through one CUDA graph.  value = batch
+    iterations per second (each advances every slice once)."""
+    import torch
+
+    import paper_2010_01371_gb300 as p
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    slices, tuned = [], []
+    for prob in probs:
+        plan = p.Plan(prob.geom)
+        tuned.append(plan.autotune(2))
+        spec = p.Spectrum(prob.Q, prob.S)
+        y_host = torch.as_tensor(prob.y.astype(np.float32)).reshape(-1).pin_memory()
+        yd = y_host.to(dev)
+        pc = p.Precond(plan, spec, kind, yd, prob.beta)
+        slices.append({"prob": prob, "plan": plan, "spec": spec, "y_host": y_host, "yd": yd, "pc": pc})
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    states = [p.State(s["plan"], s["spec"], s["pc"], s["yd"], s["prob"].beta, graph=True) for s in slices]
+    batch = p.Batch(states)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(args.warmup):
+        p.psps_batch_step(batch, 1, history=False)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = p.psps_batch_launch_count(batch)
+    times = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.psps_batch_step(batch, 1, history=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
+    clk = clocks.stop()
+    launches = p.psps_batch_launch_count(batch) - launches0
+    ms = float(np.sum(times))
+    value = args.steps / (ms / 1000.0)
+
+    # dominant kernel: the 2 n_mat-channel transpose of every slice, timed
+    # alone per slice (CUDA events, L2 flushed) and summed over the batch
+    back_ms, alg_bytes = 0.0, 0
+    for s in slices:
+        prob, plan = s["prob"], s["plan"]
+        nm = prob.Q.shape[1]
+        sino = torch.rand((2 * nm, plan.n_rays), device=dev)
+        img = torch.empty((2 * nm,) + plan.image_shape, device=dev)
+        p.mbir_backproject(plan, sino, img)
+        reps = []
+        for _ in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.mbir_backproject(plan, sino, img)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            reps.append(e0.elapsed_time(e1))
+        back_ms += float(np.median(reps))
+        alg_bytes += 2 * nm * 4 * (plan.n_rays + plan.n_pix)
+    hbm, src = peaks()
+    achieved = alg_bytes / (back_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "backproject (all slices, timed alone)", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "backproject_ms_per_iter": round(back_ms, 4)}
+
+    # end to end: every step uploads each slice's counts from pinned host
+    # memory and reads back every slice's objective history
+    states2 = [p.State(s["plan"], s["spec"], s["pc"], s["yd"], s["prob"].beta, graph=True) for s in slices]
+    batch2 = p.Batch(states2)
+    p.psps_batch_step(batch2, 1, history=True)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        for st, s in zip(states2, slices):
+            p.psps_state_set_data(st, s["y_host"])
+        p.psps_batch_step(batch2, 1, history=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    sizes = [int(s["prob"].geom.nx) for s in slices]
+    line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload, "problem": desc, "precond": kind, "line_search": True,
+                       "graph": "one per batch iteration (one branch per slice)", "slices": len(slices),
+                       "slice_sizes": sizes, "views_per_cta": tuned,
+                       "slice_iters_per_s": value * len(slices),
+                       "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3)},
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline,
+            "e2e": {"value": args.steps / e2e_s, "unit": "iter/s",
+                    "h2d_bytes_per_step": int(sum(s["y_host"].numel() for s in slices) * 4),
+                    "d2h_bytes_per_step": len(slices) * (2 * 8 + DEVLS_BYTES)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def kernel_bench(args, prob):
@@ -372,6 +500,9 @@ def main():
     prob = getattr(synth, builder)()
     if args.workload != WORKLOAD:
         args.no_cpu = True
+    if isinstance(prob, list):
+        ours_batch(args, prob, args.workload, kind, desc)
+        return
     ours(args, prob, args.workload, kind, desc)
 
 

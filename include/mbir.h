@@ -114,6 +114,14 @@ mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
  * the work split (and the FP32 summation order), not the result's definition.
  * MBIR_ERR_ARG outside 1..180. */
 mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
+/* Autotuner: times the 2-D tile transpose (n_channels channels, zero data, a
+ * warm-up and three launches per candidate, CUDA events on `stream`) for
+ * 30/45/60/90/120/180 views per CTA and keeps the fastest in the plan
+ * (written to *views_per_cta if non-NULL).  Synchronises; allocates and frees
+ * temporary device buffers; not allowed while `stream` is capturing
+ * (MBIR_ERR_ARG).  Cone-beam plans have nothing to tune and return at once.
+ * MBIR_ERR_ARG if n_channels is outside 1..n_mat_max. */
+mbir_status mbir_plan_autotune(mbir_plan *plan, int n_channels, mbir_stream stream, int *views_per_cta);
 /* Select the forward projector's algorithm: 0 = per-tile partial sums through
  * shared memory, combined with one FP32 atomic per (tile, ray); 1 = one thread
  * per ray with Kahan-compensated sums (default; deterministic, and faster on
@@ -243,10 +251,41 @@ mbir_status psps_state_destroy(psps_state *st);
  * re-projection).  Returns MBIR_ERR_NONFINITE if a reduction went non-finite. */
 mbir_status psps_step(psps_state *st, int n_iter, double *objective_history, mbir_stream stream);
 
+/* Replace the measured counts y of the state (n = n_chan * n_rays values,
+ * [n_chan][n_rays]; HOST or device pointer: the copy direction follows the
+ * pointer, pinned host memory keeps it asynchronous on `stream`).  The next
+ * iterations fit the new data; the preconditioner, x, l and the line-search
+ * state are kept (Eq. 3 with the new y).  MBIR_ERR_ARG if n does not match. */
+mbir_status psps_state_set_data(psps_state *st, const float *y, int64_t n, mbir_stream stream);
+
 /* Copy the current image x (device, [n_mat][image]) / step lengths (host,
  * the last n alphas of the most recent psps_step call; synchronises). */
 mbir_status psps_get_image(psps_state *st, float *x, mbir_stream stream);
 mbir_status psps_get_alphas(psps_state *st, double *alphas, int n, mbir_stream stream);
+
+/* Batches: independent reconstructions (e.g. the slices of a volume, each
+ * with its own plan, spectrum handle, preconditioner and state) advanced
+ * together.  One CUDA graph per iteration holds every state's iteration as a
+ * parallel branch, so the slices' kernels overlap on the GPU and the batch
+ * costs one graph launch per iteration.  The paper has no counterpart: this
+ * is the batched execution of its per-slice iteration (Eqs. 5-7 with the
+ * preconditioned direction of Eq. 15).
+ *
+ * psps_batch_create keeps the n state pointers (the caller keeps ownership and
+ * must keep them alive); MBIR_ERR_ARG if a state is NULL or repeated, if two
+ * states share a plan or a preconditioner (their scratch buffers would race
+ * in concurrent branches), or if their reproject_every differ.
+ * psps_batch_step runs n_iter iterations of every state on `stream`; with
+ * objective_history (HOST, n * (n_iter + 1) doubles, row i = state i, as
+ * psps_step) it synchronises and returns MBIR_ERR_NONFINITE if a state went
+ * non-finite.  Not thread-safe per batch; a state in a batch must not be
+ * stepped on its own concurrently. */
+typedef struct psps_batch psps_batch;
+mbir_status psps_batch_create(psps_state *const *states, int n, psps_batch **out);
+mbir_status psps_batch_destroy(psps_batch *batch);
+mbir_status psps_batch_step(psps_batch *batch, int n_iter, double *objective_history, mbir_stream stream);
+/* Kernels launched by psps_batch_step so far (graph kernel nodes x replays). */
+mbir_status psps_batch_launch_count(psps_batch *batch, int64_t *count);
 
 /* Stage timers.  psps_profile(st, 1) resets and enables CUDA-event timers
  * around the contiguous stages of an iteration (indices below); after every

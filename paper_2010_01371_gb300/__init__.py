@@ -86,6 +86,13 @@ class Plan:
         """Views per CTA of the 'tile' transpose (1..180)."""
         _call(lib().mbir_plan_set_tiling, self.h, int(views_per_cta))
 
+    def autotune(self, n_channels: int = 2) -> int:
+        """Time the tile transpose's view splits and keep the fastest
+        (synchronises); returns the chosen views per CTA."""
+        v = ctypes.c_int()
+        _call(lib().mbir_plan_autotune, self.h, int(n_channels), _stream(), ctypes.byref(v))
+        return int(v.value)
+
     def set_projector(self, mode: str):
         """'ray' (default: one thread per ray, deterministic) or 'tile'."""
         _call(lib().mbir_plan_set_projector, self.h, {"tile": 0, "ray": 1}[mode])
@@ -243,6 +250,50 @@ def psps_step(state: State, n_iter: int, history: bool = True):
         return h
     _call(lib().psps_step, state.h, int(n_iter), None, _stream())
     return None
+
+
+class Batch:
+    """Independent states advanced together, one CUDA graph per iteration
+    (``psps_batch_create``); keeps references to its states."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        arr = (ctypes.c_void_p * len(self.states))(*[s.h for s in self.states])
+        h = ctypes.c_void_p()
+        _call(lib().psps_batch_create, arr, len(self.states), ctypes.byref(h))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _abi._lib is not None:
+            _abi._lib.psps_batch_destroy(self.h)
+            self.h = None
+
+
+def psps_batch_step(batch: Batch, n_iter: int, history: bool = True):
+    """Run n_iter iterations of every state; returns the objective histories
+    ([n_states, n_iter + 1], synchronising) or None (asynchronous)."""
+    if history:
+        h = np.zeros((len(batch.states), n_iter + 1))
+        _call(lib().psps_batch_step, batch.h, int(n_iter), h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+              _stream())
+        return h
+    _call(lib().psps_batch_step, batch.h, int(n_iter), None, _stream())
+    return None
+
+
+def psps_batch_launch_count(batch: Batch) -> int:
+    c = ctypes.c_int64()
+    _call(lib().psps_batch_launch_count, batch.h, ctypes.byref(c))
+    return int(c.value)
+
+
+def psps_state_set_data(state: State, y):
+    """Copy new measured counts into the state: a host tensor (pinned for an
+    asynchronous copy) or a CUDA tensor of n_chan * n_rays float32 values."""
+    torch = _torch()
+    if not isinstance(y, torch.Tensor) or y.dtype != torch.float32 or not y.is_contiguous():
+        raise TypeError("y must be a contiguous float32 tensor")
+    _call(lib().psps_state_set_data, state.h, ctypes.c_void_p(y.data_ptr()), int(y.numel()), _stream())
 
 
 def psps_get_image(state: State, x=None):

@@ -36,6 +36,7 @@ SIGNATURES = [
     ("mbir_plan_n_pix", c_int64, [c_void_p]),
     ("mbir_plan_set_backprojector", c_int, [c_void_p, c_int]),
     ("mbir_plan_set_tiling", c_int, [c_void_p, c_int]),
+    ("mbir_plan_autotune", c_int, [c_void_p, c_int, c_void_p, P(c_int)]),
     ("mbir_plan_set_projector", c_int, [c_void_p, c_int]),
     ("mbir_project", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("mbir_backproject", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -55,7 +56,12 @@ SIGNATURES = [
     ("psps_state_create", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, P(c_double), c_void_p, c_int,
                                   c_int, c_void_p, P(c_void_p)]),
     ("psps_state_destroy", c_int, [c_void_p]),
+    ("psps_state_set_data", c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     ("psps_step", c_int, [c_void_p, c_int, P(c_double), c_void_p]),
+    ("psps_batch_create", c_int, [P(c_void_p), c_int, P(c_void_p)]),
+    ("psps_batch_destroy", c_int, [c_void_p]),
+    ("psps_batch_step", c_int, [c_void_p, c_int, P(c_double), c_void_p]),
+    ("psps_batch_launch_count", c_int, [c_void_p, P(c_int64)]),
     ("psps_get_image", c_int, [c_void_p, c_void_p, c_void_p]),
     ("psps_get_alphas", c_int, [c_void_p, P(c_double), c_int, c_void_p]),
     ("psps_profile", c_int, [c_void_p, c_int]),

@@ -3,14 +3,18 @@
 // the image grid (periodic, per material) and s a real spectrum
 // (Lambda~^-1/2, or the spectrum of the absolute kernel for |M|).
 //
-// One kernel runs radix-2 Stockham passes (self-sorting, natural order) on B
-// transforms of length N held in shared memory; loads and stores are
-// coalesced for both row transforms (unit element stride) and column
-// transforms (unit batch stride).  A 2-D apply is three launches:
+// One kernel runs mixed-radix Stockham passes (self-sorting, natural order;
+// radices 4, 2, 3, 5, 7) on B transforms of length N held in shared memory;
+// loads and stores are coalesced for both row transforms (unit element
+// stride) and column transforms (unit batch stride).  Pass s with radix R
+// after a product Ns of the earlier radices maps, for j < N/R, the inputs
+// X[j + r N/R] (r < R), times the twiddles e^{-/+2 pi i r (j mod Ns)/(Ns R)},
+// through an R-point DFT to Y[(j div Ns) Ns R + (j mod Ns) + r Ns].
+// A 2-D apply is three launches:
 //   rows forward (real input, times m0) -> columns forward, spectral
 //   multiply, columns inverse -> rows inverse (real part, 1/(nx ny), times m0).
-// Twiddles e^{-2 pi i k/N} are generated in FP64 on the host, stored FP32.
-// Power-of-two sizes up to 1024.
+// Twiddles e^{-2 pi i k/N} and the R-point roots of unity are generated in
+// FP64 on the host and stored FP32.  Sizes 2^a 3^b 5^c 7^d up to 1024.
 #include <cmath>
 #include <vector>
 
@@ -25,26 +29,105 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Stockham radix-2 over B transforms of length N in shared memory X (result
-// left in the returned buffer).  dir = -1 forward (e^{-i}), +1 inverse.
-__device__ float2 *stockham(float2 *X, float2 *Y, int N, int B, int dir, const float2 *__restrict__ tw) {
-    const int half = N / 2;
-    for (int Ns = 1; Ns < N; Ns *= 2) {
-        const int tstep = N / (2 * Ns);
-        for (int t = threadIdx.x; t < B * half; t += blockDim.x) {
-            const int b = t / half, j = t % half;
-            const float2 v0 = X[b * N + j];
-            float2 w = tw[(j % Ns) * tstep];
-            if (dir > 0) w.y = -w.y;
-            const float2 v1 = cmul(X[b * N + j + half], w);
-            const int idx = (j / Ns) * 2 * Ns + (j % Ns);
-            Y[b * N + idx] = make_float2(v0.x + v1.x, v0.y + v1.y);
-            Y[b * N + idx + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+// Roots of unity of the small DFTs, stored after the N twiddles of a table:
+// offsets of the R = 3, 5, 7 roots e^{-2 pi i k/R}, k < R.
+constexpr int kRoot3 = 0, kRoot5 = 3, kRoot7 = 8, kRoots = 15;
+constexpr int kMaxPasses = 12;
+
+// R-point DFT of v in place; root[k] = e^{-2 pi i k/R} (conjugated for the
+// inverse, dir = +1).
+template <int R>
+__device__ __forceinline__ void small_dft(float2 (&v)[R], int dir, const float2 *__restrict__ root) {
+    if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = make_float2(a.x + b.x, a.y + b.y);
+        v[1] = make_float2(a.x - b.x, a.y - b.y);
+    } else if constexpr (R == 4) {
+        const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+        const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+        const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+        const float2 e = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
+        // d = e * (i dir): e^{dir 2 pi i / 4} = i dir
+        const float2 d = dir > 0 ? make_float2(-e.y, e.x) : make_float2(e.y, -e.x);
+        v[0] = make_float2(a.x + c.x, a.y + c.y);
+        v[2] = make_float2(a.x - c.x, a.y - c.y);
+        v[1] = make_float2(b.x + d.x, b.y + d.y);
+        v[3] = make_float2(b.x - d.x, b.y - d.y);
+    } else {
+        float2 w[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            w[k] = root[k];
+            if (dir > 0) w[k].y = -w[k].y;
+        }
+        float2 out[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            float2 acc = v[0];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 t = cmul(v[r], w[(m * r) % R]);
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+            out[m] = acc;
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = out[m];
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ X, float2 *__restrict__ Y, int N, int B,
+                                              int Ns, int dir, const float2 *__restrict__ tw,
+                                              const float2 *__restrict__ root) {
+    const int NR = N / R;
+    const int tstep = N / (Ns * R);
+    for (int t = threadIdx.x; t < B * NR; t += blockDim.x) {
+        const int b = t / NR, j = t - b * NR;
+        const int jm = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            v[r] = X[b * N + j + r * NR];
+            if (r > 0) {
+                float2 w = tw[jm * r * tstep];
+                if (dir > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        small_dft<R>(v, dir, root);
+        const int idx = (j / Ns) * Ns * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) Y[b * N + idx + r * Ns] = v[r];
+    }
+}
+
+struct Radices {
+    int n = 0;
+    int r[kMaxPasses] = {};
+};
+
+// Stockham over B transforms of length N in shared memory X (result left in
+// the returned buffer).  dir = -1 forward (e^{-i}), +1 inverse.
+__device__ float2 *stockham(float2 *X, float2 *Y, int N, int B, int dir, const Radices &rad,
+                            const float2 *__restrict__ tw) {
+    const float2 *roots = tw + N;
+    int Ns = 1;
+    for (int s = 0; s < rad.n; ++s) {
+        const int R = rad.r[s];
+        switch (R) {
+            case 4: stockham_pass<4>(X, Y, N, B, Ns, dir, tw, roots); break;
+            case 2: stockham_pass<2>(X, Y, N, B, Ns, dir, tw, roots); break;
+            case 3: stockham_pass<3>(X, Y, N, B, Ns, dir, tw, roots + kRoot3); break;
+            case 5: stockham_pass<5>(X, Y, N, B, Ns, dir, tw, roots + kRoot5); break;
+            default: stockham_pass<7>(X, Y, N, B, Ns, dir, tw, roots + kRoot7); break;
         }
         __syncthreads();
         float2 *t = X;
         X = Y;
         Y = t;
+        Ns *= R;
     }
     return X;
 }
@@ -54,6 +137,7 @@ struct Pass {
     int64_t ks, bs;      // element stride, batch stride (in elements)
     int nbatch;          // total transforms per channel
     int64_t ch_stride;   // elements per channel
+    Radices rad;         // radix of each Stockham pass
 };
 
 __device__ __forceinline__ void lin(const Pass &p, int idx, int &b, int &k) {
@@ -100,9 +184,9 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     float2 *R;
     if (mode == 0 || mode == 3) {
-        R = stockham(X, Y, p.N, p.B, -1, tw);
+        R = stockham(X, Y, p.N, p.B, -1, p.rad, tw);
     } else if (mode == 1) {
-        R = stockham(X, Y, p.N, p.B, -1, tw);
+        R = stockham(X, Y, p.N, p.B, -1, p.rad, tw);
         for (int idx = threadIdx.x; idx < p.N * p.B; idx += blockDim.x) {
             const int b = idx / p.N, k = idx % p.N;
             if (b >= nb) continue;
@@ -111,9 +195,9 @@ __global__ void __launch_bounds__(kThreads)
             R[idx].y *= s;
         }
         __syncthreads();
-        R = stockham(R, R == X ? Y : X, p.N, p.B, +1, tw);
+        R = stockham(R, R == X ? Y : X, p.N, p.B, +1, p.rad, tw);
     } else {  // modes 2 and 4
-        R = stockham(X, Y, p.N, p.B, +1, tw);
+        R = stockham(X, Y, p.N, p.B, +1, p.rad, tw);
     }
     for (int idx = threadIdx.x; idx < p.N * p.B; idx += blockDim.x) {
         int b, k;
@@ -137,25 +221,51 @@ int pick_B(int N) {
     return B < 1 ? 1 : B;
 }
 
+// Radix plan of N: radix-4 passes while 4 divides N, one radix-2 pass for an
+// odd power of two, then 3, 5, 7.  False if another prime divides N.
+bool factor(int N, Radices &rad) {
+    rad.n = 0;
+    while (N % 4 == 0 && rad.n < kMaxPasses) rad.r[rad.n++] = 4, N /= 4;
+    if (N % 2 == 0 && rad.n < kMaxPasses) rad.r[rad.n++] = 2, N /= 2;
+    for (int R : {3, 5, 7})
+        while (N % R == 0 && rad.n < kMaxPasses) rad.r[rad.n++] = R, N /= R;
+    return N == 1;
+}
+
+Pass make_pass(int N, int64_t ks, int64_t bs, int nbatch, int64_t ch_stride) {
+    Pass p{N, pick_B(N), ks, bs, nbatch, ch_stride, {}};
+    factor(N, p.rad);
+    return p;
+}
+
 }  // namespace
 
-bool fft_supported(int n) { return n >= 2 && n <= 1024 && (n & (n - 1)) == 0; }
+bool fft_supported(int n) {
+    Radices r;
+    return n >= 2 && n <= 1024 && factor(n, r);
+}
 
 mbir_status FftPlan::init(int nx_, int ny_) {
     nx = nx_;
     ny = ny_;
     if (!fft_supported(nx) || !fft_supported(ny))
-        return fail(MBIR_ERR_UNIMPLEMENTED, "FFT sizes must be powers of two in 2..1024 (got %d x %d)", nx, ny);
+        return fail(MBIR_ERR_UNIMPLEMENTED, "FFT sizes must be 2^a 3^b 5^c 7^d in 2..1024 (got %d x %d)", nx, ny);
     for (int a = 0; a < 2; ++a) {
         const int N = a == 0 ? nx : ny;
-        std::vector<float2> h(N);
+        std::vector<float2> h(N + kRoots);
         for (int k = 0; k < N; ++k) {
             const double ang = -2.0 * M_PI * (double)k / (double)N;
             h[k] = make_float2((float)cos(ang), (float)sin(ang));
         }
+        const int radix[3] = {3, 5, 7}, off[3] = {kRoot3, kRoot5, kRoot7};
+        for (int q = 0; q < 3; ++q)
+            for (int k = 0; k < radix[q]; ++k) {
+                const double ang = -2.0 * M_PI * (double)k / (double)radix[q];
+                h[N + off[q] + k] = make_float2((float)cos(ang), (float)sin(ang));
+            }
         DBuf<float2> &t = a == 0 ? twx : twy;
-        PSPS_TRY(t.alloc(N));
-        PSPS_CUDA(cudaMemcpy(t.p, h.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+        PSPS_TRY(t.alloc(N + kRoots));
+        PSPS_CUDA(cudaMemcpy(t.p, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice));
     }
     static bool attr_done = false;
     if (!attr_done) {
@@ -168,14 +278,14 @@ mbir_status FftPlan::init(int nx_, int ny_) {
 mbir_status FftPlan::forward(int channels, const float *in, float2 *Z, cudaStream_t s) const {
     const int64_t npix = (int64_t)nx * ny;
     {
-        Pass p{nx, pick_B(nx), 1, nx, ny, npix};
+        const Pass p = make_pass(nx, 1, nx, ny, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(p, 0, in, Z, nullptr, nullptr,
                                                                                     nullptr, 0, 0, 1.f, twx.p);
         PSPS_LAUNCH_CHECK();
     }
     {
-        Pass p{ny, pick_B(ny), nx, 1, nx, npix};
+        const Pass p = make_pass(ny, nx, 1, nx, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 3, nullptr, Z, nullptr, nullptr,
                                                                                     nullptr, 0, 0, 1.f, twy.p);
@@ -187,14 +297,14 @@ mbir_status FftPlan::forward(int channels, const float *in, float2 *Z, cudaStrea
 mbir_status FftPlan::inverse(int channels, float2 *Z, float *out, const float *post, cudaStream_t s) const {
     const int64_t npix = (int64_t)nx * ny;
     {
-        Pass p{ny, pick_B(ny), nx, 1, nx, npix};
+        const Pass p = make_pass(ny, nx, 1, nx, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 4, nullptr, Z, nullptr, nullptr,
                                                                                     nullptr, 0, 0, 1.f, twy.p);
         PSPS_LAUNCH_CHECK();
     }
     {
-        Pass p{nx, pick_B(nx), 1, nx, ny, npix};
+        const Pass p = make_pass(nx, 1, nx, ny, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(
             p, 2, nullptr, Z, out, post, nullptr, 0, 0, (float)(1.0 / (double)npix), twx.p);
@@ -208,7 +318,7 @@ mbir_status FftPlan::filter(int channels, const float *in, float2 *Z, float *out
     const int64_t npix = (int64_t)nx * ny;
     // rows: ny transforms of length nx, element stride 1, batch stride nx
     {
-        Pass p{nx, pick_B(nx), 1, nx, ny, npix};
+        const Pass p = make_pass(nx, 1, nx, ny, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(p, 0, in, Z, nullptr, m0, nullptr,
                                                                                     0, 0, 1.f, twx.p);
@@ -216,14 +326,14 @@ mbir_status FftPlan::filter(int channels, const float *in, float2 *Z, float *out
     }
     // columns: nx transforms of length ny, element stride nx, batch stride 1
     {
-        Pass p{ny, pick_B(ny), nx, 1, nx, npix};
+        const Pass p = make_pass(ny, nx, 1, nx, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 1, nullptr, Z, nullptr, nullptr,
                                                                                     spec, nx, 1, 1.f, twy.p);
         PSPS_LAUNCH_CHECK();
     }
     {
-        Pass p{nx, pick_B(nx), 1, nx, ny, npix};
+        const Pass p = make_pass(nx, 1, nx, ny, npix);
         const size_t sm = 2 * sizeof(float2) * p.N * p.B;
         fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(
             p, 2, nullptr, Z, out, m0, nullptr, 0, 0, (float)(1.0 / (double)npix), twx.p);

@@ -947,6 +947,54 @@ extern "C" mbir_status mbir_plan_set_tiling(mbir_plan *p, int views_per_cta) {
     return MBIR_OK;
 }
 
+extern "C" mbir_status mbir_plan_autotune(mbir_plan *p, int n_channels, mbir_stream stream, int *views_per_cta) {
+    if (!p || n_channels < 1 || n_channels > p->n_mat_max)
+        return fail(MBIR_ERR_ARG, "mbir_plan_autotune: bad argument (n_channels must be 1..n_mat_max)");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PSPS_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return fail(MBIR_ERR_ARG, "mbir_plan_autotune: stream is capturing");
+    if (p->g.kind == MBIR_CONE3D) {  // nothing to tune: the 3-D transpose has no view split
+        if (views_per_cta) *views_per_cta = p->back_views;
+        return MBIR_OK;
+    }
+    DBuf<float> sino, img;
+    PSPS_TRY(sino.alloc((size_t)n_channels * p->n_rays));
+    PSPS_TRY(img.alloc((size_t)n_channels * p->n_pix));
+    PSPS_CUDA(cudaMemsetAsync(sino.p, 0, sizeof(float) * sino.n, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mbir_status st = MBIR_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        st = fail(MBIR_ERR_CUDA, "mbir_plan_autotune: event creation failed");
+    const int mode = p->back_mode, keep = p->back_views;
+    p->back_mode = 0;
+    int best = keep;
+    float best_ms = 3.0e38f;
+    const int cand[] = {30, 45, 60, 90, 120, 180};
+    for (int vs : cand) {
+        if (st != MBIR_OK) break;
+        if (vs > p->g.n_views && vs != cand[0]) continue;
+        p->back_views = vs;
+        float ms = 0.f;
+        if ((st = backproject(p, sino.p, img.p, n_channels, 0, s)) != MBIR_OK) break;  // warm-up
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(MBIR_ERR_CUDA, "mbir_plan_autotune: event record");
+        for (int r = 0; r < 3 && st == MBIR_OK; ++r) st = backproject(p, sino.p, img.p, n_channels, 0, s);
+        if (st != MBIR_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = fail(MBIR_ERR_CUDA, "mbir_plan_autotune: timing failed");
+            break;
+        }
+        if (ms < best_ms) best_ms = ms, best = vs;
+    }
+    p->back_mode = mode;
+    p->back_views = st == MBIR_OK ? best : keep;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st == MBIR_OK && views_per_cta) *views_per_cta = best;
+    return st;
+}
+
 extern "C" mbir_status mbir_plan_set_projector(mbir_plan *p, int mode) {
     if (!p || mode < 0 || mode > 1) return fail(MBIR_ERR_ARG, "mbir_plan_set_projector: bad argument");
     p->fwd_mode = mode;

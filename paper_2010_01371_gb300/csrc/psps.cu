@@ -265,6 +265,20 @@ mbir_status final_objective(psps_state *st, cudaStream_t s) {
     return MBIR_OK;
 }
 
+// Kernel nodes of a captured graph (the launches one replay makes).
+int64_t count_kernel_nodes(cudaGraph_t g) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    int64_t nk = 0;
+    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+        }
+    return nk;
+}
+
 mbir_status ensure_graph(psps_state *st, int which, cudaStream_t s) {
     if (st->graph[which]) return MBIR_OK;
     cudaStream_t cs;
@@ -285,16 +299,7 @@ mbir_status ensure_graph(psps_state *st, int which, cudaStream_t s) {
     cudaStreamDestroy(cs);
     if (st_ != MBIR_OK) return st_;
     if (e != cudaSuccess) return fail(MBIR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    size_t nn = 0;
-    cudaGraphGetNodes(g, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    int64_t nk = 0;
-    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
-        for (auto nd : nodes) {
-            cudaGraphNodeType t;
-            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
-        }
-    st->graph_kernels[which] = nk;
+    st->graph_kernels[which] = count_kernel_nodes(g);
     e = cudaGraphInstantiate(&st->graph[which], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(MBIR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -453,6 +458,15 @@ extern "C" mbir_status psps_step(psps_state *st, int n_iter, double *objective_h
     return MBIR_OK;
 }
 
+extern "C" mbir_status psps_state_set_data(psps_state *st, const float *y, int64_t n, mbir_stream stream) {
+    if (!st || !y) return fail(MBIR_ERR_ARG, "psps_state_set_data: null argument");
+    if (n != (int64_t)st->nc * st->n_rays)
+        return fail(MBIR_ERR_ARG, "psps_state_set_data: %lld values given, the state holds %lld", (long long)n,
+                    (long long)st->nc * st->n_rays);
+    PSPS_CUDA(cudaMemcpyAsync(st->y.p, y, sizeof(float) * n, cudaMemcpyDefault, (cudaStream_t)stream));
+    return MBIR_OK;
+}
+
 extern "C" mbir_status psps_get_image(psps_state *st, float *x, mbir_stream s) {
     if (!st || !x) return fail(MBIR_ERR_ARG, "psps_get_image: null argument");
     PSPS_CUDA(cudaMemcpyAsync(x, st->x.p, sizeof(float) * st->nm * st->n, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
@@ -486,6 +500,158 @@ extern "C" mbir_status psps_profile_read(psps_state *st, double *ms, int64_t *co
         ms[k] = st->prof_ms[k];
         count[k] = st->prof_cnt[k];
     }
+    return MBIR_OK;
+}
+
+// ----------------------------------------------------------------- batches
+// Independent reconstructions (the slices of a batched workload) advanced
+// together: one CUDA graph per iteration holds every state's iteration as a
+// parallel branch (fork/join through events during capture), so the small
+// kernels of different slices run concurrently and the whole batch costs one
+// graph launch per iteration.
+struct psps_batch {
+    std::vector<psps_state *> st;
+    int reproject_every = 10;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+    int64_t launches = 0;
+    int hist_cap = 0;
+    void drop_graphs() {
+        for (auto &g : graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    ~psps_batch() { drop_graphs(); }
+};
+
+namespace {
+
+mbir_status batch_graph(psps_batch *b, int which) {
+    if (b->graph[which]) return MBIR_OK;
+    const size_t n = b->st.size();
+    std::vector<cudaStream_t> side(n, nullptr);
+    std::vector<cudaEvent_t> join(n, nullptr);
+    cudaStream_t cs = nullptr;
+    cudaEvent_t fork = nullptr;
+    mbir_status res = MBIR_OK;
+    cudaGraph_t g = nullptr;
+    auto cuda = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && res == MBIR_OK) res = fail(MBIR_ERR_CUDA, "batch graph: %s: %s", what, cudaGetErrorString(e));
+        return e == cudaSuccess;
+    };
+    bool ok = cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream") &&
+              cuda(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
+    for (size_t i = 0; ok && i < n; ++i)
+        ok = cuda(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking), "stream") &&
+             cuda(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming), "event");
+    if (ok && cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture")) {
+        bool cap = cuda(cudaEventRecord(fork, cs), "fork");
+        for (size_t i = 0; cap && i < n; ++i) {
+            cap = cuda(cudaStreamWaitEvent(side[i], fork, 0), "fork wait");
+            if (cap) {
+                const mbir_status r = iterate(b->st[i], which == 1, side[i]);
+                if (r != MBIR_OK) {
+                    if (res == MBIR_OK) res = r;
+                    cap = false;
+                }
+            }
+            if (cap) cap = cuda(cudaEventRecord(join[i], side[i]), "join") && cuda(cudaStreamWaitEvent(cs, join[i], 0), "join wait");
+        }
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (res == MBIR_OK) cuda(e, "end capture");
+    }
+    if (res == MBIR_OK) {
+        b->graph_kernels[which] = count_kernel_nodes(g);
+        cuda(cudaGraphInstantiate(&b->graph[which], g, 0), "instantiate");
+    }
+    if (g) cudaGraphDestroy(g);
+    for (size_t i = 0; i < n; ++i) {
+        if (side[i]) cudaStreamDestroy(side[i]);
+        if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cs) cudaStreamDestroy(cs);
+    return res;
+}
+
+}  // namespace
+
+extern "C" mbir_status psps_batch_create(psps_state *const *states, int n, psps_batch **out) {
+    if (!states || !out || n < 1) return fail(MBIR_ERR_ARG, "psps_batch_create: bad argument");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!states[i]) return fail(MBIR_ERR_ARG, "psps_batch_create: state %d is NULL", i);
+        if (states[i]->reproject_every != states[0]->reproject_every)
+            return fail(MBIR_ERR_ARG, "psps_batch_create: the states must share reproject_every");
+        for (int j = 0; j < i; ++j) {
+            if (states[j] == states[i]) return fail(MBIR_ERR_ARG, "psps_batch_create: state %d appears twice", i);
+            // plans and preconditioners hold per-call scratch: concurrent
+            // branches may not share them
+            if (states[i]->plan && states[j]->plan == states[i]->plan)
+                return fail(MBIR_ERR_ARG, "psps_batch_create: states %d and %d share a plan", j, i);
+            if (states[i]->pc && states[j]->pc == states[i]->pc)
+                return fail(MBIR_ERR_ARG, "psps_batch_create: states %d and %d share a preconditioner", j, i);
+        }
+    }
+    psps_batch *b = new psps_batch();
+    b->st.assign(states, states + n);
+    b->reproject_every = states[0]->reproject_every;
+    *out = b;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status psps_batch_destroy(psps_batch *b) {
+    delete b;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status psps_batch_step(psps_batch *b, int n_iter, double *objective_history, mbir_stream stream) {
+    if (!b || n_iter < 0) return fail(MBIR_ERR_ARG, "psps_batch_step: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->hist_cap < n_iter + 1) {
+        for (psps_state *st : b->st)
+            if (st->hist_cap < n_iter + 1) {
+                PSPS_TRY(st->history.alloc(n_iter + 1));
+                PSPS_TRY(st->alphas.alloc(n_iter + 1));
+                st->hist_cap = n_iter + 1;
+                st->drop_graphs();
+            }
+        b->hist_cap = n_iter + 1;
+        b->drop_graphs();
+    }
+    for (psps_state *st : b->st) {
+        reset_counter_kernel<<<1, 1, 0, s>>>(st->ls.p);
+        PSPS_LAUNCH_CHECK();
+    }
+    for (int it = 0; it < n_iter; ++it) {
+        const int rp = (it > 0 && b->reproject_every > 0 && it % b->reproject_every == 0) ? 1 : 0;
+        PSPS_TRY(batch_graph(b, rp));
+        PSPS_CUDA(cudaGraphLaunch(b->graph[rp], s));
+        b->launches += b->graph_kernels[rp];
+    }
+    if (objective_history) {
+        const size_t n = b->st.size();
+        std::vector<DevLS> h(n);
+        for (size_t i = 0; i < n; ++i) {
+            psps_state *st = b->st[i];
+            PSPS_TRY(final_objective(st, s));
+            PSPS_CUDA(cudaMemcpyAsync(objective_history + i * (size_t)(n_iter + 1), st->history.p,
+                                      sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, s));
+            PSPS_CUDA(cudaMemcpyAsync(&h[i], st->ls.p, sizeof(DevLS), cudaMemcpyDeviceToHost, s));
+        }
+        PSPS_CUDA(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < n; ++i)
+            if (h[i].nonfinite)
+                return fail(MBIR_ERR_NONFINITE, "psps_batch_step: state %zu went non-finite", i);
+    }
+    return MBIR_OK;
+}
+
+extern "C" mbir_status psps_batch_launch_count(psps_batch *b, int64_t *count) {
+    if (!b || !count) return fail(MBIR_ERR_ARG, "psps_batch_launch_count: null argument");
+    *count = b->launches;
     return MBIR_OK;
 }
 

@@ -435,6 +435,36 @@ def config4_slice(nx: int = 512, n_views: int = 720, n_u: int = 888, slice_id: i
                         "block_fourier", f"c4_mbmd_{nx}")
 
 
+CONFIG4_SIZES = (256, 320, 384, 448, 512)
+
+
+def config4(n_slices: int = 16, n_views: int = 720, shrink: int = 1) -> list:
+    """The batched one-step MBMD workload: n_slices independent slices whose
+    sizes are drawn (seeded) from 256^2 .. 512^2; pixels stay 0.5 mm, so the
+    field of view follows the slice, and each slice gets 4 ceil(888 N / 2048)
+    curved bins of 1 mm (fan beam as config 2, 3 materials, 4 photon-counting
+    channels, CONFIG4_BETA).  shrink > 1 divides every size, the bin count and
+    the phantom by it (pixels and bins grow by the same factor) for
+    oracle-sized runs of the same batch."""
+    E = np.arange(20.0, 121.0)
+    Q = material_Q(E, ["water", "bone", "iodine"], rng(4, "materials"))
+    S = pc_channels(E, 120.0, [25.0, 40.0, 60.0, 80.0], 1e5)
+    sizes = rng(4, "slices").choice(CONFIG4_SIZES, size=n_slices)
+    g = rng(4, "phantom")
+    out = []
+    for k, n_full in enumerate(sizes):
+        n_full = int(n_full)
+        n = n_full // shrink
+        n_u = 4 * math.ceil(888 * n_full / (4 * 512)) // shrink
+        dx = 0.5 * shrink
+        geom = Geometry(FAN2D, n, n, 1, dx, dx, 1.0, n_views, 0.0, 2 * math.pi, n_u, 1, 1.0 * shrink, 1.0,
+                        500.0, 1000.0)
+        gk = np.random.Generator(np.random.PCG64(g.integers(2 ** 63)))
+        out.append(mbmd_problem(4, geom, mbmd_phantom(gk, n_full / 512.0), ["water", "bone", "iodine"], Q, S,
+                                CONFIG4_BETA, 100, "block_fourier", f"c4_slice{k}_{n_full}"))
+    return out
+
+
 CONFIG5_BETA = np.array([[0.5, 3.0], [3.0, 2000.0]])
 
 

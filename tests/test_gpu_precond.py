@@ -93,3 +93,37 @@ def test_paper_single_test_function(psps, oracle_lib):
     check_ops(psps, gpu_precond_from(psps, plan, spec, "haar", data), P, (1, 64, 64), APPLY_TOL)
     pc = psps.Precond(plan, spec, "haar", to_dev(prob.y), prob.beta, haar_lattice=0)
     check_ops(psps, pc, P, (1, 64, 64), 1e-2)
+
+
+def mixed_radix_problem():
+    """Non-square image whose sides need the radix-3, 5 and 7 FFT passes
+    (45 = 3^2 5, 56 = 2^3 7), parallel beam."""
+    import math
+    g = synth.rng(1, "phantom")
+    geom = synth.Geometry(synth.PAR2D, 45, 56, 1, 1.0, 1.0, 1.0, 60, 0.0, math.pi, 80, 1, 1.0, 1.0)
+    shapes = synth.random_ellipses(g, 4, radius=20.0, amin=3.0, amax=12.0, vmin=0.01, vmax=0.03)
+    return synth.mbir_problem(1, geom, shapes, 1e4, 1e3, 50, "fourier", "mixed_radix_45x56")
+
+
+@pytest.mark.parametrize("kind", ["fourier", "mod_fourier"])
+def test_mixed_radix_fourier(psps, oracle_lib, kind):
+    """Fourier preconditioners (Eqs. 27-33) on a 45 x 56 image: apply from the
+    oracle's spectrum and GPU build, against numpy's FFT in the oracle."""
+    prob = mixed_radix_problem()
+    st, P, data = oracle_precond(oracle_lib, prob, kind)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (1,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+
+
+@pytest.mark.parametrize("n", [40, 48, 56])
+def test_mixed_radix_cross_material(psps, oracle_lib, n):
+    """Cross-material Fourier (Eq. 57) on the uneven slice sizes of the batched
+    MBMD workload (320/384/448 shrunk by 8: radix 5, 3 and 7)."""
+    prob = next(p for p in synth.config4(n_views=90, shrink=8) if p.geom.nx == n)
+    st, P, data = oracle_precond(oracle_lib, prob, "block_fourier")
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (3,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, "block_fourier", data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)

@@ -185,3 +185,17 @@ def test_cone_full_size_sampled(psps, oracle_lib):
     Aty = to_host(psps.mbir_backproject(plan, to_dev(y)))
     lhs, rhs = float(np.dot(got.astype(np.float64), y[0].astype(np.float64))), float(np.sum(x * Aty))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_autotune_keeps_parity(psps, oracle_lib):
+    """The autotuner picks one of its candidate view splits that exist for the
+    scan (47 views: 30 or 45) and the transpose stays exact."""
+    g = small_geoms()["fan2d_ragged"]
+    plan = psps.Plan(g)
+    v = plan.autotune(2)
+    assert v in (30, 45)
+    s = np.random.default_rng(11).random((2, g.n_rays))
+    got = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    assert rel_l2(got, oracle_lib.Projector(g).backproject(s)) < TOL
+    with pytest.raises(RuntimeError):
+        plan.autotune(0)

@@ -193,3 +193,63 @@ def test_graph_replay_matches(psps):
     hc = psps.psps_step(c, 10)
     assert np.all(np.diff(hc) <= 1e-7 * hc[0])
     assert psps.psps_launch_count(c) > 0
+
+
+def test_set_data_replaces_counts(psps):
+    """psps_state_set_data from a pinned host tensor: a state that starts on
+    other counts and receives the real ones before its first step runs the
+    same iterations as a state created on the real counts (graph replay
+    included, since the graph reads the state's own buffer); with the other
+    counts kept, the run differs."""
+    import torch
+    prob = synth.config1()
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    yd = to_dev(prob.y)
+    pc = psps.Precond(plan, spec, "haar", yd, prob.beta)
+    a = psps.State(plan, spec, pc, yd, prob.beta, graph=True)
+    b = psps.State(plan, spec, pc, yd * 0.5 + 3.0, prob.beta, graph=True)
+    psps.psps_state_set_data(b, torch.as_tensor(prob.y.astype(np.float32)).reshape(-1).pin_memory())
+    ha, hb = psps.psps_step(a, 8), psps.psps_step(b, 8)
+    # equal up to the summation order of the transpose's FP32 atomics
+    assert np.allclose(ha, hb, rtol=1e-6)
+    assert rel_l2(to_host(psps.psps_get_image(b)), to_host(psps.psps_get_image(a))) < 1e-5
+    c = psps.State(plan, spec, pc, yd * 0.5 + 3.0, prob.beta, graph=True)
+    assert not np.allclose(psps.psps_step(c, 8), ha, rtol=1e-3)
+    with pytest.raises(RuntimeError):
+        psps.psps_state_set_data(b, torch.zeros(5, dtype=torch.float32))
+
+
+def test_batch_matches_single_states(psps):
+    """Four uneven slices of the batched MBMD workload (shrunk by 8: 32..64
+    pixels, mixed-radix cross-material Fourier) advanced together by one
+    graph per iteration give each slice's own run: same objective histories
+    and images as the states stepped one by one, and the same kernel count."""
+    probs = synth.config4(n_slices=4, n_views=90, shrink=8)
+    setups = []
+    for p in probs:
+        plan, spec, yd = psps.Plan(p.geom), psps.Spectrum(p.Q, p.S), to_dev(p.y)
+        setups.append((p, plan, spec, yd, psps.Precond(plan, spec, "block_fourier", yd, p.beta)))
+    n_iter = 12   # crosses one exact re-projection (every 10)
+    single, h_single = [], []
+    for p, plan, spec, yd, pc in setups:
+        s = psps.State(plan, spec, pc, yd, p.beta, graph=True)
+        h_single.append(psps.psps_step(s, n_iter))
+        single.append(s)
+    states = [psps.State(plan, spec, pc, yd, p.beta, graph=True) for p, plan, spec, yd, pc in setups]
+    batch = psps.Batch(states)
+    hb = psps.psps_batch_step(batch, n_iter)
+    assert hb.shape == (4, n_iter + 1)
+    # the transposes' FP32 atomics add in a different order on every run; over
+    # 12 line-searched iterations that moves the image by ~1e-5 (measured
+    # 1.4e-5) while the objectives agree to ~1e-7
+    for i in range(4):
+        assert np.allclose(hb[i], h_single[i], rtol=1e-6), i
+        assert rel_l2(to_host(psps.psps_get_image(states[i])), to_host(psps.psps_get_image(single[i]))) < 1e-4
+    assert psps.psps_batch_launch_count(batch) == sum(psps.psps_launch_count(s) for s in single)
+    # states may not repeat or share a plan / preconditioner
+    with pytest.raises(RuntimeError):
+        psps.Batch([states[0], states[0]])
+    p, plan, spec, yd, pc = setups[0]
+    other = psps.State(plan, spec, None, yd, p.beta)
+    with pytest.raises(RuntimeError):
+        psps.Batch([states[0], other])
