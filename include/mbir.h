@@ -102,12 +102,14 @@ mbir_status mbir_project(mbir_plan *plan, const float *x, float *l, int n_mat, m
 mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_mat, int accumulate,
                              mbir_stream stream);
 
-/* Select the transpose's algorithm (2-D): 0 = tile scatter through shared
+/* Select the transpose's algorithm.  2-D: 0 = tile scatter through shared
  * memory (default; lanes of a warp on consecutive driving indices of one ray),
  * 1 = pixel-driven gather (deterministic: no atomics, bitwise reproducible),
- * 2 = ray-driven scatter with global FP32 atomics.  All use the forward
- * projector's per-ray weights and are the exact transpose of mbir_project up
- * to FP32 rounding.  MBIR_ERR_ARG for another mode. */
+ * 2 = ray-driven scatter with global FP32 atomics.  3-D (cone): 0 and 1 =
+ * voxel-driven gather (default, deterministic), 2 = ray-driven scatter with
+ * global FP32 atomics.  All use the forward projector's per-ray weights and
+ * are the exact transpose of mbir_project up to FP32 rounding.  MBIR_ERR_ARG
+ * for another mode. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 /* Views handled by one CTA of the tile transpose (mode 0), 1..180: the
  * grid is (image tiles) x ceil(n_views / views_per_cta) CTAs.  Only changes

@@ -179,6 +179,22 @@ __device__ inline void block_sum_partials_k(const dfloat *p, int n, double (&out
     __syncthreads();
 }
 
+// Joseph sample split shared by every forward projector and transpose
+// (identical arithmetic on both sides, so each pair is an exact transpose up
+// to the summation order): with h = f - 1/2 = i * df + (f0 - 1/2) and
+// |h| < 2^22, h + 1.5 * 2^23 rounds to the integer nearest h, which is
+// floor(f) except at integer f, where it may give floor(f) - 1 with fraction
+// 1 — the same two weights on the same pixel, since the linear interpolation
+// is continuous there.  Returns the lower interpolation index; f gets the
+// weight of the upper one.  No conversion instructions are used.
+constexpr float kSplitMagic = 12582912.0f;  // 1.5 * 2^23
+
+__device__ __forceinline__ int joseph_split(float h, float &f) {
+    const float rn = h + kSplitMagic;
+    f = (h - (rn - kSplitMagic)) + 0.5f;
+    return __float_as_int(rn) - __float_as_int(kSplitMagic);
+}
+
 // Sum `n` partials (fixed order, one block) into dst[0..K) (dst += if add).
 mbir_status reduce_partials(const dfloat *partials, int n, int K, double *dst, int add, cudaStream_t s);
 
@@ -204,8 +220,12 @@ struct mbir_plan {
     int back_mode = 0;            // 0 tile scatter (default), 1 pixel gather, 2 ray-driven atomics
     int back_views = 60;          // views per CTA of the tile transpose
     int fwd_mode = 1;             // 0 tile sums, 1 one thread per ray (default)
-    // 3-D per-view set-up (source, detector origin and axes) in FP64
-    psps::DBuf<double> view3d;
+    // 3-D per-ray Joseph set-up (cone_ray, computed once): (fb_mid, dfb,
+    // fc_mid, dfc) in `ray` and (weight, bits(axis | lo << 2 | hi << 17)) in
+    // ray3b; per view, the set of driving axes its rays use (bit a)
+    psps::DBuf<float2> ray3b;
+    psps::DBuf<int> view_axes;
+    psps::DBuf<float> wsino;      // 3-D gather: weighted sinogram, up to 4 channels interleaved
     // scratch: packed / transposed image copies for the forward projector
     // (3-D: one copy per driving axis)
     psps::DBuf<float> xrow, xcol, xcol3;

@@ -13,11 +13,27 @@
 // interpolation coordinates f(i) = f_mid + (i - c_a) df carry no
 // large-number rounding.
 //
+// The set-up runs once per plan and is stored per ray (24 bytes: 1.7 GB for
+// 360 x 384 x 512 rays; the central-plane coordinates less 1/2, for the
+// conversion-free sample split), so the forward and the transposes read
+// bitwise the same interpolation coordinates and weights.
+//
 // Forward: one thread per ray (neighbouring threads = neighbouring detector
 // columns of one row), reading a packed copy of the volume laid out so the
 // two interpolated axes are the fastest (b fastest), for each driving axis;
-// Kahan-compensated FP32 sums.  Transpose: the same walk scattering with
-// FP32 atomics (exact transpose of the weights).
+// Kahan-compensated FP32 sums.
+//
+// Transpose (default): voxel-driven gather, one thread per voxel, no atomics
+// (bitwise reproducible), reading a weighted copy of the sinogram with up to
+// four channels interleaved per ray (16 bytes per ray of plan scratch).  For every view and every driving axis a that the
+// view's rays use, the voxel's bilinear footprint on the plane of its own
+// driving index (the voxel centre +- one voxel in the two interpolated axes)
+// is projected onto the detector; every detector cell whose centre lies in the
+// bounding box of the projected corners is a candidate ray, and a candidate
+// contributes exactly the forward's weight of this voxel: its driving axis
+// must be a and the ray's sample split must put the voxel on one of its four
+// taps.  The ray-driven scatter with global FP32 atomics
+// remains as the alternative (mbir_plan_set_backprojector mode 2).
 #include <cmath>
 
 #include "common.cuh"
@@ -117,6 +133,28 @@ __global__ void setup_view3d_kernel(mbir_geometry g, float4 *vt) {
     vt[v] = make_float4((float)(g.sid * c), (float)(g.sid * s), (float)c, (float)s);
 }
 
+__global__ void setup_rays3d_kernel(mbir_geometry g, const float4 *__restrict__ vt, int64_t n_rays,
+                                    float4 *__restrict__ ta, float2 *__restrict__ tb, int *__restrict__ view_axes) {
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n_rays) return;
+    const int per_view = g.n_u * g.n_v;
+    const int v = (int)(ray / per_view);
+    const int rem = (int)(ray % per_view);
+    const ConeRay r = cone_ray(g, vt[v], rem % g.n_u, rem / g.n_u);
+    ta[ray] = make_float4(r.fb_mid - 0.5f, r.dfb, r.fc_mid - 0.5f, r.dfc);
+    const bool empty = r.lo > r.hi;
+    const int bits = r.axis | ((empty ? 1 : r.lo) << 2) | ((empty ? 0 : r.hi) << 17);
+    tb[ray] = make_float2(r.w, __int_as_float(bits));
+    if (!empty) atomicOr(view_axes + v, 1 << r.axis);
+}
+
+__device__ __forceinline__ void decode3(float2 b, int &axis, int &lo, int &hi) {
+    const int bits = __float_as_int(b.y);
+    axis = bits & 3;
+    lo = (bits >> 2) & 0x7fff;
+    hi = (bits >> 17) & 0x7fff;
+}
+
 // Packed copies of x[m][z][y][x] for the three driving axes, materials
 // innermost with stride P: layout[a][c][b][m] (see the file comment).
 __global__ void pack3d_kernel(const float *__restrict__ x, int nm, int P, int nx, int ny, int nz,
@@ -166,27 +204,26 @@ struct P3<4> {
 
 template <int NM>
 __global__ void __launch_bounds__(kThreads)
-    fwd_cone_kernel(mbir_geometry g, const float4 *__restrict__ vt, const typename P3<NM>::T *__restrict__ ox,
-                    const typename P3<NM>::T *__restrict__ oy, const typename P3<NM>::T *__restrict__ oz, int nm,
-                    int64_t n_rays, float *__restrict__ l) {
+    fwd_cone_kernel(mbir_geometry g, const float4 *__restrict__ ta, const float2 *__restrict__ tb,
+                    const typename P3<NM>::T *__restrict__ ox, const typename P3<NM>::T *__restrict__ oy,
+                    const typename P3<NM>::T *__restrict__ oz, int nm, int64_t n_rays, float *__restrict__ l) {
     const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= n_rays) return;
-    const int per_view = g.n_u * g.n_v;
-    const int v = (int)(ray / per_view);
-    const int rem = (int)(ray % per_view);
-    const ConeRay r = cone_ray(g, vt[v], rem % g.n_u, rem / g.n_u);
-    const typename P3<NM>::T *src = r.axis == 0 ? ox : (r.axis == 1 ? oy : oz);
-    const int nb = r.axis == 0 ? g.ny : g.nx;
-    const int nc = r.axis == 2 ? g.ny : g.nz;
+    const float4 A = ta[ray];
+    const float2 B = tb[ray];
+    int axis, lo, hi;
+    decode3(B, axis, lo, hi);
+    const typename P3<NM>::T *src = axis == 0 ? ox : (axis == 1 ? oy : oz);
+    const int nb = axis == 0 ? g.ny : g.nx;
+    const int nc = axis == 2 ? g.ny : g.nz;
+    const float ca = 0.5f * ((axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz)) - 1);
     float acc[NM], comp[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
-    for (int i = r.lo; i <= r.hi; ++i) {
-        const float t = (float)i - r.ca;
-        const float fb = fmaf(t, r.dfb, r.fb_mid), fc = fmaf(t, r.dfc, r.fc_mid);
-        const float flb = floorf(fb), flc = floorf(fc);
-        const int ib0 = (int)flb, ic0 = (int)flc;
-        const float gb = fb - flb, gc = fc - flc;
+    for (int i = lo; i <= hi; ++i) {
+        const float t = (float)i - ca;
+        float gb, gc;
+        const int ib0 = joseph_split(fmaf(t, A.y, A.x), gb), ic0 = joseph_split(fmaf(t, A.w, A.z), gc);
         float s[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) s[m] = 0.f;
@@ -216,18 +253,20 @@ __global__ void __launch_bounds__(kThreads)
     }
 #pragma unroll
     for (int m = 0; m < NM; ++m)
-        if (m < nm) l[(int64_t)m * n_rays + ray] = acc[m] * r.w;
+        if (m < nm) l[(int64_t)m * n_rays + ray] = acc[m] * B.x;
 }
 
 __global__ void __launch_bounds__(kThreads)
-    back_cone_kernel(mbir_geometry g, const float4 *__restrict__ vt, const float *__restrict__ sino, int nm,
-                     int64_t n_rays, float *__restrict__ x) {
+    back_cone_kernel(mbir_geometry g, const float4 *__restrict__ ta, const float2 *__restrict__ tb,
+                     const float *__restrict__ sino, int nm, int64_t n_rays, float *__restrict__ x) {
     const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= n_rays) return;
-    const int per_view = g.n_u * g.n_v;
-    const int v = (int)(ray / per_view);
-    const int rem = (int)(ray % per_view);
-    const ConeRay r = cone_ray(g, vt[v], rem % g.n_u, rem / g.n_u);
+    const float4 A = ta[ray];
+    const float2 B = tb[ray];
+    ConeRay r;
+    decode3(B, r.axis, r.lo, r.hi);
+    r.fb_mid = A.x, r.dfb = A.y, r.fc_mid = A.z, r.dfc = A.w, r.w = B.x;
+    r.ca = 0.5f * ((r.axis == 0 ? g.nx : (r.axis == 1 ? g.ny : g.nz)) - 1);
     const int nb = r.axis == 0 ? g.ny : g.nx;
     const int nc = r.axis == 2 ? g.ny : g.nz;
     // voxel strides of the driving axis and the two interpolated axes in x[z][y][x]
@@ -242,10 +281,8 @@ __global__ void __launch_bounds__(kThreads)
         float *img = x + m * npix;
         for (int i = r.lo; i <= r.hi; ++i) {
             const float t = (float)i - r.ca;
-            const float fb = fmaf(t, r.dfb, r.fb_mid), fc = fmaf(t, r.dfc, r.fc_mid);
-            const float flb = floorf(fb), flc = floorf(fc);
-            const int ib0 = (int)flb, ic0 = (int)flc;
-            const float gb = fb - flb, gc = fc - flc;
+            float gb, gc;
+            const int ib0 = joseph_split(fmaf(t, r.dfb, r.fb_mid), gb), ic0 = joseph_split(fmaf(t, r.dfc, r.fc_mid), gc);
             for (int jc = 0; jc < 2; ++jc) {
                 const int ic = ic0 + jc;
                 if (ic < 0 || ic >= nc) continue;
@@ -260,11 +297,264 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Weighted sinogram for the gather: ws[ray][c] = w_ray * sino[c][ray],
+// channels interleaved (C = 1, 2 or 4 floats per ray; channels past nc are 0).
+template <int C>
+__global__ void weigh_sino_kernel(const float2 *__restrict__ tb, const float *__restrict__ sino, int nc,
+                                  int64_t n_rays, float *__restrict__ ws) {
+    for (int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ray < n_rays;
+         ray += (int64_t)gridDim.x * blockDim.x) {
+        const float w = tb[ray].x;
+#pragma unroll
+        for (int c = 0; c < C; ++c) ws[ray * C + c] = c < nc ? w * sino[(int64_t)c * n_rays + ray] : 0.f;
+    }
+}
+
+template <int C>
+struct Vec;
+template <>
+struct Vec<1> {
+    using T = float;
+    __device__ static void get(const T &v, float (&o)[1]) { o[0] = v; }
+};
+template <>
+struct Vec<2> {
+    using T = float2;
+    __device__ static void get(const T &v, float (&o)[2]) { o[0] = v.x, o[1] = v.y; }
+};
+template <>
+struct Vec<4> {
+    using T = float4;
+    __device__ static void get(const T &v, float (&o)[4]) { o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w; }
+};
+
+// Detector cells whose centres lie in the bounding box of the projections of
+// points (x, y, z) with x in {xs}, y in {ys}, z in {zs} (2 values each) for
+// view V (widened by 1e-3 of a cell for rounding; a ray outside the box has
+// no point in the footprint), clipped to the detector; false if a point
+// reaches the source plane (then the whole detector is returned).  NXY:
+// distinct (x, y) corners (2 when xs or ys holds one value twice, as in a
+// voxel's footprint for x- or y-driven rays; otherwise 4).
+template <int NXY>
+__device__ __forceinline__ bool footprint_box(const mbir_geometry &g, const float4 &V, const float (&xs)[2],
+                                              const float (&ys)[2], const float (&zs)[2], int &iu0, int &iu1,
+                                              int &iv0, int &iv1) {
+    const float sdd = (float)g.sdd;
+    float umin = 3.0e38f, umax = -3.0e38f, imin = 3.0e38f, imax = -3.0e38f;
+    bool behind = false;
+#pragma unroll
+    for (int k = 0; k < NXY; ++k) {
+        const float qx = xs[NXY == 4 ? (k & 1) : k] - V.x, qy = ys[NXY == 4 ? (k >> 1) : k] - V.y;
+        const float depth = -(qx * V.z + qy * V.w);   // along the central ray, source to detector
+        if (!(depth > 0.f)) behind = true;
+        const float inv = sdd / depth;
+        const float u = (-qx * V.w + qy * V.z) * inv;
+        umin = fminf(umin, u), umax = fmaxf(umax, u), imin = fminf(imin, inv), imax = fmaxf(imax, inv);
+    }
+    if (behind) {
+        iu0 = 0, iu1 = g.n_u - 1, iv0 = 0, iv1 = g.n_v - 1;
+        return false;
+    }
+    // w = z * sdd / depth over the z values and the corner magnifications
+    const float wmin = fminf(fminf(zs[0] * imin, zs[0] * imax), fminf(zs[1] * imin, zs[1] * imax));
+    const float wmax = fmaxf(fmaxf(zs[0] * imin, zs[0] * imax), fmaxf(zs[1] * imin, zs[1] * imax));
+    const float inv_du = (float)(1.0 / g.du), inv_dv = (float)(1.0 / g.dv);
+    const float cu = 0.5f * (g.n_u - 1), cv = 0.5f * (g.n_v - 1);
+    constexpr float eps = 1.0e-3f;
+    iu0 = max((int)ceilf(fmaxf(umin * inv_du + cu - eps, -2.0e9f)), 0);
+    iu1 = min((int)floorf(fminf(umax * inv_du + cu + eps, 2.0e9f)), g.n_u - 1);
+    iv0 = max((int)ceilf(fmaxf(wmin * inv_dv + cv - eps, -2.0e9f)), 0);
+    iv1 = min((int)floorf(fminf(wmax * inv_dv + cv + eps, 2.0e9f)), g.n_v - 1);
+    return true;
+}
+
+// The footprint of voxel (px, py, pz) for rays driven along A: its own
+// coordinate along A, +- one voxel along the two interpolated axes; for
+// A = 0 / 1 the two (x, y) corners are (px, py -+ dy) / (px -+ dx, py).
+template <int A>
+__device__ __forceinline__ void voxel_footprint(const mbir_geometry &g, float px, float py, float pz, float (&xs)[2],
+                                                float (&ys)[2], float (&zs)[2]) {
+    const float dx = (float)g.dx, dy = (float)g.dy, dz = (float)g.dz;
+    xs[0] = xs[1] = px, ys[0] = ys[1] = py, zs[0] = zs[1] = pz;
+    if (A != 0) xs[0] = px - dx, xs[1] = px + dx;
+    if (A != 1) ys[0] = py - dy, ys[1] = py + dy;
+    if (A != 2) zs[0] = pz - dz, zs[1] = pz + dz;
+}
+
+// Adds the weights of the candidate rays in cells [iu0, iu1] x [iv0, iv1] of
+// view v to sv.  Ray data come either from global memory (stage == nullptr)
+// or from a shared-memory copy of the box [su0, su0 + sw) x [sv0, ...)
+// (ray parameters, weighted channels and, for mixed views, axes).
+template <int A, int C>
+__device__ __forceinline__ void gather_cells(const mbir_geometry &g, int v, int ix, int iy, int iz, int iu0, int iu1,
+                                             int iv0, int iv1, bool check_axis, const float4 *__restrict__ ta,
+                                             const int *__restrict__ tbits, const typename Vec<C>::T *__restrict__ ws,
+                                             const float4 *s_ta, const typename Vec<C>::T *s_ws, const int *s_ax,
+                                             int su0, int sv0, int sw, float (&sv)[C]) {
+    const int id = A == 0 ? ix : (A == 1 ? iy : iz);                   // driving index
+    const int ib = A == 0 ? iy : ix, ic = A == 2 ? iy : iz;            // interpolated indices
+    const float t = (float)id - 0.5f * ((A == 0 ? g.nx : (A == 1 ? g.ny : g.nz)) - 1);
+    const int64_t view0 = (int64_t)v * g.n_u * g.n_v;
+    for (int jv = iv0; jv <= iv1; ++jv) {
+        for (int ju = iu0; ju <= iu1; ++ju) {
+            float4 R;
+            float val[C];
+            if (s_ta) {
+                const int k = (jv - sv0) * sw + (ju - su0);
+                if (check_axis && s_ax[k] != A) continue;
+                R = s_ta[k];
+                Vec<C>::get(s_ws[k], val);
+            } else {
+                const int64_t ray = view0 + (int64_t)jv * g.n_u + ju;
+                if (check_axis && (__ldg(tbits + 2 * ray + 1) & 3) != A) continue;
+                R = __ldg(ta + ray);
+                Vec<C>::get(__ldg(ws + ray), val);
+            }
+            float gb, gc;
+            const int db = ib - joseph_split(fmaf(t, R.y, R.x), gb), dc = ic - joseph_split(fmaf(t, R.w, R.z), gc);
+            if ((unsigned)db > 1u || (unsigned)dc > 1u) continue;
+            const float wbc = (db ? gb : 1.f - gb) * (dc ? gc : 1.f - gc);
+#pragma unroll
+            for (int c = 0; c < C; ++c) sv[c] = fmaf(wbc, val[c], sv[c]);
+        }
+    }
+}
+
+// Voxel-driven exact transpose (see the file comment).  A CTA owns a tile of
+// kGX x kGY x kGZ voxels; for every view and driving axis (x or y) it stages
+// the rays of the detector box that covers the whole tile's footprint in
+// shared memory once, and every thread gathers its own voxel's candidates
+// from that copy (rays driven along z, and boxes larger than the staging
+// area, are read from global memory instead).  C channels per launch from
+// the weighted interleaved sinogram; the candidates of one view are summed
+// in FP32 and the per-view sums Kahan-compensated; x[c] is written (or
+// added to) for c < nc.
+constexpr int kGX = 4, kGY = 4, kGZ = 16;   // 256 voxels per CTA
+constexpr int kStageCap = 640;              // staged detector cells per view
+
+template <int C>
+__global__ void __launch_bounds__(kGX * kGY * kGZ, 3)
+    back_cone_gather_kernel(mbir_geometry g, const float4 *__restrict__ vt, const float4 *__restrict__ ta,
+                            const float2 *__restrict__ tb, const int *__restrict__ view_axes,
+                            const typename Vec<C>::T *__restrict__ ws, int nc, float *__restrict__ x,
+                            int accumulate) {
+    __shared__ float4 s_ta[kStageCap];
+    __shared__ typename Vec<C>::T s_ws[kStageCap];
+    __shared__ int s_ax[kStageCap];
+    __shared__ int s_box[5];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kGX, y0 = blockIdx.y * kGY, z0 = blockIdx.z * kGZ;
+    const int ix = x0 + tid % kGX, iy = y0 + (tid / kGX) % kGY, iz = z0 + tid / (kGX * kGY);
+    const bool inside = ix < g.nx && iy < g.ny && iz < g.nz;
+    const float dx = (float)g.dx, dy = (float)g.dy, dz = (float)g.dz;
+    const float cx = 0.5f * (g.nx - 1), cy = 0.5f * (g.ny - 1), cz = 0.5f * (g.nz - 1);
+    const float px = (ix - cx) * dx, py = (iy - cy) * dy, pz = (iz - cz) * dz;
+    // the tile's voxel-centre extent (clipped to the volume)
+    const float tx0 = (x0 - cx) * dx, tx1 = (min(x0 + kGX, g.nx) - 1 - cx) * dx;
+    const float ty0 = (y0 - cy) * dy, ty1 = (min(y0 + kGY, g.ny) - 1 - cy) * dy;
+    const float tz0 = (z0 - cz) * dz, tz1 = (min(z0 + kGZ, g.nz) - 1 - cz) * dz;
+    const int *tbits = reinterpret_cast<const int *>(tb);  // (w, bits) pairs: bits at odd indices
+    float acc[C], comp[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = comp[c] = 0.f;
+    for (int v = 0; v < g.n_views; ++v) {
+        const int axes = view_axes[v];
+        if (!axes) continue;
+        const float4 V = vt[v];  // (sx, sy, cos beta, sin beta)
+        const bool mixed = (axes & (axes - 1)) != 0;
+        const int64_t view0 = (int64_t)v * g.n_u * g.n_v;
+        float sv[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) sv[c] = 0.f;
+#pragma unroll
+        for (int A = 0; A < 3; ++A) {
+            if (!((axes >> A) & 1)) continue;
+            // this voxel's candidate box
+            float xs[2], ys[2], zs[2];
+            int iu0, iu1, iv0, iv1;
+            if (A == 0) {
+                voxel_footprint<0>(g, px, py, pz, xs, ys, zs);
+                footprint_box<2>(g, V, xs, ys, zs, iu0, iu1, iv0, iv1);
+            } else if (A == 1) {
+                voxel_footprint<1>(g, px, py, pz, xs, ys, zs);
+                footprint_box<2>(g, V, xs, ys, zs, iu0, iu1, iv0, iv1);
+            } else {
+                voxel_footprint<2>(g, px, py, pz, xs, ys, zs);
+                footprint_box<4>(g, V, xs, ys, zs, iu0, iu1, iv0, iv1);
+            }
+            // the tile's box (same for every thread of the CTA: thread 0
+            // computes it; the barrier below publishes it)
+            __syncthreads();   // previous readers of the staging area and the box are done
+            if (tid == 0) {
+                int b0 = 0, b1 = -1, b2 = 0, b3 = -1;
+                bool ok = false;
+                if (A != 2) {
+                    const float txs[2] = {A == 0 ? tx0 : tx0 - dx, A == 0 ? tx1 : tx1 + dx};
+                    const float tys[2] = {A == 1 ? ty0 : ty0 - dy, A == 1 ? ty1 : ty1 + dy};
+                    const float tzs[2] = {tz0 - dz, tz1 + dz};
+                    ok = footprint_box<4>(g, V, txs, tys, tzs, b0, b1, b2, b3) &&
+                         (b1 - b0 + 1) * (b3 - b2 + 1) <= kStageCap;
+                }
+                s_box[0] = b0, s_box[1] = b1, s_box[2] = b2, s_box[3] = b3, s_box[4] = ok;
+            }
+            __syncthreads();
+            const int su0 = s_box[0], su1 = s_box[1], sv0 = s_box[2], sv1 = s_box[3];
+            const bool staged = s_box[4] != 0;
+            const int sw = su1 - su0 + 1;
+            if (staged) {
+                const int n = sw * (sv1 - sv0 + 1);
+                for (int k = tid; k < n; k += blockDim.x) {
+                    const int64_t ray = view0 + (int64_t)(sv0 + k / sw) * g.n_u + su0 + k % sw;
+                    s_ta[k] = __ldg(ta + ray);
+                    s_ws[k] = __ldg(ws + ray);
+                    if (mixed) s_ax[k] = __ldg(tbits + 2 * ray + 1) & 3;
+                }
+                __syncthreads();
+                iu0 = max(iu0, su0), iu1 = min(iu1, su1), iv0 = max(iv0, sv0), iv1 = min(iv1, sv1);
+            }
+            if (!inside) continue;
+            if (A == 0)
+                gather_cells<0, C>(g, v, ix, iy, iz, iu0, iu1, iv0, iv1, mixed, ta, tbits, ws,
+                                   staged ? s_ta : nullptr, s_ws, s_ax, su0, sv0, sw, sv);
+            else if (A == 1)
+                gather_cells<1, C>(g, v, ix, iy, iz, iu0, iu1, iv0, iv1, mixed, ta, tbits, ws,
+                                   staged ? s_ta : nullptr, s_ws, s_ax, su0, sv0, sw, sv);
+            else
+                gather_cells<2, C>(g, v, ix, iy, iz, iu0, iu1, iv0, iv1, mixed, ta, tbits, ws, nullptr, s_ws, s_ax,
+                                   su0, sv0, sw, sv);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float yk = __fsub_rn(sv[c], comp[c]);
+            const float tt = __fadd_rn(acc[c], yk);
+            comp[c] = __fsub_rn(__fsub_rn(tt, acc[c]), yk);
+            acc[c] = tt;
+        }
+    }
+    if (!inside) return;
+    const int64_t npix = (int64_t)g.nx * g.ny * g.nz;
+    const int64_t j = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if (c >= nc) break;
+        float *o = x + (int64_t)c * npix + j;
+        *o = accumulate ? *o + acc[c] : acc[c];
+    }
+}
+
 }  // namespace
 
 mbir_status cone_setup(mbir_plan *p) {
     PSPS_TRY(p->view.alloc(p->g.n_views));
+    PSPS_TRY(p->ray.alloc(p->n_rays));
+    PSPS_TRY(p->ray3b.alloc(p->n_rays));
+    PSPS_TRY(p->view_axes.alloc(p->g.n_views));
+    PSPS_TRY(p->view_axes.zero(0));
+    PSPS_TRY(p->wsino.alloc((size_t)4 * p->n_rays));
     setup_view3d_kernel<<<(unsigned)cdiv(p->g.n_views, 128), 128>>>(p->g, p->view.p);
+    PSPS_LAUNCH_CHECK();
+    setup_rays3d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads>>>(p->g, p->view.p, p->n_rays, p->ray.p,
+                                                                          p->ray3b.p, p->view_axes.p);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
 }
@@ -282,23 +572,55 @@ mbir_status project_cone(mbir_plan *p, const float *x, float *l, int n_mat, cuda
         const unsigned gr = (unsigned)cdiv(p->n_rays, kThreads);
         float *lm = l + (int64_t)m0 * p->n_rays;
         if (P == 1)
-            fwd_cone_kernel<1><<<gr, kThreads, 0, s>>>(g, p->view.p, ox, oy, oz, nm, p->n_rays, lm);
+            fwd_cone_kernel<1><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, ox, oy, oz, nm, p->n_rays, lm);
         else if (P == 2)
-            fwd_cone_kernel<2><<<gr, kThreads, 0, s>>>(g, p->view.p, (const float2 *)ox, (const float2 *)oy,
-                                                       (const float2 *)oz, nm, p->n_rays, lm);
+            fwd_cone_kernel<2><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float2 *)ox,
+                                                       (const float2 *)oy, (const float2 *)oz, nm, p->n_rays, lm);
         else
-            fwd_cone_kernel<4><<<gr, kThreads, 0, s>>>(g, p->view.p, (const float4 *)ox, (const float4 *)oy,
-                                                       (const float4 *)oz, nm, p->n_rays, lm);
+            fwd_cone_kernel<4><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float4 *)ox,
+                                                       (const float4 *)oy, (const float4 *)oz, nm, p->n_rays, lm);
         PSPS_LAUNCH_CHECK();
     }
     return MBIR_OK;
 }
 
 mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s) {
-    if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
-    back_cone_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->g, p->view.p, sino, n_mat, p->n_rays,
-                                                                             x);
-    PSPS_LAUNCH_CHECK();
+    if (p->back_mode == 2) {
+        if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
+        back_cone_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads, 0, s>>>(p->g, p->ray.p, p->ray3b.p, sino,
+                                                                                 n_mat, p->n_rays, x);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
+    const dim3 grd((unsigned)cdiv(p->g.nx, kGX), (unsigned)cdiv(p->g.ny, kGY), (unsigned)cdiv(p->g.nz, kGZ));
+    const int nthr = kGX * kGY * kGZ;
+    const unsigned gw = (unsigned)(cdiv(p->n_rays, kThreads) < 65535 * 16 ? cdiv(p->n_rays, kThreads) : 65535 * 16);
+    for (int m0 = 0; m0 < n_mat;) {
+        const int left = n_mat - m0;
+        const float *sm = sino + (int64_t)m0 * p->n_rays;
+        float *xm = x + (int64_t)m0 * p->n_pix;
+        const int nc = left >= 4 ? 4 : left;                 // channels of this launch
+        const int C = nc == 1 ? 1 : (nc == 2 ? 2 : 4);      // interleaved floats per ray
+        float *w = p->wsino.p;
+        if (C == 4) {
+            weigh_sino_kernel<4><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
+            PSPS_LAUNCH_CHECK();
+            back_cone_gather_kernel<4><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                                p->view_axes.p, (const float4 *)w, nc, xm, accumulate);
+        } else if (C == 2) {
+            weigh_sino_kernel<2><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
+            PSPS_LAUNCH_CHECK();
+            back_cone_gather_kernel<2><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                                p->view_axes.p, (const float2 *)w, nc, xm, accumulate);
+        } else {
+            weigh_sino_kernel<1><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
+            PSPS_LAUNCH_CHECK();
+            back_cone_gather_kernel<1><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                                p->view_axes.p, w, nc, xm, accumulate);
+        }
+        PSPS_LAUNCH_CHECK();
+        m0 += nc;
+    }
     return MBIR_OK;
 }
 

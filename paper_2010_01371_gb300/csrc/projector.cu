@@ -233,21 +233,6 @@ __device__ __forceinline__ void decode(float4 r, int &axis, int &lo, int &hi) {
     hi = (bits >> 16) & 0x7fff;
 }
 
-// Joseph sample split shared by the forward projector and the tile transpose
-// (identical arithmetic on both sides, so the pair is an exact transpose up
-// to the summation order): with h = fy - 1/2 = i * df + (f0 - 1/2) and
-// |h| < 2^22, h + 1.5 * 2^23 rounds to the integer nearest h, which is
-// floor(fy) except at integer fy, where it may give floor(fy) - 1 with
-// fraction 1 — the same two weights on the same pixel, since the linear
-// interpolation is continuous there.  No conversion instructions are used.
-constexpr float kSplitMagic = 12582912.0f;  // 1.5 * 2^23
-
-__device__ __forceinline__ int joseph_split(float h, float &f) {
-    const float rn = h + kSplitMagic;
-    f = (h - (rn - kSplitMagic)) + 0.5f;
-    return __float_as_int(rn) - __float_as_int(kSplitMagic);
-}
-
 template <int NM>
 __global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restrict__ tab, int64_t n_rays, int nx,
                                                           int ny, const typename Pack<NM>::T *__restrict__ xrow,

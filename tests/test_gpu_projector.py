@@ -161,12 +161,31 @@ def test_cone_project_parity(psps, oracle_lib, name, nm):
 
 
 @pytest.mark.parametrize("name", list(cone_geoms()))
-def test_cone_backproject_parity(psps, oracle_lib, name):
+@pytest.mark.parametrize("mode", ["tile", "atomic"])
+@pytest.mark.parametrize("nch", [1, 2, 3, 5])
+def test_cone_backproject_parity(psps, oracle_lib, name, mode, nch):
+    """3-D transposes: the voxel-driven gather (default; channel groups of 4 /
+    2 / 1) and the ray-driven atomic scatter; accumulate adds."""
     g = cone_geoms()[name]
-    s = np.random.default_rng(12).random((2, g.n_rays))
-    got = to_host(psps.mbir_backproject(psps.Plan(g), to_dev(s)))
+    s = np.random.default_rng(12).random((nch, g.n_rays))
+    plan = psps.Plan(g)
+    plan.set_backprojector(mode)
+    got = to_host(psps.mbir_backproject(plan, to_dev(s)))
     want = oracle_lib.Projector(g).backproject(s)
     assert rel_l2(got, want) < TOL, rel_l2(got, want)
+    base = to_dev(np.ones((nch,) + g.image_shape))
+    psps.mbir_backproject(plan, to_dev(s), base, accumulate=True)
+    assert rel_l2(to_host(base), want + 1.0) < TOL
+
+
+def test_cone_gather_deterministic(psps):
+    """The 3-D gather has no atomics: two runs are bitwise equal."""
+    g = cone_geoms()["cone_small"]
+    s = to_dev(np.random.default_rng(14).random((2, g.n_rays)))
+    plan = psps.Plan(g)
+    a = to_host(psps.mbir_backproject(plan, s))
+    b = to_host(psps.mbir_backproject(plan, s))
+    assert np.array_equal(a, b)
 
 
 def test_cone_full_size_sampled(psps, oracle_lib):
