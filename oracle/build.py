@@ -16,7 +16,7 @@ import numpy as np
 from . import model, precond
 from .psps import Setup
 
-KINDS = ("none", "fourier", "mod_fourier", "haar", "block", "block_fourier")
+KINDS = ("none", "fourier", "mod_fourier", "haar", "block", "block_fourier", "block_haar")
 
 
 def t_hat(st: Setup) -> np.ndarray:
@@ -74,4 +74,7 @@ def build(st: Setup, kind: str):
     if kind == "block_fourier":
         L = precond.cross_fourier_blocks(apply_H, M0, st.shape, st.nm)
         return precond.CrossFourier(L, M0)
+    if kind == "block_haar":
+        K = precond.cross_haar_blocks(apply_H, M0, st.shape, st.nm)
+        return precond.CrossHaar(K, M0)
     raise ValueError(kind)

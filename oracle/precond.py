@@ -249,6 +249,62 @@ class Haar:
     absMT = absM
 
 
+class CrossHaar:
+    """Cross-material wavelet preconditioner (Eq. 61):
+    M = M0^T U^T K^-1/2 U M0 with U the orthonormal 2-D Haar transform applied
+    to every material and K block diagonal over the wavelet coefficients (one
+    N_k x N_k block per coefficient).  The estimated blocks are not symmetric;
+    as for the cross-material Fourier blocks, K^-1/2 is taken of the polar
+    factor (K^T K)^1/2 with the eigenvalue floor 1e-6 of the largest over all
+    blocks.  |M| = |M0|^T |U|^T |K^-1/2| |U| |M0| (R7: elementwise absolute
+    values of the factors bound |M| elementwise)."""
+
+    def __init__(self, K: np.ndarray, M0: Block):
+        self.shape = K.shape[:-2]
+        nm = K.shape[-1]
+        P = polar_real(K)
+        self.Ki = inv_sqrt_blocks(P.reshape(-1, nm, nm), floor="global", zero_rule=False).reshape(K.shape)
+        self.Ki_abs = np.abs(self.Ki)
+        self.M0 = M0
+
+    def _mid(self, W, v, absolute):
+        c = np.stack([haar.forward(v[k], absolute) for k in range(v.shape[0])])
+        out = np.einsum("...ij,j...->i...", W, c)
+        return np.stack([haar.transpose(out[k], absolute) for k in range(v.shape[0])])
+
+    def M(self, v):
+        return self.M0.MT(self._mid(self.Ki, self.M0.M(v), False))
+
+    def MT(self, v):
+        return self.M0.MT(self._mid(np.swapaxes(self.Ki, -1, -2), self.M0.M(v), False))
+
+    def absM(self, v):
+        return self.M0.absMT(self._mid(self.Ki_abs, self.M0.absM(v), True))
+
+    def absMT(self, v):
+        return self.M0.absMT(self._mid(np.swapaxes(self.Ki_abs, -1, -2), self.M0.absM(v), True))
+
+
+def cross_haar_blocks(apply_H, M0: Block, shape, nm: int, lattice: int = 3) -> np.ndarray:
+    """K_k of Eqs. 59-60 for every material k, with the wavelet test
+    functions of the Haar reading (``haar_test_sets``): for each coefficient
+    set xi the test function dx = U^T xi placed in material k gives column k
+    of the blocks of the coefficients j in the set,
+    K[j][k', k] = [U M0^T H M0 dx_k]_{k'}(j) / [U dx](j).  Returned as
+    K[h, w, k', k] (real, not symmetric in general)."""
+    K = np.zeros(tuple(shape) + (nm, nm))
+    for sel in haar_test_sets(shape, lattice):
+        dx = haar.transpose(sel.astype(np.float64))
+        den = haar.forward(dx)
+        for k in range(nm):
+            d = np.zeros((nm,) + tuple(shape))
+            d[k] = dx
+            r = M0.MT(apply_H(M0.M(d)))
+            for kp in range(nm):
+                K[..., kp, k][sel] = haar.forward(r[kp])[sel] / den[sel]
+    return K
+
+
 def haar_test_sets(shape, lattice: int = 3):
     """Coefficient sets (boolean masks in the Mallat layout) whose indicator
     xi gives one test function U^T xi: per level, per detail subband (HL top

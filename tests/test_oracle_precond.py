@@ -151,7 +151,7 @@ def test_abs_bounds_dominate(oracle_lib):
     img = synth.render(g, [synth.Ellipse(0.5, -0.3, 2.5, 3.0, 0.2, 0.02)])
     y = np.round(1e4 * np.exp(-A.project(img[None])))
     st = psps.Setup(A, np.ones((1, 1)), np.full((1, 1), 1e4), y, np.array([[50.0]]))
-    for kind in ["fourier", "mod_fourier", "haar", "block"]:
+    for kind in ["fourier", "mod_fourier", "haar", "block", "block_haar"]:
         P = build.build(st, kind)
         Md = dense(P.M, st.shape)
         MTd = dense(P.MT, st.shape)
@@ -160,3 +160,46 @@ def test_abs_bounds_dominate(oracle_lib):
         assert np.allclose(MTd, Md.T, atol=1e-12 * np.abs(Md).max())
         assert (Ad >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all(), kind
         assert np.allclose(ATd, Ad.T, atol=1e-12 * np.abs(Ad).max())
+
+
+def test_cross_haar_exact_on_wavelet_block_diagonal():
+    """H = U^T K U per material with SPD cross-material blocks K (one per Haar
+    coefficient), M0 = I: the estimator of Eqs. 59-60 recovers K exactly and
+    the cross-material wavelet M of Eq. 61 whitens H (M^T H M = I)."""
+    from oracle import haar, precond
+    shape, nm = (8, 8), 3
+    rng = np.random.default_rng(6)
+    G = rng.standard_normal(shape + (nm, nm))
+    Kt = np.einsum("...ij,...kj->...ik", G, G) + 0.5 * np.eye(nm)
+
+    def apply_H(v):
+        c = np.stack([haar.forward(v[k]) for k in range(nm)])
+        out = np.einsum("...ij,j...->i...", Kt, c)
+        return np.stack([haar.transpose(out[k]) for k in range(nm)])
+    M0 = precond.Block(np.tile(np.eye(nm), (int(np.prod(shape)), 1, 1)), shape)
+    K = precond.cross_haar_blocks(apply_H, M0, shape, nm)
+    assert np.allclose(K, Kt, rtol=1e-11, atol=1e-11)
+    P = precond.CrossHaar(K, M0)
+    v = rng.standard_normal((nm,) + shape)
+    assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-10, atol=1e-10)
+    # M^T is the transpose of M, and |M| dominates M elementwise
+    Md = dense(P.M, shape, nm)
+    assert np.allclose(dense(P.MT, shape, nm), Md.T, atol=1e-12 * np.abs(Md).max())
+    assert (dense(P.absM, shape, nm) >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all()
+
+
+def test_cross_haar_one_material_is_haar(oracle_lib):
+    """With one material the cross-material wavelet preconditioner is the Haar
+    preconditioner of Eq. 34 (same test functions, modulus, floor and M0)."""
+    import synth
+    from oracle import build, psps
+    g = Geometry(PAR2D, 16, 16, 1, 1.0, 1.0, 1.0, 24, 0.0, math.pi, 25, 1, 1.0, 1.0)
+    A = oracle_lib.Projector(g)
+    img = synth.render(g, [synth.Ellipse(0.5, -0.3, 5.0, 6.0, 0.2, 0.02)])
+    y = np.round(1e4 * np.exp(-A.project(img[None])))
+    st = psps.Setup(A, np.ones((1, 1)), np.full((1, 1), 1e4), y, np.array([[50.0]]))
+    Ph, Pc = build.build(st, "haar"), build.build(st, "block_haar")
+    v = np.random.default_rng(7).standard_normal((1,) + st.shape)
+    for op in ["M", "MT", "absM", "absMT"]:
+        a, b = getattr(Ph, op)(v), getattr(Pc, op)(v)
+        assert np.allclose(a, b, rtol=1e-10, atol=1e-12 * np.abs(a).max()), op
