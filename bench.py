@@ -54,6 +54,9 @@ WORKLOADS = {
     "c4_mbmd_512_blockfourier": ("config4_slice", "block_fourier",
                                  "512x512@0.5mm, 3 materials x 4 PC channels (101 energies), 3x3 blocks + "
                                  "cross-material Fourier"),
+    "c4_mbmd_512_blockhaar": ("config4_slice", "block_haar",
+                              "512x512@0.5mm, 3 materials x 4 PC channels (101 energies), 3x3 blocks + "
+                              "cross-material wavelet (Haar)"),
     "c4_mbmd_16slices_blockfourier": ("config4", "block_fourier",
                                       "16 slices 256^2..512^2 @0.5mm (seeded sizes), 720 views, 3 materials x 4 PC "
                                       "channels, 3x3 blocks + cross-material Fourier, one graph per batch iteration"),

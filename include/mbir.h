@@ -190,7 +190,8 @@ enum {
     PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U M0 (Eqs. 30-33)       */
     PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT M0 (Eq. 34)   */
     PSPS_PRECOND_BLOCK = 4,         /* per-pixel / per-ray N_k x N_k M0 (Eqs. 42, 54) */
-    PSPS_PRECOND_BLOCK_FOURIER = 5  /* cross-material Fourier (Eqs. 56-57)            */
+    PSPS_PRECOND_BLOCK_FOURIER = 5, /* cross-material Fourier (Eqs. 56-57)            */
+    PSPS_PRECOND_BLOCK_HAAR = 6     /* cross-material wavelet (Eqs. 58-61)            */
 };
 enum { PSPS_APPLY_M = 0, PSPS_APPLY_MT = 1, PSPS_APPLY_ABS_M = 2, PSPS_APPLY_ABS_MT = 3 };
 
@@ -200,7 +201,13 @@ enum { PSPS_APPLY_M = 0, PSPS_APPLY_MT = 1, PSPS_APPLY_ABS_M = 2, PSPS_APPLY_ABS
  * from Eq. 18 taken in modulus (the phase-corrected ratio is complex for a
  * shift-variant Hessian), clamped to >= 1e-6 of the largest.  Haar
  * eigenvalues use Eq. 18 with one test function per (level, subband, class of
- * a P x P position lattice).
+ * a P x P position lattice); the cross-material wavelet blocks (Eqs. 59-60)
+ * use the same test functions once per material.  Cross-material blocks are
+ * not symmetric: K^-1/2 and L^-1/2 are taken of their polar factors
+ * (K^T K)^1/2, Re (L^H L)^1/2, with the eigenvalue floor 1e-6 of the largest
+ * over all blocks.  HAAR and BLOCK_HAAR need a square power-of-two image;
+ * FOURIER kinds need sides 2^a 3^b 5^c 7^d <= 1024; 3-D volumes take BLOCK
+ * only (MBIR_ERR_UNIMPLEMENTED otherwise).
  * y: device [n_chan][n_rays]; beta: host [n_mat][n_mat] penalty strengths
  * (NULL = no penalty); haar_lattice: lattice size P of the Haar test
  * functions (0 = the paper's single U^T 1; 3 is the default); plan == NULL
@@ -218,6 +225,11 @@ mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spectrum *spec, 
  *     FOURIER).  lam is taken in modulus, clamped to >= 1e-6 of its largest
  *     and raised to -1/2 exactly as psps_precondition_build does.
  *   BLOCK: blocks = the M0 blocks themselves (device [n_mat][n_mat][n]).
+ *   BLOCK_FOURIER / BLOCK_HAAR (plan required): blocks = M0 as for BLOCK;
+ *     lam = the symmetric polar factors of the cross-material blocks, one
+ *     [n_mat][n_mat] block per DFT frequency ([ny][nx]) / Haar coefficient
+ *     (Mallat layout), device [n_mat][n_mat][n]; inverted with the same
+ *     global floor as the build.
  * n = pixels per material (plan) or rays (plan == NULL, BLOCK only).
  * Synchronises `stream`. */
 mbir_status psps_precondition_create(mbir_plan *plan, int kind, int n_mat, int64_t n, const float *lam,

@@ -14,7 +14,8 @@ MBIR_OK = 0
 STATUS = {0: "MBIR_OK", -1: "MBIR_ERR_ARG", -2: "MBIR_ERR_CUDA", -3: "MBIR_ERR_OOM", -4: "MBIR_ERR_NONFINITE",
           -5: "MBIR_ERR_TIMEOUT", -6: "MBIR_ERR_UNIMPLEMENTED"}
 
-PSPS_PRECOND = {"none": 0, "fourier": 1, "mod_fourier": 2, "haar": 3, "block": 4, "block_fourier": 5}
+PSPS_PRECOND = {"none": 0, "fourier": 1, "mod_fourier": 2, "haar": 3, "block": 4, "block_fourier": 5,
+                "block_haar": 6}
 PSPS_APPLY = {"M": 0, "MT": 1, "absM": 2, "absMT": 3}
 FLAG_LINESEARCH, FLAG_NONNEG, FLAG_GRAPH = 1, 2, 4
 PROF_STAGES = ["reproject", "model", "backproject", "precond", "project", "linesearch", "update"]

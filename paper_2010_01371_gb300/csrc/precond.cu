@@ -132,6 +132,20 @@ __global__ void masked_ratio_kernel(const float *mask, const float *r, const flo
         if (mask[i] != 0.f) lam[i] = r[i] / den[i];
 }
 
+// Column k of the cross-material wavelet blocks (Eqs. 59-60) at the
+// coefficients of one test set: K[m][k][j] = r[m][j] / den[j] where mask[j].
+__global__ void masked_block_ratio_kernel(const float *mask, const float *r, const float *den, float *K, int nm, int k,
+                                          int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (mask[i] != 0.f)
+            for (int m = 0; m < nm; ++m) K[((int64_t)m * nm + k) * n + i] = r[(int64_t)m * n + i] / den[i];
+}
+
+__global__ void to_complex_kernel(const float *in, float2 *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(in[i], 0.f);
+}
+
 // Symmetric inverse square root of nm x nm blocks (FP64, cyclic Jacobi).
 // H[a][b][j] full (both triangles); writes B and |B| as [a][b][j].
 __global__ void block_invsqrt_kernel(int nm, int64_t n, const float *__restrict__ H, double max_trace,
@@ -367,6 +381,29 @@ __global__ void invsqrt_floor_kernel(int nm, int64_t n, const float *__restrict_
         }
 }
 
+// The Haar test sets of an n x n image: one per (level block h, detail band,
+// lattice class (a, c) mod P), plus the final low-pass block; P = 0 gives the
+// paper's single all-ones set.
+struct HaarSet {
+    int h, band, a, c;
+};
+
+std::vector<HaarSet> haar_sets(int nx, int P) {
+    std::vector<HaarSet> sets;
+    if (P == 0) {
+        sets.push_back({nx, 0, 0, 0});
+        return sets;
+    }
+    for (int h = nx; h >= 2; h /= 2) {
+        const int h2 = h / 2;
+        for (int band = 0; band < 3; ++band)
+            for (int a = 0; a < (P < h2 ? P : h2); ++a)
+                for (int c = 0; c < (P < h2 ? P : h2); ++c) sets.push_back({h, band, a, c});
+    }
+    sets.push_back({2, 3, 0, 0});
+    return sets;
+}
+
 unsigned gs(int64_t n) {
     int64_t b = cdiv(n, kThreads);
     return (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
@@ -482,6 +519,24 @@ mbir_status finish_cross_fourier(psps_precond *pc, const float *P, const float *
     return MBIR_OK;
 }
 
+// Ki = P^-1/2 (global eigenvalue floor 1e-6 of the largest), |Ki| elementwise
+// (the wavelet-domain operator is block diagonal, so |.| acts per block).
+mbir_status finish_cross_haar(psps_precond *pc, const float *P, const float *lmax, cudaStream_t s) {
+    const int nm = pc->nm;
+    const int64_t n = pc->n;
+    double mx;
+    PSPS_TRY(host_max_abs(lmax, n, mx, s));
+    if (!(mx > 0) || !std::isfinite(mx)) return fail(MBIR_ERR_NONFINITE, "cross-material eigenvalues are not positive");
+    PSPS_TRY(pc->Li.alloc((size_t)nm * nm * n));
+    PSPS_TRY(pc->Li_abs.alloc((size_t)nm * nm * n));
+    invsqrt_floor_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(nm, n, P, 1e-6 * mx, pc->Li.p);
+    PSPS_LAUNCH_CHECK();
+    abs_copy_kernel<<<gs((int64_t)nm * nm * n), kThreads, 0, s>>>(pc->Li.p, pc->Li_abs.p, (int64_t)nm * nm * n);
+    PSPS_LAUNCH_CHECK();
+    PSPS_CUDA(cudaStreamSynchronize(s));
+    return MBIR_OK;
+}
+
 mbir_status launch_block_lmax(int nm, int64_t n, const float *P, float *lmax, cudaStream_t s) {
     block_lmax_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(nm, n, P, lmax);
     PSPS_LAUNCH_CHECK();
@@ -542,6 +597,23 @@ mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out,
             PSPS_LAUNCH_CHECK();
             return MBIR_OK;
         }
+        case PSPS_PRECOND_BLOCK_HAAR: {
+            // M = M0^T U^T K^-1/2 U M0 (Eq. 61), U per material; M^T swaps
+            // the blocks of K^-1/2; |M| uses |M0|, |U| and |K^-1/2|.
+            const float *Bm = absm ? pc->Babs.p : pc->B.p;
+            const unsigned amask = absm ? 0xffffffffu : 0u;
+            float *t0 = pc->tmp.p, *t1 = pc->tmp.p + pc->n * pc->nm;
+            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
+            PSPS_LAUNCH_CHECK();
+            PSPS_TRY(haar_forward(pc->nx, pc->nm, t0, t1, nullptr, nullptr, amask, s));
+            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Li_abs.p : pc->Li.p, t1, t0,
+                                                              tr ? 1 : 0);
+            PSPS_LAUNCH_CHECK();
+            PSPS_TRY(haar_inverse(pc->nx, pc->nm, t0, t1, nullptr, amask, s));
+            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
+            PSPS_LAUNCH_CHECK();
+            return MBIR_OK;
+        }
         default:
             return fail(MBIR_ERR_UNIMPLEMENTED, "preconditioner kind %d not built", pc->kind);
     }
@@ -581,10 +653,10 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         return fail(MBIR_ERR_ARG, "Fourier / modified Fourier / Haar preconditioners are single-material (n_mat = 1)");
     if (plan && plan->g.kind == MBIR_CONE3D && kind != PSPS_PRECOND_BLOCK)
         return fail(MBIR_ERR_UNIMPLEMENTED, "3-D volumes support the BLOCK preconditioner only");
-    if (kind == PSPS_PRECOND_HAAR && !haar_supported(pc->nx, plan->g.ny))
-        return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
-    if (kind == PSPS_PRECOND_HAAR && (haar_lattice < 0 || haar_lattice > 64))
-        return fail(MBIR_ERR_ARG, "haar_lattice must be 0..64");
+    const bool haar_kind = kind == PSPS_PRECOND_HAAR || kind == PSPS_PRECOND_BLOCK_HAAR;
+    if (haar_kind && !haar_supported(pc->nx, plan->g.ny))
+        return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048)");
+    if (haar_kind && (haar_lattice < 0 || haar_lattice > 64)) return fail(MBIR_ERR_ARG, "haar_lattice must be 0..64");
     if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_BLOCK_FOURIER)
         PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
 
@@ -676,6 +748,50 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_TRY(launch_polar(nm, n, Lc.p, P.p, lmax.p, s));
         return finish_cross_fourier(pc, P.p, lmax.p, s);
     }
+    if (kind == PSPS_PRECOND_BLOCK_HAAR) {
+        // K_k of Eqs. 59-60 with the lattice test functions: for every test
+        // set xi and material k, dx = U^T xi in material k; column k of the
+        // blocks of the set's coefficients = U M0^T H M0 dx / (U dx)
+        const int nx = pc->nx;
+        const std::vector<HaarSet> sets = haar_sets(nx, haar_lattice);
+        DBuf<float> K, mask, coef, dx, den, d, v, hv, r;
+        PSPS_TRY(K.alloc((size_t)nm * nm * n));
+        PSPS_TRY(mask.alloc(n));
+        PSPS_TRY(coef.alloc(n));
+        PSPS_TRY(dx.alloc(n));
+        PSPS_TRY(den.alloc(n));
+        PSPS_TRY(d.alloc((size_t)nm * n));
+        PSPS_TRY(v.alloc((size_t)nm * n));
+        PSPS_TRY(hv.alloc((size_t)nm * n));
+        PSPS_TRY(r.alloc((size_t)nm * n));
+        PSPS_CUDA(cudaMemsetAsync(K.p, 0, sizeof(float) * K.n, s));
+        for (const HaarSet &st : sets) {
+            haar_mask_kernel<<<gs(n), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.c, haar_lattice, mask.p);
+            PSPS_LAUNCH_CHECK();
+            PSPS_CUDA(cudaMemcpyAsync(coef.p, mask.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+            PSPS_TRY(haar_inverse(nx, 1, coef.p, dx.p, nullptr, 0u, s));
+            PSPS_TRY(haar_forward(nx, 1, dx.p, den.p, nullptr, nullptr, 0u, s));
+            for (int k = 0; k < nm; ++k) {
+                PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * nm * n, s));
+                PSPS_CUDA(cudaMemcpyAsync(d.p + (int64_t)k * n, dx.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+                PSPS_TRY(launch_block_apply(nm, n, pc->B.p, d.p, v.p, 0, s));
+                PSPS_TRY(H.apply(v.p, hv.p, 1, s));
+                PSPS_TRY(launch_block_apply(nm, n, pc->B.p, hv.p, v.p, 1, s));
+                PSPS_TRY(haar_forward(nx, nm, v.p, r.p, nullptr, nullptr, 0u, s));
+                masked_block_ratio_kernel<<<gs(n), kThreads, 0, s>>>(mask.p, r.p, den.p, K.p, nm, k, n);
+                PSPS_LAUNCH_CHECK();
+            }
+        }
+        DBuf<float2> Kc;
+        DBuf<float> P, lmax;
+        PSPS_TRY(Kc.alloc((size_t)nm * nm * n));
+        to_complex_kernel<<<gs((int64_t)nm * nm * n), kThreads, 0, s>>>(K.p, Kc.p, (int64_t)nm * nm * n);
+        PSPS_LAUNCH_CHECK();
+        PSPS_TRY(P.alloc((size_t)nm * nm * n));
+        PSPS_TRY(lmax.alloc(n));
+        PSPS_TRY(launch_polar(nm, n, Kc.p, P.p, lmax.p, s));
+        return finish_cross_haar(pc, P.p, lmax.p, s);
+    }
     // one material from here on: m0 = B
     PSPS_TRY(pc->m0.alloc(n));
     if (kind == PSPS_PRECOND_FOURIER) {
@@ -714,21 +830,7 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     // ---- Haar
     {
         const int P = haar_lattice;
-        struct Set {
-            int h, band, a, c;
-        };
-        std::vector<Set> sets;
-        if (P == 0) {
-            sets.push_back({nx, 0, 0, 0});
-        } else {
-            for (int h = nx; h >= 2; h /= 2) {
-                const int h2 = h / 2;
-                for (int band = 0; band < 3; ++band)
-                    for (int a = 0; a < (P < h2 ? P : h2); ++a)
-                        for (int c = 0; c < (P < h2 ? P : h2); ++c) sets.push_back({h, band, a, c});
-            }
-            sets.push_back({2, 3, 0, 0});
-        }
+        const std::vector<HaarSet> sets = haar_sets(nx, P);
         const int batch = plan->n_mat_max;
         DBuf<float> mask, dx, r, den, coef;
         PSPS_TRY(mask.alloc((size_t)batch * n));
@@ -742,7 +844,7 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         for (size_t s0 = 0; s0 < sets.size(); s0 += batch) {
             const int nb = (int)(sets.size() - s0 < (size_t)batch ? sets.size() - s0 : batch);
             for (int b = 0; b < nb; ++b) {
-                const Set &st = sets[s0 + b];
+                const HaarSet &st = sets[s0 + b];
                 haar_mask_kernel<<<gs(n), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.c, P, mask.p + (int64_t)b * n);
             }
             PSPS_LAUNCH_CHECK();
@@ -770,7 +872,7 @@ extern "C" mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spect
                                                psps_precond **out) {
     if (!spec || !y || !out) return fail(MBIR_ERR_ARG, "psps_precondition_build: null argument");
     *out = nullptr;
-    if (kind < PSPS_PRECOND_NONE || kind > PSPS_PRECOND_BLOCK_FOURIER)
+    if (kind < PSPS_PRECOND_NONE || kind > PSPS_PRECOND_BLOCK_HAAR)
         return fail(MBIR_ERR_ARG, "psps_precondition_build: unknown kind %d", kind);
     if (plan && n_rays != plan->n_rays) return fail(MBIR_ERR_ARG, "psps_precondition_build: n_rays does not match plan");
     if (n_rays < 1) return fail(MBIR_ERR_ARG, "psps_precondition_build: n_rays must be >= 1");
@@ -819,6 +921,21 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
         PSPS_TRY(launch_block_lmax(nm, n, lam, lmax.p, s));
         return finish_cross_fourier(pc, lam, lmax.p, s);
     }
+    if (kind == PSPS_PRECOND_BLOCK_HAAR) {
+        if (!plan || !lam || !blocks)
+            return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK_HAAR needs a plan, lam (P blocks) and blocks");
+        if (!haar_supported(plan->g.nx, plan->g.ny))
+            return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048)");
+        PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
+        PSPS_TRY(pc->Babs.alloc((size_t)nm * nm * n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->B.p, blocks, sizeof(float) * pc->B.n, cudaMemcpyDeviceToDevice, s));
+        PSPS_TRY(launch_abs_copy(blocks, pc->Babs.p, (int64_t)pc->B.n, s));
+        PSPS_TRY(pc->tmp.alloc((size_t)n * nm * 2));
+        DBuf<float> lmax;
+        PSPS_TRY(lmax.alloc(n));
+        PSPS_TRY(launch_block_lmax(nm, n, lam, lmax.p, s));
+        return finish_cross_haar(pc, lam, lmax.p, s);
+    }
     if (!plan || nm != 1 || !lam)
         return fail(MBIR_ERR_ARG, "psps_precondition_create: Fourier/Haar kinds need a plan, n_mat = 1 and lam");
     if (kind == PSPS_PRECOND_HAAR && !haar_supported(plan->g.nx, plan->g.ny))
@@ -847,7 +964,7 @@ extern "C" mbir_status psps_precondition_create(mbir_plan *plan, int kind, int n
                                                 psps_precond **out) {
     if (!out) return fail(MBIR_ERR_ARG, "psps_precondition_create: null out");
     *out = nullptr;
-    if (kind < PSPS_PRECOND_NONE || kind > PSPS_PRECOND_BLOCK_FOURIER)
+    if (kind < PSPS_PRECOND_NONE || kind > PSPS_PRECOND_BLOCK_HAAR)
         return fail(MBIR_ERR_ARG, "psps_precondition_create: unknown kind %d", kind);
     if (n_mat < 1 || n_mat > 4) return fail(MBIR_ERR_ARG, "psps_precondition_create: n_mat must be 1..4");
     if (plan && n != plan->n_pix) return fail(MBIR_ERR_ARG, "psps_precondition_create: n must equal the plan's pixels");

@@ -82,6 +82,12 @@ def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True):
         P = precond.polar_real(L)
         lam = np.ascontiguousarray(np.transpose(P.reshape(-1, st.nm, st.nm), (1, 2, 0)))
         return st, precond.CrossFourier(L, M0), {"lam": lam, "blocks": blocks}
+    if kind == "block_haar":
+        M0 = precond.Block(B, st.shape)
+        K = precond.cross_haar_blocks(aH, M0, st.shape, st.nm, lattice)
+        P = precond.polar_real(K)
+        lam = np.ascontiguousarray(np.transpose(P.reshape(-1, st.nm, st.nm), (1, 2, 0)))
+        return st, precond.CrossHaar(K, M0), {"lam": lam, "blocks": blocks}
     m0 = B[:, 0, 0].reshape(st.shape)
 
     def aN(v):

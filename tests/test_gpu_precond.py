@@ -61,11 +61,12 @@ def test_build_parity(psps, oracle_lib, pname, kind):
     check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOL)
 
 
-@pytest.mark.parametrize("kind", ["block", "block_fourier"])
+@pytest.mark.parametrize("kind", ["block", "block_fourier", "block_haar"])
 def test_mbmd_apply_and_build(psps, oracle_lib, kind):
-    """One-step MBMD (3 materials): per-pixel 3x3 blocks and the cross-material
-    Fourier preconditioner (Eq. 57), created from the oracle's data (apply
-    tolerance) and built on the GPU (build tolerance)."""
+    """One-step MBMD (3 materials): per-pixel 3x3 blocks, the cross-material
+    Fourier (Eq. 57) and the cross-material wavelet (Eq. 61) preconditioners,
+    created from the oracle's data (apply tolerance) and built on the GPU
+    (build tolerance)."""
     prob = synth.config4_slice(nx=64, n_views=90, n_u=111)
     st, P, data = oracle_precond(oracle_lib, prob, kind)
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)

@@ -118,6 +118,7 @@ def step_cases():
             "c1-block": (c1, "block", True), "c2-haar": (c2, "haar", True), "c2-none": (c2, "none", True),
             "c3-block": (c3, "block", False),
             "c4-block": (c4, "block", True), "c4-block_fourier": (c4, "block_fourier", True),
+            "c4-block_haar": (c4, "block_haar", True),
             "c5-block": (c5, "block", True)}
 
 
