@@ -62,6 +62,8 @@ WORKLOADS = {
                                       "channels, 3x3 blocks + cross-material Fourier, one graph per batch iteration"),
     "c5_cone3d_256_block": ("config5", "block", "256^3@0.5mm, 360x384x512 cone flat, 2 materials x 2 kVp, 2x2 "
                                                 "per-voxel blocks"),
+    "c5_cone3d_256_blockfourier": ("config5", "block_fourier", "256^3@0.5mm, 360x384x512 cone flat, 2 materials x "
+                                                              "2 kVp, 2x2 per-voxel blocks + 3-D cross-material Fourier"),
     "c5_cone3d_128_block": ("config5", "block", "128^3@1mm, 180x192x256 cone flat (the 256^3 scan scaled down), "
                                                 "2 materials x 2 kVp, 2x2 per-voxel blocks",
                             {"n": 128, "n_views": 180, "n_u": 256, "n_v": 192}),

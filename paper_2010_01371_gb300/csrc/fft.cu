@@ -245,13 +245,16 @@ bool fft_supported(int n) {
     return n >= 2 && n <= 1024 && factor(n, r);
 }
 
-mbir_status FftPlan::init(int nx_, int ny_) {
+mbir_status FftPlan::init(int nx_, int ny_, int nz_) {
     nx = nx_;
     ny = ny_;
-    if (!fft_supported(nx) || !fft_supported(ny))
-        return fail(MBIR_ERR_UNIMPLEMENTED, "FFT sizes must be 2^a 3^b 5^c 7^d in 2..1024 (got %d x %d)", nx, ny);
-    for (int a = 0; a < 2; ++a) {
-        const int N = a == 0 ? nx : ny;
+    nz = nz_;
+    if (!fft_supported(nx) || !fft_supported(ny) || (nz > 1 && !fft_supported(nz)))
+        return fail(MBIR_ERR_UNIMPLEMENTED, "FFT sizes must be 2^a 3^b 5^c 7^d in 2..1024 (got %d x %d x %d)", nx, ny,
+                    nz);
+    for (int a = 0; a < 3; ++a) {
+        const int N = a == 0 ? nx : (a == 1 ? ny : nz);
+        if (a == 2 && nz <= 1) break;
         std::vector<float2> h(N + kRoots);
         for (int k = 0; k < N; ++k) {
             const double ang = -2.0 * M_PI * (double)k / (double)N;
@@ -263,7 +266,7 @@ mbir_status FftPlan::init(int nx_, int ny_) {
                 const double ang = -2.0 * M_PI * (double)k / (double)radix[q];
                 h[N + off[q] + k] = make_float2((float)cos(ang), (float)sin(ang));
             }
-        DBuf<float2> &t = a == 0 ? twx : twy;
+        DBuf<float2> &t = a == 0 ? twx : (a == 1 ? twy : twz);
         PSPS_TRY(t.alloc(N + kRoots));
         PSPS_CUDA(cudaMemcpy(t.p, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice));
     }
@@ -275,71 +278,62 @@ mbir_status FftPlan::init(int nx_, int ny_) {
     return MBIR_OK;
 }
 
+// One pass of 1-D transforms along axis 0 (x, rows), 1 (y, columns) or 2 (z)
+// of [channels][nz][ny][nx] data; see fft_pass_kernel for the modes.  A
+// spectral multiply (mode 1) reads spec[z][y][x].
+mbir_status FftPlan::run(int axis, int mode, int channels, const float *rin, float2 *Z, float *rout,
+                         const float *pre_post, const float *spec, cudaStream_t s) const {
+    const int64_t plane = (int64_t)nx * ny, nvox = plane * nz;
+    Pass p;
+    dim3 grid;
+    int64_t sks = 0, sbs = 0;
+    const float2 *tw;
+    if (axis == 0) {
+        p = make_pass(nx, 1, nx, ny * nz, nvox);
+        grid = dim3((unsigned)cdiv((int64_t)ny * nz, p.B), channels);
+        tw = twx.p;
+    } else if (axis == 1) {
+        p = make_pass(ny, nx, 1, nx, plane);   // every z-plane of every channel is its own batch
+        grid = dim3((unsigned)cdiv(nx, p.B), channels * nz);
+        sks = nx, sbs = 1;
+        tw = twy.p;
+    } else {
+        p = make_pass(nz, plane, 1, (int)plane, nvox);
+        grid = dim3((unsigned)cdiv(plane, p.B), channels);
+        sks = plane, sbs = 1;
+        tw = twz.p;
+    }
+    const size_t sm = 2 * sizeof(float2) * p.N * p.B;
+    fft_pass_kernel<<<grid, kThreads, sm, s>>>(p, mode, rin, Z, rout, pre_post, spec, sks, sbs,
+                                               (float)(1.0 / (double)nvox), tw);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
 mbir_status FftPlan::forward(int channels, const float *in, float2 *Z, cudaStream_t s) const {
-    const int64_t npix = (int64_t)nx * ny;
-    {
-        const Pass p = make_pass(nx, 1, nx, ny, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(p, 0, in, Z, nullptr, nullptr,
-                                                                                    nullptr, 0, 0, 1.f, twx.p);
-        PSPS_LAUNCH_CHECK();
-    }
-    {
-        const Pass p = make_pass(ny, nx, 1, nx, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 3, nullptr, Z, nullptr, nullptr,
-                                                                                    nullptr, 0, 0, 1.f, twy.p);
-        PSPS_LAUNCH_CHECK();
-    }
+    PSPS_TRY(run(0, 0, channels, in, Z, nullptr, nullptr, nullptr, s));
+    PSPS_TRY(run(1, 3, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
+    if (nz > 1) PSPS_TRY(run(2, 3, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
     return MBIR_OK;
 }
 
 mbir_status FftPlan::inverse(int channels, float2 *Z, float *out, const float *post, cudaStream_t s) const {
-    const int64_t npix = (int64_t)nx * ny;
-    {
-        const Pass p = make_pass(ny, nx, 1, nx, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 4, nullptr, Z, nullptr, nullptr,
-                                                                                    nullptr, 0, 0, 1.f, twy.p);
-        PSPS_LAUNCH_CHECK();
-    }
-    {
-        const Pass p = make_pass(nx, 1, nx, ny, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(
-            p, 2, nullptr, Z, out, post, nullptr, 0, 0, (float)(1.0 / (double)npix), twx.p);
-        PSPS_LAUNCH_CHECK();
-    }
-    return MBIR_OK;
+    if (nz > 1) PSPS_TRY(run(2, 4, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
+    PSPS_TRY(run(1, 4, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
+    return run(0, 2, channels, nullptr, Z, out, post, nullptr, s);
 }
 
 mbir_status FftPlan::filter(int channels, const float *in, float2 *Z, float *out, const float *m0, const float *spec,
                             cudaStream_t s) const {
-    const int64_t npix = (int64_t)nx * ny;
-    // rows: ny transforms of length nx, element stride 1, batch stride nx
-    {
-        const Pass p = make_pass(nx, 1, nx, ny, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(p, 0, in, Z, nullptr, m0, nullptr,
-                                                                                    0, 0, 1.f, twx.p);
-        PSPS_LAUNCH_CHECK();
+    PSPS_TRY(run(0, 0, channels, in, Z, nullptr, m0, nullptr, s));
+    if (nz > 1) {
+        PSPS_TRY(run(1, 3, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
+        PSPS_TRY(run(2, 1, channels, nullptr, Z, nullptr, nullptr, spec, s));   // forward, multiply, inverse in z
+        PSPS_TRY(run(1, 4, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
+    } else {
+        PSPS_TRY(run(1, 1, channels, nullptr, Z, nullptr, nullptr, spec, s));   // forward, multiply, inverse in y
     }
-    // columns: nx transforms of length ny, element stride nx, batch stride 1
-    {
-        const Pass p = make_pass(ny, nx, 1, nx, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(nx, p.B), channels), kThreads, sm, s>>>(p, 1, nullptr, Z, nullptr, nullptr,
-                                                                                    spec, nx, 1, 1.f, twy.p);
-        PSPS_LAUNCH_CHECK();
-    }
-    {
-        const Pass p = make_pass(nx, 1, nx, ny, npix);
-        const size_t sm = 2 * sizeof(float2) * p.N * p.B;
-        fft_pass_kernel<<<dim3((unsigned)cdiv(ny, p.B), channels), kThreads, sm, s>>>(
-            p, 2, nullptr, Z, out, m0, nullptr, 0, 0, (float)(1.0 / (double)npix), twx.p);
-        PSPS_LAUNCH_CHECK();
-    }
-    return MBIR_OK;
+    return run(0, 2, channels, nullptr, Z, out, m0, nullptr, s);
 }
 
 }  // namespace psps

@@ -284,12 +284,14 @@ __global__ void mix_kernel(int nm, int64_t n, const float *__restrict__ L, float
 }
 
 // Lc[a][k][f] = Z[a][f] / DFT(delta_c)(f) = Z[a][f] exp(+2 pi i (fy cy/ny + fx cx/nx))
-__global__ void phase_kernel(int nm, int nx, int ny, int cx, int cy, const float2 *__restrict__ Z, int k,
-                             float2 *__restrict__ Lc) {
-    const int64_t n = (int64_t)nx * ny;
+__global__ void phase_kernel(int nm, int nx, int ny, int nz, int cx, int cy, int cz, const float2 *__restrict__ Z,
+                             int k, float2 *__restrict__ Lc) {
+    const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
-        const int fy = (int)(f / nx), fx = (int)(f % nx);
-        const double ang = 2.0 * M_PI * ((double)((int64_t)fy * cy % ny) / ny + (double)((int64_t)fx * cx % nx) / nx);
+        const int fx = (int)(f % nx), fy = (int)((f / nx) % ny), fz = (int)(f / ((int64_t)nx * ny));
+        const double ang = 2.0 * M_PI *
+                           ((double)((int64_t)fz * cz % nz) / nz + (double)((int64_t)fy * cy % ny) / ny +
+                            (double)((int64_t)fx * cx % nx) / nx);
         double sn, cs;
         sincos(ang, &sn, &cs);
         for (int a = 0; a < nm; ++a) {
@@ -549,8 +551,8 @@ mbir_status launch_polar(int nm, int64_t n, const float2 *Lc, float *P, float *l
     return MBIR_OK;
 }
 
-mbir_status launch_phase(int nm, int nx, int ny, const float2 *Z, int k, float2 *Lc, cudaStream_t s) {
-    phase_kernel<<<gs((int64_t)nx * ny), kThreads, 0, s>>>(nm, nx, ny, nx / 2, ny / 2, Z, k, Lc);
+mbir_status launch_phase(int nm, int nx, int ny, int nz, const float2 *Z, int k, float2 *Lc, cudaStream_t s) {
+    phase_kernel<<<gs((int64_t)nx * ny * nz), kThreads, 0, s>>>(nm, nx, ny, nz, nx / 2, ny / 2, nz / 2, Z, k, Lc);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
 }
@@ -639,7 +641,8 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     pc->image = plan != nullptr;
     if (plan) {
         pc->nx = plan->g.nx;
-        pc->ny = plan->g.ny * (plan->g.kind == MBIR_CONE3D ? plan->g.nz : 1);
+        pc->ny = plan->g.ny;
+        pc->nz = plan->g.kind == MBIR_CONE3D ? plan->g.nz : 1;
         pc->n = plan->n_pix;
     } else {
         pc->nx = (int)n_rays;
@@ -651,16 +654,18 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         return fail(MBIR_ERR_ARG, "projection-domain decomposition supports NONE and BLOCK preconditioners");
     if ((kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_HAAR) && nm != 1)
         return fail(MBIR_ERR_ARG, "Fourier / modified Fourier / Haar preconditioners are single-material (n_mat = 1)");
-    if (plan && plan->g.kind == MBIR_CONE3D && kind != PSPS_PRECOND_BLOCK)
-        return fail(MBIR_ERR_UNIMPLEMENTED, "3-D volumes support the BLOCK preconditioner only");
+    if (plan && plan->g.kind == MBIR_CONE3D && (kind == PSPS_PRECOND_HAAR || kind == PSPS_PRECOND_BLOCK_HAAR))
+        return fail(MBIR_ERR_UNIMPLEMENTED, "Haar preconditioners are 2-D (3-D volumes: BLOCK and the Fourier kinds)");
     const bool haar_kind = kind == PSPS_PRECOND_HAAR || kind == PSPS_PRECOND_BLOCK_HAAR;
     if (haar_kind && !haar_supported(pc->nx, plan->g.ny))
         return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048)");
     if (haar_kind && (haar_lattice < 0 || haar_lattice > 64)) return fail(MBIR_ERR_ARG, "haar_lattice must be 0..64");
     if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_BLOCK_FOURIER)
-        PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+        PSPS_TRY(pc->fft.init(pc->nx, pc->ny, pc->nz));
 
     const int64_t n = pc->n;
+    // the impulse of the Fourier estimates sits at the centre voxel
+    const int64_t centre = ((int64_t)(pc->nz / 2) * pc->ny + pc->ny / 2) * pc->nx + pc->nx / 2;
     const int nF = nm * (nm + 1) / 2;
     DBuf<float> F;
     PSPS_TRY(F.alloc((size_t)nF * n_rays));
@@ -727,7 +732,6 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     if (kind == PSPS_PRECOND_BLOCK_FOURIER) {
         // L_k of Eq. 56: DFT of M0^T H M0 delta_{c,k} over DFT(delta_c), for
         // each material k with the impulse at the centre pixel c
-        const int nx = pc->nx, ny = pc->ny;
         DBuf<float2> Lc;
         DBuf<float> d, v, hv, P, lmax;
         PSPS_TRY(Lc.alloc((size_t)nm * nm * n));
@@ -736,12 +740,12 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_TRY(hv.alloc((size_t)nm * n));
         for (int k = 0; k < nm; ++k) {
             PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * nm * n, s));
-            set_value_kernel<<<1, 1, 0, s>>>(d.p, (int64_t)k * n + (int64_t)(ny / 2) * nx + nx / 2, 1.f);
+            set_value_kernel<<<1, 1, 0, s>>>(d.p, (int64_t)k * n + centre, 1.f);
             PSPS_TRY(launch_block_apply(nm, n, pc->B.p, d.p, v.p, 0, s));
             PSPS_TRY(H.apply(v.p, hv.p, 1, s));
             PSPS_TRY(launch_block_apply(nm, n, pc->B.p, hv.p, v.p, 1, s));
             PSPS_TRY(pc->fft.forward(nm, v.p, pc->Z.p, s));
-            PSPS_TRY(launch_phase(nm, nx, ny, pc->Z.p, k, Lc.p, s));
+            PSPS_TRY(launch_phase(nm, pc->nx, pc->ny, pc->nz, pc->Z.p, k, Lc.p, s));
         }
         PSPS_TRY(P.alloc((size_t)nm * nm * n));
         PSPS_TRY(lmax.alloc(n));
@@ -800,7 +804,7 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_CUDA(cudaMemcpyAsync(pc->m0.p, pc->B.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
     }
     const float *m0 = pc->m0.p;
-    const int nx = pc->nx, ny = plan->g.ny;
+    const int nx = pc->nx;
     // N v = m0 .* H (m0 .* v)
     auto applyN = [&](const float *v, float *out, int nprobe) -> mbir_status {
         float *w = pc->tmp.p;  // nprobe * n
@@ -818,7 +822,7 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_TRY(d.alloc(n));
         PSPS_TRY(r.alloc(n));
         PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * n, s));
-        set_value_kernel<<<1, 1, 0, s>>>(d.p, (int64_t)(ny / 2) * nx + nx / 2, 1.f);
+        set_value_kernel<<<1, 1, 0, s>>>(d.p, centre, 1.f);
         PSPS_TRY(applyN(d.p, r.p, 1));
         PSPS_TRY(pc->fft.forward(1, r.p, pc->Z.p, s));
         modulus_kernel<<<gs(n), kThreads, 0, s>>>(pc->Z.p, lam.p, n);
@@ -895,7 +899,8 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
     pc->image = plan != nullptr;
     pc->n = n;
     pc->nx = plan ? plan->g.nx : (int)n;
-    pc->ny = plan ? (int)(n / plan->g.nx) : 1;
+    pc->ny = plan ? plan->g.ny : 1;
+    pc->nz = plan && plan->g.kind == MBIR_CONE3D ? plan->g.nz : 1;
     if (kind == PSPS_PRECOND_NONE) return MBIR_OK;
     if (kind == PSPS_PRECOND_BLOCK) {
         if (!blocks) return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK needs blocks");
@@ -909,7 +914,7 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
     if (kind == PSPS_PRECOND_BLOCK_FOURIER) {
         if (!plan || !lam || !blocks)
             return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK_FOURIER needs a plan, lam (P blocks) and blocks");
-        PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+        PSPS_TRY(pc->fft.init(pc->nx, pc->ny, pc->nz));
         PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
         PSPS_TRY(pc->Babs.alloc((size_t)nm * nm * n));
         PSPS_CUDA(cudaMemcpyAsync(pc->B.p, blocks, sizeof(float) * pc->B.n, cudaMemcpyDeviceToDevice, s));
@@ -924,6 +929,7 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
     if (kind == PSPS_PRECOND_BLOCK_HAAR) {
         if (!plan || !lam || !blocks)
             return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK_HAAR needs a plan, lam (P blocks) and blocks");
+        if (plan->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "Haar preconditioners are 2-D");
         if (!haar_supported(plan->g.nx, plan->g.ny))
             return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048)");
         PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
@@ -938,9 +944,12 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
     }
     if (!plan || nm != 1 || !lam)
         return fail(MBIR_ERR_ARG, "psps_precondition_create: Fourier/Haar kinds need a plan, n_mat = 1 and lam");
+    if (kind == PSPS_PRECOND_HAAR && plan->g.kind == MBIR_CONE3D)
+        return fail(MBIR_ERR_UNIMPLEMENTED, "Haar preconditioners are 2-D");
     if (kind == PSPS_PRECOND_HAAR && !haar_supported(plan->g.nx, plan->g.ny))
         return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
-    if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER) PSPS_TRY(pc->fft.init(pc->nx, pc->ny));
+    if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER)
+        PSPS_TRY(pc->fft.init(pc->nx, pc->ny, pc->nz));
     PSPS_TRY(pc->tmp.alloc((size_t)n * 4));
     PSPS_TRY(pc->Z.alloc((size_t)n * 2));
     PSPS_TRY(pc->s.alloc(n));

@@ -7,7 +7,7 @@ struct psps_precond {
     int kind = PSPS_PRECOND_NONE;
     int nm = 1;
     bool image = true;       // false: projection-domain unknowns [nm][n_rays]
-    int nx = 1, ny = 1;
+    int nx = 1, ny = 1, nz = 1;  // image grid (nz = 1: 2-D)
     int64_t n = 0;           // unknowns per material
     psps::DBuf<float> m0;    // diagonal zero-frequency normalisation (one material)
     psps::DBuf<float> s, s_abs;  // spectra / wavelet-domain scales

@@ -128,3 +128,36 @@ def test_mixed_radix_cross_material(psps, oracle_lib, n):
     shape = (3,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, "block_fourier", data), P, shape, APPLY_TOL)
     check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+
+
+def cone_mbir_problem():
+    """One-material cone-beam problem on the 32^3 scaled-down config-5 scan."""
+    g = synth.config5(n=32, n_views=24, n_u=64, n_v=48, rays=False).geom
+    shapes = [synth.Ellipsoid(0.0, 0.0, 0.0, 50.0, 40.0, 45.0, 0.3, 0.02),
+              synth.Ellipsoid(15.0, -10.0, 5.0, 12.0, 9.0, 10.0, 0.0, 0.01)]
+    return synth.mbir_problem(5, g, shapes, 1e4, 1e3, 50, "fourier", "cone_mbir_32")
+
+
+@pytest.mark.parametrize("kind", ["fourier", "mod_fourier"])
+def test_3d_fourier(psps, oracle_lib, kind):
+    """3-D Fourier preconditioners (Eqs. 27-33 over the voxel grid, 3-D FFT):
+    apply from the oracle's spectrum and GPU build."""
+    prob = cone_mbir_problem()
+    st, P, data = oracle_precond(oracle_lib, prob, kind)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (1,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+
+
+def test_3d_cross_material_fourier(psps, oracle_lib):
+    """Cross-material Fourier (Eq. 57) over the voxel grid with per-voxel 2x2
+    M0 on the two-material cone-beam workload (32^3)."""
+    prob = synth.config5(n=32, n_views=24, n_u=64, n_v=48)
+    st, P, data = oracle_precond(oracle_lib, prob, "block_fourier")
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (2,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, "block_fourier", data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    with pytest.raises(RuntimeError):
+        psps.Precond(plan, spec, "block_haar", to_dev(prob.y), prob.beta)

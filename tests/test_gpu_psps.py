@@ -119,7 +119,7 @@ def step_cases():
             "c3-block": (c3, "block", False),
             "c4-block": (c4, "block", True), "c4-block_fourier": (c4, "block_fourier", True),
             "c4-block_haar": (c4, "block_haar", True),
-            "c5-block": (c5, "block", True)}
+            "c5-block": (c5, "block", True), "c5-block_fourier": (c5, "block_fourier", True)}
 
 
 @pytest.mark.parametrize("case", list(step_cases()))
