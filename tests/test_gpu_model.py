@@ -101,3 +101,64 @@ def test_autograd_adjoint(psps, oracle_lib):
     fd = (fp - fm) / (2 * h)
     an = float(np.sum(want * v))
     assert abs(fd - an) <= 1e-3 * abs(an)
+
+
+def test_full_size_projection_domain(psps, oracle_lib):
+    """Full projection-domain workload (720 x 888 rays, 2 materials x 2 kVp,
+    121 energies): the per-ray gradient numerators of every ray and the data
+    term over all rays against the oracle."""
+    from oracle import model
+    prob = synth.config3()
+    l = 0.7 * prob.truth
+    spec = psps.Spectrum(prob.Q, prob.S)
+    grad, obj = psps.mbmd_gradient(None, spec, to_dev(l), to_dev(prob.y))
+    want = model.data_grad_l(prob.Q, prob.S, l, prob.y)
+    assert rel_l2(to_host(grad), want) < 1e-5, rel_l2(to_host(grad), want)
+    want_obj = model.data_objective(prob.Q, prob.S, l, prob.y)
+    assert abs(float(obj.item()) - want_obj) <= 1e-5 * abs(want_obj)
+
+
+def test_full_size_mbmd_slice(psps, oracle_lib):
+    """Full 512^2 one-step MBMD slice (3 materials, 4 photon-counting
+    channels, 101 energies, 720 x 888 fan beam): data term and image gradient
+    A^T g against the oracle."""
+    from oracle import model
+    prob = synth.config4_slice()
+    A = oracle_lib.Projector(prob.geom)
+    x = 0.8 * prob.truth
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    grad, obj = psps.mbmd_gradient(plan, spec, to_dev(x), to_dev(prob.y))
+    lx = A.project(x)
+    want = A.backproject(model.data_grad_l(prob.Q, prob.S, lx, prob.y))
+    assert rel_l2(to_host(grad), want) < 1e-5, rel_l2(to_host(grad), want)
+    want_obj = model.data_objective(prob.Q, prob.S, lx, prob.y)
+    assert abs(float(obj.item()) - want_obj) <= 1e-5 * abs(want_obj)
+
+
+def test_size_limits_and_degenerate_counts(psps, oracle_lib):
+    """Largest spectral sizes the library takes (4 materials, 256 energies, 8
+    channels), counts that are all zero (w = 1) and a single ray; sizes past
+    the limits are rejected."""
+    from oracle import model
+    rng = np.random.default_rng(21)
+    E = np.linspace(15.0, 150.0, 256)
+    Q = synth.material_Q(E, ["water", "bone", "iodine", "water"], rng)
+    edges = np.linspace(15.0, 151.0, 9)
+    S = np.stack([1e4 * synth.kramers(E, 150.0) * ((E >= a) & (E < b)) for a, b in zip(edges[:-1], edges[1:])])
+    l = np.stack([rng.uniform(0, 100, 777), rng.uniform(0, 10, 777), rng.uniform(0, 0.5, 777),
+                  rng.uniform(0, 50, 777)])
+    spec = psps.Spectrum(Q, S)
+    got = to_host(psps.mbmd_forward_model(spec, to_dev(l)))
+    assert rel_l2(got, model.forward_model(Q, S, l)) < 1e-5
+    for y in [np.zeros((8, 777)), rng.poisson(model.forward_model(Q, S, 1.1 * l)).astype(float)]:
+        grad, obj = psps.mbmd_gradient(None, spec, to_dev(l), to_dev(y))
+        assert rel_l2(to_host(grad), model.data_grad_l(Q, S, l, y)) < 1e-5
+        want = model.data_objective(Q, S, l, y)
+        assert abs(float(obj.item()) - want) <= 1e-5 * abs(want)
+    one = l[:, :1]
+    grad, obj = psps.mbmd_gradient(None, spec, to_dev(one), to_dev(np.ones((8, 1))))
+    assert rel_l2(to_host(grad), model.data_grad_l(Q, S, one, np.ones((8, 1)))) < 1e-5
+    with pytest.raises(RuntimeError):
+        psps.Spectrum(np.ones((257, 1)), np.ones((1, 257)))
+    with pytest.raises(RuntimeError):
+        psps.Spectrum(np.ones((4, 5)), np.ones((1, 4)))

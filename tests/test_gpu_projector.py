@@ -1,9 +1,12 @@
 """GPU Joseph projector / backprojector parity with the FP64 oracle."""
+import math
+
 import numpy as np
 import pytest
 
 import synth
 from _helpers import cone_geoms, phantom, rel_l2, small_geoms, to_dev, to_host
+from synth import FAN2D, PAR2D, Geometry
 
 pytestmark = pytest.mark.gpu
 
@@ -218,3 +221,25 @@ def test_autotune_keeps_parity(psps, oracle_lib):
     assert rel_l2(got, oracle_lib.Projector(g).backproject(s)) < TOL
     with pytest.raises(RuntimeError):
         plan.autotune(0)
+
+
+def test_degenerate_geometries(psps, oracle_lib):
+    """One view of one bin, a single-pixel image and a one-column image:
+    forward and transpose against the oracle in every transpose mode."""
+    cases = [
+        Geometry(PAR2D, 9, 7, 1, 1.0, 1.0, 1.0, 1, 0.3, math.pi, 1, 1, 1.0, 1.0),
+        Geometry(PAR2D, 1, 1, 1, 1.0, 1.0, 1.0, 5, 0.0, math.pi, 3, 1, 0.7, 1.0),
+        Geometry(FAN2D, 1, 16, 1, 1.0, 1.0, 1.0, 7, 0.1, 2 * math.pi, 11, 1, 1.0, 1.0, 60.0, 120.0),
+    ]
+    for g in cases:
+        x = phantom(g, seed=5, nm=1) + 0.1
+        A = oracle_lib.Projector(g)
+        for mode in ["tile", "ray"]:
+            plan = psps.Plan(g)
+            plan.set_projector(mode)
+            assert rel_l2(to_host(psps.mbir_project(plan, to_dev(x))), A.project(x)) < TOL
+        s = np.random.default_rng(6).random((2, g.n_rays))
+        for mode in ["tile", "gather", "atomic"]:
+            plan = psps.Plan(g)
+            plan.set_backprojector(mode)
+            assert rel_l2(to_host(psps.mbir_backproject(plan, to_dev(s))), A.backproject(s)) < TOL, (g, mode)

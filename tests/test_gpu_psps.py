@@ -254,3 +254,30 @@ def test_batch_matches_single_states(psps):
     other = psps.State(plan, spec, None, yd, p.beta)
     with pytest.raises(RuntimeError):
         psps.Batch([states[0], other])
+
+
+def test_full_size_step(psps, oracle_lib):
+    """The full 512^2 / 720 x 888 fan-beam workload in the launch
+    configuration the benchmark times (CUDA graph, line search): two
+    iterations from x = 0 with the per-pixel M0 preconditioner created from
+    the oracle's blocks, against the oracle's two iterations."""
+    from oracle import psps as opsps
+    prob = synth.config2()
+    st, P, data = oracle_precond(oracle_lib, prob, "block")
+    xo, ho, ao = opsps.run(st, P, 2, opsps.LineSearch(), return_alphas=True)
+    state, keep = gpu_state(psps, prob, "block", data, graph=True)
+    hg = psps.psps_step(state, 2)
+    ag = psps.psps_get_alphas(state, 2)
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL, (hg, ho)
+    assert np.allclose(ag, ao, rtol=1e-4), (ag, ao)
+    assert rel_l2(to_host(psps.psps_get_image(state)), xo) < IMG_TOL
+
+
+def test_zero_iterations(psps):
+    """psps_step with n_iter = 0 returns the objective at x0 only."""
+    prob = synth.config1()
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    st = psps.State(plan, spec, None, to_dev(prob.y), prob.beta)
+    h = psps.psps_step(st, 0)
+    assert h.shape == (1,) and np.isfinite(h[0]) and h[0] > 0
+    assert np.array_equal(psps.psps_step(st, 0), h)
