@@ -209,6 +209,7 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
     spec = p.Spectrum(prob.Q, prob.S)
     beta = prob.beta if plan is not None else None
     pc = p.Precond(plan, spec, kind, yd, beta)
+    tuned = plan.autotune(2 * prob.Q.shape[1]) if plan is not None else None
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     st = p.State(plan, spec, pc, yd, beta, line_search=True, graph=True)
@@ -292,7 +293,8 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "problem": desc or WORKLOADS[workload][2], "precond": kind,
                        "line_search": True, "graph": True,
-                       "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3)},
+                       "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3),
+                       "views_per_cta": tuned},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline,
             "e2e": {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": int(y_host.numel() * 4),
                     "d2h_bytes_per_step": 2 * 8 + DEVLS_BYTES}}

@@ -112,13 +112,14 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
  * for another mode. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 /* Views handled by one CTA of the tile transpose (mode 0), 1..180: the
- * grid is (image tiles) x ceil(n_views / views_per_cta) CTAs.  Only changes
+ * grid is (image tiles) x ceil(n_views / views_per_cta) CTAs.  The plan's
+ * default aims at about six CTAs per SM (4..60 views).  Only changes
  * the work split (and the FP32 summation order), not the result's definition.
  * MBIR_ERR_ARG outside 1..180. */
 mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
 /* Autotuner: times the 2-D tile transpose (n_channels channels, zero data, a
  * warm-up and three launches per candidate, CUDA events on `stream`) for
- * 30/45/60/90/120/180 views per CTA and keeps the fastest in the plan
+ * 4/8/15/30/45/60/90/120/180 views per CTA and keeps the fastest in the plan
  * (written to *views_per_cta if non-NULL).  Synchronises; allocates and frees
  * temporary device buffers; not allowed while `stream` is capturing
  * (MBIR_ERR_ARG).  Cone-beam plans have nothing to tune and return at once.

@@ -215,9 +215,17 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-int pick_B(int N) {
-    // about 4096 complex values per CTA in each of the two buffers
-    int B = 4096 / N;
+// Transforms per CTA: at most ~4096 complex values per buffer, and few
+// enough that the grid has about two CTAs per SM (small images would
+// otherwise run on a handful of CTAs).  Strided (column) transforms read B
+// consecutive elements per row: keep at least four (one 32-byte sector) when
+// the buffer allows.
+int pick_B(int N, int64_t transforms, bool strided) {
+    const int cap = 4096 / N < 1 ? 1 : 4096 / N;
+    int B = cap;
+    const int64_t want = cdiv(transforms, 2 * 152);
+    if (want < B) B = (int)want;
+    if (strided && B < 4) B = cap < 4 ? cap : 4;
     return B < 1 ? 1 : B;
 }
 
@@ -232,8 +240,8 @@ bool factor(int N, Radices &rad) {
     return N == 1;
 }
 
-Pass make_pass(int N, int64_t ks, int64_t bs, int nbatch, int64_t ch_stride) {
-    Pass p{N, pick_B(N), ks, bs, nbatch, ch_stride, {}};
+Pass make_pass(int N, int64_t ks, int64_t bs, int nbatch, int64_t ch_stride, int64_t transforms) {
+    Pass p{N, pick_B(N, transforms, ks != 1), ks, bs, nbatch, ch_stride, {}};
     factor(N, p.rad);
     return p;
 }
@@ -289,16 +297,17 @@ mbir_status FftPlan::run(int axis, int mode, int channels, const float *rin, flo
     int64_t sks = 0, sbs = 0;
     const float2 *tw;
     if (axis == 0) {
-        p = make_pass(nx, 1, nx, ny * nz, nvox);
+        p = make_pass(nx, 1, nx, ny * nz, nvox, (int64_t)ny * nz * channels);
         grid = dim3((unsigned)cdiv((int64_t)ny * nz, p.B), channels);
         tw = twx.p;
     } else if (axis == 1) {
-        p = make_pass(ny, nx, 1, nx, plane);   // every z-plane of every channel is its own batch
+        // every z-plane of every channel is its own batch
+        p = make_pass(ny, nx, 1, nx, plane, (int64_t)nx * nz * channels);
         grid = dim3((unsigned)cdiv(nx, p.B), channels * nz);
         sks = nx, sbs = 1;
         tw = twy.p;
     } else {
-        p = make_pass(nz, plane, 1, (int)plane, nvox);
+        p = make_pass(nz, plane, 1, (int)plane, nvox, plane * channels);
         grid = dim3((unsigned)cdiv(plane, p.B), channels);
         sks = plane, sbs = 1;
         tw = twz.p;

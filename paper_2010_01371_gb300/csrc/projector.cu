@@ -881,6 +881,13 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
         *out = p;
         return MBIR_OK;
     }
+    {
+        // default views per CTA of the tile transpose: about six CTAs per SM
+        // on a 152-SM GPU, between 4 and 60 views (mbir_plan_autotune refines)
+        const int64_t tiles = cdiv(p->g.nx, kBT) * cdiv(p->g.ny, kBT);
+        const int64_t v = tiles * p->g.n_views / (152 * 6);
+        p->back_views = (int)(v < 4 ? 4 : (v > 60 ? 60 : v));
+    }
     if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->view.alloc(p->g.n_views)) != MBIR_OK) {
         delete p;
         return st;
@@ -955,7 +962,7 @@ extern "C" mbir_status mbir_plan_autotune(mbir_plan *p, int n_channels, mbir_str
     p->back_mode = 0;
     int best = keep;
     float best_ms = 3.0e38f;
-    const int cand[] = {30, 45, 60, 90, 120, 180};
+    const int cand[] = {4, 8, 15, 30, 45, 60, 90, 120, 180};
     for (int vs : cand) {
         if (st != MBIR_OK) break;
         if (vs > p->g.n_views && vs != cand[0]) continue;

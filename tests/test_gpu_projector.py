@@ -211,11 +211,11 @@ def test_cone_full_size_sampled(psps, oracle_lib):
 
 def test_autotune_keeps_parity(psps, oracle_lib):
     """The autotuner picks one of its candidate view splits that exist for the
-    scan (47 views: 30 or 45) and the transpose stays exact."""
+    scan (47 views: 4 .. 45) and the transpose stays exact."""
     g = small_geoms()["fan2d_ragged"]
     plan = psps.Plan(g)
     v = plan.autotune(2)
-    assert v in (30, 45)
+    assert v in (4, 8, 15, 30, 45)
     s = np.random.default_rng(11).random((2, g.n_rays))
     got = to_host(psps.mbir_backproject(plan, to_dev(s)))
     assert rel_l2(got, oracle_lib.Projector(g).backproject(s)) < TOL
