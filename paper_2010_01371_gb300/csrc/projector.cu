@@ -575,10 +575,11 @@ __device__ __forceinline__ void red_shared_pair(unsigned addr, float lo, float h
 
 // Kept rays [j0, j1) of one driving axis: fi = this lane's driving index,
 // rowbase = the tile's first interpolated index - 1, addr = byte address of
-// this lane's column in the axis' first accumulator plane.
+// this lane's column in the axis' first accumulator plane; ws2 holds the
+// weighted channels 2 and 3 (NC > 2).
 template <int NC>
-__device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, int j0, int j1, float fi, int rowbase,
-                                               unsigned addr) {
+__device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, const float2 *__restrict__ ws2, int j0,
+                                               int j1, float fi, int rowbase, unsigned addr) {
     constexpr unsigned kPlaneBytes = 4u * (kBT + 2) * kBT;
 #pragma unroll 2
     for (int j = j0; j < j1; ++j) {
@@ -589,9 +590,18 @@ __device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, in
             const unsigned q = addr + (unsigned)jr * (4u * kBT);
             const float u0 = f * a.z;
             red_shared_pair(q, a.z - u0, u0);
-            if (NC == 2) {
+            if (NC >= 2) {
                 const float u1 = f * a.w;
                 red_shared_pair(q + kPlaneBytes, a.w - u1, u1);
+            }
+            if (NC >= 3) {
+                const float2 b = ws2[j];
+                const float u2 = f * b.x;
+                red_shared_pair(q + 2 * kPlaneBytes, b.x - u2, u2);
+                if (NC == 4) {
+                    const float u3 = f * b.y;
+                    red_shared_pair(q + 3 * kPlaneBytes, b.y - u3, u3);
+                }
             }
         }
     }
@@ -602,12 +612,13 @@ __global__ void __launch_bounds__(kThreads, 5)
     back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
                         const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x, int vs) {
     static_assert(kBT == 32, "one lane per driving index of the tile");
-    static_assert(NC == 1 || NC == 2, "one or two channels");
+    static_assert(NC >= 1 && NC <= 4, "one to four channels");
     constexpr int kRows = kBT + 2;
     constexpr int kPlane = kRows * kBT;
     __shared__ float acc[2 * NC * kPlane];
     __shared__ TileItems ti;
     __shared__ float4 stage[kThreads];
+    __shared__ float2 stage2[NC > 2 ? kThreads : 1];
     const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
     if (threadIdx.x == 0) {
         ti.v_begin = blockIdx.z * vs;
@@ -621,17 +632,22 @@ __global__ void __launch_bounds__(kThreads, 5)
     const unsigned below = (1u << lane) - 1u;
     const unsigned col = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
     float4 *ws = stage + warp * 32;
+    float2 *ws2 = stage2 + (NC > 2 ? warp * 32 : 0);
     int k = 0;
     for (int base = warp * 32; base < total; base += nwarps * 32) {
         const int item = base + lane;
         bool keep = false;
         int axis = 0;
         float4 lr;
+        float2 lr2 = make_float2(0.f, 0.f);
         if (item < total) {
             while (item >= ti.prefix[k + 1]) ++k;
             const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
             const float4 r = __ldg(tab + ray);
-            const float s0 = __ldg(sino + ray), s1 = NC == 2 ? __ldg(sino + n_rays + ray) : 0.f;
+            const float s0 = __ldg(sino + ray), s1 = NC >= 2 ? __ldg(sino + n_rays + ray) : 0.f;
+            if (NC >= 3)
+                lr2 = make_float2(r.z * __ldg(sino + 2 * n_rays + ray),
+                                  NC == 4 ? r.z * __ldg(sino + 3 * n_rays + ray) : 0.f);
             int d0, o0, ia, ib;
             tile_ray_range_approx(r, c0, r0, axis, d0, o0, ia, ib);
             keep = ia <= ib;
@@ -639,10 +655,14 @@ __global__ void __launch_bounds__(kThreads, 5)
         }
         const unsigned kx = __ballot_sync(0xffffffffu, keep && axis == 0);
         const unsigned ky = __ballot_sync(0xffffffffu, keep && axis == 1);
-        if (keep) ws[axis == 0 ? __popc(kx & below) : 31 - __popc(ky & below)] = lr;
+        if (keep) {
+            const int pos = axis == 0 ? __popc(kx & below) : 31 - __popc(ky & below);
+            ws[pos] = lr;
+            if (NC > 2) ws2[pos] = lr2;
+        }
         __syncwarp();
-        tile_lane_pass<NC>(ws, 0, __popc(kx), (float)(c0 + lane), r0 - 1, col);
-        tile_lane_pass<NC>(ws, 32 - __popc(ky), 32, (float)(r0 + lane), c0 - 1, col + 4u * NC * kPlane);
+        tile_lane_pass<NC>(ws, ws2, 0, __popc(kx), (float)(c0 + lane), r0 - 1, col);
+        tile_lane_pass<NC>(ws, ws2, 32 - __popc(ky), 32, (float)(r0 + lane), c0 - 1, col + 4u * NC * kPlane);
         __syncwarp();
     }
     __syncthreads();
@@ -802,17 +822,17 @@ mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, in
         const int vs = p->back_views;
         const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT), (unsigned)cdiv(p->g.n_views, vs));
         for (int m0 = 0; m0 < n_mat;) {
-            const int left = n_mat - m0;
+            const int nc = n_mat - m0 < 4 ? n_mat - m0 : 4;   // channels of this launch
             const float *sm = sino + (int64_t)m0 * p->n_rays;
             float *xm = x + (int64_t)m0 * p->n_pix;
-            if (left >= 2) {
-                back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs);
-                m0 += 2;
-            } else {
-                back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs);
-                m0 += 1;
+            switch (nc) {
+                case 4: back_tile_2d_kernel<4><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
+                case 3: back_tile_2d_kernel<3><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
+                case 2: back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
+                default: back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
             }
             PSPS_LAUNCH_CHECK();
+            m0 += nc;
         }
         return MBIR_OK;
     }
