@@ -7,10 +7,54 @@ line integrals (l = A x_m for the image problems, l = x for projection-domain
 decomposition), Q[E,m] mass attenuation per unit density, S[c,E] the channel
 sensitivity with the gain folded in (MBIR: one energy, one channel, Q = 1,
 S = I0).  Everything is FP64.
+
+The operator outside the exponential (Eq. 1) is B S: the spectral
+sensitivity S followed, optionally, by a detector blur B (``Blur``) that
+mixes neighbouring detector cells of one row in every channel.  With B the
+SPS quantities of Eqs. 8 and 10 couple neighbouring rays:
+eta = S^T B^T Sigma^-1 B S 1 and rho = S^T B^T Sigma^-1 (B S t - y) - eta t.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+class Blur:
+    """Detector blur B: in every channel and detector row (n_u consecutive
+    rays), [B v]_i = sum_k b_k v_{i+k} for k = -R..R, zero past the ends of
+    the row.  taps = (b_-R, ..., b_R)."""
+
+    def __init__(self, taps, n_u: int):
+        self.b = np.asarray(taps, dtype=np.float64)
+        assert self.b.ndim == 1 and self.b.size % 2 == 1
+        self.R = self.b.size // 2
+        self.n_u = int(n_u)
+
+    def _corr(self, v, b):
+        shp = v.shape
+        rows = v.reshape(shp[0], -1, self.n_u)
+        pad = np.zeros(rows.shape[:-1] + (self.n_u + 2 * self.R,))
+        pad[..., self.R:self.R + self.n_u] = rows
+        out = np.zeros_like(rows)
+        for j, bk in enumerate(b):          # k = j - R
+            out += bk * pad[..., j:j + self.n_u]
+        return out.reshape(shp)
+
+    def apply(self, v):
+        """B v for v[c, rays]."""
+        return self._corr(v, self.b)
+
+    def applyT(self, v):
+        """B^T v: [B^T v]_i = sum_k b_k v_{i-k}."""
+        return self._corr(v, self.b[::-1])
+
+
+def _B(blur, v):
+    return v if blur is None else blur.apply(v)
+
+
+def _BT(blur, v):
+    return v if blur is None else blur.applyT(v)
 
 
 def weights(y: np.ndarray) -> np.ndarray:
@@ -24,27 +68,40 @@ def transmission(Q: np.ndarray, l: np.ndarray) -> np.ndarray:
     return np.exp(-(Q @ l))
 
 
-def forward_model(Q: np.ndarray, S: np.ndarray, l: np.ndarray) -> np.ndarray:
-    """Mean counts y_bar[c,i] = sum_E S[c,E] exp(-[Q l]_E,i)  (Eq. 1 with the
-    operator outside the exponential B -> S, inside A -> Q or QA)."""
-    return S @ transmission(Q, l)
+def forward_model(Q: np.ndarray, S: np.ndarray, l: np.ndarray, blur: Blur | None = None) -> np.ndarray:
+    """Mean counts y_bar[c,i] = [B sum_E S[c,E] exp(-[Q l]_E)]_i  (Eq. 1 with the
+    operator outside the exponential B -> B S, inside A -> Q or QA)."""
+    return _B(blur, S @ transmission(Q, l))
 
 
-def data_objective(Q, S, l, y) -> float:
+def data_objective(Q, S, l, y, blur: Blur | None = None) -> float:
     """L = 1/2 (y - y_bar)^T Sigma^-1 (y - y_bar)  (Eq. 3)."""
-    r = forward_model(Q, S, l) - y
+    r = forward_model(Q, S, l, blur) - y
     return 0.5 * float(np.sum(weights(y) * r * r))
 
 
-def data_grad_l(Q, S, l, y) -> np.ndarray:
-    """dL/dl[m,i] = -sum_E Q[E,m] t[E,i] sum_c S[c,E] w[c,i] (y_bar - y)[c,i]."""
+def data_grad_l(Q, S, l, y, blur: Blur | None = None) -> np.ndarray:
+    """dL/dl[m,i] = -sum_E Q[E,m] t[E,i] sum_c S[c,E] [B^T W (y_bar - y)][c,i]."""
     t = transmission(Q, l)
-    r = S @ t - y
-    v = S.T @ (weights(y) * r)
+    r = _B(blur, S @ t) - y
+    v = S.T @ _BT(blur, weights(y) * r)
     return -(Q.T @ (t * v))
 
 
-def sps_curvature(Q, S, l, y) -> np.ndarray:
+def sps_eta_rho(Q, S, l, y, blur: Blur | None = None):
+    """eta = (B S)^T Sigma^-1 (B S) 1 and rho = (B S)^T Sigma^-1 (B S) t
+    - eta t - (B S)^T Sigma^-1 y, per (energy, ray) (Eqs. 8, 10; the paper's
+    rho printed with x^n where the current transmission t^n belongs)."""
+    w = weights(y)
+    t = transmission(Q, l)
+    r = _B(blur, S @ t) - y
+    ones = np.broadcast_to(S.sum(axis=1)[:, None], r.shape)   # S 1 = sigma_c per ray
+    eta = S.T @ _BT(blur, w * _B(blur, np.array(ones)))
+    rho = S.T @ _BT(blur, w * r) - eta * t
+    return eta, rho, t
+
+
+def sps_curvature(Q, S, l, y, blur: Blur | None = None) -> np.ndarray:
     """Per (energy, ray) maximum curvature c of the separable surrogate.
 
     The data term is majorised, for each ray and energy, by the 1-D function
@@ -57,35 +114,30 @@ def sps_curvature(Q, S, l, y) -> np.ndarray:
     cited maximum-curvature rule is not in the paper; this is its derivation
     for this h.)
     """
-    w = weights(y)
-    t = transmission(Q, l)
-    r = S @ t - y
-    sigma = S.sum(axis=1)                    # sum_E S[c,E]
-    eta = S.T @ (w * sigma[:, None])         # [E, i]
-    rho = S.T @ (w * r) - eta * t            # [E, i]
+    eta, rho, t = sps_eta_rho(Q, S, l, y, blur)
     u_hi = np.maximum(1.0, t)
     return np.maximum(0.0, 2.0 * eta * u_hi * u_hi + rho * u_hi)
 
 
-def curvature_numerator(Q, S, l, y, gamma_m: np.ndarray) -> np.ndarray:
+def curvature_numerator(Q, S, l, y, gamma_m: np.ndarray, blur: Blur | None = None) -> np.ndarray:
     """kappa[m,i] = sum_E Q[E,m] gamma[E,i] c[E,i] with gamma[E,i] =
     sum_m Q[E,m] gamma_m[m,i]; the separable curvature is then
     d = A^T kappa (Eq. 6: d = diag(A^T D{gamma} c) with A -> QA)."""
-    c = sps_curvature(Q, S, l, y)
+    c = sps_curvature(Q, S, l, y, blur)
     gE = Q @ gamma_m
     return Q.T @ (gE * c)
 
 
-def line_terms(Q, S, l, q, y, alpha: float):
+def line_terms(Q, S, l, q, y, alpha: float, blur: Blur | None = None):
     """Data part of phi(alpha) = L(l + alpha q) and its first two derivatives
     in alpha, summed over all rays."""
     w = weights(y)
     la = l + alpha * q
     t = transmission(Q, la)
-    r = S @ t - y
+    r = _B(blur, S @ t) - y
     dz = Q @ q
-    dyb = -(S @ (t * dz))
-    d2yb = S @ (t * dz * dz)
+    dyb = -_B(blur, S @ (t * dz))
+    d2yb = _B(blur, S @ (t * dz * dz))
     f = 0.5 * float(np.sum(w * r * r))
     f1 = float(np.sum(w * r * dyb))
     f2 = float(np.sum(w * (dyb * dyb + r * d2yb)))

@@ -165,3 +165,100 @@ def test_penalty_pairs_and_gradient(shape):
         nb[j] += 1
         nb[k] += 1
     assert np.allclose(pen.abs_apply(np.ones((2,) + shape))[0].ravel(), 2 * nb * np.abs(beta[0]).sum())
+
+
+# ---------------------------------------------------------------------------
+# detector blur B (the operator outside the exponential is B S)
+
+def _blur_case(seed=8, nm=2, ne=5, nc=2, n_rows=3, n_u=7):
+    from oracle import model
+    rng = np.random.default_rng(seed)
+    Q, S = small_spectral(nm=nm, ne=ne, nc=nc, seed=seed)
+    blur = model.Blur([0.2, 0.5, 0.3], n_u)          # deliberately not symmetric
+    n = n_rows * n_u
+    l = rng.uniform(0.0, 30.0, (nm, n))
+    y = rng.poisson(model.forward_model(Q, S, rng.uniform(0, 30, (nm, n)), blur)).astype(float)
+    return Q, S, blur, l, y, n
+
+
+def _dense_blur(blur, n):
+    """B as a dense n x n matrix, built from its definition cell by cell."""
+    Bd = np.zeros((n, n))
+    for i in range(n):
+        row, j = divmod(i, blur.n_u)
+        for k in range(-blur.R, blur.R + 1):
+            if 0 <= j + k < blur.n_u:
+                Bd[i, row * blur.n_u + j + k] = blur.b[k + blur.R]
+    return Bd
+
+
+def test_blur_definition_and_transpose():
+    """B applied to unit vectors gives the taps clipped at the row ends; B^T is
+    its transpose (<B u, v> = <u, B^T v>)."""
+    from oracle import model
+    blur = model.Blur([0.1, 0.2, 0.4, 0.2, 0.1], 6)
+    n = 18
+    Bd = _dense_blur(blur, n)
+    eye = np.eye(n)
+    got = np.stack([blur.apply(eye[j][None])[0] for j in range(n)], 1)
+    assert np.allclose(got, Bd, atol=1e-15)
+    gotT = np.stack([blur.applyT(eye[j][None])[0] for j in range(n)], 1)
+    assert np.allclose(gotT, Bd.T, atol=1e-15)
+
+
+def test_identity_blur_is_no_blur():
+    from oracle import model
+    Q, S, _, l, y, n = _blur_case()
+    one = model.Blur([1.0], 7)
+    assert np.allclose(model.forward_model(Q, S, l, one), model.forward_model(Q, S, l), rtol=1e-15)
+    assert np.allclose(model.data_grad_l(Q, S, l, y, one), model.data_grad_l(Q, S, l, y), rtol=1e-14)
+    assert np.allclose(model.sps_curvature(Q, S, l, y, one), model.sps_curvature(Q, S, l, y), rtol=1e-14)
+
+
+def test_blur_eta_rho_dense():
+    """eta and rho of Eqs. 8 and 10 with the dense operator (B S) over the
+    (energy, ray) unknowns: eta = P 1, rho = P t - eta t - (BS)^T W y,
+    P = (BS)^T W (BS)."""
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case()
+    ne, nc = S.shape[1], S.shape[0]
+    Bd = _dense_blur(blur, n)
+    # (B S) maps t[E, i] (flattened E-major) to y_bar[c, i] (c-major)
+    BS = np.einsum("ce,ij->ciej", S, Bd).reshape(nc * n, ne * n)
+    W = np.diag(model.weights(y).ravel())
+    P = BS.T @ W @ BS
+    t = model.transmission(Q, l).ravel()
+    eta_d = P @ np.ones(ne * n)
+    rho_d = P @ t - eta_d * t - BS.T @ W @ y.ravel()
+    eta, rho, _ = model.sps_eta_rho(Q, S, l, y, blur)
+    assert np.allclose(eta.ravel(), eta_d, rtol=1e-12)
+    assert np.allclose(rho.ravel(), rho_d, rtol=1e-10, atol=1e-10 * np.abs(rho_d).max())
+
+
+def test_blur_gradient_finite_differences():
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=9)
+    _fd_check(lambda z: model.data_objective(Q, S, z, y, blur), model.data_grad_l(Q, S, l, y, blur), l)
+
+
+def test_blur_surrogate_majorises():
+    """With eta = P 1 (P = (BS)^T W (BS) has nonnegative entries) the separable
+    sum of h(z) = 1/2 eta e^{-2z} + rho e^{-z} over every (energy, ray)
+    majorises the data term as a function of the exponents z, touching it at
+    the current point: L(z) - L(z^n) <= sum h(z) - h(z^n) for any z."""
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=10)
+    eta, rho, t0 = model.sps_eta_rho(Q, S, l, y, blur)
+    z0 = Q @ l
+    w = model.weights(y)
+
+    def L(z):
+        r = blur.apply(S @ np.exp(-z)) - y
+        return 0.5 * float(np.sum(w * r * r))
+
+    def H(z):
+        return float(np.sum(0.5 * eta * np.exp(-2 * z) + rho * np.exp(-z)))
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        z = z0 + rng.normal(0.0, 0.5, z0.shape)
+        assert L(z) - L(z0) <= H(z) - H(z0) + 1e-9 * (abs(L(z0)) + 1)
