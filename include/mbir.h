@@ -143,6 +143,21 @@ mbir_status mbmd_spectrum_create(int n_mat, int n_energy, int n_chan, const doub
                                  mbmd_spectrum **out);
 mbir_status mbmd_spectrum_destroy(mbmd_spectrum *spec);
 
+/* Detector blur in the outer operator B S of the forward model (Eq. 1): the
+ * mean counts become y_bar[c] = B (sum_E S[c][E] exp(-[Q l]_E)) with
+ * [B v]_i = sum_{k=-radius..radius} taps[k + radius] v_{i+k}, taken within
+ * detector rows of `row` consecutive rays (rays past a row's ends count as
+ * zero).  The SPS numerators of Eqs. 8 and 10 then use B^T of the weighted
+ * residual and of w .* B 1 (Sec. II-B's rank-one bound applied to the rows of
+ * B S).  The preconditioners still use blur-free Fisher blocks.
+ * radius 0..3 (0 removes the blur; taps and row are then ignored); taps:
+ * host FP64 [2 radius + 1], finite and >= 0, stored in FP32; row >= 1.
+ * Every model call, state and batch on this spectrum then needs n_rays to be
+ * a multiple of row (MBIR_ERR_ARG otherwise).  A PSPS state keeps the blur
+ * the spectrum had when it was created.  Bad arguments leave the spectrum
+ * unchanged and return MBIR_ERR_ARG. */
+mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, int row, const double *taps);
+
 /* Mean counts y_bar[c][i] = sum_E S[c][E] exp(-sum_m Q[E][m] l[m][i]) (Eq. 1).
  * l: [n_mat][n_rays], ybar: [n_chan][n_rays]. */
 mbir_status mbmd_forward_model(const mbmd_spectrum *spec, const float *l, float *ybar, int64_t n_rays,

@@ -118,6 +118,20 @@ class Spectrum:
         _call(lib().mbmd_spectrum_create, self.n_mat, self.n_energy, self.n_chan, Q.ctypes.data_as(dp),
               S.ctypes.data_as(dp), ctypes.byref(h))
         self.h = h
+        self.blur = None
+
+    def set_blur(self, taps, row: int):
+        """Detector blur B of the outer operator B S (Eq. 1): odd-length taps
+        b[-r..r] (r <= 3) applied along rows of `row` consecutive rays; an
+        empty or None `taps` removes it."""
+        taps = np.ascontiguousarray(np.asarray([] if taps is None else taps, dtype=np.float64).ravel())
+        if taps.size % 2 == 0 and taps.size:
+            raise ValueError("blur taps must have odd length 2 r + 1")
+        radius = taps.size // 2
+        dp = ctypes.POINTER(ctypes.c_double)
+        _call(lib().mbmd_spectrum_set_blur, self.h, int(radius), int(row),
+              taps.ctypes.data_as(dp) if taps.size else None)
+        self.blur = (taps.copy(), int(row)) if radius else None
 
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:

@@ -234,6 +234,10 @@ struct mbir_plan {
 struct mbmd_spectrum {
     int n_mat = 1, n_energy = 1, n_chan = 1;
     psps::DBuf<float> qs;   // device: Q[E][m] then S[c][E] then sigma[c]
+    // optional detector blur (outer operator B S): taps b[-r..r] along rows
+    // of blur_row consecutive rays; r = 0: none
+    int blur_r = 0, blur_row = 1;
+    float blur_b[7] = {};
     double *hQ = nullptr, *hS = nullptr;  // host FP64 copies
     ~mbmd_spectrum() {
         delete[] hQ;

@@ -16,6 +16,7 @@
 // Exponentials and per-ray sums run in FP32 (expf); the objective and
 // line-search sums over rays are double-float reductions.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "model.cuh"
@@ -257,6 +258,342 @@ __global__ void __launch_bounds__(kModelThreads)
     }
 }
 
+// ---------------------------------------------------------------- blur
+// With a detector blur B in the outer operator (B S, Eq. 1) the mean counts
+// of a ray mix the unblurred counts of its row neighbours, and the SPS
+// quantities of Eqs. 8 and 10 become, per ray i and energy E,
+//   eta = sum_c S[c][E] sigma_c [B^T (w_c .* B 1)]_i
+//   rho = sum_c S[c][E] [B^T (w_c .* r_c)]_i - eta t_E,   r = B S t - y.
+// The blurred path runs in passes: unblurred counts per ray, then the
+// blurred residual and its weights, then the numerators from B^T of those.
+
+// [B v]_i (dir = +1) or [B^T v]_i (dir = -1), one channel, within the row.
+__device__ __forceinline__ float blur_at(const BlurDev &B, const float *__restrict__ v, int64_t i, int dir) {
+    const int j = (int)(i % B.row);
+    float s = 0.f;
+    for (int k = -B.r; k <= B.r; ++k) {
+        const int jj = j + dir * k;
+        if (jj >= 0 && jj < B.row) s = fmaf(B.b[k + B.r], v[i + dir * k], s);
+    }
+    return s;
+}
+
+// (B 1)_j at row position j.
+__device__ __forceinline__ float blur_ones(const BlurDev &B, int j) {
+    float s = 0.f;
+    for (int k = -B.r; k <= B.r; ++k)
+        if (j + k >= 0 && j + k < B.row) s += B.b[k + B.r];
+    return s;
+}
+
+// [B^T (w .* B 1)]_i for one channel of counts y (w = 1 / max(y, 1)).
+__device__ __forceinline__ float blur_eta_weight(const BlurDev &B, const float *__restrict__ y, int64_t i) {
+    const int j = (int)(i % B.row);
+    float s = 0.f;
+    for (int k = -B.r; k <= B.r; ++k) {
+        const int jj = j - k;
+        if (jj >= 0 && jj < B.row) s = fmaf(B.b[k + B.r], blur_ones(B, jj) / fmaxf(y[i - k], 1.f), s);
+    }
+    return s;
+}
+
+// Unblurred counts y0[c][i] = sum_E S[c][E] exp(-[Q l]_E,i).
+template <int NM, int CM>
+__global__ void __launch_bounds__(kModelThreads)
+    model_y0_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, float *__restrict__ y0) {
+    extern __shared__ float sh[];
+    load_spec(sp, sh);
+    const float *Q = sh;
+    const float *S = sh + sp.ne * NM;
+    const int nc = sp.nc, ne = sp.ne;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
+        float lm[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) lm[m] = l[(int64_t)m * n_rays + i];
+        float yb[CM];
+#pragma unroll
+        for (int c = 0; c < CM; ++c) yb[c] = 0.f;
+        for (int e = 0; e < ne; ++e) {
+            float z = 0.f;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], lm[m], z);
+            const float t = expf(-z);
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CM; ++c)
+            if (c < nc) y0[(int64_t)c * n_rays + i] = yb[c];
+    }
+}
+
+// Blurred residual r = B y0 - y: weighted residual qw = w r (if qw) and the
+// data term 1/2 sum w r^2 (block partials); ybar = B y0 when asked.
+__global__ void __launch_bounds__(kModelThreads)
+    blur_resid_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ y0, const float *__restrict__ y,
+                      float *__restrict__ qw, float *__restrict__ ybar, dfloat *__restrict__ partials) {
+    dfloat obj{0.f, 0.f};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < sp.nc; ++c) {
+            const float yb = blur_at(sp.blur, y0 + (int64_t)c * n_rays, i, +1);
+            if (ybar) ybar[(int64_t)c * n_rays + i] = yb;
+            if (!y) continue;
+            const float yc = y[(int64_t)c * n_rays + i];
+            const float w = 1.f / fmaxf(yc, 1.f);
+            const float r = yb - yc;
+            if (qw) qw[(int64_t)c * n_rays + i] = w * r;
+            df_add(obj, 0.5f * w * r * r);
+        }
+    if (partials) {
+        dfloat v[1] = {obj};
+        block_sum_store<1>(v, partials);
+    }
+}
+
+// Numerators with the blur: u_c = [B^T qw_c]_i replaces w_c r_c and
+// sigma_c [B^T (w_c .* B 1)]_i replaces w_c sigma_c (see above).
+template <int NM, int CM>
+__global__ void __launch_bounds__(kModelThreads)
+    model_grad_blur_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
+                           const float *__restrict__ qw, const float *__restrict__ gamma, float *__restrict__ g,
+                           float *__restrict__ kappa) {
+    extern __shared__ float sh[];
+    load_spec(sp, sh);
+    const float *Q = sh;
+    const float *S = sh + sp.ne * NM;
+    const float *sig = S + sp.nc * sp.ne;
+    const int nc = sp.nc, ne = sp.ne;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
+        float lm[NM], gm[NM], km[NM], gam[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            lm[m] = l[(int64_t)m * n_rays + i];
+            gm[m] = km[m] = 0.f;
+            gam[m] = kappa ? gamma[(int64_t)m * n_rays + i] : 0.f;
+        }
+        float u[CM], ws[CM];
+#pragma unroll
+        for (int c = 0; c < CM; ++c) {
+            u[c] = ws[c] = 0.f;
+            if (c < nc) {
+                u[c] = blur_at(sp.blur, qw + (int64_t)c * n_rays, i, -1);
+                ws[c] = kappa ? sig[c] * blur_eta_weight(sp.blur, y + (int64_t)c * n_rays, i) : 0.f;
+            }
+        }
+        for (int e = 0; e < ne; ++e) {
+            float z = 0.f, gE = 0.f;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                z = fmaf(Q[e * NM + m], lm[m], z);
+                gE = fmaf(Q[e * NM + m], gam[m], gE);
+            }
+            const float t = expf(-z);
+            float v = 0.f, eta = 0.f;
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) {
+                    v = fmaf(S[c * ne + e], u[c], v);
+                    eta = fmaf(S[c * ne + e], ws[c], eta);
+                }
+            const float tv = t * v;
+            float cE = 0.f;
+            if (kappa) {
+                const float rho = v - eta * t;
+                const float uh = fmaxf(1.f, t);
+                cE = fmaxf(0.f, (2.f * eta * uh + rho) * uh);
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                gm[m] = fmaf(-Q[e * NM + m], tv, gm[m]);
+                km[m] = fmaf(Q[e * NM + m], gE * cE, km[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            if (g) g[(int64_t)m * n_rays + i] = gm[m];
+            if (kappa) kappa[(int64_t)m * n_rays + i] = km[m];
+        }
+    }
+}
+
+// Line search with the blur, pass 1: unblurred counts (and, for the Newton
+// evaluation, their first two alpha-derivatives) per ray into buf, and the
+// rays leaving the domain z >= z_min (partial streams 3, resp. kMaxHalve+k).
+//   MODE 0: buf[0|1|2][c][i] = y0, dy0/dalpha, d2y0/dalpha2 at ls->alpha
+//   MODE 1: buf[k][c][i] = y0 at the k-th halving candidate
+template <int NM, int CM, int MODE>
+__global__ void __launch_bounds__(kModelThreads)
+    ls_blur_pre_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
+                       DevLS *ls, LsCfg cfg, float *__restrict__ buf, dfloat *__restrict__ partials) {
+    if (MODE == 1 && ls->done) return;  // same value for every block
+    extern __shared__ float sh[];
+    load_spec(sp, sh);
+    const float *Q = sh;
+    const float *S = sh + sp.ne * NM;
+    const int nc = sp.nc, ne = sp.ne;
+    const int nb = gridDim.x;
+    const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
+    if constexpr (MODE == 0) {
+        const float alpha = (float)ls->alpha;
+        dfloat bad[1] = {dfloat{0.f, 0.f}};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            float la[NM], qm[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                qm[m] = q[(int64_t)m * n_rays + i];
+                la[m] = fmaf(alpha, qm[m], l[(int64_t)m * n_rays + i]);
+            }
+            float yb[CM], d1[CM], d2[CM];
+#pragma unroll
+            for (int c = 0; c < CM; ++c) yb[c] = d1[c] = d2[c] = 0.f;
+            float zlo = 3.0e38f;
+            for (int e = 0; e < ne; ++e) {
+                float z = 0.f, dz = 0.f;
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    z = fmaf(Q[e * NM + m], la[m], z);
+                    dz = fmaf(Q[e * NM + m], qm[m], dz);
+                }
+                zlo = fminf(zlo, z);
+                const float t = expf(-z);
+                const float tdz = t * dz;
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) {
+                        const float s = S[c * ne + e];
+                        yb[c] = fmaf(s, t, yb[c]);
+                        d1[c] = fmaf(-s, tdz, d1[c]);
+                        d2[c] = fmaf(s, tdz * dz, d2[c]);
+                    }
+            }
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) {
+                    buf[(int64_t)c * n_rays + i] = yb[c];
+                    buf[(int64_t)(nc + c) * n_rays + i] = d1[c];
+                    buf[(int64_t)(2 * nc + c) * n_rays + i] = d2[c];
+                }
+            if (!(zlo >= cfg.z_min)) df_add(bad[0], 1.f);
+        }
+        block_sum_store<1>(bad, partials + 3 * (int64_t)nb);
+    } else {
+        float alphas[kMaxHalve];
+        double ak = ls->best_a;
+#pragma unroll
+        for (int k = 0; k < kMaxHalve; ++k) {
+            ak *= 0.5;
+            alphas[k] = (float)ak;
+        }
+        dfloat bad[kMaxHalve];
+#pragma unroll
+        for (int k = 0; k < kMaxHalve; ++k) bad[k] = dfloat{0.f, 0.f};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            float lm[NM], qm[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                qm[m] = q[(int64_t)m * n_rays + i];
+                lm[m] = l[(int64_t)m * n_rays + i];
+            }
+#pragma unroll
+            for (int k = 0; k < kMaxHalve; ++k) {
+                if (k >= nh) break;
+                float yb[CM];
+#pragma unroll
+                for (int c = 0; c < CM; ++c) yb[c] = 0.f;
+                float zlo = 3.0e38f;
+                for (int e = 0; e < ne; ++e) {
+                    float z = 0.f;
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alphas[k], qm[m], lm[m]), z);
+                    zlo = fminf(zlo, z);
+                    const float t = expf(-z);
+#pragma unroll
+                    for (int c = 0; c < CM; ++c)
+                        if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) buf[((int64_t)k * nc + c) * n_rays + i] = yb[c];
+                if (!(zlo >= cfg.z_min)) df_add(bad[k], 1.f);
+            }
+        }
+        block_sum_store<kMaxHalve>(bad, partials + (int64_t)kMaxHalve * nb);
+    }
+}
+
+// Line search with the blur, pass 2: blurred counts and the data terms
+// (phi, phi', phi'' or the candidates' phi) as block partials; the last
+// block runs the same control as the fused kernel.
+template <int MODE>
+__global__ void __launch_bounds__(kModelThreads)
+    ls_blur_sum_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ y, const float *__restrict__ buf,
+                       DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
+    if (MODE == 1 && ls->done) return;
+    const int nc = sp.nc;
+    const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
+    if constexpr (MODE == 0) {
+        dfloat acc[3] = {dfloat{0.f, 0.f}, dfloat{0.f, 0.f}, dfloat{0.f, 0.f}};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            float f = 0.f, f1 = 0.f, f2 = 0.f;
+            for (int c = 0; c < nc; ++c) {
+                const float yb = blur_at(sp.blur, buf + (int64_t)c * n_rays, i, +1);
+                const float d1 = blur_at(sp.blur, buf + (int64_t)(nc + c) * n_rays, i, +1);
+                const float d2 = blur_at(sp.blur, buf + (int64_t)(2 * nc + c) * n_rays, i, +1);
+                const float yc = y[(int64_t)c * n_rays + i];
+                const float w = 1.f / fmaxf(yc, 1.f);
+                const float r = yb - yc;
+                f = fmaf(0.5f * w * r, r, f);
+                f1 = fmaf(w * r, d1, f1);
+                f2 = fmaf(w, fmaf(d1, d1, r * d2), f2);
+            }
+            df_add(acc[0], f);
+            df_add(acc[1], f1);
+            df_add(acc[2], f2);
+        }
+        block_sum_store<3>(acc, partials);
+    } else {
+        dfloat acc[kMaxHalve];
+#pragma unroll
+        for (int k = 0; k < kMaxHalve; ++k) acc[k] = dfloat{0.f, 0.f};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+            for (int k = 0; k < kMaxHalve; ++k) {
+                if (k >= nh) break;
+                float f = 0.f;
+                for (int c = 0; c < nc; ++c) {
+                    const float yb = blur_at(sp.blur, buf + ((int64_t)k * nc + c) * n_rays, i, +1);
+                    const float yc = y[(int64_t)c * n_rays + i];
+                    const float r = yb - yc;
+                    f = fmaf(0.5f * r / fmaxf(yc, 1.f), r, f);
+                }
+                df_add(acc[k], f);
+            }
+        block_sum_store<kMaxHalve>(acc, partials);
+    }
+    if (!last_block_arrive(&ls->ticket)) return;
+    const int nb = gridDim.x;
+    if constexpr (MODE == 0) {
+        double sums[4];
+        block_sum_partials_k<4>(partials, nb, sums);
+        if (threadIdx.x == 0) {
+            ls_newton_control(ls, sums[0], sums[1], sums[2], sums[3], last, cfg);
+            ls->ticket = 0;
+        }
+    } else {
+        double sums[2 * kMaxHalve];
+        block_sum_partials_k<2 * kMaxHalve>(partials, nb, sums);
+        if (threadIdx.x == 0) {
+            ls_halve_control(ls, sums, sums + kMaxHalve, nh);
+            ls->ticket = 0;
+        }
+    }
+}
+
 __global__ void forward_model_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, float *__restrict__ ybar) {
     extern __shared__ float sh[];
     load_spec(sp, sh);
@@ -359,9 +696,69 @@ void model_grad_launch_nm(SpecDev sp, int64_t n_rays, const float *l, const floa
     }
 }
 
+// Calls F::template run<NM, CM>() for the material count and channel bound
+// of the spectrum.
+template <class F>
+mbir_status dispatch_nm_cm(const SpecDev &sp, F &&f) {
+    const int cm = channel_bound(sp.nc);
+    auto with_cm = [&](auto nm_tag) {
+        constexpr int NM = decltype(nm_tag)::value;
+        switch (cm) {
+            case 1: f.template run<NM, 1>(); break;
+            case 2: f.template run<NM, 2>(); break;
+            case 4: f.template run<NM, 4>(); break;
+            default: f.template run<NM, 8>(); break;
+        }
+    };
+    switch (sp.nm) {
+        case 1: with_cm(std::integral_constant<int, 1>{}); break;
+        case 2: with_cm(std::integral_constant<int, 2>{}); break;
+        case 3: with_cm(std::integral_constant<int, 3>{}); break;
+        case 4: with_cm(std::integral_constant<int, 4>{}); break;
+        default: return fail(MBIR_ERR_ARG, "n_mat %d unsupported", sp.nm);
+    }
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
+struct BlurModelLaunch {
+    SpecDev sp;
+    int64_t n;
+    const float *l, *y, *gamma;
+    float *g, *kappa;
+    const BlurScratch *scr;
+    int nblocks;
+    size_t smem;
+    cudaStream_t s;
+    int stage;  // 0: unblurred counts, 1: numerators
+    template <int NM, int CM>
+    void run() {
+        if (stage == 0)
+            model_y0_kernel<NM, CM><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, scr->y0);
+        else
+            model_grad_blur_kernel<NM, CM><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, y, scr->qw, gamma, g, kappa);
+    }
+};
+
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
-                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s) {
+                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s,
+                              const BlurScratch *scr) {
     const size_t smem = spec_smem(sp);
+    if (sp.blur.r > 0) {
+        const bool grads = g || kappa;
+        if (!scr || !scr->y0 || (grads && !scr->qw))
+            return fail(MBIR_ERR_ARG, "the blurred model needs scratch buffers");
+        BlurModelLaunch L{sp, n_rays, l, y, gamma, g, kappa, scr, nblocks, smem, s, 0};
+        PSPS_TRY(dispatch_nm_cm(sp, L));
+        blur_resid_kernel<<<nblocks, kModelThreads, 0, s>>>(sp, n_rays, scr->y0, y, grads ? scr->qw : nullptr,
+                                                             nullptr, partials);
+        PSPS_LAUNCH_CHECK();
+        if (grads) {
+            L.stage = 1;
+            PSPS_TRY(dispatch_nm_cm(sp, L));
+        }
+        return MBIR_OK;
+    }
     switch (sp.nm) {
         case 1: model_grad_launch_nm<1>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
         case 2: model_grad_launch_nm<2>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
@@ -393,9 +790,41 @@ void ls_fused_launch_nm(SpecDev sp, int64_t n_rays, const float *l, const float 
     }
 }
 
+struct BlurLsLaunch {
+    SpecDev sp;
+    int64_t n;
+    const float *l, *q;
+    DevLS *ls;
+    LsCfg cfg;
+    float *buf;
+    dfloat *partials;
+    int mode, nblocks;
+    size_t smem;
+    cudaStream_t s;
+    template <int NM, int CM>
+    void run() {
+        if (mode == 0)
+            ls_blur_pre_kernel<NM, CM, 0><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, q, ls, cfg, buf, partials);
+        else
+            ls_blur_pre_kernel<NM, CM, 1><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, q, ls, cfg, buf, partials);
+    }
+};
+
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
-                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s) {
+                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s,
+                            const BlurScratch *scr) {
     const size_t smem = spec_smem(sp);
+    if (sp.blur.r > 0) {
+        if (!scr || !scr->ls) return fail(MBIR_ERR_ARG, "the blurred line search needs a scratch buffer");
+        BlurLsLaunch L{sp, n_rays, l, q, ls, cfg, scr->ls, partials, mode, nblocks, smem, s};
+        PSPS_TRY(dispatch_nm_cm(sp, L));
+        if (mode == 0)
+            ls_blur_sum_kernel<0><<<nblocks, kModelThreads, 0, s>>>(sp, n_rays, y, scr->ls, ls, cfg, last, partials);
+        else
+            ls_blur_sum_kernel<1><<<nblocks, kModelThreads, 0, s>>>(sp, n_rays, y, scr->ls, ls, cfg, last, partials);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
     switch (sp.nm) {
         case 1: ls_fused_launch_nm<1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
         case 2: ls_fused_launch_nm<2>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
@@ -407,7 +836,17 @@ mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const fl
     return MBIR_OK;
 }
 
-mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s) {
+mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s,
+                                 float *y0) {
+    if (sp.blur.r > 0) {
+        if (!y0) return fail(MBIR_ERR_ARG, "the blurred forward model needs a scratch buffer");
+        forward_model_kernel<<<model_blocks(n_rays), kModelThreads, spec_smem(sp), s>>>(sp, n_rays, l, y0);
+        PSPS_LAUNCH_CHECK();
+        blur_resid_kernel<<<model_blocks(n_rays), kModelThreads, 0, s>>>(sp, n_rays, y0, nullptr, nullptr, ybar,
+                                                                        nullptr);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
     forward_model_kernel<<<model_blocks(n_rays), kModelThreads, spec_smem(sp), s>>>(sp, n_rays, l, ybar);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
@@ -484,13 +923,37 @@ extern "C" mbir_status mbmd_forward_model(const mbmd_spectrum *spec, const float
                                           mbir_stream s) {
     if (!spec || !l || !ybar || n_rays < 0) return fail(MBIR_ERR_ARG, "mbmd_forward_model: bad argument");
     if (n_rays == 0) return MBIR_OK;
-    return launch_forward_model(spec_dev(spec), n_rays, l, ybar, (cudaStream_t)s);
+    if (spec->blur_r == 0) return launch_forward_model(spec_dev(spec), n_rays, l, ybar, (cudaStream_t)s);
+    if (n_rays % spec->blur_row) return fail(MBIR_ERR_ARG, "mbmd_forward_model: n_rays is not a multiple of the blur row");
+    DBuf<float> y0;
+    PSPS_TRY(y0.alloc((size_t)spec->n_chan * n_rays));
+    PSPS_TRY(launch_forward_model(spec_dev(spec), n_rays, l, ybar, (cudaStream_t)s, y0.p));
+    PSPS_CUDA(cudaStreamSynchronize((cudaStream_t)s));  // y0 is released on return
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, int row, const double *taps) {
+    if (!spec) return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_blur: spec is null");
+    if (radius < 0 || radius > 3) return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_blur: radius %d outside 0..3", radius);
+    if (radius > 0 && (!taps || row < 1))
+        return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_blur: taps must be given and row must be >= 1");
+    float b[7] = {};
+    for (int k = 0; radius > 0 && k < 2 * radius + 1; ++k) {
+        if (!std::isfinite(taps[k]) || taps[k] < 0)
+            return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_blur: taps must be finite and >= 0");
+        b[k] = (float)taps[k];
+    }
+    spec->blur_r = radius;
+    spec->blur_row = radius > 0 ? row : 1;
+    for (int k = 0; k < 7; ++k) spec->blur_b[k] = b[k];
+    return MBIR_OK;
 }
 
 namespace {
-// Scratch for the stateless model calls: l and g sinograms plus partials.
+// Scratch for the stateless model calls: l and g sinograms, partials and,
+// with a detector blur, the unblurred counts and weighted residuals.
 struct ModelScratch {
-    DBuf<float> l, g;
+    DBuf<float> l, g, y0, qw;
     DBuf<dfloat> part;
 };
 
@@ -501,6 +964,7 @@ mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x
         return fail(MBIR_ERR_ARG, "mbmd: n_rays %lld does not match the plan (%lld)", (long long)n_rays,
                     (long long)plan->n_rays);
     if (plan && spec->n_mat > plan->n_mat_max) return fail(MBIR_ERR_ARG, "mbmd: n_mat exceeds the plan's n_mat_max");
+    if (n_rays % spec->blur_row) return fail(MBIR_ERR_ARG, "mbmd: n_rays is not a multiple of the blur row");
     ModelScratch sc;
     const int nm = spec->n_mat;
     const float *l = x_or_l;
@@ -520,7 +984,16 @@ mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x
             g = grad;
         }
     }
-    PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, nullptr, g, nullptr, sc.part.p, nb, s));
+    BlurScratch bs;
+    if (spec->blur_r > 0) {
+        PSPS_TRY(sc.y0.alloc((size_t)spec->n_chan * n_rays));
+        bs.y0 = sc.y0.p;
+        if (grad) {
+            PSPS_TRY(sc.qw.alloc((size_t)spec->n_chan * n_rays));
+            bs.qw = sc.qw.p;
+        }
+    }
+    PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, nullptr, g, nullptr, sc.part.p, nb, s, &bs));
     if (objective) PSPS_TRY(reduce_partials(sc.part.p, nb, 1, objective, 0, s));
     if (grad && plan) PSPS_TRY(backproject(plan, g, grad, nm, 0, s));
     PSPS_CUDA(cudaStreamSynchronize(s));  // scratch is released on return

@@ -6,12 +6,33 @@
 
 namespace psps {
 
+// Detector blur of the outer operator (B S): [B v]_i = sum_k b[k + r] v_{i+k},
+// k = -r..r, within rows of `row` consecutive rays (zero past the row ends).
+struct BlurDev {
+    int r = 0, row = 1;
+    float b[7] = {};
+};
+
 struct SpecDev {
     int nm, ne, nc;
     const float *qs;  // Q[ne][nm], S[nc][ne], sigma[nc] (sigma_c = sum_E S[c][E])
+    BlurDev blur;
 };
 
-inline SpecDev spec_dev(const mbmd_spectrum *s) { return SpecDev{s->n_mat, s->n_energy, s->n_chan, s->qs.p}; }
+inline SpecDev spec_dev(const mbmd_spectrum *s) {
+    SpecDev d{s->n_mat, s->n_energy, s->n_chan, s->qs.p, {}};
+    d.blur.r = s->blur_r;
+    d.blur.row = s->blur_row;
+    for (int k = 0; k < 7; ++k) d.blur.b[k] = s->blur_b[k];
+    return d;
+}
+
+// Scratch of the blurred model ([n_chan][n_rays] each: unblurred mean counts
+// and weighted residuals) and of the blurred line search
+// ([kMaxHalve][n_chan][n_rays]); unused (may be null) without a blur.
+struct BlurScratch {
+    float *y0 = nullptr, *qw = nullptr, *ls = nullptr;
+};
 
 constexpr int kModelThreads = 256;
 constexpr int kModelMaxBlocks = 2048;  // grid-stride; partial sums per block
@@ -25,14 +46,19 @@ inline int model_blocks(int64_t n) {
 // data term partials (1 per block); g, kappa optional ([nm][n_rays]).
 // gamma: per-ray gamma_m = [A |M| 1]_m ([nm][n_rays]) for kappa.
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
-                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s);
+                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s,
+                              const BlurScratch *scr = nullptr);
 // Fused line-search evaluation: mode 0 evaluates phi, phi', phi'' at
 // ls->alpha and its last block runs the Newton control; mode 1 (skipped when
 // the search is done) evaluates the n_halve halving candidates at once and
 // its last block picks the step.  partials: 2 kMaxHalve per block.
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
-                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s);
-mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s);
+                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s,
+                            const BlurScratch *scr = nullptr);
+// ybar = B S exp(-Q l); with a blur, y0 ([n_chan][n_rays]) holds the unblurred
+// counts.
+mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s,
+                                 float *y0 = nullptr);
 // Per-ray Fisher blocks F_i = Q^T D S^T W S D Q (upper triangle, packed
 // [nm(nm+1)/2][n_rays]) with D = y / I0 (one energy/channel) or the water fit.
 mbir_status launch_fisher_blocks(const mbmd_spectrum *spec, int64_t n_rays, const float *y, float *F,

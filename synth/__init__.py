@@ -500,3 +500,27 @@ def config5(n: int = 256, n_views: int = 360, n_u: int = 512, n_v: int = 384, ra
     l = np.stack([chord_lengths(shapes, o, d) for shapes in mats])
     y = poisson(rng(5, "noise"), S @ np.exp(-(Q @ l)))
     return Problem("c5_cone3d", geom, Q, S, y, CONFIG5_BETA, truth, 50, "block", geom.n_rays)
+
+
+# Detector cross-talk taps for the blurred-detector variants: a symmetric
+# 3-cell kernel and an asymmetric 7-cell one (both sum to 1).
+BLUR_TAPS = {"r1": (0.15, 0.70, 0.15), "r3": (0.02, 0.06, 0.20, 0.44, 0.18, 0.07, 0.03)}
+
+
+def with_detector_blur(prob: Problem, taps: Sequence[float], n_u: int | None = None) -> Problem:
+    """The same scan read out by a detector whose cells leak into their row
+    neighbours: new counts are Poisson draws around the row-wise weighted sum
+    of the measured counts with ``taps`` (2 r + 1 weights b_-r..b_r, cells past
+    a row's ends contribute nothing).  Rows are n_u consecutive rays (default:
+    the geometry's detector columns)."""
+    b = np.asarray(taps, dtype=np.float64)
+    r = b.size // 2
+    n_u = int(n_u if n_u is not None else prob.geom.n_u)
+    rows = prob.y.reshape(prob.y.shape[0], -1, n_u)
+    pad = np.zeros(rows.shape[:-1] + (n_u + 2 * r,))
+    pad[..., r:r + n_u] = rows
+    mean = np.zeros_like(rows)
+    for j, bj in enumerate(b):
+        mean += bj * pad[..., j:j + n_u]
+    y = poisson(rng(len(b), "misc"), mean.reshape(prob.y.shape))
+    return dataclasses.replace(prob, y=y, name=prob.name + f"_blur{r}")

@@ -59,12 +59,14 @@ def phantom(geom, seed=0, nm=1):
     return np.stack(out)
 
 
-def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True):
+def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None):
     """Oracle preconditioner for a problem plus the data that defines it
-    (eigenvalues, m0, blocks in the library's [m][k][n] layout)."""
+    (eigenvalues, m0, blocks in the library's [m][k][n] layout).  blur: an
+    ``oracle.model.Blur`` in the outer operator (the preconditioners use the
+    blur-free Fisher blocks either way)."""
     from oracle import build, precond, psps as opsps
     A = oracle_lib.Projector(prob.geom) if proj else oracle_lib.IdentityProjector(prob.n_rays)
-    st = opsps.Setup(A, prob.Q, prob.S, prob.y, prob.beta if proj else None)
+    st = opsps.Setup(A, prob.Q, prob.S, prob.y, prob.beta if proj else None, blur=blur)
     if kind == "none":
         return st, precond.Identity(), {}
     F = build.fisher(st)
