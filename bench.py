@@ -67,6 +67,12 @@ WORKLOADS = {
     "c5_cone3d_128_block": ("config5", "block", "128^3@1mm, 180x192x256 cone flat (the 256^3 scan scaled down), "
                                                 "2 materials x 2 kVp, 2x2 per-voxel blocks",
                             {"n": 128, "n_views": 180, "n_u": 256, "n_v": 192}),
+    "c2_fan2d_512_haar_blur1": ("config2", "haar", "config 2 read out through a 3-tap detector blur along the "
+                                                   "888-bin rows (outer operator B S)", {"blur": "r1"}),
+    "c4_mbmd_512_blockfourier_blur3": ("config4_slice", "block_fourier",
+                                       "config 4 slice read out through a 7-tap asymmetric detector blur along the "
+                                       "888-bin rows (outer operator B S), 3x3 blocks + cross-material Fourier",
+                                       {"blur": "r3"}),
 }
 
 
@@ -220,7 +226,7 @@ def gap_runs(p, plan, spec, yd, beta, pc, n_star: int, n_cmp: int):
     return phi_star, out
 
 
-def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
+def ours(args, prob, workload=WORKLOAD, kind="haar", desc="", blur=None):
     import torch
 
     import paper_2010_01371_gb300 as p
@@ -237,6 +243,8 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc=""):
     t0 = time.perf_counter()
     plan = p.Plan(prob.geom) if prob.geom is not None else None
     spec = p.Spectrum(prob.Q, prob.S)
+    if blur is not None:
+        spec.set_blur(blur, prob.geom.n_u)
     beta = prob.beta if plan is not None else None
     pc = p.Precond(plan, spec, kind, yd, beta)
     tuned = plan.autotune(2 * prob.Q.shape[1]) if plan is not None else None
@@ -548,13 +556,18 @@ def main():
         reference_arm(args, synth.config2())
         return
     builder, kind, desc, *kw = WORKLOADS[args.workload]
-    prob = getattr(synth, builder)(**(kw[0] if kw else {}))
+    kw = dict(kw[0]) if kw else {}
+    blur = kw.pop("blur", None)
+    prob = getattr(synth, builder)(**kw)
+    if blur is not None:
+        blur = synth.BLUR_TAPS[blur]
+        prob = synth.with_detector_blur(prob, blur)
     if args.workload != WORKLOAD:
         args.no_cpu = True
     if isinstance(prob, list):
         ours_batch(args, prob, args.workload, kind, desc)
         return
-    ours(args, prob, args.workload, kind, desc)
+    ours(args, prob, args.workload, kind, desc, blur)
 
 
 if __name__ == "__main__":
