@@ -224,7 +224,7 @@ def polar_real(L: np.ndarray) -> np.ndarray:
 
 class Haar:
     """M = M0 U_DWT^T Lambda~^-1/2 U_DWT M0 (Eq. 34); |M| uses |U| and |M0|.
-    One material, 2-D images."""
+    One material, 2-D images or 3-D volumes."""
 
     def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None):
         self.s = 1.0 / np.sqrt(clamp_eigs(lam))
@@ -251,7 +251,7 @@ class Haar:
 
 class CrossHaar:
     """Cross-material wavelet preconditioner (Eq. 61):
-    M = M0^T U^T K^-1/2 U M0 with U the orthonormal 2-D Haar transform applied
+    M = M0^T U^T K^-1/2 U M0 with U the orthonormal Haar transform (2-D or 3-D) applied
     to every material and K block diagonal over the wavelet coefficients (one
     N_k x N_k block per coefficient).  The estimated blocks are not symmetric;
     as for the cross-material Fourier blocks, K^-1/2 is taken of the polar
@@ -313,6 +313,8 @@ def haar_test_sets(shape, lattice: int = 3):
     more set.  ``lattice=0`` returns the single all-ones set."""
     if lattice == 0:
         return [np.ones(shape, dtype=bool)]
+    if len(shape) == 3:
+        return _haar_test_sets3(shape, lattice)
     sets = []
     ii, jj = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
     lv = haar._levels(*shape)
@@ -327,6 +329,30 @@ def haar_test_sets(shape, lattice: int = 3):
                         sets.append(sel)
     h, w = lv[-1] if lv else shape
     sets.append((ii < h // 2 if lv else ii < h) & (jj < w // 2 if lv else jj < w))
+    return sets
+
+
+def _haar_test_sets3(shape, lattice: int):
+    """3-D: per level, per detail octant (sz, sy, sx) != (0, 0, 0) and per
+    class (a, b, c) of the position within the octant modulo ``lattice``,
+    then the final low-pass block."""
+    sets = []
+    zz, yy, xx = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    lv = haar.levels3(*shape)
+    for d, h, w in lv:
+        d2, h2, w2 = d // 2, h // 2, w // 2
+        for s in haar.OCTANTS[1:]:
+            z0, y0, x0 = s[0] * d2, s[1] * h2, s[2] * w2
+            inband = ((zz >= z0) & (zz < z0 + d2) & (yy >= y0) & (yy < y0 + h2) & (xx >= x0) & (xx < x0 + w2))
+            for a in range(min(lattice, d2)):
+                for b in range(min(lattice, h2)):
+                    for c in range(min(lattice, w2)):
+                        sel = (inband & ((zz - z0) % lattice == a) & ((yy - y0) % lattice == b)
+                               & ((xx - x0) % lattice == c))
+                        if sel.any():
+                            sets.append(sel)
+    d, h, w = (lv[-1][0] // 2, lv[-1][1] // 2, lv[-1][2] // 2) if lv else shape
+    sets.append((zz < d) & (yy < h) & (xx < w))
     return sets
 
 

@@ -203,3 +203,119 @@ def test_cross_haar_one_material_is_haar(oracle_lib):
     for op in ["M", "MT", "absM", "absMT"]:
         a, b = getattr(Ph, op)(v), getattr(Pc, op)(v)
         assert np.allclose(a, b, rtol=1e-10, atol=1e-12 * np.abs(a).max()), op
+
+
+# ---------------------------------------------------------------------------
+# 3-D Haar (volumes [z, y, x])
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (2, 4, 8)])
+def test_haar3_orthonormal_and_abs(shape):
+    from oracle import haar
+    n = int(np.prod(shape))
+    U = dense(lambda v: haar.forward(v[0])[None], shape)
+    UT = dense(lambda v: haar.transpose(v[0])[None], shape)
+    assert np.allclose(U @ U.T, np.eye(n), atol=1e-14)
+    assert np.allclose(UT, U.T, atol=1e-15)
+    Ua = dense(lambda v: haar.forward(v[0], absolute=True)[None], shape)
+    UaT = dense(lambda v: haar.transpose(v[0], absolute=True)[None], shape)
+    assert np.allclose(Ua, np.abs(U), atol=1e-15)
+    assert np.allclose(UaT, np.abs(U).T, atol=1e-15)
+
+
+def _haar1_pyramid(f, n_levels):
+    """Textbook 1-D Haar, level by level: returns the (low, detail) pair of
+    each level, low/detail = (f[2i] +- f[2i+1]) / sqrt(2) of the previous low."""
+    out, low = [], np.asarray(f, dtype=np.float64)
+    for _ in range(n_levels):
+        lo = (low[0::2] + low[1::2]) / math.sqrt(2.0)
+        hi = (low[0::2] - low[1::2]) / math.sqrt(2.0)
+        out.append((lo, hi))
+        low = lo
+    return out
+
+
+def test_haar3_separable_volume():
+    """A separable volume f(z) g(y) h(x): every 3-D Haar coefficient is the
+    product of the three 1-D Haar coefficients of the same level (a detail
+    octant takes the detail part along the axes where its index bit is 1),
+    and the last low-pass value is the product of the three last lows."""
+    from oracle import haar
+    rng = np.random.default_rng(11)
+    f, g, h = rng.standard_normal(8), rng.standard_normal(8), rng.standard_normal(8)
+    vol = np.einsum("i,j,k->ijk", f, g, h)
+    c = haar.forward(vol)
+    pf, pg, ph = (_haar1_pyramid(v, 3) for v in (f, g, h))
+    n = 8
+    for lev in range(3):
+        n2 = n // 2
+        for s in haar.OCTANTS[1:]:
+            want = np.einsum("i,j,k->ijk", pf[lev][s[0]], pg[lev][s[1]], ph[lev][s[2]])
+            got = c[s[0] * n2:(s[0] + 1) * n2, s[1] * n2:(s[1] + 1) * n2, s[2] * n2:(s[2] + 1) * n2]
+            assert np.allclose(got, want, atol=1e-13), (lev, s)
+        n = n2
+    assert abs(c[0, 0, 0] - pf[2][0][0] * pg[2][0][0] * ph[2][0][0]) < 1e-13
+
+
+def test_haar3_test_sets_partition():
+    from oracle.precond import haar_test_sets
+    for shape in [(8, 8, 8), (16, 16, 16), (4, 8, 8)]:
+        cnt = np.zeros(shape, int)
+        for s in haar_test_sets(shape, 3):
+            cnt += s
+        assert (cnt == 1).all(), shape
+
+
+@pytest.mark.parametrize("lattice", [0, 2, 3])
+def test_haar3_exact_on_wavelet_diagonal(lattice):
+    from oracle import haar, precond
+    shape = (8, 8, 8)
+    rng = np.random.default_rng(12)
+    lam = rng.uniform(0.2, 5.0, shape)
+
+    def apply_H(v):
+        return np.stack([haar.transpose(lam * haar.forward(v[k])) for k in range(v.shape[0])])
+    est = precond.haar_eigenvalues(apply_H, shape, lattice=lattice)
+    assert np.allclose(est, lam, rtol=1e-12)
+    P = precond.Haar(est)
+    v = rng.standard_normal((1,) + shape)
+    assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-11, atol=1e-11)
+
+
+def test_cross_haar3_exact_on_wavelet_block_diagonal():
+    from oracle import haar, precond
+    shape, nm = (4, 4, 4), 2
+    rng = np.random.default_rng(13)
+    G = rng.standard_normal(shape + (nm, nm))
+    Kt = np.einsum("...ij,...kj->...ik", G, G) + 0.5 * np.eye(nm)
+
+    def apply_H(v):
+        c = np.stack([haar.forward(v[k]) for k in range(nm)])
+        out = np.einsum("...ij,j...->i...", Kt, c)
+        return np.stack([haar.transpose(out[k]) for k in range(nm)])
+    M0 = precond.Block(np.tile(np.eye(nm), (int(np.prod(shape)), 1, 1)), shape)
+    K = precond.cross_haar_blocks(apply_H, M0, shape, nm)
+    assert np.allclose(K, Kt, rtol=1e-11, atol=1e-11)
+    P = precond.CrossHaar(K, M0)
+    v = rng.standard_normal((nm,) + shape)
+    assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-10, atol=1e-10)
+    Md = dense(P.M, shape, nm)
+    assert np.allclose(dense(P.MT, shape, nm), Md.T, atol=1e-12 * np.abs(Md).max())
+    assert (dense(P.absM, shape, nm) >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all()
+
+
+def test_abs_bounds_dominate_3d(oracle_lib):
+    """|M| >= |M_ij| for the Haar kinds on a tiny cone-beam volume."""
+    import synth
+    from oracle import build, psps
+    g = Geometry(synth.CONE3D, 4, 4, 4, 1.0, 1.0, 1.0, 8, 0.0, 2 * math.pi, 8, 8, 1.5, 1.5, 20.0, 40.0)
+    A = oracle_lib.Projector(g)
+    img = synth.render(g, [synth.Ellipsoid(0.3, -0.2, 0.1, 1.5, 1.2, 1.4, 0.2, 0.02)])
+    y = np.round(1e4 * np.exp(-A.project(img[None])))
+    st = psps.Setup(A, np.ones((1, 1)), np.full((1, 1), 1e4), y, np.array([[50.0]]))
+    for kind in ["haar", "block_haar"]:
+        P = build.build(st, kind)
+        Md = dense(P.M, st.shape)
+        Ad = dense(P.absM, st.shape)
+        assert np.allclose(dense(P.MT, st.shape), Md.T, atol=1e-12 * np.abs(Md).max())
+        assert (Ad >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all(), kind
