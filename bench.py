@@ -67,6 +67,10 @@ WORKLOADS = {
     "c5_cone3d_128_block": ("config5", "block", "128^3@1mm, 180x192x256 cone flat (the 256^3 scan scaled down), "
                                                 "2 materials x 2 kVp, 2x2 per-voxel blocks",
                             {"n": 128, "n_views": 180, "n_u": 256, "n_v": 192}),
+    "c5_cone3d_128_blockhaar": ("config5", "block_haar", "128^3@1mm, 180x192x256 cone flat (the 256^3 scan scaled "
+                                                         "down), 2 materials x 2 kVp, 2x2 per-voxel blocks + 3-D "
+                                                         "cross-material wavelet (Haar)",
+                                {"n": 128, "n_views": 180, "n_u": 256, "n_v": 192}),
     "c2_fan2d_512_haar_blur1": ("config2", "haar", "config 2 read out through a 3-tap detector blur along the "
                                                    "888-bin rows (outer operator B S)", {"blur": "r1"}),
     "c4_mbmd_512_blockfourier_blur3": ("config4_slice", "block_fourier",

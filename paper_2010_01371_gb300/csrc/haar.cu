@@ -13,6 +13,16 @@
 // by m0 on input and scaled by Lambda^-1/2 on output); one CTA then finishes
 // the (n/T) x (n/T) low-pass block.  The inverse runs the same in reverse.
 // Square power-of-two images only (n <= 2048).
+//
+// 3-D volumes [z][y][x] (cubes n^3, n a power of two <= 256): every 2x2x2
+// group v[dz][dy][dx] of the current low-pass block goes to the eight outputs
+//   c[sz][sy][sx] = 2^-3/2 sum (-1)^(sz dz + sy dy + sx dx) v[dz][dy][dx]
+// (three in-place +/- butterflies, one per axis), stored in octant
+// (sz, sy, sx) of the block; the pyramid recurses on octant (0, 0, 0).  The
+// sign matrix is symmetric and, scaled, orthogonal, so the inverse step runs
+// the same butterflies on the octants.  The first log2(T) levels (T =
+// min(16, n)) are local to T^3 tiles in shared memory; one CTA per channel
+// finishes the (n/T)^3 low-pass block.
 #include "haar.cuh"
 
 namespace psps {
@@ -205,15 +215,232 @@ __global__ void coarse_kernel(int n, int C, float *__restrict__ coef, const floa
     for (int k = threadIdx.x; k < C * C; k += blockDim.x) c0[(int64_t)(k / C) * n + k % C] = B[k];
 }
 
+
+// ---------------------------------------------------------------- 3-D
+constexpr int kT3 = 16;
+constexpr int kMaxC3 = 16;  // coarse block side: n / kT3 for n <= 256
+constexpr float kR3 = 0.353553390593273762f;  // 2^-3/2
+
+// In place on v[dz*4 + dy*2 + dx]: afterwards v[sz*4 + sy*2 + sx] holds the
+// output of octant (sz, sy, sx); the same call inverts it.
+__device__ __forceinline__ void bfly8(float (&v)[8], bool ab) {
+    if (ab) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += v[q];
+        t *= kR3;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = t;
+        return;
+    }
+#pragma unroll
+    for (int stride = 1; stride < 8; stride *= 2)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (!(q & stride)) {
+                const float a = v[q], b = v[q + stride];
+                v[q] = a + b;
+                v[q + stride] = a - b;
+            }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] *= kR3;
+}
+
+__device__ __forceinline__ int64_t at3(int n, int z, int y, int x) { return ((int64_t)z * n + y) * n + x; }
+
+// Forward over the tile levels.  grid: (C, C, C * channels), C = n / T.
+__global__ void __launch_bounds__(kThreads)
+    fwd3_tile_kernel(int n, int T, int C, const float *__restrict__ in, float *__restrict__ coef,
+                     const float *__restrict__ pre, const float *__restrict__ scale, unsigned abs_mask) {
+    __shared__ float A[kT3 * kT3 * kT3];
+    const int ch = blockIdx.z / C, tz = blockIdx.z % C, ty = blockIdx.y, tx = blockIdx.x;
+    const bool ab = (abs_mask >> ch) & 1u;
+    const int64_t nnn = (int64_t)n * n * n;
+    const float *src = in + ch * nnn;
+    float *dst = coef + ch * nnn;
+    for (int q = threadIdx.x; q < T * T * T; q += blockDim.x) {
+        const int z = q / (T * T), y = (q / T) % T, x = q % T;
+        const int64_t gi = at3(n, tz * T + z, ty * T + y, tx * T + x);
+        float v = src[gi];
+        if (pre) v *= pre[gi];
+        A[q] = v;
+    }
+    __syncthreads();
+    int h = T, Ng = n;
+    while (h >= 2) {
+        const int h2 = h / 2, N2 = Ng / 2;
+        float ll[2];
+        int cnt = 0;
+        // at most (16/2)^3 = 512 groups: two per thread
+        for (int g = threadIdx.x; g < h2 * h2 * h2; g += blockDim.x, ++cnt) {
+            const int i = g / (h2 * h2), j = (g / h2) % h2, k = g % h2;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = A[((2 * i + (q >> 2)) * T + 2 * j + ((q >> 1) & 1)) * T + 2 * k + (q & 1)];
+            bfly8(v, ab);
+            const int gz = tz * h2 + i, gy = ty * h2 + j, gx = tx * h2 + k;
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+                const int64_t o = at3(n, (q >> 2) * N2 + gz, ((q >> 1) & 1) * N2 + gy, (q & 1) * N2 + gx);
+                dst[o] = scale ? v[q] * scale[o] : v[q];
+            }
+            ll[cnt & 1] = v[0];
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int g = threadIdx.x; g < h2 * h2 * h2; g += blockDim.x, ++cnt) {
+            const int i = g / (h2 * h2), j = (g / h2) % h2, k = g % h2;
+            A[(i * T + j) * T + k] = ll[cnt & 1];
+        }
+        __syncthreads();
+        h = h2;
+        Ng = N2;
+    }
+    if (threadIdx.x == 0) dst[at3(n, tz, ty, tx)] = A[0];
+}
+
+// Inverse over the tile levels: the tile's low-pass value at (tz, ty, tx)
+// and its detail coefficients to voxels (times post, if given).
+__global__ void __launch_bounds__(kThreads)
+    inv3_tile_kernel(int n, int T, int C, const float *__restrict__ coef, float *__restrict__ out,
+                     const float *__restrict__ post, unsigned abs_mask) {
+    __shared__ float A[kT3 * kT3 * kT3];
+    const int ch = blockIdx.z / C, tz = blockIdx.z % C, ty = blockIdx.y, tx = blockIdx.x;
+    const bool ab = (abs_mask >> ch) & 1u;
+    const int64_t nnn = (int64_t)n * n * n;
+    const float *src = coef + ch * nnn;
+    float *dst = out + ch * nnn;
+    if (threadIdx.x == 0) A[0] = src[at3(n, tz, ty, tx)];
+    __syncthreads();
+    int h = 2, Ng = 2 * n / T;
+    while (h <= T) {
+        const int h2 = h / 2, N2 = Ng / 2;
+        float a8[2][8];
+        int cnt = 0;
+        for (int g = threadIdx.x; g < h2 * h2 * h2; g += blockDim.x, ++cnt) {
+            const int i = g / (h2 * h2), j = (g / h2) % h2, k = g % h2;
+            const int gz = tz * h2 + i, gy = ty * h2 + j, gx = tx * h2 + k;
+            float v[8];
+            v[0] = A[(i * T + j) * T + k];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) v[q] = src[at3(n, (q >> 2) * N2 + gz, ((q >> 1) & 1) * N2 + gy, (q & 1) * N2 + gx)];
+            bfly8(v, ab);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a8[cnt & 1][q] = v[q];
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int g = threadIdx.x; g < h2 * h2 * h2; g += blockDim.x, ++cnt) {
+            const int i = g / (h2 * h2), j = (g / h2) % h2, k = g % h2;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                A[((2 * i + (q >> 2)) * T + 2 * j + ((q >> 1) & 1)) * T + 2 * k + (q & 1)] = a8[cnt & 1][q];
+        }
+        __syncthreads();
+        h *= 2;
+        Ng *= 2;
+    }
+    for (int q = threadIdx.x; q < T * T * T; q += blockDim.x) {
+        const int z = q / (T * T), y = (q / T) % T, x = q % T;
+        const int64_t gi = at3(n, tz * T + z, ty * T + y, tx * T + x);
+        float v = A[q];
+        if (post) v *= post[gi];
+        dst[gi] = v;
+    }
+}
+
+// The C^3 low-pass block in one CTA per channel (modes as coarse_kernel).
+__global__ void coarse3_kernel(int n, int C, float *__restrict__ coef, const float *__restrict__ scale, int mode,
+                               unsigned abs_mask) {
+    extern __shared__ float B[];  // C^3 + C^3
+    const int C3 = C * C * C;
+    float *tmp = B + C3;
+    const int ch = blockIdx.x;
+    const bool ab = (abs_mask >> ch) & 1u;
+    float *c0 = coef + (int64_t)ch * n * n * n;
+    for (int q = threadIdx.x; q < C3; q += blockDim.x) B[q] = c0[at3(n, q / (C * C), (q / C) % C, q % C)];
+    __syncthreads();
+    if (mode & 1) {
+        for (int h = C; h >= 2; h /= 2) {
+            const int h2 = h / 2;
+            for (int g = threadIdx.x; g < h2 * h2 * h2; g += blockDim.x) {
+                const int i = g / (h2 * h2), j = (g / h2) % h2, k = g % h2;
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    v[q] = B[((2 * i + (q >> 2)) * C + 2 * j + ((q >> 1) & 1)) * C + 2 * k + (q & 1)];
+                bfly8(v, ab);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    tmp[(((q >> 2) * h2 + i) * C + ((q >> 1) & 1) * h2 + j) * C + (q & 1) * h2 + k] = v[q];
+            }
+            __syncthreads();
+            for (int g = threadIdx.x; g < h * h * h; g += blockDim.x) {
+                const int idx = ((g / (h * h)) * C + (g / h) % h) * C + g % h;
+                B[idx] = tmp[idx];
+            }
+            __syncthreads();
+        }
+    }
+    if (mode & 2) {
+        for (int q = threadIdx.x; q < C3; q += blockDim.x) B[q] *= scale[at3(n, q / (C * C), (q / C) % C, q % C)];
+        __syncthreads();
+    }
+    if (mode & 4) {
+        for (int h = 2; h <= C; h *= 2) {
+            const int h2 = h / 2;
+            for (int g = threadIdx.x; g < h2 * h2 * h2; g += blockDim.x) {
+                const int i = g / (h2 * h2), j = (g / h2) % h2, k = g % h2;
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    v[q] = B[(((q >> 2) * h2 + i) * C + ((q >> 1) & 1) * h2 + j) * C + (q & 1) * h2 + k];
+                bfly8(v, ab);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    tmp[((2 * i + (q >> 2)) * C + 2 * j + ((q >> 1) & 1)) * C + 2 * k + (q & 1)] = v[q];
+            }
+            __syncthreads();
+            for (int g = threadIdx.x; g < h * h * h; g += blockDim.x) {
+                const int idx = ((g / (h * h)) * C + (g / h) % h) * C + g % h;
+                B[idx] = tmp[idx];
+            }
+            __syncthreads();
+        }
+    }
+    for (int q = threadIdx.x; q < C3; q += blockDim.x) c0[at3(n, q / (C * C), (q / C) % C, q % C)] = B[q];
+}
+
 }  // namespace
 
-bool haar_supported(int nx, int ny) {
+bool haar_supported(int nx, int ny, int nz) {
+    if (nz > 1) {
+        if (nx != ny || ny != nz || nx < 2 || nx > kT3 * kMaxC3) return false;
+        return (nx & (nx - 1)) == 0;
+    }
     if (nx != ny || nx < 2 || nx > 2048) return false;
     return (nx & (nx - 1)) == 0;
 }
 
+namespace {
+struct Haar3Launch {
+    int T, C;
+    size_t smem;
+    explicit Haar3Launch(int n) : T(n < kT3 ? n : kT3), C(n / (n < kT3 ? n : kT3)), smem(2 * sizeof(float) * C * C * C) {}
+};
+}  // namespace
+
 mbir_status haar_forward(int n, int channels, const float *in, float *coef, const float *pre, const float *scale,
-                         unsigned abs_mask, cudaStream_t s) {
+                         unsigned abs_mask, cudaStream_t s, int nz) {
+    if (nz > 1) {
+        const Haar3Launch L(n);
+        fwd3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, in, coef, pre, scale,
+                                                                              abs_mask);
+        PSPS_LAUNCH_CHECK();
+        coarse3_kernel<<<channels, kThreads, L.smem, s>>>(n, L.C, coef, scale, scale ? 3 : 1, abs_mask);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
     const int T = n < kT ? n : kT, C = n / T;
     fwd_tile_kernel<<<dim3(C, C, channels), kThreads, 0, s>>>(n, T, in, coef, pre, scale, abs_mask);
     PSPS_LAUNCH_CHECK();
@@ -223,7 +450,15 @@ mbir_status haar_forward(int n, int channels, const float *in, float *coef, cons
 }
 
 mbir_status haar_inverse(int n, int channels, float *coef, float *out, const float *post, unsigned abs_mask,
-                         cudaStream_t s) {
+                         cudaStream_t s, int nz) {
+    if (nz > 1) {
+        const Haar3Launch L(n);
+        coarse3_kernel<<<channels, kThreads, L.smem, s>>>(n, L.C, coef, nullptr, 4, abs_mask);
+        PSPS_LAUNCH_CHECK();
+        inv3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, coef, out, post, abs_mask);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
     const int T = n < kT ? n : kT, C = n / T;
     coarse_kernel<<<channels, kThreads, 2 * C * C * sizeof(float), s>>>(n, C, coef, nullptr, 4, abs_mask);
     PSPS_LAUNCH_CHECK();
@@ -233,7 +468,18 @@ mbir_status haar_inverse(int n, int channels, float *coef, float *out, const flo
 }
 
 mbir_status haar_apply(int n, int channels, const float *in, float *tmp, float *out, const float *m0,
-                       const float *scale, unsigned abs_mask, cudaStream_t s) {
+                       const float *scale, unsigned abs_mask, cudaStream_t s, int nz) {
+    if (nz > 1) {
+        const Haar3Launch L(n);
+        fwd3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, in, tmp, m0, scale,
+                                                                              abs_mask);
+        PSPS_LAUNCH_CHECK();
+        coarse3_kernel<<<channels, kThreads, L.smem, s>>>(n, L.C, tmp, scale, 7, abs_mask);
+        PSPS_LAUNCH_CHECK();
+        inv3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, tmp, out, m0, abs_mask);
+        PSPS_LAUNCH_CHECK();
+        return MBIR_OK;
+    }
     const int T = n < kT ? n : kT, C = n / T;
     fwd_tile_kernel<<<dim3(C, C, channels), kThreads, 0, s>>>(n, T, in, tmp, m0, scale, abs_mask);
     PSPS_LAUNCH_CHECK();

@@ -127,6 +127,32 @@ __global__ void haar_mask_kernel(int n, int h, int band, int a, int c, int P, fl
     }
 }
 
+// 3-D: indicator of one test set of an n^3 volume: level block size h, detail
+// octant (sz, sy, sx) = bits of band + 1 (band 0..6), band 7 = final
+// low-pass block; lattice class (a, b, c) of the (z, y, x) position inside
+// the octant modulo P (P = 0: all ones).
+__global__ void haar_mask3_kernel(int n, int h, int band, int a, int b, int c, int P, float *out) {
+    const int64_t nnn = (int64_t)n * n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnn; t += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(t / ((int64_t)n * n)), y = (int)((t / n) % n), x = (int)(t % n);
+        float v = 1.f;
+        if (P != 0) {
+            const int h2 = h / 2;
+            bool in;
+            if (band == 7) {
+                in = z < h2 && y < h2 && x < h2;
+            } else {
+                const int oct = band + 1;
+                const int z0 = (oct >> 2) * h2, y0 = ((oct >> 1) & 1) * h2, x0 = (oct & 1) * h2;
+                in = z >= z0 && z < z0 + h2 && y >= y0 && y < y0 + h2 && x >= x0 && x < x0 + h2;
+                if (in) in = ((z - z0) % P == a) && ((y - y0) % P == b) && ((x - x0) % P == c);
+            }
+            v = in ? 1.f : 0.f;
+        }
+        out[t] = v;
+    }
+}
+
 __global__ void masked_ratio_kernel(const float *mask, const float *r, const float *den, float *lam, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         if (mask[i] != 0.f) lam[i] = r[i] / den[i];
@@ -384,31 +410,43 @@ __global__ void invsqrt_floor_kernel(int nm, int64_t n, const float *__restrict_
 }
 
 // The Haar test sets of an n x n image: one per (level block h, detail band,
-// lattice class (a, c) mod P), plus the final low-pass block; P = 0 gives the
-// paper's single all-ones set.
+// lattice class (a, c) mod P), plus the final low-pass block; of an n^3
+// volume: one per (h, detail octant, class (a, b, c) mod P), plus the final
+// low-pass block.  P = 0 gives the paper's single all-ones set.
 struct HaarSet {
-    int h, band, a, c;
+    int h, band, a, b, c;
 };
 
-std::vector<HaarSet> haar_sets(int nx, int P) {
+std::vector<HaarSet> haar_sets(int nx, int P, int nz) {
     std::vector<HaarSet> sets;
     if (P == 0) {
-        sets.push_back({nx, 0, 0, 0});
+        sets.push_back({nx, 0, 0, 0, 0});
         return sets;
     }
+    const bool vol = nz > 1;
     for (int h = nx; h >= 2; h /= 2) {
-        const int h2 = h / 2;
-        for (int band = 0; band < 3; ++band)
-            for (int a = 0; a < (P < h2 ? P : h2); ++a)
-                for (int c = 0; c < (P < h2 ? P : h2); ++c) sets.push_back({h, band, a, c});
+        const int h2 = h / 2, L = P < h2 ? P : h2;
+        for (int band = 0; band < (vol ? 7 : 3); ++band)
+            for (int a = 0; a < L; ++a)
+                for (int b = 0; b < (vol ? L : 1); ++b)
+                    for (int c = 0; c < L; ++c) sets.push_back({h, band, a, b, c});
     }
-    sets.push_back({2, 3, 0, 0});
+    sets.push_back({2, vol ? 7 : 3, 0, 0, 0});
     return sets;
 }
+
+void launch_haar_mask(int nx, int nz, const HaarSet &st, int P, float *out, cudaStream_t s);
 
 unsigned gs(int64_t n) {
     int64_t b = cdiv(n, kThreads);
     return (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+void launch_haar_mask(int nx, int nz, const HaarSet &st, int P, float *out, cudaStream_t s) {
+    if (nz > 1)
+        haar_mask3_kernel<<<gs((int64_t)nx * nx * nx), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.b, st.c, P, out);
+    else
+        haar_mask_kernel<<<gs((int64_t)nx * nx), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.c, P, out);
 }
 
 // Matrix-free Hessian H v = A^T F A v + R v for nprobe stacked vectors of nm
@@ -578,7 +616,8 @@ mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out,
             return pc->fft.filter(pc->nm, in, pc->Z.p, out, pc->kind == PSPS_PRECOND_MOD_FOURIER ? pc->m0.p : nullptr,
                                   absm ? pc->s_abs.p : pc->s.p, s);
         case PSPS_PRECOND_HAAR:
-            return haar_apply(pc->nx, pc->nm, in, pc->tmp.p, out, pc->m0.p, pc->s.p, absm ? 0xffffffffu : 0u, s);
+            return haar_apply(pc->nx, pc->nm, in, pc->tmp.p, out, pc->m0.p, pc->s.p, absm ? 0xffffffffu : 0u, s,
+                              pc->nz);
         case PSPS_PRECOND_BLOCK:
             block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Babs.p : pc->B.p, in, out,
                                                               tr ? 1 : 0);
@@ -607,11 +646,11 @@ mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out,
             float *t0 = pc->tmp.p, *t1 = pc->tmp.p + pc->n * pc->nm;
             block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
             PSPS_LAUNCH_CHECK();
-            PSPS_TRY(haar_forward(pc->nx, pc->nm, t0, t1, nullptr, nullptr, amask, s));
+            PSPS_TRY(haar_forward(pc->nx, pc->nm, t0, t1, nullptr, nullptr, amask, s, pc->nz));
             block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Li_abs.p : pc->Li.p, t1, t0,
                                                               tr ? 1 : 0);
             PSPS_LAUNCH_CHECK();
-            PSPS_TRY(haar_inverse(pc->nx, pc->nm, t0, t1, nullptr, amask, s));
+            PSPS_TRY(haar_inverse(pc->nx, pc->nm, t0, t1, nullptr, amask, s, pc->nz));
             block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
             PSPS_LAUNCH_CHECK();
             return MBIR_OK;
@@ -654,11 +693,11 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         return fail(MBIR_ERR_ARG, "projection-domain decomposition supports NONE and BLOCK preconditioners");
     if ((kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_HAAR) && nm != 1)
         return fail(MBIR_ERR_ARG, "Fourier / modified Fourier / Haar preconditioners are single-material (n_mat = 1)");
-    if (plan && plan->g.kind == MBIR_CONE3D && (kind == PSPS_PRECOND_HAAR || kind == PSPS_PRECOND_BLOCK_HAAR))
-        return fail(MBIR_ERR_UNIMPLEMENTED, "Haar preconditioners are 2-D (3-D volumes: BLOCK and the Fourier kinds)");
     const bool haar_kind = kind == PSPS_PRECOND_HAAR || kind == PSPS_PRECOND_BLOCK_HAAR;
-    if (haar_kind && !haar_supported(pc->nx, plan->g.ny))
-        return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048)");
+    if (haar_kind && !haar_supported(pc->nx, plan->g.ny, pc->nz))
+        return fail(MBIR_ERR_ARG,
+                    "Haar preconditioners need a square power-of-two image (<= 2048) or a cubic power-of-two volume "
+                    "(<= 256)");
     if (haar_kind && (haar_lattice < 0 || haar_lattice > 64)) return fail(MBIR_ERR_ARG, "haar_lattice must be 0..64");
     if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER || kind == PSPS_PRECOND_BLOCK_FOURIER)
         PSPS_TRY(pc->fft.init(pc->nx, pc->ny, pc->nz));
@@ -755,36 +794,50 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     if (kind == PSPS_PRECOND_BLOCK_HAAR) {
         // K_k of Eqs. 59-60 with the lattice test functions: for every test
         // set xi and material k, dx = U^T xi in material k; column k of the
-        // blocks of the set's coefficients = U M0^T H M0 dx / (U dx)
-        const int nx = pc->nx;
-        const std::vector<HaarSet> sets = haar_sets(nx, haar_lattice);
+        // blocks of the set's coefficients = U M0^T H M0 dx / (U dx).  The
+        // (set, material) probes go through the Hessian in batches that fill
+        // the plan's channels.
+        const int nx = pc->nx, nz = pc->nz;
+        const std::vector<HaarSet> sets = haar_sets(nx, haar_lattice, nz);
+        const int np = max_ch / nm > 1 ? max_ch / nm : 1;
         DBuf<float> K, mask, coef, dx, den, d, v, hv, r;
         PSPS_TRY(K.alloc((size_t)nm * nm * n));
-        PSPS_TRY(mask.alloc(n));
-        PSPS_TRY(coef.alloc(n));
-        PSPS_TRY(dx.alloc(n));
-        PSPS_TRY(den.alloc(n));
-        PSPS_TRY(d.alloc((size_t)nm * n));
-        PSPS_TRY(v.alloc((size_t)nm * n));
-        PSPS_TRY(hv.alloc((size_t)nm * n));
-        PSPS_TRY(r.alloc((size_t)nm * n));
+        PSPS_TRY(mask.alloc((size_t)np * n));
+        PSPS_TRY(coef.alloc((size_t)np * n));
+        PSPS_TRY(dx.alloc((size_t)np * n));
+        PSPS_TRY(den.alloc((size_t)np * n));
+        PSPS_TRY(d.alloc((size_t)np * nm * n));
+        PSPS_TRY(v.alloc((size_t)np * nm * n));
+        PSPS_TRY(hv.alloc((size_t)np * nm * n));
+        PSPS_TRY(r.alloc((size_t)np * nm * n));
         PSPS_CUDA(cudaMemsetAsync(K.p, 0, sizeof(float) * K.n, s));
-        for (const HaarSet &st : sets) {
-            haar_mask_kernel<<<gs(n), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.c, haar_lattice, mask.p);
+        const size_t n_pairs = sets.size() * (size_t)nm;
+        for (size_t p0 = 0; p0 < n_pairs; p0 += np) {
+            const int nb = (int)(n_pairs - p0 < (size_t)np ? n_pairs - p0 : np);
+            for (int b = 0; b < nb; ++b)
+                launch_haar_mask(nx, nz, sets[(p0 + b) / nm], haar_lattice, mask.p + (int64_t)b * n, s);
             PSPS_LAUNCH_CHECK();
-            PSPS_CUDA(cudaMemcpyAsync(coef.p, mask.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-            PSPS_TRY(haar_inverse(nx, 1, coef.p, dx.p, nullptr, 0u, s));
-            PSPS_TRY(haar_forward(nx, 1, dx.p, den.p, nullptr, nullptr, 0u, s));
-            for (int k = 0; k < nm; ++k) {
-                PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * nm * n, s));
-                PSPS_CUDA(cudaMemcpyAsync(d.p + (int64_t)k * n, dx.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-                PSPS_TRY(launch_block_apply(nm, n, pc->B.p, d.p, v.p, 0, s));
-                PSPS_TRY(H.apply(v.p, hv.p, 1, s));
-                PSPS_TRY(launch_block_apply(nm, n, pc->B.p, hv.p, v.p, 1, s));
-                PSPS_TRY(haar_forward(nx, nm, v.p, r.p, nullptr, nullptr, 0u, s));
-                masked_block_ratio_kernel<<<gs(n), kThreads, 0, s>>>(mask.p, r.p, den.p, K.p, nm, k, n);
-                PSPS_LAUNCH_CHECK();
+            PSPS_CUDA(cudaMemcpyAsync(coef.p, mask.p, sizeof(float) * nb * n, cudaMemcpyDeviceToDevice, s));
+            PSPS_TRY(haar_inverse(nx, nb, coef.p, dx.p, nullptr, 0u, s, nz));
+            PSPS_TRY(haar_forward(nx, nb, dx.p, den.p, nullptr, nullptr, 0u, s, nz));
+            PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * nb * nm * n, s));
+            for (int b = 0; b < nb; ++b) {
+                const int k = (int)((p0 + b) % nm);
+                PSPS_CUDA(cudaMemcpyAsync(d.p + ((int64_t)b * nm + k) * n, dx.p + (int64_t)b * n, sizeof(float) * n,
+                                          cudaMemcpyDeviceToDevice, s));
             }
+            for (int b = 0; b < nb; ++b)
+                PSPS_TRY(launch_block_apply(nm, n, pc->B.p, d.p + (int64_t)b * nm * n, v.p + (int64_t)b * nm * n, 0, s));
+            PSPS_TRY(H.apply(v.p, hv.p, nb, s));
+            for (int b = 0; b < nb; ++b)
+                PSPS_TRY(launch_block_apply(nm, n, pc->B.p, hv.p + (int64_t)b * nm * n, v.p + (int64_t)b * nm * n, 1, s));
+            PSPS_TRY(haar_forward(nx, nb * nm, v.p, r.p, nullptr, nullptr, 0u, s, nz));
+            for (int b = 0; b < nb; ++b) {
+                const int k = (int)((p0 + b) % nm);
+                masked_block_ratio_kernel<<<gs(n), kThreads, 0, s>>>(mask.p + (int64_t)b * n, r.p + (int64_t)b * nm * n,
+                                                                     den.p + (int64_t)b * n, K.p, nm, k, n);
+            }
+            PSPS_LAUNCH_CHECK();
         }
         DBuf<float2> Kc;
         DBuf<float> P, lmax;
@@ -834,7 +887,8 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     // ---- Haar
     {
         const int P = haar_lattice;
-        const std::vector<HaarSet> sets = haar_sets(nx, P);
+        const int nz = pc->nz;
+        const std::vector<HaarSet> sets = haar_sets(nx, P, nz);
         const int batch = plan->n_mat_max;
         DBuf<float> mask, dx, r, den, coef;
         PSPS_TRY(mask.alloc((size_t)batch * n));
@@ -847,17 +901,14 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_CUDA(cudaMemsetAsync(lam.p, 0, sizeof(float) * n, s));
         for (size_t s0 = 0; s0 < sets.size(); s0 += batch) {
             const int nb = (int)(sets.size() - s0 < (size_t)batch ? sets.size() - s0 : batch);
-            for (int b = 0; b < nb; ++b) {
-                const HaarSet &st = sets[s0 + b];
-                haar_mask_kernel<<<gs(n), kThreads, 0, s>>>(nx, st.h, st.band, st.a, st.c, P, mask.p + (int64_t)b * n);
-            }
+            for (int b = 0; b < nb; ++b) launch_haar_mask(nx, nz, sets[s0 + b], P, mask.p + (int64_t)b * n, s);
             PSPS_LAUNCH_CHECK();
             // dx = U^T xi  (haar_inverse uses its coefficient input as scratch)
             PSPS_CUDA(cudaMemcpyAsync(coef.p, mask.p, sizeof(float) * nb * n, cudaMemcpyDeviceToDevice, s));
-            PSPS_TRY(haar_inverse(nx, nb, coef.p, dx.p, nullptr, 0u, s));
+            PSPS_TRY(haar_inverse(nx, nb, coef.p, dx.p, nullptr, 0u, s, nz));
             PSPS_TRY(applyN(dx.p, tmp2.p, nb));
-            PSPS_TRY(haar_forward(nx, nb, tmp2.p, r.p, nullptr, nullptr, 0u, s));
-            PSPS_TRY(haar_forward(nx, nb, dx.p, den.p, nullptr, nullptr, 0u, s));
+            PSPS_TRY(haar_forward(nx, nb, tmp2.p, r.p, nullptr, nullptr, 0u, s, nz));
+            PSPS_TRY(haar_forward(nx, nb, dx.p, den.p, nullptr, nullptr, 0u, s, nz));
             for (int b = 0; b < nb; ++b)
                 masked_ratio_kernel<<<gs(n), kThreads, 0, s>>>(mask.p + (int64_t)b * n, r.p + (int64_t)b * n,
                                                                den.p + (int64_t)b * n, lam.p, n);
@@ -929,9 +980,9 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
     if (kind == PSPS_PRECOND_BLOCK_HAAR) {
         if (!plan || !lam || !blocks)
             return fail(MBIR_ERR_ARG, "psps_precondition_create: BLOCK_HAAR needs a plan, lam (P blocks) and blocks");
-        if (plan->g.kind == MBIR_CONE3D) return fail(MBIR_ERR_UNIMPLEMENTED, "Haar preconditioners are 2-D");
-        if (!haar_supported(plan->g.nx, plan->g.ny))
-            return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048)");
+        if (!haar_supported(plan->g.nx, plan->g.ny, pc->nz))
+            return fail(MBIR_ERR_ARG, "Haar preconditioners need a square power-of-two image (<= 2048) or a cubic "
+                                      "power-of-two volume (<= 256)");
         PSPS_TRY(pc->B.alloc((size_t)nm * nm * n));
         PSPS_TRY(pc->Babs.alloc((size_t)nm * nm * n));
         PSPS_CUDA(cudaMemcpyAsync(pc->B.p, blocks, sizeof(float) * pc->B.n, cudaMemcpyDeviceToDevice, s));
@@ -944,10 +995,9 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
     }
     if (!plan || nm != 1 || !lam)
         return fail(MBIR_ERR_ARG, "psps_precondition_create: Fourier/Haar kinds need a plan, n_mat = 1 and lam");
-    if (kind == PSPS_PRECOND_HAAR && plan->g.kind == MBIR_CONE3D)
-        return fail(MBIR_ERR_UNIMPLEMENTED, "Haar preconditioners are 2-D");
-    if (kind == PSPS_PRECOND_HAAR && !haar_supported(plan->g.nx, plan->g.ny))
-        return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048)");
+    if (kind == PSPS_PRECOND_HAAR && !haar_supported(plan->g.nx, plan->g.ny, pc->nz))
+        return fail(MBIR_ERR_ARG, "Haar preconditioner needs a square power-of-two image (<= 2048) or a cubic "
+                                  "power-of-two volume (<= 256)");
     if (kind == PSPS_PRECOND_FOURIER || kind == PSPS_PRECOND_MOD_FOURIER)
         PSPS_TRY(pc->fft.init(pc->nx, pc->ny, pc->nz));
     PSPS_TRY(pc->tmp.alloc((size_t)n * 4));

@@ -159,5 +159,81 @@ def test_3d_cross_material_fourier(psps, oracle_lib):
     shape = (2,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, "block_fourier", data), P, shape, APPLY_TOL)
     check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
-    with pytest.raises(RuntimeError):
-        psps.Precond(plan, spec, "block_haar", to_dev(prob.y), prob.beta)
+
+
+def cone_haar_problem(n=16):
+    """One-material cone-beam problem on the config-5 scan scaled to n^3."""
+    g = synth.config5(n=n, n_views=12 * n // 16, n_u=2 * n, n_v=3 * n // 2, rays=False).geom
+    shapes = [synth.Ellipsoid(0.0, 0.0, 0.0, 50.0, 40.0, 45.0, 0.3, 0.02),
+              synth.Ellipsoid(15.0, -10.0, 5.0, 12.0, 9.0, 10.0, 0.0, 0.01)]
+    return synth.mbir_problem(5, g, shapes, 1e4, 1e3, 50, "haar", f"cone_mbir_{n}")
+
+
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_3d_haar_apply(psps, oracle_lib, n):
+    """3-D Haar preconditioner (Eq. 34 over the voxel grid) from given
+    eigenvalues and m0: 16^3 is one shared-memory tile, 32^3 and 64^3 add the
+    coarse low-pass stage (2^3 and 4^3 tiles)."""
+    from oracle import precond
+    geom = synth.config5(n=n, n_views=12, n_u=2 * n, n_v=3 * n // 2, rays=False).geom
+    rng = np.random.default_rng(n)
+    lam = rng.uniform(0.1, 10.0, geom.image_shape)
+    m0 = rng.uniform(0.5, 2.0, geom.image_shape)
+    P = precond.Haar(lam, m0)
+    plan, spec = psps.Plan(geom), psps.Spectrum(np.ones((1, 1)), np.full((1, 1), 1e4))
+    pc = psps.Precond(plan, spec, "haar", lam=to_dev(lam), m0=to_dev(m0))
+    check_ops(psps, pc, P, (1,) + geom.image_shape, APPLY_TOL)
+
+
+def test_3d_cross_haar_apply(psps, oracle_lib):
+    """Cross-material wavelet (Eq. 61) over a 32^3 volume from given blocks."""
+    from oracle import precond
+    geom = synth.config5(n=32, n_views=12, n_u=64, n_v=48, rays=False).geom
+    nm, shape = 2, geom.image_shape
+    n = int(np.prod(shape))
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal(shape + (nm, nm))
+    K = np.einsum("...ij,...kj->...ik", G, G) + 0.3 * np.eye(nm) + 0.2 * rng.standard_normal(shape + (nm, nm))
+    Gb = rng.standard_normal((n, nm, nm))
+    B = np.einsum("nij,nkj->nik", Gb, Gb) + np.eye(nm)
+    M0 = precond.Block(B, shape)
+    P = precond.CrossHaar(K, M0)
+    Pp = precond.polar_real(K)
+    lam = np.ascontiguousarray(np.transpose(Pp.reshape(-1, nm, nm), (1, 2, 0)))
+    blocks = np.ascontiguousarray(np.transpose(B, (1, 2, 0)))
+    E = np.arange(20.0, 141.0)
+    spec = psps.Spectrum(synth.material_Q(E, ["water", "iodine"], rng), np.ones((2, E.size)))
+    pc = psps.Precond(psps.Plan(geom), spec, "block_haar", lam=to_dev(lam), blocks=to_dev(blocks))
+    check_ops(psps, pc, P, (nm,) + shape, APPLY_TOL)
+
+
+def test_3d_haar_build(psps, oracle_lib):
+    """GPU build of the 3-D Haar eigenvalues (Eq. 18 with the 3-D lattice test
+    functions) against the FP64 build on a 16^3 cone-beam problem."""
+    prob = cone_haar_problem(16)
+    st, P, data = oracle_precond(oracle_lib, prob, "haar")
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (1,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, "haar", data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "haar", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+
+
+def test_3d_cross_material_wavelet_build(psps, oracle_lib):
+    """Cross-material wavelet blocks (Eqs. 59-60) over a 16^3 volume with the
+    two-material cone-beam workload: apply from the oracle's blocks and GPU
+    build (batched (set, material) probes)."""
+    prob = synth.config5(n=16, n_views=12, n_u=32, n_v=24)
+    st, P, data = oracle_precond(oracle_lib, prob, "block_haar")
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    shape = (2,) + prob.geom.image_shape
+    check_ops(psps, gpu_precond_from(psps, plan, spec, "block_haar", data), P, shape, APPLY_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "block_haar", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+
+
+def test_3d_haar_rejects_non_cubes(psps):
+    from paper_2010_01371_gb300._abi import MbirError
+    geom = synth.Geometry(synth.CONE3D, 16, 16, 8, 1.0, 1.0, 1.0, 12, 0.0, 6.283185307179586, 32, 24, 1.0, 1.0,
+                          60.0, 120.0)
+    plan, spec = psps.Plan(geom), psps.Spectrum(np.ones((1, 1)), np.full((1, 1), 1e4))
+    with pytest.raises(MbirError):
+        psps.Precond(plan, spec, "haar", lam=to_dev(np.ones(geom.image_shape)))

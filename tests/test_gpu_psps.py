@@ -98,6 +98,14 @@ def test_config4_slice_no_ls(psps, oracle_lib, kind):
     assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
 
 
+def test_config5_16_block_haar_no_ls(psps, oracle_lib):
+    """3-D cross-material wavelet (Eq. 61 over the voxel grid), 16^3."""
+    prob = synth.config5(n=16, n_views=12, n_u=32, n_v=24)
+    xo, ho, ao, xg, hg, ag = run_both(psps, oracle_lib, prob, "block_haar", 20, line_search=False)
+    assert np.max(np.abs(hg - ho) / np.abs(ho)) < OBJ_TOL, np.max(np.abs(hg - ho) / np.abs(ho))
+    assert rel_l2(xg, xo) < IMG_TOL, rel_l2(xg, xo)
+
+
 @pytest.mark.parametrize("kind", ["none", "block"])
 def test_config5_reduced_no_ls(psps, oracle_lib, kind):
     """3-D cone-beam one-step MBMD (2 materials, dual energy), 32^3 reduction."""
@@ -113,7 +121,8 @@ def step_cases():
     c3 = lambda: synth.config3(n_views=12, n_u=301)            # noqa: E731
     c4 = lambda: synth.config4_slice(nx=64, n_views=90, n_u=111)   # noqa: E731
     c5 = lambda: synth.config5(n=32, n_views=24, n_u=64, n_v=48)   # noqa: E731
-    return {"c1-none": (c1, "none", True), "c1-fourier": (c1, "fourier", True),
+    c5s = lambda: synth.config5(n=16, n_views=12, n_u=32, n_v=24)  # noqa: E731
+    return {"c5_16-block_haar": (c5s, "block_haar", True), "c1-none": (c1, "none", True), "c1-fourier": (c1, "fourier", True),
             "c1-mod_fourier": (c1, "mod_fourier", True), "c1-haar": (c1, "haar", True),
             "c1-block": (c1, "block", True), "c2-haar": (c2, "haar", True), "c2-none": (c2, "none", True),
             "c3-block": (c3, "block", False),
