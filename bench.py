@@ -39,13 +39,7 @@ DEVLS_BYTES = 80
 # Counters of the dominant kernel from one ncu capture of the same kernel and
 # workload (summaries under profiles/): DRAM bytes read + written per launch,
 # and the unit that binds it.  Remove an entry when its kernel changes.
-NCU_CAPTURES = {
-    ("c2_fan2d_512_haar", "backproject"): {
-        "traffic": 14.02e6,
-        "binding": {"unit": "SM shared-memory pipe (wavefronts)", "frac_of_peak": 0.772,
-                    "source": "profiles/back_tile_2d_c2_fan512.md"},
-    },
-}
+NCU_CAPTURES = {}
 
 WORKLOADS = {
     "c2_fan2d_512_haar": ("config2", "haar", "512x512@0.5mm, 720x888 fan curved, Haar(M0, lattice 3)"),

@@ -229,6 +229,12 @@ struct mbir_plan {
     // scratch: packed / transposed image copies for the forward projector
     // (3-D: one copy per driving axis)
     psps::DBuf<float> xrow, xcol, xcol3;
+    // 2-D tile transpose: per channel, max_i |w_i s_i| as float bits (sets
+    // the fixed-point scale of the shared-memory accumulators)
+    psps::DBuf<unsigned> wmax;
+    // bound on the rays of one view that add to one tile accumulator (0: none
+    // known; the CTA's candidate count bounds it then)
+    int cell_rays = 0;
 };
 
 struct mbmd_spectrum {

@@ -23,6 +23,7 @@
 //    gather (deterministic, no atomics) and a ray-driven scatter with global
 //    FP32 atomics, all with the forward's per-ray weights
 //    (mbir_plan_set_backprojector).
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -565,57 +566,109 @@ __device__ __forceinline__ void tile_ray_range_approx(const float4 &r, int c0, i
 // epilogue drops.
 //
 // Samples are split with joseph_split, like the forward projector's.
-__device__ __forceinline__ void red_shared_pair(unsigned addr, float lo, float hi) {
+//
+// The accumulators are 32-bit fixed point: shared-memory integer adds are
+// native, while an FP32 shared-memory add costs a load and a compare-and-swap
+// (three wavefronts of the shared-memory pipe that bounds this kernel against
+// one).  Channel c uses the power-of-two scale
+//   sc = min(2^21 / M_c, 2^30 / (T M_c)),  M_c = max_i |w_i s_c,i|,
+// T = a bound on the terms one accumulator receives: a ray adds at most one
+// term to a given accumulator, so T = min(the CTA's candidate rays, its
+// views x the plan's bound on the rays of one view that reach one
+// accumulator, cell_rays).  Every term is at most M_c sc <= 2^21 (so the
+// conversion below is exact rounding to nearest) and T of them stay below
+// 2^30 + T < 2^31.
+// Each term is rounded once (half a unit of 2^-21 M_c at most); the sums are
+// exact and order-independent, and the epilogue converts back by 1 / sc.
+constexpr float kFixMagic = 12582912.f;  // 1.5 * 2^23: x + magic rounds x (|x| <= 2^22) to an integer
+constexpr int kFixMagicBits = 0x4B400000;
+
+__device__ __forceinline__ int fix_round(float x) { return __float_as_int(x + kFixMagic) - kFixMagicBits; }
+
+__device__ __forceinline__ void red_shared_pair(unsigned addr, int lo, int hi) {
     asm volatile(
-        "red.shared.add.f32 [%0], %1;\n\t"
-        "red.shared.add.f32 [%0+128], %2;" ::"r"(addr),
-        "f"(lo), "f"(hi)
+        "red.shared.add.s32 [%0], %1;\n\t"
+        "red.shared.add.s32 [%0+128], %2;" ::"r"(addr),
+        "r"(lo), "r"(hi)
         : "memory");
 }
 
 // Kept rays [j0, j1) of one driving axis: fi = this lane's driving index,
 // rowbase = the tile's first interpolated index - 1, addr = byte address of
-// this lane's column in the axis' first accumulator plane; ws2 holds the
-// weighted channels 2 and 3 (NC > 2).
+// this lane's column in the axis' first accumulator plane; ws holds the
+// scaled, weighted channels 0 and 1, ws2 channels 2 and 3 (NC > 2).
 template <int NC>
 __device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, const float2 *__restrict__ ws2, int j0,
                                                int j1, float fi, int rowbase, unsigned addr) {
     constexpr unsigned kPlaneBytes = 4u * (kBT + 2) * kBT;
 #pragma unroll 2
     for (int j = j0; j < j1; ++j) {
-        const float4 a = ws[j];  // f0 - 1/2, df, w * sino[0], w * sino[1]
+        const float4 a = ws[j];  // f0 - 1/2, df, sc0 w sino[0], sc1 w sino[1]
         float f;                 // weight of the upper pixel
         const int jr = joseph_split(fmaf(fi, a.y, a.x), f) - rowbase;  // interpolated index - (first index - 1)
         if ((unsigned)jr <= (unsigned)kBT) {
             const unsigned q = addr + (unsigned)jr * (4u * kBT);
             const float u0 = f * a.z;
-            red_shared_pair(q, a.z - u0, u0);
+            red_shared_pair(q, fix_round(a.z - u0), fix_round(u0));
             if (NC >= 2) {
                 const float u1 = f * a.w;
-                red_shared_pair(q + kPlaneBytes, a.w - u1, u1);
+                red_shared_pair(q + kPlaneBytes, fix_round(a.w - u1), fix_round(u1));
             }
             if (NC >= 3) {
                 const float2 b = ws2[j];
                 const float u2 = f * b.x;
-                red_shared_pair(q + 2 * kPlaneBytes, b.x - u2, u2);
+                red_shared_pair(q + 2 * kPlaneBytes, fix_round(b.x - u2), fix_round(u2));
                 if (NC == 4) {
                     const float u3 = f * b.y;
-                    red_shared_pair(q + 3 * kPlaneBytes, b.y - u3, u3);
+                    red_shared_pair(q + 3 * kPlaneBytes, fix_round(b.y - u3), fix_round(u3));
                 }
             }
         }
     }
 }
 
+// Fixed-point scale of one channel (see above); 0 when M is not finite.
+__device__ __forceinline__ float fix_scale(unsigned mbits, int total) {
+    const float M = __uint_as_float(mbits);
+    if (!(M <= 3.0e38f)) return 0.f;
+    if (M == 0.f) return 1.f;
+    float sc = fminf(2097152.f / M, (1073741824.f / (float)(total > 1 ? total : 1)) / M);
+    sc = fminf(sc, 0x1p126f);
+    return __int_as_float(__float_as_int(sc) & 0xff800000);  // power of two <= sc
+}
+
+// M_c = max_i |w_i s_c,i| over the rays, as float bits (atomicMax on the bits
+// orders non-negative floats; a NaN input propagates as NaN bits).
+__global__ void __launch_bounds__(kThreads)
+    tile_wmax_kernel(const float4 *__restrict__ tab, const float *__restrict__ sino, int64_t n_rays, int nch,
+                     unsigned *__restrict__ out) {
+    for (int c = 0; c < nch; ++c) {
+        unsigned m = 0u;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const float v = fabsf(__ldg(&tab[i].z) * __ldg(sino + (int64_t)c * n_rays + i));
+            const unsigned b = v != v ? 0x7fc00000u : __float_as_uint(v);
+            m = b > m ? b : m;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned t = __shfl_xor_sync(0xffffffffu, m, o);
+            m = t > m ? t : m;
+        }
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(out + c, m);
+    }
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kThreads, 5)
     back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
-                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x, int vs) {
+                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x, int vs,
+                        const unsigned *__restrict__ wmax, int cell_rays) {
     static_assert(kBT == 32, "one lane per driving index of the tile");
     static_assert(NC >= 1 && NC <= 4, "one to four channels");
     constexpr int kRows = kBT + 2;
     constexpr int kPlane = kRows * kBT;
-    __shared__ float acc[2 * NC * kPlane];
+    __shared__ int acc[2 * NC * kPlane];
     __shared__ TileItems ti;
     __shared__ float4 stage[kThreads];
     __shared__ float2 stage2[NC > 2 ? kThreads : 1];
@@ -624,10 +677,14 @@ __global__ void __launch_bounds__(kThreads, 5)
         ti.v_begin = blockIdx.z * vs;
         ti.nv = min(g.n_views - ti.v_begin, vs);
     }
-    for (int k = threadIdx.x; k < 2 * NC * kPlane; k += blockDim.x) acc[k] = 0.f;
+    for (int k = threadIdx.x; k < 2 * NC * kPlane; k += blockDim.x) acc[k] = 0;
     __syncthreads();
     tile_items(ti, vt, g, c0, r0);
     const int total = ti.prefix[ti.nv];
+    const int bound = cell_rays > 0 ? min(total, ti.nv * cell_rays) : total;
+    float sc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sc[c] = fix_scale(__ldg(wmax + c), bound);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const unsigned col = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
@@ -646,12 +703,12 @@ __global__ void __launch_bounds__(kThreads, 5)
             const float4 r = __ldg(tab + ray);
             const float s0 = __ldg(sino + ray), s1 = NC >= 2 ? __ldg(sino + n_rays + ray) : 0.f;
             if (NC >= 3)
-                lr2 = make_float2(r.z * __ldg(sino + 2 * n_rays + ray),
-                                  NC == 4 ? r.z * __ldg(sino + 3 * n_rays + ray) : 0.f);
+                lr2 = make_float2(r.z * __ldg(sino + 2 * n_rays + ray) * sc[NC >= 3 ? 2 : 0],
+                                  NC == 4 ? r.z * __ldg(sino + 3 * n_rays + ray) * sc[NC == 4 ? 3 : 0] : 0.f);
             int d0, o0, ia, ib;
             tile_ray_range_approx(r, c0, r0, axis, d0, o0, ia, ib);
             keep = ia <= ib;
-            lr = make_float4(r.x - 0.5f, r.y, r.z * s0, r.z * s1);
+            lr = make_float4(r.x - 0.5f, r.y, r.z * s0 * sc[0], NC >= 2 ? r.z * s1 * sc[NC >= 2 ? 1 : 0] : 0.f);
         }
         const unsigned kx = __ballot_sync(0xffffffffu, keep && axis == 0);
         const unsigned ky = __ballot_sync(0xffffffffu, keep && axis == 1);
@@ -666,6 +723,7 @@ __global__ void __launch_bounds__(kThreads, 5)
         __syncwarp();
     }
     __syncthreads();
+    if (total == 0) return;
     const int64_t npix = (int64_t)g.nx * g.ny;
     for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
         const int rr = q / kBT, cc = q % kBT;
@@ -674,7 +732,8 @@ __global__ void __launch_bounds__(kThreads, 5)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             // x-driven rays: [row][column]; y-driven rays: [column][row]
-            const float v = acc[c * kPlane + (rr + 1) * kBT + cc] + acc[(NC + c) * kPlane + (cc + 1) * kBT + rr];
+            const int a = acc[c * kPlane + (rr + 1) * kBT + cc], b = acc[(NC + c) * kPlane + (cc + 1) * kBT + rr];
+            const float v = sc[c] > 0.f ? ((float)a + (float)b) / sc[c] : __int_as_float(0x7fc00000);
             atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, v);
         }
     }
@@ -821,15 +880,24 @@ mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, in
         if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
         const int vs = p->back_views;
         const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT), (unsigned)cdiv(p->g.n_views, vs));
+        if (n_mat > (int)p->wmax.n) return fail(MBIR_ERR_ARG, "backproject: %d channels exceed the plan's n_mat_max", n_mat);
+        PSPS_CUDA(cudaMemsetAsync(p->wmax.p, 0, sizeof(unsigned) * n_mat, s));
+        {
+            const int64_t b = cdiv(p->n_rays, kThreads);
+            tile_wmax_kernel<<<(unsigned)(b < 1024 ? b : 1024), kThreads, 0, s>>>(p->ray.p, sino, p->n_rays, n_mat,
+                                                                                   p->wmax.p);
+            PSPS_LAUNCH_CHECK();
+        }
         for (int m0 = 0; m0 < n_mat;) {
             const int nc = n_mat - m0 < 4 ? n_mat - m0 : 4;   // channels of this launch
             const float *sm = sino + (int64_t)m0 * p->n_rays;
             float *xm = x + (int64_t)m0 * p->n_pix;
+            const unsigned *wm = p->wmax.p + m0;
             switch (nc) {
-                case 4: back_tile_2d_kernel<4><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
-                case 3: back_tile_2d_kernel<3><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
-                case 2: back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
-                default: back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs); break;
+                case 4: back_tile_2d_kernel<4><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
+                case 3: back_tile_2d_kernel<3><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
+                case 2: back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
+                default: back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
             }
             PSPS_LAUNCH_CHECK();
             m0 += nc;
@@ -902,13 +970,31 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
         return MBIR_OK;
     }
     {
+        // Rays of one view reaching one tile accumulator: their samples at a
+        // fixed driving index lie in a window two pixels wide, and adjacent
+        // rays of a view are at least delta pixels apart there: parallel
+        // beam du / pixel; fan beam (equiangular bins du / sdd) D du / sdd /
+        // pixel with D >= sid - R the distance from the source to any point
+        // within a pixel of the grid.
+        const double pix = std::max(p->g.dx, p->g.dy);
+        double delta = 0.0;
+        if (p->g.kind == MBIR_PAR2D) {
+            delta = p->g.du / pix;
+        } else if (p->g.kind == MBIR_FAN2D && p->g.sdd > 0) {
+            const double R = std::hypot((0.5 * p->g.nx + 1.0) * p->g.dx, (0.5 * p->g.ny + 1.0) * p->g.dy);
+            if (p->g.sid > R) delta = (p->g.sid - R) * (p->g.du / p->g.sdd) / pix;
+        }
+        p->cell_rays = delta > 1e-3 ? (int)std::floor(2.0 / delta) + 2 : 0;
+    }
+    {
         // default views per CTA of the tile transpose: about six CTAs per SM
         // on a 152-SM GPU, between 4 and 60 views (mbir_plan_autotune refines)
         const int64_t tiles = cdiv(p->g.nx, kBT) * cdiv(p->g.ny, kBT);
         const int64_t v = tiles * p->g.n_views / (152 * 6);
         p->back_views = (int)(v < 4 ? 4 : (v > 60 ? 60 : v));
     }
-    if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->view.alloc(p->g.n_views)) != MBIR_OK) {
+    if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->view.alloc(p->g.n_views)) != MBIR_OK ||
+        (st = p->wmax.alloc(n_mat_max)) != MBIR_OK) {
         delete p;
         return st;
     }
