@@ -565,76 +565,86 @@ __device__ __forceinline__ void tile_ray_range_approx(const float4 &r, int c0, i
 // those, like lanes past the grid's edge, land in rows or columns that the
 // epilogue drops.
 //
-// Samples are split with joseph_split, like the forward projector's.
+// A sample at interpolated coordinate h goes to pixels floor(h) and
+// floor(h) + 1 with weights 1 - f and f, f = h - floor(h): the same split as
+// the forward projector's joseph_split, computed with one round-down add.
 //
 // The accumulators are 32-bit fixed point: shared-memory integer adds are
 // native, while an FP32 shared-memory add costs a load and a compare-and-swap
 // (three wavefronts of the shared-memory pipe that bounds this kernel against
-// one).  Channel c uses the power-of-two scale
-//   sc = min(2^21 / M_c, 2^30 / (T M_c)),  M_c = max_i |w_i s_c,i|,
+// one).  Channel c uses the scale
+//   sc = min(2^22, 2^30 / T) / M_c,  M_c = max_i |w_i s_c,i|,
 // T = a bound on the terms one accumulator receives: a ray adds at most one
 // term to a given accumulator, so T = min(the CTA's candidate rays, its
 // views x the plan's bound on the rays of one view that reach one
-// accumulator, cell_rays).  Every term is at most M_c sc <= 2^21 (so the
-// conversion below is exact rounding to nearest) and T of them stay below
-// 2^30 + T < 2^31.
-// Each term is rounded once (half a unit of 2^-21 M_c at most); the sums are
-// exact and order-independent, and the epilogue converts back by 1 / sc.
+// accumulator, cell_rays).  A sample's value v = sc w s is at most 2^22 (so
+// the magic-number conversions below are exact rounding to nearest), its two
+// terms round(f v) and round(v) - round(f v) at most min(2^22, 2^30 / T) + 1,
+// and T of them stay below 2^30 + T < 2^31.  The terms carry at most one
+// unit of 1 / sc (2^-22 M_c when T <= 256) of rounding; the sums are exact and
+// order-independent, and the epilogue divides by sc.
 constexpr float kFixMagic = 12582912.f;  // 1.5 * 2^23: x + magic rounds x (|x| <= 2^22) to an integer
 constexpr int kFixMagicBits = 0x4B400000;
 
-__device__ __forceinline__ int fix_round(float x) { return __float_as_int(x + kFixMagic) - kFixMagicBits; }
-
+// The pair of adds of one sample: [addr] += lo, [addr + OFF] += hi.
+template <int OFF>
 __device__ __forceinline__ void red_shared_pair(unsigned addr, int lo, int hi) {
     asm volatile(
         "red.shared.add.s32 [%0], %1;\n\t"
-        "red.shared.add.s32 [%0+128], %2;" ::"r"(addr),
-        "r"(lo), "r"(hi)
+        "red.shared.add.s32 [%0+%3], %2;" ::"r"(addr),
+        "r"(lo), "r"(hi), "n"(OFF)
         : "memory");
+}
+
+// One channel of one sample: with v = the ray's scaled, weighted value, the
+// upper term round(f v) comes from one FMA, hb = bits(f v + magic), and the
+// lower one is round(v) - round(f v) = bits(v + magic) - hb, so the two terms
+// of a ray add up to round(v) exactly.
+template <int OFF>
+__device__ __forceinline__ void fix_sample(unsigned addr, float f, float v) {
+    const int hb = __float_as_int(fmaf(f, v, kFixMagic));
+    red_shared_pair<OFF>(addr, __float_as_int(v + kFixMagic) - hb, hb - kFixMagicBits);
 }
 
 // Kept rays [j0, j1) of one driving axis: fi = this lane's driving index,
 // rowbase = the tile's first interpolated index - 1, addr = byte address of
-// this lane's column in the axis' first accumulator plane; ws holds the
-// scaled, weighted channels 0 and 1, ws2 channels 2 and 3 (NC > 2).
-template <int NC>
+// this lane's column in the axis' first accumulator plane (rows of STRIDE
+// words); ws holds (f0, df, v0, v1), ws2 v2, v3 (NC > 2).
+template <int NC, int STRIDE>
 __device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, const float2 *__restrict__ ws2, int j0,
                                                int j1, float fi, int rowbase, unsigned addr) {
-    constexpr unsigned kPlaneBytes = 4u * (kBT + 2) * kBT;
-#pragma unroll 2
+    constexpr unsigned kRowBytes = 4u * STRIDE;
+    constexpr unsigned kPlaneBytes = kRowBytes * (kBT + 2);
+#pragma unroll 4
     for (int j = j0; j < j1; ++j) {
-        const float4 a = ws[j];  // f0 - 1/2, df, sc0 w sino[0], sc1 w sino[1]
-        float f;                 // weight of the upper pixel
-        const int jr = joseph_split(fmaf(fi, a.y, a.x), f) - rowbase;  // interpolated index - (first index - 1)
+        const float4 a = ws[j];
+        // interpolated coordinate h = f0 + fi df: lower pixel floor(h), weight
+        // of the upper one f = h - floor(h) (the magic add rounding down)
+        const float h = fmaf(fi, a.y, a.x);
+        const float rn = __fadd_rd(h, kFixMagic);
+        const float f = h - (rn - kFixMagic);
+        const int jr = (__float_as_int(rn) - kFixMagicBits) - rowbase;  // interpolated index - (first index - 1)
         if ((unsigned)jr <= (unsigned)kBT) {
-            const unsigned q = addr + (unsigned)jr * (4u * kBT);
-            const float u0 = f * a.z;
-            red_shared_pair(q, fix_round(a.z - u0), fix_round(u0));
-            if (NC >= 2) {
-                const float u1 = f * a.w;
-                red_shared_pair(q + kPlaneBytes, fix_round(a.w - u1), fix_round(u1));
-            }
+            const unsigned q = addr + (unsigned)jr * kRowBytes;
+            fix_sample<kRowBytes>(q, f, a.z);
+            if (NC >= 2) fix_sample<kRowBytes>(q + kPlaneBytes, f, a.w);
             if (NC >= 3) {
-                const float2 b = ws2[j];
-                const float u2 = f * b.x;
-                red_shared_pair(q + 2 * kPlaneBytes, fix_round(b.x - u2), fix_round(u2));
-                if (NC == 4) {
-                    const float u3 = f * b.y;
-                    red_shared_pair(q + 3 * kPlaneBytes, fix_round(b.y - u3), fix_round(u3));
-                }
+                const float2 c = ws2[j];
+                fix_sample<kRowBytes>(q + 2 * kPlaneBytes, f, c.x);
+                if (NC == 4) fix_sample<kRowBytes>(q + 3 * kPlaneBytes, f, c.y);
             }
         }
     }
 }
 
 // Fixed-point scale of one channel (see above); 0 when M is not finite.
-__device__ __forceinline__ float fix_scale(unsigned mbits, int total) {
+// The quotient is rounded down so that M sc never exceeds its limit.
+__device__ __forceinline__ float fix_scale(unsigned mbits, int bound) {
     const float M = __uint_as_float(mbits);
     if (!(M <= 3.0e38f)) return 0.f;
     if (M == 0.f) return 1.f;
-    float sc = fminf(2097152.f / M, (1073741824.f / (float)(total > 1 ? total : 1)) / M);
-    sc = fminf(sc, 0x1p126f);
-    return __int_as_float(__float_as_int(sc) & 0xff800000);  // power of two <= sc
+    const float lim = fminf(4194304.f, 1073741824.f / (float)(bound > 1 ? bound : 1));
+    return fminf(__fdiv_rd(lim, M), 0x1p126f);
 }
 
 // M_c = max_i |w_i s_c,i| over the rays, as float bits (atomicMax on the bits
@@ -667,17 +677,21 @@ __global__ void __launch_bounds__(kThreads, 5)
     static_assert(kBT == 32, "one lane per driving index of the tile");
     static_assert(NC >= 1 && NC <= 4, "one to four channels");
     constexpr int kRows = kBT + 2;
-    constexpr int kPlane = kRows * kBT;
-    __shared__ int acc[2 * NC * kPlane];
+    // x-driven planes [row][32 columns]; y-driven planes [column][33]: the
+    // pad word keeps the epilogue's transposed reads conflict-free
+    constexpr int kSX = kBT, kSY = kBT;
+    constexpr int kPX = kRows * kSX, kPY = kRows * kSY;
+    __shared__ int acc[NC * (kPX + kPY)];
     __shared__ TileItems ti;
     __shared__ float4 stage[kThreads];
     __shared__ float2 stage2[NC > 2 ? kThreads : 1];
+    __shared__ int tr[kBT * (kBT + 1)];
     const int c0 = blockIdx.x * kBT, r0 = blockIdx.y * kBT;
     if (threadIdx.x == 0) {
         ti.v_begin = blockIdx.z * vs;
         ti.nv = min(g.n_views - ti.v_begin, vs);
     }
-    for (int k = threadIdx.x; k < 2 * NC * kPlane; k += blockDim.x) acc[k] = 0;
+    for (int k = threadIdx.x; k < NC * (kPX + kPY); k += blockDim.x) acc[k] = 0;
     __syncthreads();
     tile_items(ti, vt, g, c0, r0);
     const int total = ti.prefix[ti.nv];
@@ -687,7 +701,8 @@ __global__ void __launch_bounds__(kThreads, 5)
     for (int c = 0; c < NC; ++c) sc[c] = fix_scale(__ldg(wmax + c), bound);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const unsigned col = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
+    const unsigned colx = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
+    const unsigned coly = colx + 4u * NC * kPX;
     float4 *ws = stage + warp * 32;
     float2 *ws2 = stage2 + (NC > 2 ? warp * 32 : 0);
     int k = 0;
@@ -695,47 +710,51 @@ __global__ void __launch_bounds__(kThreads, 5)
         const int item = base + lane;
         bool keep = false;
         int axis = 0;
-        float4 lr;
-        float2 lr2 = make_float2(0.f, 0.f);
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
         if (item < total) {
             while (item >= ti.prefix[k + 1]) ++k;
             const int64_t ray = (int64_t)(ti.v_begin + k) * g.n_u + ti.b0[k] + (item - ti.prefix[k]);
-            const float4 r = __ldg(tab + ray);
-            const float s0 = __ldg(sino + ray), s1 = NC >= 2 ? __ldg(sino + n_rays + ray) : 0.f;
-            if (NC >= 3)
-                lr2 = make_float2(r.z * __ldg(sino + 2 * n_rays + ray) * sc[NC >= 3 ? 2 : 0],
-                                  NC == 4 ? r.z * __ldg(sino + 3 * n_rays + ray) * sc[NC == 4 ? 3 : 0] : 0.f);
+            r = __ldg(tab + ray);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] = r.z * __ldg(sino + c * n_rays + ray) * sc[c];
             int d0, o0, ia, ib;
             tile_ray_range_approx(r, c0, r0, axis, d0, o0, ia, ib);
             keep = ia <= ib;
-            lr = make_float4(r.x - 0.5f, r.y, r.z * s0 * sc[0], NC >= 2 ? r.z * s1 * sc[NC >= 2 ? 1 : 0] : 0.f);
         }
         const unsigned kx = __ballot_sync(0xffffffffu, keep && axis == 0);
         const unsigned ky = __ballot_sync(0xffffffffu, keep && axis == 1);
         if (keep) {
             const int pos = axis == 0 ? __popc(kx & below) : 31 - __popc(ky & below);
-            ws[pos] = lr;
-            if (NC > 2) ws2[pos] = lr2;
+            ws[pos] = make_float4(r.x, r.y, v[0], v[1]);
+            if (NC > 2) ws2[pos] = make_float2(v[2], v[3]);
         }
         __syncwarp();
-        tile_lane_pass<NC>(ws, ws2, 0, __popc(kx), (float)(c0 + lane), r0 - 1, col);
-        tile_lane_pass<NC>(ws, ws2, 32 - __popc(ky), 32, (float)(r0 + lane), c0 - 1, col + 4u * NC * kPlane);
+        tile_lane_pass<NC, kSX>(ws, ws2, 0, __popc(kx), (float)(c0 + lane), r0 - 1, colx);
+        tile_lane_pass<NC, kSY>(ws, ws2, 32 - __popc(ky), 32, (float)(r0 + lane), c0 - 1, coly);
         __syncwarp();
     }
     __syncthreads();
     if (total == 0) return;
     const int64_t npix = (int64_t)g.nx * g.ny;
-    for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
-        const int rr = q / kBT, cc = q % kBT;
-        const int iy = r0 + rr, ix = c0 + cc;
-        if (iy >= g.ny || ix >= g.nx) continue;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            // x-driven rays: [row][column]; y-driven rays: [column][row]
-            const int a = acc[c * kPlane + (rr + 1) * kBT + cc], b = acc[(NC + c) * kPlane + (cc + 1) * kBT + rr];
-            const float v = sc[c] > 0.f ? ((float)a + (float)b) / sc[c] : __int_as_float(0x7fc00000);
-            atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, v);
+    // y-driven planes are [column][row]: turn them around through a padded
+    // buffer (reads along rows, writes with stride kBT + 1) so that neither
+    // side has bank conflicts, then flush row-major with coalesced atomics
+    for (int c = 0; c < NC; ++c) {
+        for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+            const int cc = q / kBT, rr = q % kBT;
+            tr[rr * (kBT + 1) + cc] = acc[NC * kPX + c * kPY + (cc + 1) * kSY + rr];
         }
+        __syncthreads();
+        for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+            const int rr = q / kBT, cc = q % kBT;
+            const int iy = r0 + rr, ix = c0 + cc;
+            if (iy >= g.ny || ix >= g.nx) continue;
+            const int a = acc[c * kPX + (rr + 1) * kSX + cc], b = tr[rr * (kBT + 1) + cc];
+            const float val = sc[c] > 0.f ? __fdiv_rn((float)a + (float)b, sc[c]) : __int_as_float(0x7fc00000);
+            atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, val);
+        }
+        __syncthreads();
     }
 }
 
