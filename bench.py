@@ -39,7 +39,13 @@ DEVLS_BYTES = 80
 # Counters of the dominant kernel from one ncu capture of the same kernel and
 # workload (summaries under profiles/): DRAM bytes read + written per launch,
 # and the unit that binds it.  Remove an entry when its kernel changes.
-NCU_CAPTURES = {}
+NCU_CAPTURES = {
+    ("c2_fan2d_512_haar", "backproject"): {
+        "traffic": 16.12e6,
+        "binding": {"unit": "SM instruction issue (issue active, % of cycles)", "frac_of_peak": 0.858,
+                    "source": "profiles/back_tile_2d_c2_fan512.md"},
+    },
+}
 
 WORKLOADS = {
     "c2_fan2d_512_haar": ("config2", "haar", "512x512@0.5mm, 720x888 fan curved, Haar(M0, lattice 3)"),

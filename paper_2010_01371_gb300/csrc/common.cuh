@@ -229,9 +229,13 @@ struct mbir_plan {
     // scratch: packed / transposed image copies for the forward projector
     // (3-D: one copy per driving axis)
     psps::DBuf<float> xrow, xcol, xcol3;
-    // 2-D tile transpose: per channel, max_i |w_i s_i| as float bits (sets
-    // the fixed-point scale of the shared-memory accumulators)
+    // 2-D tile transpose: per channel, max_i |s_i| as float bits, and the
+    // largest ray weight: M = w_max max|s| bounds every |w_i s_i| and sets
+    // the fixed-point scale of the shared-memory accumulators
     psps::DBuf<unsigned> wmax;
+    float w_max = 0.f;
+    // 2-D tile transpose: 64-bit fixed-point image sums ([n_mat_max][n_pix])
+    psps::DBuf<long long> xfix;
     // bound on the rays of one view that add to one tile accumulator (0: none
     // known; the CTA's candidate count bounds it then)
     int cell_rays = 0;

@@ -25,6 +25,8 @@
 //    (mbir_plan_set_backprojector).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -573,16 +575,19 @@ __device__ __forceinline__ void tile_ray_range_approx(const float4 &r, int c0, i
 // native, while an FP32 shared-memory add costs a load and a compare-and-swap
 // (three wavefronts of the shared-memory pipe that bounds this kernel against
 // one).  Channel c uses the scale
-//   sc = min(2^22, 2^30 / T) / M_c,  M_c = max_i |w_i s_c,i|,
+//   sc = min(2^22, 2^30 / T) / M_c,  M_c = w_max max_i |s_c,i| >= |w_i s_c,i|,
 // T = a bound on the terms one accumulator receives: a ray adds at most one
 // term to a given accumulator, so T = min(the CTA's candidate rays, its
 // views x the plan's bound on the rays of one view that reach one
-// accumulator, cell_rays).  A sample's value v = sc w s is at most 2^22 (so
+// accumulator, cell_rays; one T, and so one scale, for the whole launch).  A
+// sample's value v = sc w s is at most 2^22 (so
 // the magic-number conversions below are exact rounding to nearest), its two
 // terms round(f v) and round(v) - round(f v) at most min(2^22, 2^30 / T) + 1,
 // and T of them stay below 2^30 + T < 2^31.  The terms carry at most one
-// unit of 1 / sc (2^-22 M_c when T <= 256) of rounding; the sums are exact and
-// order-independent, and the epilogue divides by sc.
+// unit of 1 / sc (2^-22 M_c when T <= 256) of rounding.  Each CTA adds its
+// tile sums into a 64-bit fixed-point image with integer atomics and a last
+// pass divides by sc: every sum is exact, so the transpose is bitwise
+// reproducible whatever order the adds run in.
 constexpr float kFixMagic = 12582912.f;  // 1.5 * 2^23: x + magic rounds x (|x| <= 2^22) to an integer
 constexpr int kFixMagicBits = 0x4B400000;
 
@@ -638,27 +643,44 @@ __device__ __forceinline__ void tile_lane_pass(const float4 *__restrict__ ws, co
 }
 
 // Fixed-point scale of one channel (see above); 0 when M is not finite.
-// The quotient is rounded down so that M sc never exceeds its limit.
-__device__ __forceinline__ float fix_scale(unsigned mbits, int bound) {
-    const float M = __uint_as_float(mbits);
+// M = w_max max|s| rounded up bounds every rounded product w_i s_i; the
+// quotient is rounded down so that M sc never exceeds its limit.
+__device__ __forceinline__ float fix_scale(unsigned sbits, float w_max, int bound) {
+    const float M = __fmul_ru(w_max, __uint_as_float(sbits));
     if (!(M <= 3.0e38f)) return 0.f;
     if (M == 0.f) return 1.f;
     const float lim = fminf(4194304.f, 1073741824.f / (float)(bound > 1 ? bound : 1));
     return fminf(__fdiv_rd(lim, M), 0x1p126f);
 }
 
-// M_c = max_i |w_i s_c,i| over the rays, as float bits (atomicMax on the bits
-// orders non-negative floats; a NaN input propagates as NaN bits).
+// max_i |s_c,i| over the rays, as float bits (atomicMax on the bits orders
+// non-negative floats; a NaN input propagates as NaN bits).
 __global__ void __launch_bounds__(kThreads)
-    tile_wmax_kernel(const float4 *__restrict__ tab, const float *__restrict__ sino, int64_t n_rays, int nch,
-                     unsigned *__restrict__ out) {
+    tile_smax_kernel(const float *__restrict__ sino, int64_t n_rays, int nch, unsigned *__restrict__ out) {
     for (int c = 0; c < nch; ++c) {
+        const float *sc = sino + (int64_t)c * n_rays;
         unsigned m = 0u;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const float v = fabsf(__ldg(&tab[i].z) * __ldg(sino + (int64_t)c * n_rays + i));
-            const unsigned b = v != v ? 0x7fc00000u : __float_as_uint(v);
+        auto take = [&m](float v) {
+            const float a = fabsf(v);
+            const unsigned b = a != a ? 0x7fc00000u : __float_as_uint(a);
             m = b > m ? b : m;
+        };
+        // float4 loads from the first 16-byte boundary of the channel
+        const int64_t head = ((16 - ((uintptr_t)sc & 15)) & 15) / 4;
+        const int64_t h = head < n_rays ? head : n_rays;
+        const int64_t n4 = (n_rays - h) / 4;
+        const float4 *v4 = reinterpret_cast<const float4 *>(sc + h);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const float4 v = __ldg(v4 + i);
+            take(v.x);
+            take(v.y);
+            take(v.z);
+            take(v.w);
+        }
+        if (blockIdx.x == 0) {
+            for (int64_t i = threadIdx.x; i < h; i += blockDim.x) take(sc[i]);
+            for (int64_t i = h + 4 * n4 + threadIdx.x; i < n_rays; i += blockDim.x) take(sc[i]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -669,11 +691,27 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Largest |w| of the ray table (float bits), once per plan.
+__global__ void __launch_bounds__(kThreads) ray_wmax_kernel(const float4 *__restrict__ tab, int64_t n_rays,
+                                                            unsigned *__restrict__ out) {
+    unsigned m = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned b = __float_as_uint(fabsf(tab[i].z));
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kThreads, 5)
     back_tile_2d_kernel(const float4 *__restrict__ tab, const float4 *__restrict__ vt, mbir_geometry g,
-                        const float *__restrict__ sino, int64_t n_rays, float *__restrict__ x, int vs,
-                        const unsigned *__restrict__ wmax, int cell_rays) {
+                        const float *__restrict__ sino, int64_t n_rays, int vs,
+                        const unsigned *__restrict__ smax, float w_max, int T, long long *__restrict__ xfix) {
     static_assert(kBT == 32, "one lane per driving index of the tile");
     static_assert(NC >= 1 && NC <= 4, "one to four channels");
     constexpr int kRows = kBT + 2;
@@ -695,10 +733,9 @@ __global__ void __launch_bounds__(kThreads, 5)
     __syncthreads();
     tile_items(ti, vt, g, c0, r0);
     const int total = ti.prefix[ti.nv];
-    const int bound = cell_rays > 0 ? min(total, ti.nv * cell_rays) : total;
     float sc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) sc[c] = fix_scale(__ldg(wmax + c), bound);
+    for (int c = 0; c < NC; ++c) sc[c] = fix_scale(__ldg(smax + c), w_max, T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const unsigned colx = (unsigned)__cvta_generic_to_shared(acc) + 4u * (unsigned)lane;
@@ -750,11 +787,27 @@ __global__ void __launch_bounds__(kThreads, 5)
             const int rr = q / kBT, cc = q % kBT;
             const int iy = r0 + rr, ix = c0 + cc;
             if (iy >= g.ny || ix >= g.nx) continue;
-            const int a = acc[c * kPX + (rr + 1) * kSX + cc], b = tr[rr * (kBT + 1) + cc];
-            const float val = sc[c] > 0.f ? __fdiv_rn((float)a + (float)b, sc[c]) : __int_as_float(0x7fc00000);
-            atomicAdd(x + c * npix + (int64_t)iy * g.nx + ix, val);
+            const long long v = (long long)acc[c * kPX + (rr + 1) * kSX + cc] + (long long)tr[rr * (kBT + 1) + cc];
+            if (v)
+                atomicAdd(reinterpret_cast<unsigned long long *>(xfix + c * npix + (int64_t)iy * g.nx + ix),
+                          (unsigned long long)v);
         }
         __syncthreads();
+    }
+}
+
+// x[c] (+)= xfix[c] / sc_c, the scale of the transpose launch.
+__global__ void __launch_bounds__(kThreads)
+    fix_to_float_kernel(const long long *__restrict__ xfix, float *__restrict__ x, int64_t npix, int nch,
+                        const unsigned *__restrict__ smax, float w_max, int T, int accumulate) {
+    for (int c = 0; c < nch; ++c) {
+        const float sc = fix_scale(__ldg(smax + c), w_max, T);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t k = (int64_t)c * npix + i;
+            const float v = sc > 0.f ? __fdiv_rn(__ll2float_rn(xfix[k]), sc) : __int_as_float(0x7fc00000);
+            x[k] = accumulate ? x[k] + v : v;
+        }
     }
 }
 
@@ -896,31 +949,37 @@ mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, in
         return MBIR_OK;
     }
     if (p->back_mode == 0) {
-        if (!accumulate) PSPS_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n_mat * p->n_pix, s));
         const int vs = p->back_views;
         const dim3 grd((unsigned)cdiv(p->g.nx, kBT), (unsigned)cdiv(p->g.ny, kBT), (unsigned)cdiv(p->g.n_views, vs));
         if (n_mat > (int)p->wmax.n) return fail(MBIR_ERR_ARG, "backproject: %d channels exceed the plan's n_mat_max", n_mat);
+        // one bound T for every CTA: vs views x the rays of one view that can
+        // reach one accumulator (or all bins of the views when unknown)
+        const int T = p->cell_rays > 0 ? vs * p->cell_rays : vs * p->g.n_u;
         PSPS_CUDA(cudaMemsetAsync(p->wmax.p, 0, sizeof(unsigned) * n_mat, s));
+        PSPS_CUDA(cudaMemsetAsync(p->xfix.p, 0, sizeof(long long) * (size_t)n_mat * p->n_pix, s));
         {
             const int64_t b = cdiv(p->n_rays, kThreads);
-            tile_wmax_kernel<<<(unsigned)(b < 1024 ? b : 1024), kThreads, 0, s>>>(p->ray.p, sino, p->n_rays, n_mat,
-                                                                                   p->wmax.p);
+            tile_smax_kernel<<<(unsigned)(b < 1024 ? b : 1024), kThreads, 0, s>>>(sino, p->n_rays, n_mat, p->wmax.p);
             PSPS_LAUNCH_CHECK();
         }
         for (int m0 = 0; m0 < n_mat;) {
             const int nc = n_mat - m0 < 4 ? n_mat - m0 : 4;   // channels of this launch
             const float *sm = sino + (int64_t)m0 * p->n_rays;
-            float *xm = x + (int64_t)m0 * p->n_pix;
+            long long *xm = p->xfix.p + (int64_t)m0 * p->n_pix;
             const unsigned *wm = p->wmax.p + m0;
             switch (nc) {
-                case 4: back_tile_2d_kernel<4><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
-                case 3: back_tile_2d_kernel<3><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
-                case 2: back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
-                default: back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, xm, vs, wm, p->cell_rays); break;
+                case 4: back_tile_2d_kernel<4><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, vs, wm, p->w_max, T, xm); break;
+                case 3: back_tile_2d_kernel<3><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, vs, wm, p->w_max, T, xm); break;
+                case 2: back_tile_2d_kernel<2><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, vs, wm, p->w_max, T, xm); break;
+                default: back_tile_2d_kernel<1><<<grd, kThreads, 0, s>>>(p->ray.p, p->view.p, p->g, sm, p->n_rays, vs, wm, p->w_max, T, xm); break;
             }
             PSPS_LAUNCH_CHECK();
             m0 += nc;
         }
+        const int64_t b = cdiv(p->n_pix, kThreads);
+        fix_to_float_kernel<<<(unsigned)(b < 1024 ? b : 1024), kThreads, 0, s>>>(p->xfix.p, x, p->n_pix, n_mat,
+                                                                                  p->wmax.p, p->w_max, T, accumulate);
+        PSPS_LAUNCH_CHECK();
         return MBIR_OK;
     }
     const dim3 grd((unsigned)cdiv(p->g.nx, 16), (unsigned)cdiv(p->g.ny, 16));
@@ -1013,14 +1072,20 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
         p->back_views = (int)(v < 4 ? 4 : (v > 60 ? 60 : v));
     }
     if ((st = p->ray.alloc(p->n_rays)) != MBIR_OK || (st = p->view.alloc(p->g.n_views)) != MBIR_OK ||
-        (st = p->wmax.alloc(n_mat_max)) != MBIR_OK) {
+        (st = p->wmax.alloc(n_mat_max)) != MBIR_OK || (st = p->xfix.alloc((size_t)n_mat_max * p->n_pix)) != MBIR_OK) {
         delete p;
         return st;
     }
     setup_2d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads>>>(p->g, p->n_rays, p->ray.p);
     setup_view_kernel<<<(unsigned)cdiv(p->g.n_views, 128), 128>>>(p->g, p->view.p);
+    cudaMemset(p->wmax.p, 0, sizeof(unsigned));
+    ray_wmax_kernel<<<(unsigned)std::min<int64_t>(cdiv(p->n_rays, kThreads), 1024), kThreads>>>(p->ray.p, p->n_rays,
+                                                                                              p->wmax.p);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned wbits = 0u;
+    if (e == cudaSuccess) e = cudaMemcpy(&wbits, p->wmax.p, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    std::memcpy(&p->w_max, &wbits, sizeof(float));
     if (e != cudaSuccess) {
         delete p;
         return fail(MBIR_ERR_CUDA, "mbir_plan_create: set-up kernel: %s", cudaGetErrorString(e));

@@ -181,6 +181,36 @@ def test_cone_backproject_parity(psps, oracle_lib, name, mode, nch):
     assert rel_l2(to_host(base), want + 1.0) < TOL
 
 
+@pytest.mark.parametrize("name", ["fan2d_ragged", "fan2d_c2_128"])
+def test_tile_transpose_deterministic(psps, name):
+    """The 2-D tile transpose sums in fixed point (exact integer adds), so two
+    runs, and the accumulate mode on a zero image, are bitwise equal."""
+    g = small_geoms()[name]
+    rng = np.random.default_rng(15)
+    s = to_dev(rng.standard_normal((3, g.n_rays)) * rng.uniform(0.01, 100.0, (3, 1)))
+    plan = psps.Plan(g)
+    a = to_host(psps.mbir_backproject(plan, s))
+    b = to_host(psps.mbir_backproject(plan, s))
+    assert np.array_equal(a, b)
+    import torch
+    z = torch.zeros((3,) + g.image_shape, device="cuda", dtype=torch.float32)
+    c = to_host(psps.mbir_backproject(plan, s, z, accumulate=True))
+    assert np.array_equal(a, c)
+
+
+def test_tile_transpose_nonfinite_input(psps):
+    """A NaN in a sinogram channel makes that channel's image NaN (the
+    fixed-point scale cannot be formed) and leaves the other channels alone."""
+    g = small_geoms()["par2d_ragged"]
+    s = np.random.default_rng(16).random((2, g.n_rays))
+    plan = psps.Plan(g)
+    ref = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    s[1, 7] = np.nan
+    got = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    assert np.array_equal(got[0], ref[0])
+    assert np.isnan(got[1]).all()
+
+
 def test_cone_gather_deterministic(psps):
     """The 3-D gather has no atomics: two runs are bitwise equal."""
     g = cone_geoms()["cone_small"]
