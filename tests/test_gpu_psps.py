@@ -249,12 +249,11 @@ def test_batch_matches_single_states(psps):
     batch = psps.Batch(states)
     hb = psps.psps_batch_step(batch, n_iter)
     assert hb.shape == (4, n_iter + 1)
-    # the transposes' FP32 atomics add in a different order on every run; over
-    # 12 line-searched iterations that moves the image by ~1e-5 (measured
-    # 1.4e-5) while the objectives agree to ~1e-7
+    # every kernel of the 2-D iteration is deterministic (the tile transpose
+    # sums in fixed point), so the batch reproduces the single runs bit for bit
     for i in range(4):
-        assert np.allclose(hb[i], h_single[i], rtol=1e-6), i
-        assert rel_l2(to_host(psps.psps_get_image(states[i])), to_host(psps.psps_get_image(single[i]))) < 1e-4
+        assert np.array_equal(hb[i], h_single[i]), i
+        assert np.array_equal(to_host(psps.psps_get_image(states[i])), to_host(psps.psps_get_image(single[i]))), i
     assert psps.psps_batch_launch_count(batch) == sum(psps.psps_launch_count(s) for s in single)
     # states may not repeat or share a plan / preconditioner
     with pytest.raises(RuntimeError):
