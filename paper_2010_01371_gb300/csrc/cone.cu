@@ -433,7 +433,7 @@ constexpr int kGX = 4, kGY = 4, kGZ = 16;   // 256 voxels per CTA
 constexpr int kStageCap = 640;              // staged detector cells per view
 
 template <int C>
-__global__ void __launch_bounds__(kGX * kGY * kGZ, 3)
+__global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
     back_cone_gather_kernel(mbir_geometry g, const float4 *__restrict__ vt, const float4 *__restrict__ ta,
                             const float2 *__restrict__ tb, const int *__restrict__ view_axes,
                             const typename Vec<C>::T *__restrict__ ws, int nc, float *__restrict__ x,
