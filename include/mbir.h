@@ -105,7 +105,11 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
 /* Select the transpose's algorithm.  2-D: 0 = tile scatter through shared
  * memory (default; lanes of a warp on consecutive driving indices of one ray),
  * 1 = pixel-driven gather (deterministic: no atomics, bitwise reproducible),
- * 2 = ray-driven scatter with global FP32 atomics.  3-D (cone): 0 and 1 =
+ * 2 = ray-driven scatter with global FP32 atomics.  Mode 0 accumulates in
+ * fixed point (each term rounded to a grid of M / 2^22 or finer, M the
+ * largest |weight x value| of the call; exact integer sums) and is bitwise
+ * reproducible; a non-finite input makes its channel's image NaN.  It needs
+ * 8 bytes x n_mat_max x n_pix of plan scratch.  3-D (cone): 0 and 1 =
  * voxel-driven gather (default, deterministic), 2 = ray-driven scatter with
  * global FP32 atomics.  All use the forward projector's per-ray weights and
  * are the exact transpose of mbir_project up to FP32 rounding.  MBIR_ERR_ARG
@@ -114,7 +118,8 @@ mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 /* Views handled by one CTA of the tile transpose (mode 0), 1..180: the
  * grid is (image tiles) x ceil(n_views / views_per_cta) CTAs.  The plan's
  * default aims at about six CTAs per SM (4..60 views).  Only changes
- * the work split (and the FP32 summation order), not the result's definition.
+ * the work split (and the fixed-point grid, through the bound on the terms
+ * one accumulator receives), not the result's definition.
  * MBIR_ERR_ARG outside 1..180. */
 mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
 /* Autotuner: times the 2-D tile transpose (n_channels channels, zero data, a
@@ -177,6 +182,18 @@ mbir_status mbmd_objective(mbir_plan *plan, const mbmd_spectrum *spec, const flo
  * (overwritten); objective (device, nullable) receives L. */
 mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
                           int64_t n_rays, float *grad, double *objective, mbir_stream stream);
+
+/* Plain-SPS separable curvature of the data term at x (Eqs. 6 and 8-11 with
+ * M = I): curv = A^T kappa with, per ray and material,
+ *   kappa[m][i] = sum_E Q[E][m] gamma[E][i] c[E][i],  gamma = Q (A 1),
+ * c the maximum curvature of the per-ray, per-energy surrogate built from
+ * eta and rho (with the spectrum's detector blur, if set).  plan == NULL:
+ * projection domain (A = I, gamma = Q 1) and curv = kappa per ray.  The PSPS
+ * iteration forms the same numerators with gamma = Q A|M|1.  curv: device,
+ * [n_mat][image] (plan) or [n_mat][n_rays], overwritten.  Errors as
+ * mbmd_gradient. */
+mbir_status mbmd_curvature(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
+                           int64_t n_rays, float *curv, mbir_stream stream);
 
 /* mbmd_objective for projection-domain line integrals (the plan == NULL
  * case) that allocates no device memory.  The paper has no counterpart; this

@@ -186,6 +186,17 @@ def mbmd_gradient(plan: Plan | None, spec: Spectrum, x_or_l, y, grad=None, with_
     return grad, obj
 
 
+def mbmd_curvature(plan: Plan | None, spec: Spectrum, x_or_l, y, curv=None):
+    """Plain-SPS separable curvature A^T kappa (``mbmd_curvature``)."""
+    torch = _torch()
+    n_rays = y.numel() // spec.n_chan
+    if curv is None:
+        curv = torch.empty_like(x_or_l)
+    _call(lib().mbmd_curvature, plan.h if plan else None, spec.h, _dev(x_or_l, "x_or_l"), _dev(y, "y"), int(n_rays),
+          _dev(curv, "curv"), _stream())
+    return curv
+
+
 class Precond:
     """One-time preconditioner build (``psps_precondition_build``)."""
 

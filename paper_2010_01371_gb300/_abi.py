@@ -47,6 +47,7 @@ SIGNATURES = [
     ("mbmd_forward_model", c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     ("mbmd_objective", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("mbmd_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    ("mbmd_curvature", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("mbmd_objective_noalloc", c_int, [c_int, c_int, c_int, P(c_double), P(c_double), c_void_p, c_void_p, c_int64,
                                        c_void_p, c_void_p]),
     ("psps_precondition_build", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int64, P(c_double), c_int,

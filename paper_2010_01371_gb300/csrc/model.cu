@@ -865,6 +865,18 @@ mbir_status launch_fisher_blocks(const mbmd_spectrum *spec, int64_t n_rays, cons
     return MBIR_OK;
 }
 
+__global__ void model_fill_ones_kernel(float *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 1.f;
+}
+
+mbir_status fill_ones(float *p, int64_t n, cudaStream_t s) {
+    const int64_t b = cdiv(n, 256);
+    model_fill_ones_kernel<<<(unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096), 256, 0, s>>>(p, n);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
 }  // namespace psps
 
 using namespace psps;
@@ -950,15 +962,17 @@ extern "C" mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, i
 }
 
 namespace {
-// Scratch for the stateless model calls: l and g sinograms, partials and,
-// with a detector blur, the unblurred counts and weighted residuals.
+// Scratch for the stateless model calls: l, g and kappa sinograms, gamma,
+// partials and, with a detector blur, the unblurred counts and weighted
+// residuals.
 struct ModelScratch {
-    DBuf<float> l, g, y0, qw;
+    DBuf<float> l, g, kap, gam, ones, y0, qw;
     DBuf<dfloat> part;
 };
 
+
 mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y, int64_t n_rays,
-                      float *grad, double *objective, cudaStream_t s) {
+                      float *grad, double *objective, cudaStream_t s, float *curv = nullptr) {
     if (!spec || !x_or_l || !y || n_rays < 1) return fail(MBIR_ERR_ARG, "mbmd: bad argument");
     if (plan && n_rays != plan->n_rays)
         return fail(MBIR_ERR_ARG, "mbmd: n_rays %lld does not match the plan (%lld)", (long long)n_rays,
@@ -984,18 +998,34 @@ mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x
             g = grad;
         }
     }
+    // plain-SPS curvature numerators: gamma_m = [A 1]_m (projection domain: 1)
+    float *kap = nullptr;
+    if (curv) {
+        PSPS_TRY(sc.gam.alloc((size_t)nm * n_rays));
+        if (plan) {
+            PSPS_TRY(sc.ones.alloc((size_t)nm * plan->n_pix));
+            PSPS_TRY(fill_ones(sc.ones.p, (int64_t)nm * plan->n_pix, s));
+            PSPS_TRY(project(plan, sc.ones.p, sc.gam.p, nm, s));
+            PSPS_TRY(sc.kap.alloc((size_t)nm * n_rays));
+            kap = sc.kap.p;
+        } else {
+            PSPS_TRY(fill_ones(sc.gam.p, (int64_t)nm * n_rays, s));
+            kap = curv;
+        }
+    }
     BlurScratch bs;
     if (spec->blur_r > 0) {
         PSPS_TRY(sc.y0.alloc((size_t)spec->n_chan * n_rays));
         bs.y0 = sc.y0.p;
-        if (grad) {
+        if (grad || curv) {
             PSPS_TRY(sc.qw.alloc((size_t)spec->n_chan * n_rays));
             bs.qw = sc.qw.p;
         }
     }
-    PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, nullptr, g, nullptr, sc.part.p, nb, s, &bs));
+    PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, curv ? sc.gam.p : nullptr, g, kap, sc.part.p, nb, s, &bs));
     if (objective) PSPS_TRY(reduce_partials(sc.part.p, nb, 1, objective, 0, s));
     if (grad && plan) PSPS_TRY(backproject(plan, g, grad, nm, 0, s));
+    if (curv && plan) PSPS_TRY(backproject(plan, kap, curv, nm, 0, s));
     PSPS_CUDA(cudaStreamSynchronize(s));  // scratch is released on return
     return MBIR_OK;
 }
@@ -1011,4 +1041,10 @@ extern "C" mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec,
                                      int64_t n_rays, float *grad, double *objective, mbir_stream s) {
     if (!grad) return fail(MBIR_ERR_ARG, "mbmd_gradient: grad is null");
     return data_term(plan, spec, x_or_l, y, n_rays, grad, objective, (cudaStream_t)s);
+}
+
+extern "C" mbir_status mbmd_curvature(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
+                                      int64_t n_rays, float *curv, mbir_stream s) {
+    if (!curv) return fail(MBIR_ERR_ARG, "mbmd_curvature: curv is null");
+    return data_term(plan, spec, x_or_l, y, n_rays, nullptr, nullptr, (cudaStream_t)s, curv);
 }

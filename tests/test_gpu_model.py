@@ -162,3 +162,47 @@ def test_size_limits_and_degenerate_counts(psps, oracle_lib):
         psps.Spectrum(np.ones((257, 1)), np.ones((1, 257)))
     with pytest.raises(RuntimeError):
         psps.Spectrum(np.ones((4, 5)), np.ones((1, 4)))
+
+
+@pytest.mark.parametrize("case", ["mbir", "spectral", "projdomain", "spectral-blur"])
+def test_curvature_parity(psps, oracle_lib, case):
+    """Plain-SPS separable curvature A^T kappa (Eqs. 6, 8-11 with M = I)
+    against the oracle's numerators with gamma = A 1 (projection domain:
+    gamma = 1), on image and line-integral inputs, with and without a
+    detector blur."""
+    from oracle import model
+    if case == "projdomain":
+        Q, S = spectral(2)
+        rng = np.random.default_rng(8)
+        lt = np.stack([rng.uniform(0, 300, 4099), rng.uniform(0, 30, 4099)])
+        y = rng.poisson(model.forward_model(Q, S, lt)).astype(float)
+        l = 0.8 * lt
+        spec = psps.Spectrum(Q, S)
+        got = to_host(psps.mbmd_curvature(None, spec, to_dev(l), to_dev(y)))
+        want = model.curvature_numerator(Q, S, l, y, np.ones_like(l))
+        assert rel_l2(got, want) < 1e-5, rel_l2(got, want)
+        return
+    g = small_geoms()["fan2d_ragged"]
+    A = oracle_lib.Projector(g)
+    blur = None
+    if case == "mbir":
+        Q, S = np.ones((1, 1)), np.full((1, 1), 1e5)
+        x_true = phantom(g, seed=2, nm=1)
+        x = 0.5 * x_true
+    else:
+        Q, S = spectral(2)
+        x_true = 20 * phantom(g, seed=3, nm=2)
+        x = 0.6 * x_true
+        if case == "spectral-blur":
+            blur = model.Blur([0.1, 0.2, 0.5, 0.15, 0.05], g.n_u)
+    nm = Q.shape[1]
+    y = np.random.default_rng(4).poisson(model.forward_model(Q, S, A.project(x_true), blur)).astype(float)
+    plan = psps.Plan(g)
+    spec = psps.Spectrum(Q, S)
+    if blur is not None:
+        spec.set_blur(blur.b, g.n_u)
+    got = to_host(psps.mbmd_curvature(plan, spec, to_dev(x), to_dev(y)))
+    gamma = A.project(np.ones((nm,) + g.image_shape))
+    want = A.backproject(model.curvature_numerator(Q, S, A.project(x), y, gamma, blur))
+    assert rel_l2(got, want) < 1e-5, rel_l2(got, want)
+    assert np.all(got >= -1e-6 * np.abs(want).max())
