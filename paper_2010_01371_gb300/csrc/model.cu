@@ -302,37 +302,6 @@ __device__ __forceinline__ float blur_eta_weight(const BlurDev &B, const float *
     return s;
 }
 
-// Unblurred counts y0[c][i] = sum_E S[c][E] exp(-[Q l]_E,i).
-template <int NM, int CM>
-__global__ void __launch_bounds__(kModelThreads)
-    model_y0_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, float *__restrict__ y0) {
-    extern __shared__ float sh[];
-    load_spec(sp, sh);
-    const float *Q = sh;
-    const float *S = sh + sp.ne * NM;
-    const int nc = sp.nc, ne = sp.ne;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
-        float lm[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) lm[m] = l[(int64_t)m * n_rays + i];
-        float yb[CM];
-#pragma unroll
-        for (int c = 0; c < CM; ++c) yb[c] = 0.f;
-        for (int e = 0; e < ne; ++e) {
-            float z = 0.f;
-#pragma unroll
-            for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], lm[m], z);
-            const float t = transmission(z);
-#pragma unroll
-            for (int c = 0; c < CM; ++c)
-                if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < CM; ++c)
-            if (c < nc) y0[(int64_t)c * n_rays + i] = yb[c];
-    }
-}
-
 // Blurred residual r = B y0 - y: weighted residual qw = w r (if qw) and the
 // data term 1/2 sum w r^2 (block partials); ybar = B y0 when asked.
 __global__ void __launch_bounds__(kModelThreads)
@@ -356,230 +325,296 @@ __global__ void __launch_bounds__(kModelThreads)
     }
 }
 
-// Numerators with the blur: u_c = [B^T qw_c]_i replaces w_c r_c and
-// sigma_c [B^T (w_c .* B 1)]_i replaces w_c sigma_c (see above).
+// Data term and numerators with the blur, in one kernel: a block takes
+// segments of T = blockDim - 4r rays with 2r halo rays on each side.
+// Phase 1: unblurred counts y0 of every ray of the extended segment (shared
+// memory).  Phase 2: blurred residual r = B y0 - y and weighted residual
+// qw = w r for the rays within r of the segment (the data term for its own
+// rays).  Phase 3 (own rays): u_c = [B^T qw_c]_i replaces w_c r_c and
+// sigma_c [B^T (w_c .* B 1)]_i replaces w_c sigma_c in the numerators, with a
+// second pass over the energies.
+// [B v] and [B^T v] at thread tid's ray from a shared-memory column of
+// consecutive rays (j = the ray's position in its detector row).
+__device__ __forceinline__ float blur_col(const BlurDev &Bd, const float *__restrict__ col, int tid, int j) {
+    float s = 0.f;
+    for (int k = -Bd.r; k <= Bd.r; ++k) {
+        const int jj = j + k;
+        if (jj >= 0 && jj < Bd.row) s = fmaf(Bd.b[k + Bd.r], col[tid + k], s);
+    }
+    return s;
+}
+
+__device__ __forceinline__ float blur_colT(const BlurDev &Bd, const float *__restrict__ col, int tid, int j) {
+    float s = 0.f;
+    for (int k = -Bd.r; k <= Bd.r; ++k) {
+        const int jj = j - k;
+        if (jj >= 0 && jj < Bd.row) s = fmaf(Bd.b[k + Bd.r], col[tid - k], s);
+    }
+    return s;
+}
+
 template <int NM, int CM>
 __global__ void __launch_bounds__(kModelThreads)
-    model_grad_blur_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
-                           const float *__restrict__ qw, const float *__restrict__ gamma, float *__restrict__ g,
-                           float *__restrict__ kappa) {
+    model_grad_blur_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
+                                 const float *__restrict__ gamma, float *__restrict__ g, float *__restrict__ kappa,
+                                 dfloat *__restrict__ partials) {
     extern __shared__ float sh[];
     load_spec(sp, sh);
     const float *Q = sh;
     const float *S = sh + sp.ne * NM;
     const float *sig = S + sp.nc * sp.ne;
     const int nc = sp.nc, ne = sp.ne;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
-        float lm[NM], gm[NM], km[NM], gam[NM];
+    const int B = blockDim.x, tid = threadIdx.x, r = sp.blur.r, T = B - 4 * r;
+    float *y0s = sh + (sp.ne * sp.nm + sp.nc * sp.ne + sp.nc);  // [CM][B]
+    float *qws = y0s + CM * B;                                  // [CM][B]
+    const bool grads = g || kappa;
+    const int64_t nseg = (n_rays + T - 1) / T;
+    dfloat obj{0.f, 0.f};
+    for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+        const int64_t i = seg * T - 2 * r + tid;
+        const bool valid = i >= 0 && i < n_rays;
+        const bool own = valid && tid >= 2 * r && tid < 2 * r + T;
+        const int j = valid ? (int)(i % sp.blur.row) : 0;
+        float lm[NM];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            lm[m] = l[(int64_t)m * n_rays + i];
-            gm[m] = km[m] = 0.f;
-            gam[m] = kappa ? gamma[(int64_t)m * n_rays + i] : 0.f;
-        }
-        float u[CM], ws[CM];
+        for (int m = 0; m < NM; ++m) lm[m] = valid ? l[(int64_t)m * n_rays + i] : 0.f;
+        {
+            float yb[CM];
 #pragma unroll
-        for (int c = 0; c < CM; ++c) {
-            u[c] = ws[c] = 0.f;
-            if (c < nc) {
-                u[c] = blur_at(sp.blur, qw + (int64_t)c * n_rays, i, -1);
-                ws[c] = kappa ? sig[c] * blur_eta_weight(sp.blur, y + (int64_t)c * n_rays, i) : 0.f;
-            }
-        }
-        for (int e = 0; e < ne; ++e) {
-            float z = 0.f, gE = 0.f;
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                z = fmaf(Q[e * NM + m], lm[m], z);
-                gE = fmaf(Q[e * NM + m], gam[m], gE);
-            }
-            const float t = transmission(z);
-            float v = 0.f, eta = 0.f;
-#pragma unroll
-            for (int c = 0; c < CM; ++c)
-                if (c < nc) {
-                    v = fmaf(S[c * ne + e], u[c], v);
-                    eta = fmaf(S[c * ne + e], ws[c], eta);
-                }
-            const float tv = t * v;
-            float cE = 0.f;
-            if (kappa) {
-                const float rho = v - eta * t;
-                const float uh = fmaxf(1.f, t);
-                cE = fmaxf(0.f, (2.f * eta * uh + rho) * uh);
-            }
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                gm[m] = fmaf(-Q[e * NM + m], tv, gm[m]);
-                km[m] = fmaf(Q[e * NM + m], gE * cE, km[m]);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            if (g) g[(int64_t)m * n_rays + i] = gm[m];
-            if (kappa) kappa[(int64_t)m * n_rays + i] = km[m];
-        }
-    }
-}
-
-// Line search with the blur, pass 1: unblurred counts (and, for the Newton
-// evaluation, their first two alpha-derivatives) per ray into buf, and the
-// rays leaving the domain z >= z_min (partial streams 3, resp. kMaxHalve+k).
-//   MODE 0: buf[0|1|2][c][i] = y0, dy0/dalpha, d2y0/dalpha2 at ls->alpha
-//   MODE 1: buf[k][c][i] = y0 at the k-th halving candidate
-template <int NM, int CM, int MODE>
-__global__ void __launch_bounds__(kModelThreads)
-    ls_blur_pre_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
-                       DevLS *ls, LsCfg cfg, float *__restrict__ buf, dfloat *__restrict__ partials) {
-    if (MODE == 1 && ls->done) return;  // same value for every block
-    extern __shared__ float sh[];
-    load_spec(sp, sh);
-    const float *Q = sh;
-    const float *S = sh + sp.ne * NM;
-    const int nc = sp.nc, ne = sp.ne;
-    const int nb = gridDim.x;
-    const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
-    if constexpr (MODE == 0) {
-        const float alpha = (float)ls->alpha;
-        dfloat bad[1] = {dfloat{0.f, 0.f}};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            float la[NM], qm[NM];
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                qm[m] = q[(int64_t)m * n_rays + i];
-                la[m] = fmaf(alpha, qm[m], l[(int64_t)m * n_rays + i]);
-            }
-            float yb[CM], d1[CM], d2[CM];
-#pragma unroll
-            for (int c = 0; c < CM; ++c) yb[c] = d1[c] = d2[c] = 0.f;
-            float zlo = 3.0e38f;
-            for (int e = 0; e < ne; ++e) {
-                float z = 0.f, dz = 0.f;
-#pragma unroll
-                for (int m = 0; m < NM; ++m) {
-                    z = fmaf(Q[e * NM + m], la[m], z);
-                    dz = fmaf(Q[e * NM + m], qm[m], dz);
-                }
-                zlo = fminf(zlo, z);
-                const float t = transmission(z);
-                const float tdz = t * dz;
-#pragma unroll
-                for (int c = 0; c < CM; ++c)
-                    if (c < nc) {
-                        const float s = S[c * ne + e];
-                        yb[c] = fmaf(s, t, yb[c]);
-                        d1[c] = fmaf(-s, tdz, d1[c]);
-                        d2[c] = fmaf(s, tdz * dz, d2[c]);
-                    }
-            }
-#pragma unroll
-            for (int c = 0; c < CM; ++c)
-                if (c < nc) {
-                    buf[(int64_t)c * n_rays + i] = yb[c];
-                    buf[(int64_t)(nc + c) * n_rays + i] = d1[c];
-                    buf[(int64_t)(2 * nc + c) * n_rays + i] = d2[c];
-                }
-            if (!(zlo >= cfg.z_min)) df_add(bad[0], 1.f);
-        }
-        block_sum_store<1>(bad, partials + 3 * (int64_t)nb);
-    } else {
-        float alphas[kMaxHalve];
-        double ak = ls->best_a;
-#pragma unroll
-        for (int k = 0; k < kMaxHalve; ++k) {
-            ak *= 0.5;
-            alphas[k] = (float)ak;
-        }
-        dfloat bad[kMaxHalve];
-#pragma unroll
-        for (int k = 0; k < kMaxHalve; ++k) bad[k] = dfloat{0.f, 0.f};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            float lm[NM], qm[NM];
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                qm[m] = q[(int64_t)m * n_rays + i];
-                lm[m] = l[(int64_t)m * n_rays + i];
-            }
-#pragma unroll
-            for (int k = 0; k < kMaxHalve; ++k) {
-                if (k >= nh) break;
-                float yb[CM];
-#pragma unroll
-                for (int c = 0; c < CM; ++c) yb[c] = 0.f;
-                float zlo = 3.0e38f;
+            for (int c = 0; c < CM; ++c) yb[c] = 0.f;
+            if (valid)
                 for (int e = 0; e < ne; ++e) {
                     float z = 0.f;
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alphas[k], qm[m], lm[m]), z);
-                    zlo = fminf(zlo, z);
+                    for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], lm[m], z);
                     const float t = transmission(z);
 #pragma unroll
                     for (int c = 0; c < CM; ++c)
                         if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
                 }
 #pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) y0s[c * B + tid] = yb[c];
+        }
+        __syncthreads();
+        if (valid && tid >= r && tid < B - r) {
+            float f = 0.f;
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) {
+                    const float yc = y[(int64_t)c * n_rays + i];
+                    const float w = 1.f / fmaxf(yc, 1.f);
+                    const float rr = blur_col(sp.blur, y0s + c * B, tid, j) - yc;
+                    qws[c * B + tid] = w * rr;
+                    f = fmaf(0.5f * w * rr, rr, f);
+                }
+            if (own) df_add(obj, f);
+        }
+        __syncthreads();
+        if (grads && own) {
+            float gm[NM], km[NM], gam[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                gm[m] = km[m] = 0.f;
+                gam[m] = kappa ? gamma[(int64_t)m * n_rays + i] : 0.f;
+            }
+            float u[CM], ws[CM];
+#pragma unroll
+            for (int c = 0; c < CM; ++c) {
+                u[c] = ws[c] = 0.f;
+                if (c < nc) {
+                    u[c] = blur_colT(sp.blur, qws + c * B, tid, j);
+                    ws[c] = kappa ? sig[c] * blur_eta_weight(sp.blur, y + (int64_t)c * n_rays, i) : 0.f;
+                }
+            }
+            for (int e = 0; e < ne; ++e) {
+                float z = 0.f, gE = 0.f;
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    z = fmaf(Q[e * NM + m], lm[m], z);
+                    gE = fmaf(Q[e * NM + m], gam[m], gE);
+                }
+                const float t = transmission(z);
+                float v = 0.f, eta = 0.f;
+#pragma unroll
                 for (int c = 0; c < CM; ++c)
-                    if (c < nc) buf[((int64_t)k * nc + c) * n_rays + i] = yb[c];
-                if (!(zlo >= cfg.z_min)) df_add(bad[k], 1.f);
+                    if (c < nc) {
+                        v = fmaf(S[c * ne + e], u[c], v);
+                        eta = fmaf(S[c * ne + e], ws[c], eta);
+                    }
+                const float tv = t * v;
+                float cE = 0.f;
+                if (kappa) {
+                    const float rho = v - eta * t;
+                    const float uh = fmaxf(1.f, t);
+                    cE = fmaxf(0.f, (2.f * eta * uh + rho) * uh);
+                }
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    gm[m] = fmaf(-Q[e * NM + m], tv, gm[m]);
+                    km[m] = fmaf(Q[e * NM + m], gE * cE, km[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                if (g) g[(int64_t)m * n_rays + i] = gm[m];
+                if (kappa) kappa[(int64_t)m * n_rays + i] = km[m];
             }
         }
-        block_sum_store<kMaxHalve>(bad, partials + (int64_t)kMaxHalve * nb);
+        __syncthreads();
+    }
+    if (partials) {
+        dfloat v[1] = {obj};
+        block_sum_store<1>(v, partials);
     }
 }
 
-// Line search with the blur, pass 2: blurred counts and the data terms
-// (phi, phi', phi'' or the candidates' phi) as block partials; the last
-// block runs the same control as the fused kernel.
-template <int MODE>
+// Line search with the blur, fused into one kernel per evaluation: a block
+// takes segments of T = blockDim - 2r consecutive rays plus r halo rays on
+// each side.  Every thread evaluates the unblurred counts of one ray of the
+// extended segment (and, for the Newton evaluation, their first two
+// alpha-derivatives) into shared memory; the segment's own rays then blur
+// them along their detector row and add their data terms, and the rays that
+// leave the domain z >= z_min are counted (own rays only).  Halo rays are
+// evaluated by both neighbouring segments (2r / T extra work).  Partials and
+// the last block's control are those of ls_fused_kernel.
+template <int NM, int CM, int MODE>
 __global__ void __launch_bounds__(kModelThreads)
-    ls_blur_sum_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ y, const float *__restrict__ buf,
-                       DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
-    if (MODE == 1 && ls->done) return;
-    const int nc = sp.nc;
+    ls_blur_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
+                         const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
+    if (MODE == 1 && ls->done) return;  // same value for every block
+    extern __shared__ float sh[];
+    load_spec(sp, sh);
+    const float *Q = sh;
+    const float *S = sh + sp.ne * NM;
+    const int nc = sp.nc, ne = sp.ne;
+    float *buf = sh + (sp.ne * sp.nm + sp.nc * sp.ne + sp.nc);  // [MODE 0: 3 | MODE 1: 1][CM][blockDim]
+    const int B = blockDim.x, tid = threadIdx.x, r = sp.blur.r, T = B - 2 * r;
+    const int64_t nseg = (n_rays + T - 1) / T;
     const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
-    if constexpr (MODE == 0) {
-        dfloat acc[3] = {dfloat{0.f, 0.f}, dfloat{0.f, 0.f}, dfloat{0.f, 0.f}};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            float f = 0.f, f1 = 0.f, f2 = 0.f;
-            for (int c = 0; c < nc; ++c) {
-                const float yb = blur_at(sp.blur, buf + (int64_t)c * n_rays, i, +1);
-                const float d1 = blur_at(sp.blur, buf + (int64_t)(nc + c) * n_rays, i, +1);
-                const float d2 = blur_at(sp.blur, buf + (int64_t)(2 * nc + c) * n_rays, i, +1);
-                const float yc = y[(int64_t)c * n_rays + i];
-                const float w = 1.f / fmaxf(yc, 1.f);
-                const float r = yb - yc;
-                f = fmaf(0.5f * w * r, r, f);
-                f1 = fmaf(w * r, d1, f1);
-                f2 = fmaf(w, fmaf(d1, d1, r * d2), f2);
-            }
-            df_add(acc[0], f);
-            df_add(acc[1], f1);
-            df_add(acc[2], f2);
-        }
-        block_sum_store<3>(acc, partials);
-    } else {
-        dfloat acc[kMaxHalve];
+    constexpr int NACC = MODE == 0 ? 4 : 2 * kMaxHalve;
+    dfloat acc[NACC];
 #pragma unroll
-        for (int k = 0; k < kMaxHalve; ++k) acc[k] = dfloat{0.f, 0.f};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
-             i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < NACC; ++k) acc[k] = dfloat{0.f, 0.f};
+    float alphas[kMaxHalve];
+    {
+        double ak = MODE == 0 ? 0.0 : ls->best_a;
+#pragma unroll
+        for (int k = 0; k < kMaxHalve; ++k) {
+            ak *= 0.5;
+            alphas[k] = (float)ak;
+        }
+    }
+    const float alpha = MODE == 0 ? (float)ls->alpha : 0.f;
+    for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+        const int64_t i = seg * T - r + tid;
+        const bool valid = i >= 0 && i < n_rays;
+        const bool own = valid && tid >= r && tid < r + T;
+        const int j = valid ? (int)(i % sp.blur.row) : 0;
+        float lm[NM], qm[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            qm[m] = valid ? q[(int64_t)m * n_rays + i] : 0.f;
+            lm[m] = valid ? l[(int64_t)m * n_rays + i] : 0.f;
+        }
+        if constexpr (MODE == 0) {
+            float yb[CM], d1[CM], d2[CM];
+#pragma unroll
+            for (int c = 0; c < CM; ++c) yb[c] = d1[c] = d2[c] = 0.f;
+            float zlo = 3.0e38f;
+            if (valid) {
+                float la[NM];
+#pragma unroll
+                for (int m = 0; m < NM; ++m) la[m] = fmaf(alpha, qm[m], lm[m]);
+                for (int e = 0; e < ne; ++e) {
+                    float z = 0.f, dz = 0.f;
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        z = fmaf(Q[e * NM + m], la[m], z);
+                        dz = fmaf(Q[e * NM + m], qm[m], dz);
+                    }
+                    zlo = fminf(zlo, z);
+                    const float t = transmission(z);
+                    const float tdz = t * dz;
+#pragma unroll
+                    for (int c = 0; c < CM; ++c)
+                        if (c < nc) {
+                            const float sv = S[c * ne + e];
+                            yb[c] = fmaf(sv, t, yb[c]);
+                            d1[c] = fmaf(-sv, tdz, d1[c]);
+                            d2[c] = fmaf(sv, tdz * dz, d2[c]);
+                        }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (c < nc) {
+                    buf[c * B + tid] = yb[c];
+                    buf[(CM + c) * B + tid] = d1[c];
+                    buf[(2 * CM + c) * B + tid] = d2[c];
+                }
+            if (own && !(zlo >= cfg.z_min)) df_add(acc[3], 1.f);
+            __syncthreads();
+            if (own) {
+                float f = 0.f, f1 = 0.f, f2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) {
+                        const float ybc = blur_col(sp.blur, buf + c * B, tid, j);
+                        const float d1c = blur_col(sp.blur, buf + (CM + c) * B, tid, j);
+                        const float d2c = blur_col(sp.blur, buf + (2 * CM + c) * B, tid, j);
+                        const float yc = y[(int64_t)c * n_rays + i];
+                        const float w = 1.f / fmaxf(yc, 1.f);
+                        const float rr = ybc - yc;
+                        f = fmaf(0.5f * w * rr, rr, f);
+                        f1 = fmaf(w * rr, d1c, f1);
+                        f2 = fmaf(w, fmaf(d1c, d1c, rr * d2c), f2);
+                    }
+                df_add(acc[0], f);
+                df_add(acc[1], f1);
+                df_add(acc[2], f2);
+            }
+            __syncthreads();
+        } else {
 #pragma unroll
             for (int k = 0; k < kMaxHalve; ++k) {
-                if (k >= nh) break;
-                float f = 0.f;
-                for (int c = 0; c < nc; ++c) {
-                    const float yb = blur_at(sp.blur, buf + ((int64_t)k * nc + c) * n_rays, i, +1);
-                    const float yc = y[(int64_t)c * n_rays + i];
-                    const float r = yb - yc;
-                    f = fmaf(0.5f * r / fmaxf(yc, 1.f), r, f);
+                if (k >= nh) break;  // same for every thread
+                float yb[CM];
+#pragma unroll
+                for (int c = 0; c < CM; ++c) yb[c] = 0.f;
+                float zlo = 3.0e38f;
+                if (valid)
+                    for (int e = 0; e < ne; ++e) {
+                        float z = 0.f;
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alphas[k], qm[m], lm[m]), z);
+                        zlo = fminf(zlo, z);
+                        const float t = transmission(z);
+#pragma unroll
+                        for (int c = 0; c < CM; ++c)
+                            if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
+                    }
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) buf[c * B + tid] = yb[c];
+                if (own && !(zlo >= cfg.z_min)) df_add(acc[kMaxHalve + k], 1.f);
+                __syncthreads();
+                if (own) {
+                    float f = 0.f;
+#pragma unroll
+                    for (int c = 0; c < CM; ++c)
+                        if (c < nc) {
+                            const float yc = y[(int64_t)c * n_rays + i];
+                            const float rr = blur_col(sp.blur, buf + c * B, tid, j) - yc;
+                            f = fmaf(0.5f * rr / fmaxf(yc, 1.f), rr, f);
+                        }
+                    df_add(acc[k], f);
                 }
-                df_add(acc[k], f);
+                __syncthreads();
             }
-        block_sum_store<kMaxHalve>(acc, partials);
+        }
     }
+    block_sum_store<NACC>(acc, partials);
     if (!last_block_arrive(&ls->ticket)) return;
     const int nb = gridDim.x;
     if constexpr (MODE == 0) {
@@ -731,38 +766,23 @@ struct BlurModelLaunch {
     int64_t n;
     const float *l, *y, *gamma;
     float *g, *kappa;
-    const BlurScratch *scr;
+    dfloat *partials;
     int nblocks;
     size_t smem;
     cudaStream_t s;
-    int stage;  // 0: unblurred counts, 1: numerators
     template <int NM, int CM>
     void run() {
-        if (stage == 0)
-            model_y0_kernel<NM, CM><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, scr->y0);
-        else
-            model_grad_blur_kernel<NM, CM><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, y, scr->qw, gamma, g, kappa);
+        const size_t sm = smem + sizeof(float) * 2 * CM * kModelThreads;
+        model_grad_blur_fused_kernel<NM, CM><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, y, gamma, g, kappa, partials);
     }
 };
 
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
-                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s,
-                              const BlurScratch *scr) {
+                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     if (sp.blur.r > 0) {
-        const bool grads = g || kappa;
-        if (!scr || !scr->y0 || (grads && !scr->qw))
-            return fail(MBIR_ERR_ARG, "the blurred model needs scratch buffers");
-        BlurModelLaunch L{sp, n_rays, l, y, gamma, g, kappa, scr, nblocks, smem, s, 0};
-        PSPS_TRY(dispatch_nm_cm(sp, L));
-        blur_resid_kernel<<<nblocks, kModelThreads, 0, s>>>(sp, n_rays, scr->y0, y, grads ? scr->qw : nullptr,
-                                                             nullptr, partials);
-        PSPS_LAUNCH_CHECK();
-        if (grads) {
-            L.stage = 1;
-            PSPS_TRY(dispatch_nm_cm(sp, L));
-        }
-        return MBIR_OK;
+        BlurModelLaunch L{sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s};
+        return dispatch_nm_cm(sp, L);
     }
     switch (sp.nm) {
         case 1: model_grad_launch_nm<1>(sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s); break;
@@ -798,37 +818,29 @@ void ls_fused_launch_nm(SpecDev sp, int64_t n_rays, const float *l, const float 
 struct BlurLsLaunch {
     SpecDev sp;
     int64_t n;
-    const float *l, *q;
+    const float *l, *q, *y;
     DevLS *ls;
     LsCfg cfg;
-    float *buf;
     dfloat *partials;
-    int mode, nblocks;
+    int mode, last, nblocks;
     size_t smem;
     cudaStream_t s;
     template <int NM, int CM>
     void run() {
+        const size_t sm = smem + sizeof(float) * (mode == 0 ? 3 : 1) * CM * kModelThreads;
         if (mode == 0)
-            ls_blur_pre_kernel<NM, CM, 0><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, q, ls, cfg, buf, partials);
+            ls_blur_fused_kernel<NM, CM, 0><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, q, y, ls, cfg, last, partials);
         else
-            ls_blur_pre_kernel<NM, CM, 1><<<nblocks, kModelThreads, smem, s>>>(sp, n, l, q, ls, cfg, buf, partials);
+            ls_blur_fused_kernel<NM, CM, 1><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, q, y, ls, cfg, last, partials);
     }
 };
 
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
-                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s,
-                            const BlurScratch *scr) {
+                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
     if (sp.blur.r > 0) {
-        if (!scr || !scr->ls) return fail(MBIR_ERR_ARG, "the blurred line search needs a scratch buffer");
-        BlurLsLaunch L{sp, n_rays, l, q, ls, cfg, scr->ls, partials, mode, nblocks, smem, s};
-        PSPS_TRY(dispatch_nm_cm(sp, L));
-        if (mode == 0)
-            ls_blur_sum_kernel<0><<<nblocks, kModelThreads, 0, s>>>(sp, n_rays, y, scr->ls, ls, cfg, last, partials);
-        else
-            ls_blur_sum_kernel<1><<<nblocks, kModelThreads, 0, s>>>(sp, n_rays, y, scr->ls, ls, cfg, last, partials);
-        PSPS_LAUNCH_CHECK();
-        return MBIR_OK;
+        BlurLsLaunch L{sp, n_rays, l, q, y, ls, cfg, partials, mode, last, nblocks, smem, s};
+        return dispatch_nm_cm(sp, L);
     }
     switch (sp.nm) {
         case 1: ls_fused_launch_nm<1>(sp, n_rays, l, q, y, ls, cfg, mode, last, partials, nblocks, smem, s); break;
@@ -967,11 +979,10 @@ extern "C" mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, i
 }
 
 namespace {
-// Scratch for the stateless model calls: l, g and kappa sinograms, gamma,
-// partials and, with a detector blur, the unblurred counts and weighted
-// residuals.
+// Scratch for the stateless model calls: l, g and kappa sinograms, gamma and
+// partials.
 struct ModelScratch {
-    DBuf<float> l, g, kap, gam, ones, y0, qw;
+    DBuf<float> l, g, kap, gam, ones;
     DBuf<dfloat> part;
 };
 
@@ -1018,16 +1029,7 @@ mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x
             kap = curv;
         }
     }
-    BlurScratch bs;
-    if (spec->blur_r > 0) {
-        PSPS_TRY(sc.y0.alloc((size_t)spec->n_chan * n_rays));
-        bs.y0 = sc.y0.p;
-        if (grad || curv) {
-            PSPS_TRY(sc.qw.alloc((size_t)spec->n_chan * n_rays));
-            bs.qw = sc.qw.p;
-        }
-    }
-    PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, curv ? sc.gam.p : nullptr, g, kap, sc.part.p, nb, s, &bs));
+    PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, curv ? sc.gam.p : nullptr, g, kap, sc.part.p, nb, s));
     if (objective) PSPS_TRY(reduce_partials(sc.part.p, nb, 1, objective, 0, s));
     if (grad && plan) PSPS_TRY(backproject(plan, g, grad, nm, 0, s));
     if (curv && plan) PSPS_TRY(backproject(plan, kap, curv, nm, 0, s));

@@ -27,13 +27,6 @@ inline SpecDev spec_dev(const mbmd_spectrum *s) {
     return d;
 }
 
-// Scratch of the blurred model ([n_chan][n_rays] each: unblurred mean counts
-// and weighted residuals) and of the blurred line search
-// ([kMaxHalve][n_chan][n_rays]); unused (may be null) without a blur.
-struct BlurScratch {
-    float *y0 = nullptr, *qw = nullptr, *ls = nullptr;
-};
-
 constexpr int kModelThreads = 256;
 constexpr int kModelMaxBlocks = 2048;  // grid-stride; partial sums per block
 
@@ -44,17 +37,19 @@ inline int model_blocks(int64_t n) {
 }
 
 // data term partials (1 per block); g, kappa optional ([nm][n_rays]).
-// gamma: per-ray gamma_m = [A |M| 1]_m ([nm][n_rays]) for kappa.
+// gamma: per-ray gamma_m = [A |M| 1]_m ([nm][n_rays]) for kappa.  With a
+// detector blur the same quantities come from row segments with halos (one
+// kernel, no scratch).
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
-                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s,
-                              const BlurScratch *scr = nullptr);
+                              float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s);
 // Fused line-search evaluation: mode 0 evaluates phi, phi', phi'' at
 // ls->alpha and its last block runs the Newton control; mode 1 (skipped when
 // the search is done) evaluates the n_halve halving candidates at once and
-// its last block picks the step.  partials: 2 kMaxHalve per block.
+// its last block picks the step.  partials: 2 kMaxHalve per block.  With a
+// detector blur the same evaluation runs on row segments with halos (one
+// kernel, no scratch).
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
-                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s,
-                            const BlurScratch *scr = nullptr);
+                            LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s);
 // ybar = B S exp(-Q l); with a blur, y0 ([n_chan][n_rays]) holds the unblurred
 // counts.
 mbir_status launch_forward_model(SpecDev sp, int64_t n_rays, const float *l, float *ybar, cudaStream_t s,

@@ -117,8 +117,6 @@ struct psps_state {
     PenaltyDev pd{};
     LsCfg cfg{3, 8, 1e12, 8.0, -20.0f};
     DBuf<float> x, l, y, gamma, dR, gk, G, gp, dp, pp, p, q;
-    DBuf<float> blur_y0, blur_qw, blur_ls;   // blurred model only
-    BlurScratch bscr;
     SpecDev sd;  // the spectrum (and its blur) as it was at creation
     DBuf<dfloat> part_obj, part_pen, part_ls;
     DBuf<double> history, alphas;
@@ -206,7 +204,7 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
     // per-ray numerators and the data term
     mark(st, PSPS_PROF_MODEL, 0, s);
     PSPS_TRY(launch_model_grad(sp, nr, st->l.p, st->y.p, st->gamma.p, st->gk.p, st->gk.p + (int64_t)nm * nr,
-                               st->part_obj.p, st->nb_model, s, &st->bscr));
+                               st->part_obj.p, st->nb_model, s));
     mark(st, PSPS_PROF_MODEL, 1, s);
     mark(st, PSPS_PROF_BACKPROJECT, 0, s);
     PSPS_TRY(backproject_or_copy(st, st->gk.p, st->G.p, 2 * nm, s));
@@ -237,10 +235,10 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
         const int nb = st->nb_model;
         for (int k = 0; k < st->cfg.n_ls; ++k)
             PSPS_TRY(launch_ls_fused(sp, nr, st->l.p, st->q.p, st->y.p, st->ls.p, st->cfg, 0, k + 1 == st->cfg.n_ls,
-                                     st->part_ls.p, nb, s, &st->bscr));
+                                     st->part_ls.p, nb, s));
         if (st->cfg.n_halve > 0)
             PSPS_TRY(
-                launch_ls_fused(sp, nr, st->l.p, st->q.p, st->y.p, st->ls.p, st->cfg, 1, 1, st->part_ls.p, nb, s, &st->bscr));
+                launch_ls_fused(sp, nr, st->l.p, st->q.p, st->y.p, st->ls.p, st->cfg, 1, 1, st->part_ls.p, nb, s));
     } else {
         set_alpha_one_kernel<<<1, 1, 0, s>>>(st->ls.p);
         PSPS_LAUNCH_CHECK();
@@ -261,7 +259,7 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
 mbir_status final_objective(psps_state *st, cudaStream_t s) {
     PSPS_TRY(project_or_copy(st, st->x.p, st->l.p, s));
     PSPS_TRY(launch_model_grad(st->sd, st->n_rays, st->l.p, st->y.p, nullptr, nullptr, nullptr,
-                               st->part_obj.p, st->nb_model, s, &st->bscr));
+                               st->part_obj.p, st->nb_model, s));
     if (st->has_pen) PSPS_TRY(penalty_call(st, st->x.p, nullptr, nullptr, 0, 0, st->part_pen.p, s));
     ctrl_begin_kernel<<<1, kThreads, 0, s>>>(st->ls.p, st->part_obj.p, st->nb_model,
                                              st->has_pen ? st->part_pen.p : nullptr, st->nb_pen, st->history.p);
@@ -369,12 +367,6 @@ extern "C" mbir_status psps_state_create(mbir_plan *plan, const mbmd_spectrum *s
     A(st->pp, nm * n);
     A(st->p, nm * n);
     A(st->q, nm * nr);
-    if (spec->blur_r > 0) {
-        A(st->blur_y0, (size_t)st->nc * nr);
-        A(st->blur_qw, (size_t)st->nc * nr);
-        A(st->blur_ls, (size_t)kMaxHalve * st->nc * nr);
-        st->bscr = BlurScratch{st->blur_y0.p, st->blur_qw.p, st->blur_ls.p};
-    }
     if (e == MBIR_OK) e = st->part_obj.alloc(st->nb_model);
     if (e == MBIR_OK) e = st->part_pen.alloc(3 * st->nb_pen);
     if (e == MBIR_OK) e = st->part_ls.alloc(2 * kMaxHalve * st->nb_model);
