@@ -13,8 +13,10 @@
 //                    c_E = max(0, 2 eta_E u^2 + rho_E u): the largest second
 //                    derivative of 1/2 eta e^{-2z} + rho e^{-z} on z >= min(0, z^n)
 //   curvature num.   kappa_m = sum_E Q[E][m] gamma_E c_E,  gamma_E = sum_m Q[E][m] gamma_m
-// Exponentials and per-ray sums run in FP32 (expf); the objective and
-// line-search sums over rays are double-float reductions.
+// Exponentials and per-ray sums run in FP32 (exp(-z) as exp2f(-z log2 e));
+// the objective and line-search sums over rays are double-float reductions.
+// With a detector blur B (outer operator B S) the kernels work on row
+// segments with halo rays so that B and B^T act on shared-memory copies.
 #include <cmath>
 #include <type_traits>
 #include <vector>

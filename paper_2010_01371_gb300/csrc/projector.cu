@@ -19,10 +19,11 @@
 //    float/float2/float4) with Kahan-compensated FP32 accumulation along the
 //    ray, or tile sums through shared memory (the tile decomposition below;
 //    mbir_plan_set_projector);
-//  * transpose: tile scatter into shared memory (default), a pixel-driven
-//    gather (deterministic, no atomics) and a ray-driven scatter with global
-//    FP32 atomics, all with the forward's per-ray weights
-//    (mbir_plan_set_backprojector).
+//  * transpose: tile scatter into 32-bit fixed-point shared-memory
+//    accumulators and a 64-bit fixed-point image (default; bitwise
+//    reproducible), a pixel-driven gather (deterministic, no atomics) and a
+//    ray-driven scatter with global FP32 atomics, all with the forward's
+//    per-ray weights (mbir_plan_set_backprojector).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
