@@ -163,13 +163,15 @@ mbir_status mbmd_spectrum_destroy(mbmd_spectrum *spec);
  * unchanged and return MBIR_ERR_ARG. */
 mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, int row, const double *taps);
 
-/* Mean counts y_bar[c][i] = sum_E S[c][E] exp(-sum_m Q[E][m] l[m][i]) (Eq. 1).
+/* Mean counts y_bar[c][i] = sum_E S[c][E] exp(-sum_m Q[E][m] l[m][i]) (Eq. 1),
+ * followed by the spectrum's detector blur B along detector rows when one is
+ * set (mbmd_spectrum_set_blur; n_rays must then be a multiple of its row).
  * l: [n_mat][n_rays], ybar: [n_chan][n_rays]. */
 mbir_status mbmd_forward_model(const mbmd_spectrum *spec, const float *l, float *ybar, int64_t n_rays,
                                mbir_stream stream);
 
 /* PWLS data term L = 1/2 sum_{c,i} w (y - y_bar)^2 with w = 1/max(y, 1)
- * (Eq. 3, Sigma_y = diag(max(y,1))).  plan != NULL: x_or_l is an image
+ * (Eq. 3, Sigma_y = diag(max(y,1))), y_bar as in mbmd_forward_model.  plan != NULL: x_or_l is an image
  * [n_mat][image] and l = A x is formed internally; plan == NULL: x_or_l is
  * the line-integral array [n_mat][n_rays] (projection-domain decomposition).
  * *objective is a DEVICE double written with the FP64-reduced value. */
