@@ -63,6 +63,51 @@ def weights(y: np.ndarray) -> np.ndarray:
     return 1.0 / np.maximum(y, 1.0)
 
 
+class RowCorrelation:
+    """Correlated detector noise (a non-diagonal Sigma_y, Sec. II-A: the
+    covariance is known): Sigma_y = D^1/2 C D^1/2 with D = diag(max(y, 1)) and,
+    in every channel and detector row (n_u consecutive rays), the first-order
+    autoregressive correlation C[j, k] = a^|j - k| between cells j, k of the
+    row.  Its inverse is tridiagonal: (1 / (1 - a^2)) times 1 at the row ends
+    and 1 + a^2 inside on the diagonal, -a next to it; so
+    W = Sigma_y^-1 = D^-1/2 C^-1 D^-1/2 couples neighbouring cells only.  With
+    a > 0, W has negative off-diagonal entries: the separable SPS bound then
+    uses |W| (a matrix P is majorised by diag(|P| 1), whose difference to P is
+    diagonally dominant)."""
+
+    def __init__(self, a: float, n_u: int):
+        assert 0.0 <= a < 1.0
+        self.a = float(a)
+        self.n_u = int(n_u)
+
+    def _cinv(self, v, sign):
+        rows = v.reshape(v.shape[0], -1, self.n_u)
+        a = self.a
+        out = rows.copy()
+        out[..., 1:-1] *= 1.0 + a * a
+        out[..., 1:] += sign * a * rows[..., :-1]
+        out[..., :-1] += sign * a * rows[..., 1:]
+        return (out / (1.0 - a * a)).reshape(v.shape)
+
+    def W(self, v, y):
+        """Sigma_y^-1 v for v[c, rays]."""
+        s = np.sqrt(weights(y))
+        return s * self._cinv(s * v, -1.0)
+
+    def absW(self, v, y):
+        """|Sigma_y^-1| v (elementwise absolute value of the matrix)."""
+        s = np.sqrt(weights(y))
+        return s * self._cinv(s * v, +1.0)
+
+
+def _W(noise, v, y):
+    return weights(y) * v if noise is None else noise.W(v, y)
+
+
+def _absW(noise, v, y):
+    return weights(y) * v if noise is None else noise.absW(v, y)
+
+
 def transmission(Q: np.ndarray, l: np.ndarray) -> np.ndarray:
     """t[E,i] = exp(-sum_m Q[E,m] l[m,i])  (the exp(-A x) of Eq. 1)."""
     return np.exp(-(Q @ l))
@@ -74,34 +119,34 @@ def forward_model(Q: np.ndarray, S: np.ndarray, l: np.ndarray, blur: Blur | None
     return _B(blur, S @ transmission(Q, l))
 
 
-def data_objective(Q, S, l, y, blur: Blur | None = None) -> float:
+def data_objective(Q, S, l, y, blur: Blur | None = None, noise: RowCorrelation | None = None) -> float:
     """L = 1/2 (y - y_bar)^T Sigma^-1 (y - y_bar)  (Eq. 3)."""
     r = forward_model(Q, S, l, blur) - y
-    return 0.5 * float(np.sum(weights(y) * r * r))
+    return 0.5 * float(np.sum(r * _W(noise, r, y)))
 
 
-def data_grad_l(Q, S, l, y, blur: Blur | None = None) -> np.ndarray:
+def data_grad_l(Q, S, l, y, blur: Blur | None = None, noise: RowCorrelation | None = None) -> np.ndarray:
     """dL/dl[m,i] = -sum_E Q[E,m] t[E,i] sum_c S[c,E] [B^T W (y_bar - y)][c,i]."""
     t = transmission(Q, l)
     r = _B(blur, S @ t) - y
-    v = S.T @ _BT(blur, weights(y) * r)
+    v = S.T @ _BT(blur, _W(noise, r, y))
     return -(Q.T @ (t * v))
 
 
-def sps_eta_rho(Q, S, l, y, blur: Blur | None = None):
+def sps_eta_rho(Q, S, l, y, blur: Blur | None = None, noise: RowCorrelation | None = None):
     """eta = (B S)^T Sigma^-1 (B S) 1 and rho = (B S)^T Sigma^-1 (B S) t
     - eta t - (B S)^T Sigma^-1 y, per (energy, ray) (Eqs. 8, 10; the paper's
-    rho printed with x^n where the current transmission t^n belongs)."""
-    w = weights(y)
+    rho printed with x^n where the current transmission t^n belongs).  With
+    correlated noise eta uses |Sigma^-1| (see RowCorrelation)."""
     t = transmission(Q, l)
     r = _B(blur, S @ t) - y
     ones = np.broadcast_to(S.sum(axis=1)[:, None], r.shape)   # S 1 = sigma_c per ray
-    eta = S.T @ _BT(blur, w * _B(blur, np.array(ones)))
-    rho = S.T @ _BT(blur, w * r) - eta * t
+    eta = S.T @ _BT(blur, _absW(noise, _B(blur, np.array(ones)), y))
+    rho = S.T @ _BT(blur, _W(noise, r, y)) - eta * t
     return eta, rho, t
 
 
-def sps_curvature(Q, S, l, y, blur: Blur | None = None) -> np.ndarray:
+def sps_curvature(Q, S, l, y, blur: Blur | None = None, noise: RowCorrelation | None = None) -> np.ndarray:
     """Per (energy, ray) maximum curvature c of the separable surrogate.
 
     The data term is majorised, for each ray and energy, by the 1-D function
@@ -114,33 +159,34 @@ def sps_curvature(Q, S, l, y, blur: Blur | None = None) -> np.ndarray:
     cited maximum-curvature rule is not in the paper; this is its derivation
     for this h.)
     """
-    eta, rho, t = sps_eta_rho(Q, S, l, y, blur)
+    eta, rho, t = sps_eta_rho(Q, S, l, y, blur, noise)
     u_hi = np.maximum(1.0, t)
     return np.maximum(0.0, 2.0 * eta * u_hi * u_hi + rho * u_hi)
 
 
-def curvature_numerator(Q, S, l, y, gamma_m: np.ndarray, blur: Blur | None = None) -> np.ndarray:
+def curvature_numerator(Q, S, l, y, gamma_m: np.ndarray, blur: Blur | None = None,
+                        noise: RowCorrelation | None = None) -> np.ndarray:
     """kappa[m,i] = sum_E Q[E,m] gamma[E,i] c[E,i] with gamma[E,i] =
     sum_m Q[E,m] gamma_m[m,i]; the separable curvature is then
     d = A^T kappa (Eq. 6: d = diag(A^T D{gamma} c) with A -> QA)."""
-    c = sps_curvature(Q, S, l, y, blur)
+    c = sps_curvature(Q, S, l, y, blur, noise)
     gE = Q @ gamma_m
     return Q.T @ (gE * c)
 
 
-def line_terms(Q, S, l, q, y, alpha: float, blur: Blur | None = None):
+def line_terms(Q, S, l, q, y, alpha: float, blur: Blur | None = None, noise: RowCorrelation | None = None):
     """Data part of phi(alpha) = L(l + alpha q) and its first two derivatives
     in alpha, summed over all rays."""
-    w = weights(y)
     la = l + alpha * q
     t = transmission(Q, la)
     r = _B(blur, S @ t) - y
     dz = Q @ q
     dyb = -_B(blur, S @ (t * dz))
     d2yb = _B(blur, S @ (t * dz * dz))
-    f = 0.5 * float(np.sum(w * r * r))
-    f1 = float(np.sum(w * r * dyb))
-    f2 = float(np.sum(w * (dyb * dyb + r * d2yb)))
+    Wr, Wd = _W(noise, r, y), _W(noise, dyb, y)
+    f = 0.5 * float(np.sum(r * Wr))
+    f1 = float(np.sum(dyb * Wr))
+    f2 = float(np.sum(dyb * Wd + d2yb * Wr))
     return f, f1, f2
 
 

@@ -51,9 +51,10 @@ class Setup:
     """Everything one reconstruction needs: projector (A, or identity for
     projection-domain decomposition), spectral model Q, S, data y, penalty."""
 
-    def __init__(self, proj, Q, S, y, beta=None, blur=None):
+    def __init__(self, proj, Q, S, y, beta=None, blur=None, noise=None):
         self.proj = proj
         self.blur = blur              # optional detector blur B (model.Blur)
+        self.noise = noise            # optional correlated noise (model.RowCorrelation)
         self.Q = np.asarray(Q, dtype=np.float64)
         self.S = np.asarray(S, dtype=np.float64)
         self.y = np.asarray(y, dtype=np.float64).reshape(self.S.shape[0], -1)
@@ -70,11 +71,12 @@ class Setup:
     def objective(self, x, l=None):
         if l is None:
             l = self.proj.project(x)
-        return model.data_objective(self.Q, self.S, l, self.y, self.blur) + self.pen.value(x)
+        return model.data_objective(self.Q, self.S, l, self.y, self.blur, self.noise) + self.pen.value(x)
 
     def gradient(self, x):
         l = self.proj.project(x)
-        return self.proj.backproject(model.data_grad_l(self.Q, self.S, l, self.y, self.blur)) + self.pen.apply(x)
+        return (self.proj.backproject(model.data_grad_l(self.Q, self.S, l, self.y, self.blur, self.noise))
+                + self.pen.apply(x))
 
 
 def line_search(st: Setup, x, p, l, q, phi0: float, ls: LineSearch, a0: float = 1.0):
@@ -90,7 +92,7 @@ def line_search(st: Setup, x, p, l, q, phi0: float, ls: LineSearch, a0: float = 
         # points outside the domain z = Q (l + a q) >= z_min are rejected
         if np.min(st.Q @ (l + a * q)) < ls.z_min:
             return np.inf, np.nan, np.nan
-        f, f1, f2 = model.line_terms(st.Q, st.S, l, q, st.y, a, st.blur)
+        f, f1, f2 = model.line_terms(st.Q, st.S, l, q, st.y, a, st.blur, st.noise)
         return f + R0 + a * pRx + 0.5 * a * a * pRp, f1 + pRx + a * pRp, f2 + pRp
 
     a = a0
@@ -121,7 +123,7 @@ def run(st: Setup, precond, n_iter: int, line_search_cfg: LineSearch | None = No
         nonneg: bool = False, reproject_every: int = 10, x0=None, return_alphas: bool = False):
     """Run ``n_iter`` iterations; returns (x, objective history of length
     n_iter + 1)."""
-    Q, S, y, A, B = st.Q, st.S, st.y, st.proj, st.blur
+    Q, S, y, A, B, N = st.Q, st.S, st.y, st.proj, st.blur, st.noise
     x = st.zeros() if x0 is None else np.array(x0, dtype=np.float64)
     l = A.project(x)
     absM1 = precond.absM(np.ones_like(x))
@@ -132,10 +134,10 @@ def run(st: Setup, precond, n_iter: int, line_search_cfg: LineSearch | None = No
     for n in range(n_iter):
         if n > 0 and reproject_every and n % reproject_every == 0:
             l = A.project(x)
-        phi0 = model.data_objective(Q, S, l, y, B) + st.pen.value(x)
+        phi0 = model.data_objective(Q, S, l, y, B, N) + st.pen.value(x)
         hist.append(phi0)
-        g = model.data_grad_l(Q, S, l, y, B)
-        kappa = model.curvature_numerator(Q, S, l, y, gamma_m, B)
+        g = model.data_grad_l(Q, S, l, y, B, N)
+        kappa = model.curvature_numerator(Q, S, l, y, gamma_m, B, N)
         grad = A.backproject(g) + st.pen.apply(x)
         C = A.backproject(kappa)
         gp = precond.MT(grad)
@@ -157,7 +159,7 @@ def run(st: Setup, precond, n_iter: int, line_search_cfg: LineSearch | None = No
             x = x + alpha * p
             l = l + alpha * q
     l = A.project(x)
-    hist.append(model.data_objective(Q, S, l, y, B) + st.pen.value(x))
+    hist.append(model.data_objective(Q, S, l, y, B, N) + st.pen.value(x))
     if return_alphas:
         return x, np.array(hist), np.array(alphas)
     return x, np.array(hist)

@@ -262,3 +262,131 @@ def test_blur_surrogate_majorises():
     for _ in range(50):
         z = z0 + rng.normal(0.0, 0.5, z0.shape)
         assert L(z) - L(z0) <= H(z) - H(z0) + 1e-9 * (abs(L(z0)) + 1)
+
+
+# ---------------------------------------------------------------------------
+# Correlated detector noise (non-diagonal Sigma_y)
+# ---------------------------------------------------------------------------
+
+def _dense_sigma(noise, y_c):
+    """Sigma_y of one channel as a dense matrix, from its definition:
+    D^1/2 C D^1/2, C[j, k] = a^|j-k| within each row of n_u cells."""
+    n = y_c.size
+    C = np.zeros((n, n))
+    for i in range(n):
+        ri, ji = divmod(i, noise.n_u)
+        for k in range(n):
+            rk, jk = divmod(k, noise.n_u)
+            if ri == rk:
+                C[i, k] = noise.a ** abs(ji - jk)
+    d = np.sqrt(np.maximum(y_c, 1.0))
+    return d[:, None] * C * d[None, :]
+
+
+def test_row_correlation_inverse():
+    """The tridiagonal W of RowCorrelation is the inverse of the dense
+    covariance built from the definition, and |W| its elementwise modulus."""
+    from oracle import model
+    rng = np.random.default_rng(21)
+    noise = model.RowCorrelation(0.6, 5)
+    y = rng.uniform(0.5, 400.0, (2, 15))
+    eye = np.eye(15)
+    for c in range(2):
+        Wd = np.linalg.inv(_dense_sigma(noise, y[c]))
+        cols = []
+        for j in range(15):
+            v = np.zeros((2, 15))
+            v[c] = eye[j]
+            cols.append(noise.W(v, y)[c])
+        got = np.stack(cols, 1)
+        assert np.allclose(got, Wd, rtol=1e-11, atol=1e-13 * np.abs(Wd).max())
+        cols = []
+        for j in range(15):
+            v = np.zeros((2, 15))
+            v[c] = eye[j]
+            cols.append(noise.absW(v, y)[c])
+        assert np.allclose(np.stack(cols, 1), np.abs(Wd), rtol=1e-11, atol=1e-13 * np.abs(Wd).max())
+
+
+def test_zero_correlation_is_diagonal():
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=22)
+    none = model.RowCorrelation(0.0, 7)
+    for b in (None, blur):
+        assert np.isclose(model.data_objective(Q, S, l, y, b, none), model.data_objective(Q, S, l, y, b), rtol=1e-14)
+        assert np.allclose(model.data_grad_l(Q, S, l, y, b, none), model.data_grad_l(Q, S, l, y, b), rtol=1e-13)
+        assert np.allclose(model.sps_curvature(Q, S, l, y, b, none), model.sps_curvature(Q, S, l, y, b),
+                           rtol=1e-13)
+
+
+def test_correlated_objective_dense_and_gradient():
+    """L = 1/2 r^T Sigma^-1 r with the dense covariance, and the gradient
+    against central finite differences (blur and correlation together)."""
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=23)
+    noise = model.RowCorrelation(0.45, 7)
+    r = model.forward_model(Q, S, l, blur) - y
+    want = 0.5 * sum(float(r[c] @ np.linalg.solve(_dense_sigma(noise, y[c]), r[c])) for c in range(y.shape[0]))
+    got = model.data_objective(Q, S, l, y, blur, noise)
+    assert abs(got - want) <= 1e-11 * abs(want)
+    _fd_check(lambda z: model.data_objective(Q, S, z, y, blur, noise), model.data_grad_l(Q, S, l, y, blur, noise), l)
+
+
+def test_correlated_line_terms():
+    """phi, phi', phi'' of the correlated data term along a direction equal
+    the objective and its finite-difference derivatives."""
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=24)
+    noise = model.RowCorrelation(0.3, 7)
+    q = np.random.default_rng(25).normal(0.0, 1.0, l.shape)
+    a, h = 0.2, 1e-4
+    f, f1, f2 = model.line_terms(Q, S, l, q, y, a, blur, noise)
+    phi = lambda t: model.data_objective(Q, S, l + t * q, y, blur, noise)  # noqa: E731
+    assert abs(f - phi(a)) <= 1e-12 * abs(f)
+    assert abs(f1 - (phi(a + h) - phi(a - h)) / (2 * h)) <= 1e-6 * abs(f1) + 1e-9 * abs(f)
+    assert abs(f2 - (phi(a + h) - 2 * phi(a) + phi(a - h)) / h ** 2) <= 1e-4 * abs(f2) + 1e-7 * abs(f)
+
+
+def test_correlated_surrogate_majorises():
+    """With negative off-diagonal entries in Sigma^-1 the separable bound of
+    Eqs. 8 and 10 uses eta = |P| 1 (P = (BS)^T Sigma^-1 (BS)); the sum of
+    h(z) over every (energy, ray) still majorises the data term and touches
+    it at the current point."""
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=26)
+    noise = model.RowCorrelation(0.7, 7)
+    eta, rho, t0 = model.sps_eta_rho(Q, S, l, y, blur, noise)
+    z0 = Q @ l
+
+    def L(z):
+        r = blur.apply(S @ np.exp(-z)) - y
+        return 0.5 * float(np.sum(r * noise.W(r, y)))
+
+    def H(z):
+        return float(np.sum(0.5 * eta * np.exp(-2 * z) + rho * np.exp(-z)))
+    rng = np.random.default_rng(27)
+    for _ in range(50):
+        z = z0 + rng.normal(0.0, 0.5, z0.shape)
+        assert L(z) - L(z0) <= H(z) - H(z0) + 1e-9 * (abs(L(z0)) + 1)
+    # negative control: one energy, one channel, no blur, strong correlation
+    # (P = Sigma^-1 itself): eta = P 1 instead of |P| 1 fails to majorise
+    # along a direction that moves neighbouring cells in opposite ways, while
+    # |P| 1 holds there
+    Q1, S1 = np.ones((1, 1)), np.full((1, 1), 1e4)
+    noise1 = model.RowCorrelation(0.9, 8)
+    l1 = np.full((1, 16), 1.0)
+    y1 = np.full((1, 16), 1e4 * np.exp(-1.2))
+    eta1, rho1, t1 = model.sps_eta_rho(Q1, S1, l1, y1, None, noise1)
+    eta_w = S1.T @ noise1.W(np.full((1, 16), S1.sum()), y1)
+    rho_w = rho1 + (eta1 - eta_w) * t1
+    z0 = Q1 @ l1
+    z = z0 + 0.3 * np.where(np.arange(16) % 2 == 0, 1.0, -1.0)[None, :]
+
+    def L1(zz):
+        r = S1 @ np.exp(-zz) - y1
+        return 0.5 * float(np.sum(r * noise1.W(r, y1)))
+
+    def Hs(e, rh, zz):
+        return float(np.sum(0.5 * e * np.exp(-2 * zz) + rh * np.exp(-zz)))
+    assert L1(z) - L1(z0) <= Hs(eta1, rho1, z) - Hs(eta1, rho1, z0) + 1e-9 * abs(L1(z0))
+    assert L1(z) - L1(z0) > Hs(eta_w, rho_w, z) - Hs(eta_w, rho_w, z0) + 1e-6 * abs(L1(z) - L1(z0))
