@@ -72,8 +72,9 @@ class RowCorrelation:
     and 1 + a^2 inside on the diagonal, -a next to it; so
     W = Sigma_y^-1 = D^-1/2 C^-1 D^-1/2 couples neighbouring cells only.  With
     a > 0, W has negative off-diagonal entries: the separable SPS bound then
-    uses |W| (a matrix P is majorised by diag(|P| 1), whose difference to P is
-    diagonally dominant)."""
+    takes eta = S^T B^T |W| B S 1, which bounds |P| 1 elementwise for
+    P = (B S)^T W (B S), and diag(|P| 1) - P is diagonally dominant, hence
+    positive semidefinite."""
 
     def __init__(self, a: float, n_u: int):
         assert 0.0 <= a < 1.0
