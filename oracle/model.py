@@ -77,7 +77,7 @@ class RowCorrelation:
     positive semidefinite."""
 
     def __init__(self, a: float, n_u: int):
-        assert 0.0 <= a < 1.0
+        assert 0.0 <= a < 1.0 and n_u >= 2   # the closed-form inverse needs two cells per row
         self.a = float(a)
         self.n_u = int(n_u)
 
