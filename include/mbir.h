@@ -163,6 +163,21 @@ mbir_status mbmd_spectrum_destroy(mbmd_spectrum *spec);
  * unchanged and return MBIR_ERR_ARG. */
 mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, int row, const double *taps);
 
+/* Correlated detector noise (Sec. II-A: the data covariance is known; Eq. 3
+ * weights the residual by its inverse): Sigma_y = D^1/2 C D^1/2 with
+ * D = diag(max(y, 1)) and, within each detector row of `row` consecutive rays
+ * and in every channel, C[j][k] = a^|j - k|.  Its inverse W couples
+ * neighbouring cells (tridiagonal), so the data term, its gradient, the
+ * line-search terms and the SPS numerators (Eqs. 8 and 10, with the curvature
+ * from |W|: W has negative entries next to the diagonal) couple row
+ * neighbours.  a = 0 restores the diagonal covariance (row ignored);
+ * 0 <= a < 0.99, row >= 2, equal to the blur's row when both are set.  Model
+ * calls, states and batches then need n_rays to be a multiple of row.  The
+ * forward model and the preconditioner builds do not change.  A PSPS state
+ * keeps the setting the spectrum had when it was created.  Bad arguments
+ * leave the spectrum unchanged and return MBIR_ERR_ARG. */
+mbir_status mbmd_spectrum_set_noise(mbmd_spectrum *spec, double a, int row);
+
 /* Mean counts y_bar[c][i] = sum_E S[c][E] exp(-sum_m Q[E][m] l[m][i]) (Eq. 1),
  * followed by the spectrum's detector blur B along detector rows when one is
  * set (mbmd_spectrum_set_blur; n_rays must then be a multiple of its row).

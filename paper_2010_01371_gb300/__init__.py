@@ -119,6 +119,7 @@ class Spectrum:
               S.ctypes.data_as(dp), ctypes.byref(h))
         self.h = h
         self.blur = None
+        self.noise = None
 
     def set_blur(self, taps, row: int):
         """Detector blur B of the outer operator B S (Eq. 1): odd-length taps
@@ -132,6 +133,13 @@ class Spectrum:
         _call(lib().mbmd_spectrum_set_blur, self.h, int(radius), int(row),
               taps.ctypes.data_as(dp) if taps.size else None)
         self.blur = (taps.copy(), int(row)) if radius else None
+
+    def set_noise(self, a: float, row: int = 2):
+        """Correlated detector noise: correlation a^|j-k| between cells j, k
+        of a detector row of `row` rays (``mbmd_spectrum_set_noise``); a = 0
+        restores the diagonal covariance."""
+        _call(lib().mbmd_spectrum_set_noise, self.h, float(a), int(row))
+        self.noise = (float(a), int(row)) if a > 0 else None
 
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:

@@ -44,6 +44,7 @@ SIGNATURES = [
     ("mbmd_spectrum_create", c_int, [c_int, c_int, c_int, P(c_double), P(c_double), P(c_void_p)]),
     ("mbmd_spectrum_destroy", c_int, [c_void_p]),
     ("mbmd_spectrum_set_blur", c_int, [c_void_p, c_int, c_int, P(c_double)]),
+    ("mbmd_spectrum_set_noise", c_int, [c_void_p, c_double, c_int]),
     ("mbmd_forward_model", c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     ("mbmd_objective", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("mbmd_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),

@@ -248,6 +248,10 @@ struct mbmd_spectrum {
     // of blur_row consecutive rays; r = 0: none
     int blur_r = 0, blur_row = 1;
     float blur_b[7] = {};
+    // optional correlated noise: Sigma_y = D^1/2 C D^1/2, C[j][k] = a^|j-k|
+    // within rows of noise_row consecutive rays; a = 0: diagonal
+    float noise_a = 0.f;
+    int noise_row = 1;
     double *hQ = nullptr, *hS = nullptr;  // host FP64 copies
     ~mbmd_spectrum() {
         delete[] hQ;

@@ -285,21 +285,57 @@ __device__ __forceinline__ float blur_at(const BlurDev &B, const float *__restri
     return s;
 }
 
-// (B 1)_j at row position j.
-__device__ __forceinline__ float blur_ones(const BlurDev &B, int j) {
+// (B 1)_j at row position j (rows of `row` rays).
+__device__ __forceinline__ float blur_ones(const BlurDev &B, int row, int j) {
     float s = 0.f;
     for (int k = -B.r; k <= B.r; ++k)
-        if (j + k >= 0 && j + k < B.row) s += B.b[k + B.r];
+        if (j + k >= 0 && j + k < row) s += B.b[k + B.r];
     return s;
 }
 
-// [B^T (w .* B 1)]_i for one channel of counts y (w = 1 / max(y, 1)).
-__device__ __forceinline__ float blur_eta_weight(const BlurDev &B, const float *__restrict__ y, int64_t i) {
-    const int j = (int)(i % B.row);
+// w^1/2 = max(y, 1)^-1/2 of one ray's counts.
+__device__ __forceinline__ float sqrt_weight(float y) { return sqrtf(1.f / fmaxf(y, 1.f)); }
+
+// [W v]_j for one row of cells with W = D^-1/2 C^-1 D^-1/2: v holds the
+// values of consecutive cells (shared memory), tid this cell, j its position
+// in the row, yc the channel's counts (global) and i this cell's ray.  C^-1 is
+// (1 / (1 - a^2)) times 1 (row ends) or 1 + a^2 on the diagonal and -a next
+// to it.
+__device__ __forceinline__ float noise_apply(const NoiseDev &N, int row, const float *__restrict__ v, int tid, int j,
+                                             const float *__restrict__ yc, int64_t i) {
+    const bool lo = j > 0, hi = j + 1 < row;
+    const float a = N.a;
+    const float s0 = sqrt_weight(yc[i]);
+    float acc = ((lo && hi) ? fmaf(a, a, 1.f) : 1.f) * s0 * v[tid];
+    if (lo) acc = fmaf(-a * sqrt_weight(yc[i - 1]), v[tid - 1], acc);
+    if (hi) acc = fmaf(-a * sqrt_weight(yc[i + 1]), v[tid + 1], acc);
+    return s0 * acc / fmaf(-a, a, 1.f);
+}
+
+// eta weight of one channel at ray i (row position j):
+// [B^T (|W| (B 1))]_i, with |W| = diag(w) without correlated noise; y is the
+// channel's counts (global memory), the row's neighbours of i are read from it.
+__device__ __forceinline__ float coupled_eta_weight(const SpecDev &sp, int row, const float *__restrict__ y,
+                                                    int64_t i, int j) {
+    const BlurDev &B = sp.blur;
+    const float a = sp.noise.a;
     float s = 0.f;
     for (int k = -B.r; k <= B.r; ++k) {
         const int jj = j - k;
-        if (jj >= 0 && jj < B.row) s = fmaf(B.b[k + B.r], blur_ones(B, jj) / fmaxf(y[i - k], 1.f), s);
+        if (jj < 0 || jj >= row) continue;
+        const int64_t p = i - k;
+        float v;
+        if (a > 0.f) {
+            const bool lo = jj > 0, hi = jj + 1 < row;
+            const float s0 = sqrt_weight(y[p]);
+            float acc = ((lo && hi) ? fmaf(a, a, 1.f) : 1.f) * s0 * blur_ones(B, row, jj);
+            if (lo) acc = fmaf(a * sqrt_weight(y[p - 1]), blur_ones(B, row, jj - 1), acc);
+            if (hi) acc = fmaf(a * sqrt_weight(y[p + 1]), blur_ones(B, row, jj + 1), acc);
+            v = s0 * acc / fmaf(-a, a, 1.f);
+        } else {
+            v = blur_ones(B, row, jj) / fmaxf(y[p], 1.f);
+        }
+        s = fmaf(B.b[k + B.r], v, s);
     }
     return s;
 }
@@ -327,56 +363,62 @@ __global__ void __launch_bounds__(kModelThreads)
     }
 }
 
-// Data term and numerators with the blur, in one kernel: a block takes
-// segments of T = blockDim - 4r rays with 2r halo rays on each side.
+// Data term and numerators with rays coupled along detector rows (a blur B
+// in the outer operator and / or correlated noise W), in one kernel: a block
+// takes segments of T = blockDim - 2H rays with H = 2 rb + rn halo rays on
+// each side (rb the blur radius, rn = 1 with correlated noise).
 // Phase 1: unblurred counts y0 of every ray of the extended segment (shared
-// memory).  Phase 2: blurred residual r = B y0 - y and weighted residual
-// qw = w r for the rays within r of the segment (the data term for its own
-// rays).  Phase 3 (own rays): u_c = [B^T qw_c]_i replaces w_c r_c and
-// sigma_c [B^T (w_c .* B 1)]_i replaces w_c sigma_c in the numerators, with a
-// second pass over the energies.
+// memory).  Phase 2: blurred residual r = B y0 - y (rays within rb + rn of
+// the segment).  Phase 2b: weighted residual qw = W r (rays within rb; with
+// diagonal noise qw = w r comes with phase 2) and the data term
+// 1/2 r^T W r of the segment's own rays.  Phase 3 (own rays): u_c =
+// [B^T qw_c]_i replaces w_c r_c and sigma_c [B^T (|W| B 1)]_i replaces
+// w_c sigma_c in the numerators, with a second pass over the energies.
 // [B v] and [B^T v] at thread tid's ray from a shared-memory column of
-// consecutive rays (j = the ray's position in its detector row).
-__device__ __forceinline__ float blur_col(const BlurDev &Bd, const float *__restrict__ col, int tid, int j) {
+// consecutive rays (j = the ray's position in its row of `row` rays).
+__device__ __forceinline__ float blur_col(const BlurDev &Bd, int row, const float *__restrict__ col, int tid, int j) {
     float s = 0.f;
     for (int k = -Bd.r; k <= Bd.r; ++k) {
         const int jj = j + k;
-        if (jj >= 0 && jj < Bd.row) s = fmaf(Bd.b[k + Bd.r], col[tid + k], s);
+        if (jj >= 0 && jj < row) s = fmaf(Bd.b[k + Bd.r], col[tid + k], s);
     }
     return s;
 }
 
-__device__ __forceinline__ float blur_colT(const BlurDev &Bd, const float *__restrict__ col, int tid, int j) {
+__device__ __forceinline__ float blur_colT(const BlurDev &Bd, int row, const float *__restrict__ col, int tid, int j) {
     float s = 0.f;
     for (int k = -Bd.r; k <= Bd.r; ++k) {
         const int jj = j - k;
-        if (jj >= 0 && jj < Bd.row) s = fmaf(Bd.b[k + Bd.r], col[tid - k], s);
+        if (jj >= 0 && jj < row) s = fmaf(Bd.b[k + Bd.r], col[tid - k], s);
     }
     return s;
 }
 
 template <int NM, int CM>
 __global__ void __launch_bounds__(kModelThreads)
-    model_grad_blur_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
-                                 const float *__restrict__ gamma, float *__restrict__ g, float *__restrict__ kappa,
-                                 dfloat *__restrict__ partials) {
+    model_grad_rows_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ y,
+                           const float *__restrict__ gamma, float *__restrict__ g, float *__restrict__ kappa,
+                           dfloat *__restrict__ partials) {
     extern __shared__ float sh[];
     load_spec(sp, sh);
     const float *Q = sh;
     const float *S = sh + sp.ne * NM;
     const float *sig = S + sp.nc * sp.ne;
     const int nc = sp.nc, ne = sp.ne;
-    const int B = blockDim.x, tid = threadIdx.x, r = sp.blur.r, T = B - 4 * r;
-    float *y0s = sh + (sp.ne * sp.nm + sp.nc * sp.ne + sp.nc);  // [CM][B]
-    float *qws = y0s + CM * B;                                  // [CM][B]
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int rb = sp.blur.r, rn = sp.noise.a > 0.f ? 1 : 0, H = 2 * rb + rn, T = B - 2 * H;
+    const int row = rb > 0 ? sp.blur.row : sp.noise.row;
+    float *y0s = sh + (sp.ne * sp.nm + sp.nc * sp.ne + sp.nc);  // [CM][B] unblurred counts
+    float *qws = y0s + CM * B;                                  // [CM][B] weighted residuals
+    float *rs = qws + CM * B;                                   // [CM][B] residuals (rn only)
     const bool grads = g || kappa;
     const int64_t nseg = (n_rays + T - 1) / T;
     dfloat obj{0.f, 0.f};
     for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-        const int64_t i = seg * T - 2 * r + tid;
+        const int64_t i = seg * T - H + tid;
         const bool valid = i >= 0 && i < n_rays;
-        const bool own = valid && tid >= 2 * r && tid < 2 * r + T;
-        const int j = valid ? (int)(i % sp.blur.row) : 0;
+        const bool own = valid && tid >= H && tid < H + T;
+        const int j = valid ? (int)(i % row) : 0;
         float lm[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) lm[m] = valid ? l[(int64_t)m * n_rays + i] : 0.f;
@@ -399,20 +441,38 @@ __global__ void __launch_bounds__(kModelThreads)
                 if (c < nc) y0s[c * B + tid] = yb[c];
         }
         __syncthreads();
-        if (valid && tid >= r && tid < B - r) {
+        if (valid && tid >= rb && tid < B - rb) {
             float f = 0.f;
 #pragma unroll
             for (int c = 0; c < CM; ++c)
                 if (c < nc) {
                     const float yc = y[(int64_t)c * n_rays + i];
                     const float w = 1.f / fmaxf(yc, 1.f);
-                    const float rr = blur_col(sp.blur, y0s + c * B, tid, j) - yc;
-                    qws[c * B + tid] = w * rr;
-                    f = fmaf(0.5f * w * rr, rr, f);
+                    const float rr = blur_col(sp.blur, row, y0s + c * B, tid, j) - yc;
+                    if (rn) {
+                        rs[c * B + tid] = rr;
+                    } else {
+                        qws[c * B + tid] = w * rr;
+                        f = fmaf(0.5f * w * rr, rr, f);
+                    }
                 }
-            if (own) df_add(obj, f);
+            if (!rn && own) df_add(obj, f);
         }
         __syncthreads();
+        if (rn) {
+            if (valid && tid >= rb + 1 && tid < B - rb - 1) {
+                float f = 0.f;
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if (c < nc) {
+                        const float qv = noise_apply(sp.noise, row, rs + c * B, tid, j, y + (int64_t)c * n_rays, i);
+                        qws[c * B + tid] = qv;
+                        f = fmaf(0.5f * rs[c * B + tid], qv, f);
+                    }
+                if (own) df_add(obj, f);
+            }
+            __syncthreads();
+        }
         if (grads && own) {
             float gm[NM], km[NM], gam[NM];
 #pragma unroll
@@ -425,8 +485,8 @@ __global__ void __launch_bounds__(kModelThreads)
             for (int c = 0; c < CM; ++c) {
                 u[c] = ws[c] = 0.f;
                 if (c < nc) {
-                    u[c] = blur_colT(sp.blur, qws + c * B, tid, j);
-                    ws[c] = kappa ? sig[c] * blur_eta_weight(sp.blur, y + (int64_t)c * n_rays, i) : 0.f;
+                    u[c] = blur_colT(sp.blur, row, qws + c * B, tid, j);
+                    ws[c] = kappa ? sig[c] * coupled_eta_weight(sp, row, y + (int64_t)c * n_rays, i, j) : 0.f;
                 }
             }
             for (int e = 0; e < ne; ++e) {
@@ -471,27 +531,31 @@ __global__ void __launch_bounds__(kModelThreads)
     }
 }
 
-// Line search with the blur, fused into one kernel per evaluation: a block
-// takes segments of T = blockDim - 2r consecutive rays plus r halo rays on
-// each side.  Every thread evaluates the unblurred counts of one ray of the
-// extended segment (and, for the Newton evaluation, their first two
-// alpha-derivatives) into shared memory; the segment's own rays then blur
-// them along their detector row and add their data terms, and the rays that
-// leave the domain z >= z_min are counted (own rays only).  Halo rays are
-// evaluated by both neighbouring segments (2r / T extra work).  Partials and
-// the last block's control are those of ls_fused_kernel.
+// Line search with rays coupled along detector rows (blur and / or
+// correlated noise), one kernel per evaluation: a block takes segments of
+// T = blockDim - 2H consecutive rays plus H = rb + rn halo rays on each side.
+// Every thread evaluates the unblurred counts of one ray of the extended
+// segment (and, for the Newton evaluation, their first two alpha-derivatives)
+// into shared memory; the rays within rn of the segment blur them along their
+// row; the segment's own rays then add the data terms (with correlated noise
+// through W applied to the blurred residuals and derivatives of their row
+// neighbours) and count the rays that leave the domain z >= z_min.  Partials
+// and the last block's control are those of ls_fused_kernel.
 template <int NM, int CM, int MODE>
 __global__ void __launch_bounds__(kModelThreads)
-    ls_blur_fused_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
-                         const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
+    ls_rows_kernel(SpecDev sp, int64_t n_rays, const float *__restrict__ l, const float *__restrict__ q,
+                   const float *__restrict__ y, DevLS *ls, LsCfg cfg, int last, dfloat *__restrict__ partials) {
     if (MODE == 1 && ls->done) return;  // same value for every block
     extern __shared__ float sh[];
     load_spec(sp, sh);
     const float *Q = sh;
     const float *S = sh + sp.ne * NM;
     const int nc = sp.nc, ne = sp.ne;
-    float *buf = sh + (sp.ne * sp.nm + sp.nc * sp.ne + sp.nc);  // [MODE 0: 3 | MODE 1: 1][CM][blockDim]
-    const int B = blockDim.x, tid = threadIdx.x, r = sp.blur.r, T = B - 2 * r;
+    constexpr int NV = MODE == 0 ? 3 : 1;                       // values per channel and ray
+    float *buf = sh + (sp.ne * sp.nm + sp.nc * sp.ne + sp.nc);  // [NV][CM][blockDim]
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int rb = sp.blur.r, rn = sp.noise.a > 0.f ? 1 : 0, H = rb + rn, T = B - 2 * H;
+    const int row = rb > 0 ? sp.blur.row : sp.noise.row;
     const int64_t nseg = (n_rays + T - 1) / T;
     const int nh = cfg.n_halve < kMaxHalve ? cfg.n_halve : kMaxHalve;
     constexpr int NACC = MODE == 0 ? 4 : 2 * kMaxHalve;
@@ -509,31 +573,35 @@ __global__ void __launch_bounds__(kModelThreads)
     }
     const float alpha = MODE == 0 ? (float)ls->alpha : 0.f;
     for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-        const int64_t i = seg * T - r + tid;
+        const int64_t i = seg * T - H + tid;
         const bool valid = i >= 0 && i < n_rays;
-        const bool own = valid && tid >= r && tid < r + T;
-        const int j = valid ? (int)(i % sp.blur.row) : 0;
+        const bool own = valid && tid >= H && tid < H + T;
+        const bool near = valid && tid >= rb && tid < B - rb;  // blurred values needed here
+        const int j = valid ? (int)(i % row) : 0;
         float lm[NM], qm[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             qm[m] = valid ? q[(int64_t)m * n_rays + i] : 0.f;
             lm[m] = valid ? l[(int64_t)m * n_rays + i] : 0.f;
         }
-        if constexpr (MODE == 0) {
-            float yb[CM], d1[CM], d2[CM];
 #pragma unroll
-            for (int c = 0; c < CM; ++c) yb[c] = d1[c] = d2[c] = 0.f;
+        for (int k = 0; k < (MODE == 0 ? 1 : kMaxHalve); ++k) {
+            if (MODE == 1 && k >= nh) break;  // same for every thread
+            float v0[CM], v1[CM], v2[CM];
+#pragma unroll
+            for (int c = 0; c < CM; ++c) v0[c] = v1[c] = v2[c] = 0.f;
             float zlo = 3.0e38f;
             if (valid) {
+                const float ak = MODE == 0 ? alpha : alphas[k];
                 float la[NM];
 #pragma unroll
-                for (int m = 0; m < NM; ++m) la[m] = fmaf(alpha, qm[m], lm[m]);
+                for (int m = 0; m < NM; ++m) la[m] = fmaf(ak, qm[m], lm[m]);
                 for (int e = 0; e < ne; ++e) {
                     float z = 0.f, dz = 0.f;
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
                         z = fmaf(Q[e * NM + m], la[m], z);
-                        dz = fmaf(Q[e * NM + m], qm[m], dz);
+                        if (MODE == 0) dz = fmaf(Q[e * NM + m], qm[m], dz);
                     }
                     zlo = fminf(zlo, z);
                     const float t = transmission(z);
@@ -542,78 +610,83 @@ __global__ void __launch_bounds__(kModelThreads)
                     for (int c = 0; c < CM; ++c)
                         if (c < nc) {
                             const float sv = S[c * ne + e];
-                            yb[c] = fmaf(sv, t, yb[c]);
-                            d1[c] = fmaf(-sv, tdz, d1[c]);
-                            d2[c] = fmaf(sv, tdz * dz, d2[c]);
+                            v0[c] = fmaf(sv, t, v0[c]);
+                            if (MODE == 0) {
+                                v1[c] = fmaf(-sv, tdz, v1[c]);
+                                v2[c] = fmaf(sv, tdz * dz, v2[c]);
+                            }
                         }
                 }
             }
 #pragma unroll
             for (int c = 0; c < CM; ++c)
                 if (c < nc) {
-                    buf[c * B + tid] = yb[c];
-                    buf[(CM + c) * B + tid] = d1[c];
-                    buf[(2 * CM + c) * B + tid] = d2[c];
+                    buf[c * B + tid] = v0[c];
+                    if (MODE == 0) {
+                        buf[(CM + c) * B + tid] = v1[c];
+                        buf[(2 * CM + c) * B + tid] = v2[c];
+                    }
                 }
-            if (own && !(zlo >= cfg.z_min)) df_add(acc[3], 1.f);
+            if (own && !(zlo >= cfg.z_min)) df_add(acc[MODE == 0 ? 3 : kMaxHalve + k], 1.f);
             __syncthreads();
+            // blurred residual and derivatives at the rays within rn of the
+            // segment (registers first: the neighbours still read buf)
+            float r0[CM], r1[CM], r2[CM], sw[CM];
+#pragma unroll
+            for (int c = 0; c < CM; ++c) {
+                r0[c] = r1[c] = r2[c] = 0.f;
+                sw[c] = 0.f;
+                if (c < nc && near) {
+                    const float yc = y[(int64_t)c * n_rays + i];
+                    sw[c] = 1.f / fmaxf(yc, 1.f);
+                    r0[c] = blur_col(sp.blur, row, buf + c * B, tid, j) - yc;
+                    if (MODE == 0) {
+                        r1[c] = blur_col(sp.blur, row, buf + (CM + c) * B, tid, j);
+                        r2[c] = blur_col(sp.blur, row, buf + (2 * CM + c) * B, tid, j);
+                    }
+                }
+            }
+            if (rn) {
+                __syncthreads();
+                if (near)
+#pragma unroll
+                    for (int c = 0; c < CM; ++c)
+                        if (c < nc) {
+                            buf[c * B + tid] = r0[c];
+                            if (MODE == 0) buf[(CM + c) * B + tid] = r1[c];
+                        }
+                __syncthreads();
+            }
             if (own) {
                 float f = 0.f, f1 = 0.f, f2 = 0.f;
 #pragma unroll
                 for (int c = 0; c < CM; ++c)
                     if (c < nc) {
-                        const float ybc = blur_col(sp.blur, buf + c * B, tid, j);
-                        const float d1c = blur_col(sp.blur, buf + (CM + c) * B, tid, j);
-                        const float d2c = blur_col(sp.blur, buf + (2 * CM + c) * B, tid, j);
-                        const float yc = y[(int64_t)c * n_rays + i];
-                        const float w = 1.f / fmaxf(yc, 1.f);
-                        const float rr = ybc - yc;
-                        f = fmaf(0.5f * w * rr, rr, f);
-                        f1 = fmaf(w * rr, d1c, f1);
-                        f2 = fmaf(w, fmaf(d1c, d1c, rr * d2c), f2);
-                    }
-                df_add(acc[0], f);
-                df_add(acc[1], f1);
-                df_add(acc[2], f2);
-            }
-            __syncthreads();
-        } else {
-#pragma unroll
-            for (int k = 0; k < kMaxHalve; ++k) {
-                if (k >= nh) break;  // same for every thread
-                float yb[CM];
-#pragma unroll
-                for (int c = 0; c < CM; ++c) yb[c] = 0.f;
-                float zlo = 3.0e38f;
-                if (valid)
-                    for (int e = 0; e < ne; ++e) {
-                        float z = 0.f;
-#pragma unroll
-                        for (int m = 0; m < NM; ++m) z = fmaf(Q[e * NM + m], fmaf(alphas[k], qm[m], lm[m]), z);
-                        zlo = fminf(zlo, z);
-                        const float t = transmission(z);
-#pragma unroll
-                        for (int c = 0; c < CM; ++c)
-                            if (c < nc) yb[c] = fmaf(S[c * ne + e], t, yb[c]);
-                    }
-#pragma unroll
-                for (int c = 0; c < CM; ++c)
-                    if (c < nc) buf[c * B + tid] = yb[c];
-                if (own && !(zlo >= cfg.z_min)) df_add(acc[kMaxHalve + k], 1.f);
-                __syncthreads();
-                if (own) {
-                    float f = 0.f;
-#pragma unroll
-                    for (int c = 0; c < CM; ++c)
-                        if (c < nc) {
-                            const float yc = y[(int64_t)c * n_rays + i];
-                            const float rr = blur_col(sp.blur, buf + c * B, tid, j) - yc;
-                            f = fmaf(0.5f * rr / fmaxf(yc, 1.f), rr, f);
+                        // W r and W r' at this ray (diagonal: w r, w r')
+                        float wr, wd;
+                        if (rn) {
+                            const float *yc = y + (int64_t)c * n_rays;
+                            wr = noise_apply(sp.noise, row, buf + c * B, tid, j, yc, i);
+                            wd = MODE == 0 ? noise_apply(sp.noise, row, buf + (CM + c) * B, tid, j, yc, i) : 0.f;
+                        } else {
+                            wr = sw[c] * r0[c];
+                            wd = sw[c] * r1[c];
                         }
+                        f = fmaf(0.5f * r0[c], wr, f);
+                        if (MODE == 0) {
+                            f1 = fmaf(r1[c], wr, f1);
+                            f2 = fmaf(r1[c], wd, fmaf(r2[c], wr, f2));
+                        }
+                    }
+                if (MODE == 0) {
+                    df_add(acc[0], f);
+                    df_add(acc[1], f1);
+                    df_add(acc[2], f2);
+                } else {
                     df_add(acc[k], f);
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
     }
     block_sum_store<NACC>(acc, partials);
@@ -774,15 +847,15 @@ struct BlurModelLaunch {
     cudaStream_t s;
     template <int NM, int CM>
     void run() {
-        const size_t sm = smem + sizeof(float) * 2 * CM * kModelThreads;
-        model_grad_blur_fused_kernel<NM, CM><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, y, gamma, g, kappa, partials);
+        const size_t sm = smem + sizeof(float) * (sp.noise.a > 0.f ? 3 : 2) * CM * kModelThreads;
+        model_grad_rows_kernel<NM, CM><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, y, gamma, g, kappa, partials);
     }
 };
 
 mbir_status launch_model_grad(SpecDev sp, int64_t n_rays, const float *l, const float *y, const float *gamma,
                               float *g, float *kappa, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
-    if (sp.blur.r > 0) {
+    if (row_coupled(sp)) {
         BlurModelLaunch L{sp, n_rays, l, y, gamma, g, kappa, partials, nblocks, smem, s};
         return dispatch_nm_cm(sp, L);
     }
@@ -831,16 +904,16 @@ struct BlurLsLaunch {
     void run() {
         const size_t sm = smem + sizeof(float) * (mode == 0 ? 3 : 1) * CM * kModelThreads;
         if (mode == 0)
-            ls_blur_fused_kernel<NM, CM, 0><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, q, y, ls, cfg, last, partials);
+            ls_rows_kernel<NM, CM, 0><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, q, y, ls, cfg, last, partials);
         else
-            ls_blur_fused_kernel<NM, CM, 1><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, q, y, ls, cfg, last, partials);
+            ls_rows_kernel<NM, CM, 1><<<nblocks, kModelThreads, sm, s>>>(sp, n, l, q, y, ls, cfg, last, partials);
     }
 };
 
 mbir_status launch_ls_fused(SpecDev sp, int64_t n_rays, const float *l, const float *q, const float *y, DevLS *ls,
                             LsCfg cfg, int mode, int last, dfloat *partials, int nblocks, cudaStream_t s) {
     const size_t smem = spec_smem(sp);
-    if (sp.blur.r > 0) {
+    if (row_coupled(sp)) {
         BlurLsLaunch L{sp, n_rays, l, q, y, ls, cfg, partials, mode, last, nblocks, smem, s};
         return dispatch_nm_cm(sp, L);
     }
@@ -974,9 +1047,23 @@ extern "C" mbir_status mbmd_spectrum_set_blur(mbmd_spectrum *spec, int radius, i
             return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_blur: taps must be finite and >= 0");
         b[k] = (float)taps[k];
     }
+    if (radius > 0 && spec->noise_a > 0.f && row != spec->noise_row)
+        return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_blur: row differs from the correlated noise's row");
     spec->blur_r = radius;
     spec->blur_row = radius > 0 ? row : 1;
     for (int k = 0; k < 7; ++k) spec->blur_b[k] = b[k];
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbmd_spectrum_set_noise(mbmd_spectrum *spec, double a, int row) {
+    if (!spec) return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_noise: spec is null");
+    if (!std::isfinite(a) || a < 0.0 || a >= 0.99)
+        return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_noise: correlation %g outside [0, 0.99)", a);
+    if (a > 0.0 && row < 2) return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_noise: row must be >= 2");
+    if (a > 0.0 && spec->blur_r > 0 && row != spec->blur_row)
+        return fail(MBIR_ERR_ARG, "mbmd_spectrum_set_noise: row differs from the blur's row");
+    spec->noise_a = (float)a;
+    spec->noise_row = a > 0.0 ? row : 1;
     return MBIR_OK;
 }
 
@@ -996,7 +1083,8 @@ mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x
         return fail(MBIR_ERR_ARG, "mbmd: n_rays %lld does not match the plan (%lld)", (long long)n_rays,
                     (long long)plan->n_rays);
     if (plan && spec->n_mat > plan->n_mat_max) return fail(MBIR_ERR_ARG, "mbmd: n_mat exceeds the plan's n_mat_max");
-    if (n_rays % spec->blur_row) return fail(MBIR_ERR_ARG, "mbmd: n_rays is not a multiple of the blur row");
+    if (n_rays % spec->blur_row || n_rays % spec->noise_row)
+        return fail(MBIR_ERR_ARG, "mbmd: n_rays is not a multiple of the blur / noise row");
     ModelScratch sc;
     const int nm = spec->n_mat;
     const float *l = x_or_l;

@@ -318,8 +318,8 @@ extern "C" mbir_status psps_state_create(mbir_plan *plan, const mbmd_spectrum *s
     *out = nullptr;
     if (plan && n_rays != plan->n_rays) return fail(MBIR_ERR_ARG, "psps_state_create: n_rays does not match plan");
     if (n_rays < 1) return fail(MBIR_ERR_ARG, "psps_state_create: n_rays must be >= 1");
-    if (n_rays % spec->blur_row)
-        return fail(MBIR_ERR_ARG, "psps_state_create: n_rays is not a multiple of the spectrum's blur row");
+    if (n_rays % spec->blur_row || n_rays % spec->noise_row)
+        return fail(MBIR_ERR_ARG, "psps_state_create: n_rays is not a multiple of the spectrum's blur / noise row");
     if (plan && 2 * spec->n_mat > plan->n_mat_max)
         return fail(MBIR_ERR_ARG, "psps_state_create: plan n_mat_max must be >= 2 n_mat");
     if ((flags & PSPS_FLAG_NONNEG) && pc && pc->kind != PSPS_PRECOND_NONE)
