@@ -77,6 +77,10 @@ WORKLOADS = {
                                        "config 4 slice read out through a 7-tap asymmetric detector blur along the "
                                        "888-bin rows (outer operator B S), 3x3 blocks + cross-material Fourier",
                                        {"blur": "r3"}),
+    "c4_mbmd_512_blockfourier_corr": ("config4_slice", "block_fourier",
+                                      "config 4 slice with correlated detector noise (correlation 0.4^|j-k| along "
+                                      "the 888-bin rows) and a 3-tap detector blur, 3x3 blocks + cross-material "
+                                      "Fourier", {"blur": "r1", "noise": 0.4}),
 }
 
 
@@ -230,7 +234,7 @@ def gap_runs(p, plan, spec, yd, beta, pc, n_star: int, n_cmp: int):
     return phi_star, out
 
 
-def ours(args, prob, workload=WORKLOAD, kind="haar", desc="", blur=None):
+def ours(args, prob, workload=WORKLOAD, kind="haar", desc="", blur=None, noise=None):
     import torch
 
     import paper_2010_01371_gb300 as p
@@ -249,6 +253,8 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc="", blur=None):
     spec = p.Spectrum(prob.Q, prob.S)
     if blur is not None:
         spec.set_blur(blur, prob.geom.n_u)
+    if noise is not None:
+        spec.set_noise(noise, prob.geom.n_u)
     beta = prob.beta if plan is not None else None
     pc = p.Precond(plan, spec, kind, yd, beta)
     tuned = plan.autotune(2 * prob.Q.shape[1]) if plan is not None else None
@@ -562,6 +568,7 @@ def main():
     builder, kind, desc, *kw = WORKLOADS[args.workload]
     kw = dict(kw[0]) if kw else {}
     blur = kw.pop("blur", None)
+    noise = kw.pop("noise", None)
     prob = getattr(synth, builder)(**kw)
     if blur is not None:
         blur = synth.BLUR_TAPS[blur]
@@ -571,7 +578,7 @@ def main():
     if isinstance(prob, list):
         ours_batch(args, prob, args.workload, kind, desc)
         return
-    ours(args, prob, args.workload, kind, desc, blur)
+    ours(args, prob, args.workload, kind, desc, blur, noise)
 
 
 if __name__ == "__main__":

@@ -204,7 +204,8 @@ mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec, const floa
  * M = I): curv = A^T kappa with, per ray and material,
  *   kappa[m][i] = sum_E Q[E][m] gamma[E][i] c[E][i],  gamma = Q (A 1),
  * c the maximum curvature of the per-ray, per-energy surrogate built from
- * eta and rho (with the spectrum's detector blur, if set).  plan == NULL:
+ * eta and rho (with the spectrum's detector blur and correlated noise, if
+ * set).  plan == NULL:
  * projection domain (A = I, gamma = Q 1) and curv = kappa per ray.  The PSPS
  * iteration forms the same numerators with gamma = Q A|M|1.  curv: device,
  * [n_mat][image] (plan) or [n_mat][n_rays], overwritten.  Errors as

@@ -15,8 +15,9 @@
 //   curvature num.   kappa_m = sum_E Q[E][m] gamma_E c_E,  gamma_E = sum_m Q[E][m] gamma_m
 // Exponentials and per-ray sums run in FP32 (exp(-z) as exp2f(-z log2 e));
 // the objective and line-search sums over rays are double-float reductions.
-// With a detector blur B (outer operator B S) the kernels work on row
-// segments with halo rays so that B and B^T act on shared-memory copies.
+// With a detector blur B (outer operator B S) or correlated noise (a
+// tridiagonal W = Sigma_y^-1 along detector rows) the kernels work on row
+// segments with halo rays so that B, B^T and W act on shared-memory copies.
 #include <cmath>
 #include <type_traits>
 #include <vector>

@@ -18,6 +18,8 @@ def test_workload_table():
         assert desc, name
         if kw:
             opts = dict(kw[0])
+            noise = opts.pop("noise", None)
+            assert noise is None or 0.0 < noise < 0.99
             blur = opts.pop("blur", None)
             if blur is not None:
                 taps = synth.BLUR_TAPS[blur]
