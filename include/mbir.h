@@ -106,10 +106,13 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
  * memory (default; lanes of a warp on consecutive driving indices of one ray),
  * 1 = pixel-driven gather (deterministic: no atomics, bitwise reproducible),
  * 2 = ray-driven scatter with global FP32 atomics.  Mode 0 accumulates in
- * fixed point (each term rounded to a grid of M / 2^22 or finer, M the
- * largest |weight x value| of the call; exact integer sums) and is bitwise
- * reproducible; a non-finite input makes its channel's image NaN.  It needs
- * 8 bytes x n_mat_max x n_pix of plan scratch.  3-D (cone): 0 and 1 =
+ * fixed point: each term is rounded to a grid of M max(2^-22, T 2^-30), M
+ * a bound on |weight x value| over the call and T a bound on the terms one
+ * pixel receives from one CTA's views (views per CTA x the rays of one view
+ * that reach one pixel: a few for detector bins no finer than the pixels,
+ * more for finer bins); the sums are exact integer sums, so the result is
+ * bitwise reproducible.  A non-finite input makes its channel's image NaN.
+ * It needs 8 bytes x n_mat_max x n_pix of plan scratch.  3-D (cone): 0 and 1 =
  * voxel-driven gather (default, deterministic), 2 = ray-driven scatter with
  * global FP32 atomics.  All use the forward projector's per-ray weights and
  * are the exact transpose of mbir_project up to FP32 rounding.  MBIR_ERR_ARG
