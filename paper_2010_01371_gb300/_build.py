@@ -31,6 +31,26 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+# model_inst.cu instantiates the model kernels of one material count and one
+# family per compilation (96 kernel variants in all), so it is compiled once
+# per (count, family) pair and the pairs build in parallel.
+MODEL_INST = "model_inst.cu"
+
+
+def units():
+    """(source, object name, extra flags) of every compilation."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        if os.path.basename(src) == MODEL_INST:
+            for nm in (1, 2, 3, 4):
+                for rows in (0, 1):
+                    out.append((src, f"{base}_{nm}_{rows}.o", [f"-DPSPS_MODEL_NM={nm}", f"-DPSPS_MODEL_ROWS={rows}"]))
+        else:
+            out.append((src, base + ".o", []))
+    return out
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
@@ -47,16 +67,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     objs = []
 
-    def one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    def one(unit):
+        src, name, extra = unit
+        obj = os.path.join(OUT_DIR, name)
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(one, sources()))
+    # slowest compilations first, so the pool's last worker is not left with one
+    todo = sorted(units(), key=lambda u: (os.path.basename(u[0]) != MODEL_INST, u[1]))
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        objs = list(ex.map(one, todo))
     tmp = LIB + f".{os.getpid()}.tmp"
     subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
