@@ -51,7 +51,10 @@ def m0_blocks(st: Setup, F: np.ndarray) -> np.ndarray:
     return precond.inv_sqrt_blocks(H, floor="block", zero_rule=True)
 
 
-def build(st: Setup, kind: str):
+def build(st: Setup, kind: str, sides: int = 1):
+    """The preconditioner of one kind; sides: where M0 enters the Fourier and
+    wavelet kinds (1: M = M0 C, the default reading; 2: the literal
+    M0 C M0 of Eqs. 33, 34, 57, 61)."""
     if kind == "none":
         return precond.Identity()
     F = fisher(st)
@@ -68,13 +71,13 @@ def build(st: Setup, kind: str):
         def apply_N(v):
             return m0[None] * apply_H(m0[None] * v)
         if kind == "mod_fourier":
-            return precond.Fourier(precond.fourier_eigenvalues(apply_N, st.shape), m0)
+            return precond.Fourier(precond.fourier_eigenvalues(apply_N, st.shape), m0, sides)
         if kind == "haar":
-            return precond.Haar(precond.haar_eigenvalues(apply_N, st.shape), m0)
+            return precond.Haar(precond.haar_eigenvalues(apply_N, st.shape), m0, sides)
     if kind == "block_fourier":
         L = precond.cross_fourier_blocks(apply_H, M0, st.shape, st.nm)
-        return precond.CrossFourier(L, M0)
+        return precond.CrossFourier(L, M0, sides)
     if kind == "block_haar":
         K = precond.cross_haar_blocks(apply_H, M0, st.shape, st.nm)
-        return precond.CrossHaar(K, M0)
+        return precond.CrossHaar(K, M0, sides)
     raise ValueError(kind)

@@ -28,6 +28,13 @@ Readings of the paper used here:
 * Fourier: periodic unitary 2-D DFT per material on the image grid (no
   padding); the test impulse sits at the centre pixel (ny//2, nx//2).
 * Eigenvalues are clamped to >= 1e-6 x the largest before the -1/2 power.
+* Where M0 goes (Eqs. 33, 34, 57, 61).  The paper writes M = M0^T U^H
+  Lambda~^-1/2 U M0 with Lambda~ the spectrum of N = M0^T H M0.  Then
+  M^T H M = M0^T C N C M0 = M0^T M0 when N is diagonal in U (C = U^H
+  Lambda~^-1/2 U), not the I that Sec. II-C sets as the goal, and M M^T is
+  not an approximate inverse of H.  The one-sided M = M0 C gives
+  M^T H M = C N C = I in that case and M M^T = M0 N^-1 M0^T = H^-1; it is the
+  default (``sides=1``); ``sides=2`` keeps the literal two-sided form.
 * M0 = D{(F+R)1}^-1/2 (Eq. 30) or, with several materials, the per-pixel /
   per-ray N_k x N_k blocks of (F+R)1_k (Eqs. 42, 53-54) raised to -1/2; a
   block's eigenvalues are clamped to >= 1e-6 x its largest one, and pixels
@@ -124,41 +131,48 @@ def clamp_eigs(lam: np.ndarray) -> np.ndarray:
 
 
 class Fourier:
-    """M = m0 U^H diag(lam^-1/2) U m0 (Eq. 29 with m0 = 1, Eq. 33 with the
-    zero-frequency normalisation m0 = M0 of Eq. 30).  One material.
-    |M| = m0 |C| m0 with |C| the circulant of the absolute kernel
-    |IDFT(lam^-1/2)|."""
+    """M = m0 C with C = U^H diag(lam^-1/2) U (Eq. 29 with m0 = 1, Eq. 33 with
+    the zero-frequency normalisation m0 = M0 of Eq. 30); sides=2: the literal
+    m0 C m0.  One material.  |M| = m0 |C| (m0 |C| m0) with |C| the circulant
+    of the absolute kernel |IDFT(lam^-1/2)|."""
 
-    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None):
+    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None, sides: int = 1):
         self.s = 1.0 / np.sqrt(clamp_eigs(lam))
         self.shape = lam.shape
         self.m0 = np.ones(self.shape) if m0 is None else np.asarray(m0, dtype=np.float64).reshape(self.shape)
+        self.sides = sides
         kern = np.fft.ifftn(self.s).real
         self.s_abs = np.fft.fftn(np.abs(kern)).real
 
-    def _filt(self, spec, v):
+    def _filt(self, spec, v, transpose):
+        pre = self.m0 if (self.sides == 2 or transpose) else 1.0
+        post = self.m0 if (self.sides == 2 or not transpose) else 1.0
         out = np.empty_like(v, dtype=np.float64)
         for k in range(v.shape[0]):
-            out[k] = self.m0 * np.fft.ifftn(spec * np.fft.fftn(self.m0 * v[k])).real
+            out[k] = post * np.fft.ifftn(spec * np.fft.fftn(pre * v[k])).real
         return out
 
     def M(self, v):
-        return self._filt(self.s, v)
+        return self._filt(self.s, v, False)
 
-    MT = M
+    def MT(self, v):
+        return self._filt(self.s, v, True)
 
     def absM(self, v):
-        return self._filt(self.s_abs, v)
+        return self._filt(self.s_abs, v, False)
 
-    absMT = absM
+    def absMT(self, v):
+        return self._filt(self.s_abs, v, True)
 
 
 class CrossFourier:
-    """Cross-material Fourier preconditioner (Eq. 57):
-    M = M0^T U^H L^-1/2 U M0 with L block diagonal over spatial frequencies
-    (one N_k x N_k block per frequency), M0 the per-pixel blocks."""
+    """Cross-material Fourier preconditioner (Eq. 57): M = M0 C with
+    C = U^H L^-1/2 U, L block diagonal over spatial frequencies (one N_k x N_k
+    block per frequency), M0 the per-pixel blocks; sides=2: the literal
+    M0^T C M0."""
 
-    def __init__(self, L: np.ndarray, M0: Block):
+    def __init__(self, L: np.ndarray, M0: Block, sides: int = 1):
+        self.sides = sides
         # L[f..., k', k] real symmetric blocks
         self.shape = L.shape[:-2]
         nm = L.shape[-1]
@@ -177,16 +191,20 @@ class CrossFourier:
         return np.fft.ifftn(out, axes=ax).real
 
     def M(self, v):
-        return self.M0.MT(self._mid(self.Li, self.M0.M(v)))
+        inner = self.M0.M(v) if self.sides == 2 else v
+        return self.M0.MT(self._mid(self.Li, inner))
 
     def MT(self, v):
-        return self.M0.MT(self._mid(np.swapaxes(self.Li, -1, -2), self.M0.M(v)))
+        out = self._mid(np.swapaxes(self.Li, -1, -2), self.M0.M(v))
+        return self.M0.MT(out) if self.sides == 2 else out
 
     def absM(self, v):
-        return self.M0.absMT(self._mid(self.Li_abs, self.M0.absM(v)))
+        inner = self.M0.absM(v) if self.sides == 2 else v
+        return self.M0.absMT(self._mid(self.Li_abs, inner))
 
     def absMT(self, v):
-        return self.M0.absMT(self._mid(np.swapaxes(self.Li_abs, -1, -2), self.M0.absM(v)))
+        out = self._mid(np.swapaxes(self.Li_abs, -1, -2), self.M0.absM(v))
+        return self.M0.absMT(out) if self.sides == 2 else out
 
 
 def cross_fourier_blocks(apply_H, M0: Block, shape, nm: int) -> np.ndarray:
@@ -223,35 +241,42 @@ def polar_real(L: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 class Haar:
-    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT M0 (Eq. 34); |M| uses |U| and |M0|.
-    One material, 2-D images or 3-D volumes."""
+    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT (Eq. 34 with M0 on one side; sides=2:
+    the literal M0 U^T Lambda~^-1/2 U M0); |M| uses |U| and |M0|.  One
+    material, 2-D images or 3-D volumes."""
 
-    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None):
+    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None, sides: int = 1):
         self.s = 1.0 / np.sqrt(clamp_eigs(lam))
         self.shape = lam.shape
         self.m0 = np.ones(self.shape) if m0 is None else np.asarray(m0, dtype=np.float64).reshape(self.shape)
+        self.sides = sides
 
-    def _op(self, v, absolute):
+    def _op(self, v, absolute, transpose):
+        pre = self.m0 if (self.sides == 2 or transpose) else 1.0
+        post = self.m0 if (self.sides == 2 or not transpose) else 1.0
         out = np.empty_like(v, dtype=np.float64)
         for k in range(v.shape[0]):
-            c = haar.forward(self.m0 * v[k], absolute)
-            out[k] = self.m0 * haar.transpose(self.s * c, absolute)
+            c = haar.forward(pre * v[k], absolute)
+            out[k] = post * haar.transpose(self.s * c, absolute)
         return out
 
     def M(self, v):
-        return self._op(v, False)
+        return self._op(v, False, False)
 
-    MT = M
+    def MT(self, v):
+        return self._op(v, False, True)
 
     def absM(self, v):
-        return self._op(v, True)
+        return self._op(v, True, False)
 
-    absMT = absM
+    def absMT(self, v):
+        return self._op(v, True, True)
 
 
 class CrossHaar:
     """Cross-material wavelet preconditioner (Eq. 61):
-    M = M0^T U^T K^-1/2 U M0 with U the orthonormal Haar transform (2-D or 3-D) applied
+    M = M0 U^T K^-1/2 U (sides=2: the literal M0^T U^T K^-1/2 U M0) with U the
+    orthonormal Haar transform (2-D or 3-D) applied
     to every material and K block diagonal over the wavelet coefficients (one
     N_k x N_k block per coefficient).  The estimated blocks are not symmetric;
     as for the cross-material Fourier blocks, K^-1/2 is taken of the polar
@@ -259,7 +284,8 @@ class CrossHaar:
     blocks.  |M| = |M0|^T |U|^T |K^-1/2| |U| |M0| (R7: elementwise absolute
     values of the factors bound |M| elementwise)."""
 
-    def __init__(self, K: np.ndarray, M0: Block):
+    def __init__(self, K: np.ndarray, M0: Block, sides: int = 1):
+        self.sides = sides
         self.shape = K.shape[:-2]
         nm = K.shape[-1]
         P = polar_real(K)
@@ -273,16 +299,20 @@ class CrossHaar:
         return np.stack([haar.transpose(out[k], absolute) for k in range(v.shape[0])])
 
     def M(self, v):
-        return self.M0.MT(self._mid(self.Ki, self.M0.M(v), False))
+        inner = self.M0.M(v) if self.sides == 2 else v
+        return self.M0.MT(self._mid(self.Ki, inner, False))
 
     def MT(self, v):
-        return self.M0.MT(self._mid(np.swapaxes(self.Ki, -1, -2), self.M0.M(v), False))
+        out = self._mid(np.swapaxes(self.Ki, -1, -2), self.M0.M(v), False)
+        return self.M0.MT(out) if self.sides == 2 else out
 
     def absM(self, v):
-        return self.M0.absMT(self._mid(self.Ki_abs, self.M0.absM(v), True))
+        inner = self.M0.absM(v) if self.sides == 2 else v
+        return self.M0.absMT(self._mid(self.Ki_abs, inner, True))
 
     def absMT(self, v):
-        return self.M0.absMT(self._mid(np.swapaxes(self.Ki_abs, -1, -2), self.M0.absM(v), True))
+        out = self._mid(np.swapaxes(self.Ki_abs, -1, -2), self.M0.absM(v), True)
+        return self.M0.absMT(out) if self.sides == 2 else out
 
 
 def cross_haar_blocks(apply_H, M0: Block, shape, nm: int, lattice: int = 3) -> np.ndarray:

@@ -68,12 +68,115 @@ def test_fourier_exact_on_circulant():
     P = precond.Fourier(est)
     v = rng.standard_normal((1,) + shape)
     assert np.allclose(P.MT(apply_H(P.M(v))), v, rtol=1e-11, atol=1e-11)
-    # modified Fourier (Eq. 33): M = M0 U^H Lambda~^-1/2 U M0 with Lambda~ the
-    # spectrum of N = M0 H M0.  When N is circulant its estimate is exact and
-    # the two-sided form gives M^T H M = M0 N^-1/2 N N^-1/2 M0 = M0^2.
+    # modified Fourier (Eq. 33) with Lambda~ the spectrum of N = M0 H M0.  When
+    # N is circulant its estimate is exact: the one-sided M = M0 C whitens H,
+    # the literal two-sided form gives M^T H M = M0 N^-1/2 N N^-1/2 M0 = M0^2.
     lamN = precond.fourier_eigenvalues(lambda z: 0.25 * apply_H(z), shape)
-    P2 = precond.Fourier(lamN, np.full(shape, 0.5))
+    P1 = precond.Fourier(lamN, np.full(shape, 0.5))
+    assert np.allclose(P1.MT(apply_H(P1.M(v))), v, rtol=1e-11, atol=1e-11)
+    P2 = precond.Fourier(lamN, np.full(shape, 0.5), sides=2)
     assert np.allclose(P2.MT(apply_H(P2.M(v))), 0.25 * v, rtol=1e-11, atol=1e-11)
+
+
+def _scaled(apply_N, m0):
+    """H = M0^-1 N M0^-1 for a diagonal M0 (so that N = M0 H M0)."""
+    return lambda v: apply_N(v / m0[None]) / m0[None]
+
+
+def _scaled_blocks(apply_N, M0, nm):
+    """H = M0^-1 N M0^-1 for symmetric per-pixel blocks M0."""
+    Binv = np.linalg.inv(M0.B)
+    inv = __import__("oracle").precond.Block(Binv, M0.shape)
+    return lambda v: inv.M(apply_N(inv.M(v)))
+
+
+@pytest.mark.parametrize("kind", ["mod_fourier", "haar"])
+def test_one_sided_whitens_scaled_hessian(kind):
+    """The reading of where M0 goes (Eqs. 33, 34): with N = M0 H M0 diagonal
+    in the transform basis and a non-constant M0, Eq. 18 recovers N's
+    spectrum, the one-sided M = M0 C gives M^T H M = I and M M^T = H^-1
+    (dense), and the literal two-sided M0 C M0 gives M^T H M = M0^2."""
+    from oracle import haar, precond
+    shape = (8, 8)
+    rng = np.random.default_rng(11)
+    m0 = rng.uniform(0.3, 2.0, shape)
+    if kind == "haar":
+        lam = rng.uniform(0.2, 5.0, shape)
+
+        def apply_N(v):
+            return np.stack([haar.transpose(lam * haar.forward(v[k])) for k in range(v.shape[0])])
+        est = precond.haar_eigenvalues(apply_N, shape)
+        make = precond.Haar
+    else:
+        lam = even_positive(shape, rng)
+
+        def apply_N(v):
+            return np.stack([np.fft.ifftn(lam * np.fft.fftn(v[k])).real for k in range(v.shape[0])])
+        est = precond.fourier_eigenvalues(apply_N, shape)
+        make = precond.Fourier
+    assert np.allclose(est, lam, rtol=1e-12)
+    apply_H = _scaled(apply_N, m0)
+    Hd = dense(apply_H, shape)
+    P1, P2 = make(est, m0), make(est, m0, sides=2)
+    M1, M2 = dense(P1.M, shape), dense(P2.M, shape)
+    assert np.allclose(dense(P1.MT, shape), M1.T, atol=1e-13)
+    assert np.allclose(M1.T @ Hd @ M1, np.eye(64), atol=1e-10)
+    assert np.allclose(M1 @ M1.T, np.linalg.inv(Hd), rtol=1e-9, atol=1e-9 * np.abs(np.linalg.inv(Hd)).max())
+    assert np.allclose(M2.T @ Hd @ M2, np.diag(m0.ravel() ** 2), atol=1e-10)
+    # |M| bounds M elementwise in both forms
+    for P, Md in [(P1, M1), (P2, M2)]:
+        assert (dense(P.absM, shape) >= np.abs(Md) - 1e-12).all()
+        assert np.allclose(dense(P.absMT, shape), dense(P.absM, shape).T, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["block_fourier", "block_haar"])
+def test_one_sided_cross_material_whitens(kind):
+    """Cross-material forms (Eqs. 57, 61) with symmetric per-pixel blocks M0:
+    H = M0^-1 N M0^-1 with N block diagonal in the transform basis; the
+    estimators recover N's blocks and the one-sided M = M0 C whitens H, the
+    two-sided M0 C M0 gives M^T H M = M0^2."""
+    from oracle import haar, precond
+    shape, nm = (8, 4), 2
+    if kind == "block_haar":
+        shape = (8, 8)
+    rng = np.random.default_rng(12)
+    n = int(np.prod(shape))
+    G = rng.standard_normal((n, nm, nm))
+    B = np.einsum("nij,nkj->nik", G, G) + 0.5 * np.eye(nm)       # symmetric positive blocks
+    M0 = precond.Block(B, shape)
+    if kind == "block_haar":
+        Gk = rng.standard_normal(shape + (nm, nm))
+        Kt = np.einsum("...ij,...kj->...ik", Gk, Gk) + 0.5 * np.eye(nm)
+
+        def apply_N(v):
+            c = np.stack([haar.forward(v[k]) for k in range(nm)])
+            out = np.einsum("...ij,j...->i...", Kt, c)
+            return np.stack([haar.transpose(out[k]) for k in range(nm)])
+        apply_H = _scaled_blocks(apply_N, M0, nm)
+        est = precond.cross_haar_blocks(apply_H, M0, shape, nm)
+        assert np.allclose(est, Kt, rtol=1e-9, atol=1e-9)
+        P1, P2 = precond.CrossHaar(est, M0), precond.CrossHaar(est, M0, sides=2)
+    else:
+        Gf = rng.standard_normal(shape + (nm, nm))
+        idx = tuple(np.meshgrid(*[(-np.arange(k)) % k for k in shape], indexing="ij"))
+        Gf = 0.5 * (Gf + Gf[idx])
+        Lb = np.einsum("...ij,...kj->...ik", Gf, Gf) + 0.5 * np.eye(nm)
+
+        def apply_N(v):
+            V = np.fft.fftn(v, axes=(1, 2))
+            return np.fft.ifftn(np.einsum("...ij,j...->i...", Lb, V), axes=(1, 2)).real
+        apply_H = _scaled_blocks(apply_N, M0, nm)
+        est = precond.cross_fourier_blocks(apply_H, M0, shape, nm)
+        assert np.allclose(est, Lb, rtol=1e-9, atol=1e-9)
+        P1, P2 = precond.CrossFourier(est, M0), precond.CrossFourier(est, M0, sides=2)
+    Hd = dense(apply_H, shape, nm)
+    M1, M2 = dense(P1.M, shape, nm), dense(P2.M, shape, nm)
+    assert np.allclose(dense(P1.MT, shape, nm), M1.T, atol=1e-12 * np.abs(M1).max())
+    assert np.allclose(M1.T @ Hd @ M1, np.eye(nm * n), atol=1e-9)
+    B2 = dense(lambda v: M0.M(M0.M(v)), shape, nm)
+    assert np.allclose(M2.T @ Hd @ M2, B2, atol=1e-9 * np.abs(B2).max())
+    for P, Md in [(P1, M1), (P2, M2)]:
+        assert (dense(P.absM, shape, nm) >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all()
 
 
 @pytest.mark.parametrize("lattice", [0, 3])
@@ -151,8 +254,8 @@ def test_abs_bounds_dominate(oracle_lib):
     img = synth.render(g, [synth.Ellipse(0.5, -0.3, 2.5, 3.0, 0.2, 0.02)])
     y = np.round(1e4 * np.exp(-A.project(img[None])))
     st = psps.Setup(A, np.ones((1, 1)), np.full((1, 1), 1e4), y, np.array([[50.0]]))
-    for kind in ["fourier", "mod_fourier", "haar", "block", "block_haar"]:
-        P = build.build(st, kind)
+    for kind, sides in [(k, sd) for k in ["fourier", "mod_fourier", "haar", "block", "block_haar"] for sd in (1, 2)]:
+        P = build.build(st, kind, sides)
         Md = dense(P.M, st.shape)
         MTd = dense(P.MT, st.shape)
         Ad = dense(P.absM, st.shape)
