@@ -229,9 +229,11 @@ mbir_status mbmd_curvature(mbir_plan *plan, const mbmd_spectrum *spec, const flo
  * Scratch: a static 28,928-byte device array per GPU, held until the process
  * exits; limits n_mat <= 4, n_energy <= 256, n_chan <= 8 (larger sizes return
  * MBIR_ERR_ARG with a message); n_rays is not limited.  The first call on
- * each device looks up the array's address (make it before any stream
- * capture).  Every call shares the array: calls that overlap on the GPU race
- * and must be ordered by the caller (one stream, or events). */
+ * each device looks up the array's address.  The call cannot be captured into
+ * a CUDA graph (it stages the spectral table with a pageable host copy): on a
+ * stream that is capturing it returns MBIR_ERR_ARG and enqueues nothing.
+ * Every call shares the array: calls that overlap on the GPU race and must be
+ * ordered by the caller (one stream, or events). */
 mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_chan, const double *Q, const double *S,
                                    const float *l, const float *y, int64_t n_rays, double *objective,
                                    mbir_stream stream);
@@ -241,8 +243,8 @@ mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_chan, const do
 enum {
     PSPS_PRECOND_NONE = 0,          /* M = I: plain SPS (Sec. II-B)                   */
     PSPS_PRECOND_FOURIER = 1,       /* M = U^H Lambda^-1/2 U (Eq. 29)                 */
-    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U M0 (Eqs. 30-33)       */
-    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT M0 (Eq. 34)   */
+    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U [M0] (Eqs. 30-33)     */
+    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT [M0] (Eq. 34) */
     PSPS_PRECOND_BLOCK = 4,         /* per-pixel / per-ray N_k x N_k M0 (Eqs. 42, 54) */
     PSPS_PRECOND_BLOCK_FOURIER = 5, /* cross-material Fourier (Eqs. 56-57)            */
     PSPS_PRECOND_BLOCK_HAAR = 6     /* cross-material wavelet (Eqs. 58-61)            */
@@ -289,6 +291,43 @@ mbir_status psps_precondition_build(mbir_plan *plan, const mbmd_spectrum *spec, 
 mbir_status psps_precondition_create(mbir_plan *plan, int kind, int n_mat, int64_t n, const float *lam,
                                      const float *m0, const float *blocks, mbir_stream stream, psps_precond **out);
 mbir_status psps_precondition_destroy(psps_precond *pc);
+
+/* Where M0 enters the Fourier and wavelet kinds (MOD_FOURIER, HAAR,
+ * BLOCK_FOURIER, BLOCK_HAAR; FOURIER and BLOCK are unaffected).  The paper
+ * writes M = M0^T C M0 (Eqs. 33, 34, 57, 61) with C = U^H Lambda~^-1/2 U built
+ * from the spectrum of N = M0^T H M0; then M^T H M = M0^T M0 where N is
+ * diagonal in U, not the I that Sec. II-C aims for.  sides = 1 (the default
+ * of every build and create) applies M = M0^T C, so that M^T H M = C N C = I
+ * there; sides = 2 applies the literal two-sided form.  Call it before
+ * psps_state_create: a state precomputes A|M|1 and |M|^T|R||M|1 from the
+ * preconditioner it is given.  sides other than 1 or 2 return MBIR_ERR_ARG. */
+mbir_status psps_precondition_set_sides(psps_precond *pc, int sides);
+
+/* Copy one array of a preconditioner into caller-owned device memory (for
+ * checking a build against an independent one element by element; the
+ * arrays are those of psps_precondition_create):
+ *   PSPS_EXPORT_SCALES  FOURIER / MOD_FOURIER / HAAR: the scales
+ *                       clamp(Lambda~)^-1/2 of Eqs. 29, 33, 34, [n];
+ *                       BLOCK_FOURIER / BLOCK_HAAR: the per-frequency /
+ *                       per-coefficient blocks L^-1/2, K^-1/2 of Eqs. 57, 61,
+ *                       [n_mat][n_mat][n];
+ *   PSPS_EXPORT_BLOCKS  the M0 blocks of Eqs. 30, 42, 53-54, [n_mat][n_mat][n]
+ *                       (built kinds other than FOURIER);
+ *   PSPS_EXPORT_M0      the scalar M0 of the one-material kinds, [n] (ones
+ *                       for FOURIER);
+ *   PSPS_EXPORT_HBLOCKS built only: the blocks (F+R)1_k that M0 is the
+ *                       inverse square root of, [n_mat][n_mat][n];
+ *   PSPS_EXPORT_ESTIMATE built Fourier / wavelet kinds only: the Eq. 18
+ *                       estimates before the modulus, floor and -1/2 power:
+ *                       Lambda~ [n] (FOURIER, MOD_FOURIER: already the
+ *                       modulus; HAAR: signed ratios), the polar factors
+ *                       Re (L^H L)^1/2 (BLOCK_FOURIER) or the estimated blocks
+ *                       K (BLOCK_HAAR), [n_mat][n_mat][n].
+ * n_out must equal the array's length; a kind without the array returns
+ * MBIR_ERR_ARG.  Asynchronous on `stream`. */
+enum { PSPS_EXPORT_SCALES = 0, PSPS_EXPORT_BLOCKS = 1, PSPS_EXPORT_M0 = 2, PSPS_EXPORT_HBLOCKS = 3,
+       PSPS_EXPORT_ESTIMATE = 4 };
+mbir_status psps_precondition_export(psps_precond *pc, int what, float *out, int64_t n_out, mbir_stream stream);
 
 /* out = op(M) in for op in PSPS_APPLY_*, arrays shaped like the unknowns
  * ([n_mat][image] or [n_mat][n_rays]); in and out must not alias. */

@@ -209,12 +209,17 @@ class Precond:
     """One-time preconditioner build (``psps_precondition_build``)."""
 
     def __init__(self, plan: Plan | None, spec: Spectrum, kind: str, y=None, beta=None, haar_lattice: int = 3,
-                 lam=None, m0=None, blocks=None):
+                 lam=None, m0=None, blocks=None, sides: int = 1):
         """Build from data (``y``) or, when ``lam`` / ``blocks`` is given,
         create from precomputed eigenvalues / blocks
-        (``psps_precondition_create``)."""
+        (``psps_precondition_create``).  sides: M = M0^T C (1) or the
+        literal M0^T C M0 (2) for the Fourier and wavelet kinds
+        (``psps_precondition_set_sides``)."""
+        self.sides = sides
         self.kind = kind
         self.plan, self.spec = plan, spec
+        self.n_rays = plan.n_rays if plan else (blocks.shape[-1] if blocks is not None else
+                                                 (y.numel() // spec.n_chan if y is not None else 0))
         if y is None:
             n = plan.n_pix if plan else (blocks.shape[-1] if blocks is not None else 0)
             h = ctypes.c_void_p()
@@ -222,6 +227,8 @@ class Precond:
                   _dev(lam, "lam") if lam is not None else None, _dev(m0, "m0") if m0 is not None else None,
                   _dev(blocks, "blocks") if blocks is not None else None, _stream(), ctypes.byref(h))
             self.h = h
+            if sides != 1:
+                _call(lib().psps_precondition_set_sides, h, int(sides))
             return
         n_rays = y.numel() // spec.n_chan
         b = None
@@ -232,6 +239,8 @@ class Precond:
         _call(lib().psps_precondition_build, plan.h if plan else None, spec.h, PSPS_PRECOND[kind], _dev(y, "y"),
               int(n_rays), b, int(haar_lattice), _stream(), ctypes.byref(h))
         self.h = h
+        if sides != 1:
+            _call(lib().psps_precondition_set_sides, h, int(sides))
 
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:
@@ -244,6 +253,24 @@ def psps_precondition(pc: Precond, op: str, inp, out=None):
     if out is None:
         out = torch.empty_like(inp)
     _call(lib().psps_precondition, pc.h, PSPS_APPLY[op], _dev(inp, "in"), _dev(out, "out"), _stream())
+    return out
+
+
+def psps_precondition_export(pc: Precond, what: str):
+    """Copy of one array of a preconditioner (``psps_precondition_export``):
+    'scales' (clamp(Lambda~)^-1/2 [n], or the cross-material blocks
+    [n_mat][n_mat][n]), 'blocks' (M0 blocks [n_mat][n_mat][n]), 'm0' ([n]),
+    'hblocks' ((F+R)1_k blocks, built only) or 'estimate' (the Eq. 18
+    estimates, built Fourier / wavelet kinds only)."""
+    torch = _torch()
+    nm = pc.spec.n_mat
+    n = pc.plan.n_pix if pc.plan else pc.n_rays
+    cross = pc.kind in ("block_fourier", "block_haar")
+    blocky = what in ("blocks", "hblocks") or (what in ("scales", "estimate") and cross)
+    shape = (nm, nm, n) if blocky else (n,)
+    out = torch.empty(shape, device="cuda", dtype=torch.float32)
+    _call(lib().psps_precondition_export, pc.h, _abi.PSPS_EXPORT[what], _dev(out, "out"), int(out.numel()),
+          _stream())
     return out
 
 

@@ -17,6 +17,7 @@ STATUS = {0: "MBIR_OK", -1: "MBIR_ERR_ARG", -2: "MBIR_ERR_CUDA", -3: "MBIR_ERR_O
 PSPS_PRECOND = {"none": 0, "fourier": 1, "mod_fourier": 2, "haar": 3, "block": 4, "block_fourier": 5,
                 "block_haar": 6}
 PSPS_APPLY = {"M": 0, "MT": 1, "absM": 2, "absMT": 3}
+PSPS_EXPORT = {"scales": 0, "blocks": 1, "m0": 2, "hblocks": 3, "estimate": 4}
 FLAG_LINESEARCH, FLAG_NONNEG, FLAG_GRAPH = 1, 2, 4
 PROF_STAGES = ["reproject", "model", "backproject", "precond", "project", "linesearch", "update"]
 
@@ -57,6 +58,8 @@ SIGNATURES = [
                                          P(c_void_p)]),
     ("psps_precondition_destroy", c_int, [c_void_p]),
     ("psps_precondition", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("psps_precondition_export", c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p]),
+    ("psps_precondition_set_sides", c_int, [c_void_p, c_int]),
     ("psps_state_create", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, P(c_double), c_void_p, c_int,
                                   c_int, c_void_p, P(c_void_p)]),
     ("psps_state_destroy", c_int, [c_void_p]),

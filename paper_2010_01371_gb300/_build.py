@@ -67,9 +67,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     objs = []
 
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "mbir.h"), __file__]
+    t_head = max(os.path.getmtime(h) for h in headers if os.path.exists(h))
+
     def one(unit):
         src, name, extra = unit
         obj = os.path.join(OUT_DIR, name)
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(t_head, os.path.getmtime(src)):
+            return obj   # up to date: newer than its source and every header
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)

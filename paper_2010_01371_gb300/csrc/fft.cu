@@ -332,9 +332,9 @@ mbir_status FftPlan::inverse(int channels, float2 *Z, float *out, const float *p
     return run(0, 2, channels, nullptr, Z, out, post, nullptr, s);
 }
 
-mbir_status FftPlan::filter(int channels, const float *in, float2 *Z, float *out, const float *m0, const float *spec,
-                            cudaStream_t s) const {
-    PSPS_TRY(run(0, 0, channels, in, Z, nullptr, m0, nullptr, s));
+mbir_status FftPlan::filter(int channels, const float *in, float2 *Z, float *out, const float *pre, const float *post,
+                            const float *spec, cudaStream_t s) const {
+    PSPS_TRY(run(0, 0, channels, in, Z, nullptr, pre, nullptr, s));
     if (nz > 1) {
         PSPS_TRY(run(1, 3, channels, nullptr, Z, nullptr, nullptr, nullptr, s));
         PSPS_TRY(run(2, 1, channels, nullptr, Z, nullptr, nullptr, spec, s));   // forward, multiply, inverse in z
@@ -342,7 +342,7 @@ mbir_status FftPlan::filter(int channels, const float *in, float2 *Z, float *out
     } else {
         PSPS_TRY(run(1, 1, channels, nullptr, Z, nullptr, nullptr, spec, s));   // forward, multiply, inverse in y
     }
-    return run(0, 2, channels, nullptr, Z, out, m0, nullptr, s);
+    return run(0, 2, channels, nullptr, Z, out, post, nullptr, s);
 }
 
 }  // namespace psps

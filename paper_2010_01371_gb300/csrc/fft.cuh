@@ -6,8 +6,8 @@ namespace psps {
 bool fft_supported(int n);
 
 // 2-D / 3-D FFT filter for images [channels][nz][ny][nx] (nz = 1: 2-D):
-//   out = m0 .* Re( IDFT( spec .* DFT(m0 .* in) ) )
-// with a real spectrum spec[kz][ky][kx] (m0 nullable).  Z is an
+//   out = post .* Re( IDFT( spec .* DFT(pre .* in) ) )
+// with a real spectrum spec[kz][ky][kx] (pre, post nullable).  Z is an
 // nx*ny*nz*channels complex scratch buffer.
 struct FftPlan {
     int nx = 0, ny = 0, nz = 1;
@@ -19,8 +19,8 @@ struct FftPlan {
     mbir_status forward(int channels, const float *in, float2 *Z, cudaStream_t s) const;
     // out = post .* Re(IDFT(Z)) (normalised by 1/(nx ny nz)); Z is overwritten.
     mbir_status inverse(int channels, float2 *Z, float *out, const float *post, cudaStream_t s) const;
-    mbir_status filter(int channels, const float *in, float2 *Z, float *out, const float *m0, const float *spec,
-                       cudaStream_t s) const;
+    mbir_status filter(int channels, const float *in, float2 *Z, float *out, const float *pre, const float *post,
+                       const float *spec, cudaStream_t s) const;
 };
 
 }  // namespace psps

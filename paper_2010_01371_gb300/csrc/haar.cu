@@ -467,25 +467,25 @@ mbir_status haar_inverse(int n, int channels, float *coef, float *out, const flo
     return MBIR_OK;
 }
 
-mbir_status haar_apply(int n, int channels, const float *in, float *tmp, float *out, const float *m0,
-                       const float *scale, unsigned abs_mask, cudaStream_t s, int nz) {
+mbir_status haar_apply(int n, int channels, const float *in, float *tmp, float *out, const float *pre,
+                       const float *post, const float *scale, unsigned abs_mask, cudaStream_t s, int nz) {
     if (nz > 1) {
         const Haar3Launch L(n);
-        fwd3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, in, tmp, m0, scale,
+        fwd3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, in, tmp, pre, scale,
                                                                               abs_mask);
         PSPS_LAUNCH_CHECK();
         coarse3_kernel<<<channels, kThreads, L.smem, s>>>(n, L.C, tmp, scale, 7, abs_mask);
         PSPS_LAUNCH_CHECK();
-        inv3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, tmp, out, m0, abs_mask);
+        inv3_tile_kernel<<<dim3(L.C, L.C, L.C * channels), kThreads, 0, s>>>(n, L.T, L.C, tmp, out, post, abs_mask);
         PSPS_LAUNCH_CHECK();
         return MBIR_OK;
     }
     const int T = n < kT ? n : kT, C = n / T;
-    fwd_tile_kernel<<<dim3(C, C, channels), kThreads, 0, s>>>(n, T, in, tmp, m0, scale, abs_mask);
+    fwd_tile_kernel<<<dim3(C, C, channels), kThreads, 0, s>>>(n, T, in, tmp, pre, scale, abs_mask);
     PSPS_LAUNCH_CHECK();
     coarse_kernel<<<channels, kThreads, 2 * C * C * sizeof(float), s>>>(n, C, tmp, scale, 7, abs_mask);
     PSPS_LAUNCH_CHECK();
-    inv_tile_kernel<<<dim3(C, C, channels), kThreads, 0, s>>>(n, T, tmp, out, m0, abs_mask);
+    inv_tile_kernel<<<dim3(C, C, channels), kThreads, 0, s>>>(n, T, tmp, out, post, abs_mask);
     PSPS_LAUNCH_CHECK();
     return MBIR_OK;
 }

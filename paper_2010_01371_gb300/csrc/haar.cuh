@@ -15,9 +15,9 @@ mbir_status haar_forward(int n, int channels, const float *in, float *coef, cons
 // overwritten).
 mbir_status haar_inverse(int n, int channels, float *coef, float *out, const float *post, unsigned abs_mask,
                          cudaStream_t s, int nz = 1);
-// out = m0 .* U^T (scale .* U (m0 .* in)); tmp is a (image size) * channels
-// scratch.
-mbir_status haar_apply(int n, int channels, const float *in, float *tmp, float *out, const float *m0,
-                       const float *scale, unsigned abs_mask, cudaStream_t s, int nz = 1);
+// out = post .* U^T (scale .* U (pre .* in)) (pre, post nullable); tmp is a
+// (image size) * channels scratch.
+mbir_status haar_apply(int n, int channels, const float *in, float *tmp, float *out, const float *pre,
+                       const float *post, const float *scale, unsigned abs_mask, cudaStream_t s, int nz = 1);
 
 }  // namespace psps

@@ -12,7 +12,10 @@
 // code the array's name only stands in for the symbol and is never used as a
 // pointer: the device address is looked up with cudaGetSymbolAddress on the
 // first call on each device (with that device current) and handed to the
-// kernels.  Make that first call before any stream capture.  All calls share
+// kernels.  The call cannot be captured into a CUDA graph: it stages the
+// spectral table from a stack array with a pageable copy, which a graph would
+// replay from a buffer that no longer exists, so a stream that is capturing
+// is rejected with MBIR_ERR_ARG before anything is enqueued.  All calls share
 // the array, so calls that overlap on the GPU (different streams, or several
 // host threads) race on it.
 #include <mutex>
@@ -68,6 +71,14 @@ extern "C" mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_cha
                     "(n_mat <= 4, n_energy <= 256, n_chan <= 8)",
                     n_mat, n_energy, n_chan);
     if (n_rays < 1) return fail(MBIR_ERR_ARG, "mbmd_objective_noalloc: n_rays must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess)
+        return fail(MBIR_ERR_CUDA, "mbmd_objective_noalloc: cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(MBIR_ERR_ARG, "mbmd_objective_noalloc: the stream is capturing a CUDA graph; this call cannot be "
+                                  "captured (it stages its table with a pageable host copy)");
     const size_t nt = (size_t)n_energy * n_mat + (size_t)n_chan * n_energy + n_chan;
     float table[kTableFloats];  // host staging on the stack, no allocation
     for (size_t i = 0; i < (size_t)n_energy * n_mat; ++i) table[i] = (float)Q[i];
@@ -83,7 +94,6 @@ extern "C" mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_cha
     PSPS_TRY(scratch_address(&base));
     float *qs = (float *)base;
     dfloat *partials = (dfloat *)((unsigned char *)base + kTableBytes);
-    cudaStream_t s = (cudaStream_t)stream;
     // pageable source: the copy is staged before the call returns, so the
     // stack table may go out of scope afterwards
     PSPS_CUDA(cudaMemcpyAsync(qs, table, sizeof(float) * nt, cudaMemcpyHostToDevice, s));

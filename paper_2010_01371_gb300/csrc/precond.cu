@@ -466,7 +466,12 @@ struct HessOp {
         }
         return MBIR_OK;
     }
-    mbir_status apply(const float *v, float *out, int nprobe, cudaStream_t s) {
+    // precise: sum the transpose in FP32 with the deterministic pixel gather
+    // instead of the fixed-point tile kernel (2-D plans), for the build steps
+    // with few probes (M0 blocks, Fourier impulses), where each pixel's
+    // response spans many decades and a grid of the launch-wide largest term
+    // would dominate the error of its small values.
+    mbir_status apply(const float *v, float *out, int nprobe, cudaStream_t s, bool precise = false) {
         const int ch = nprobe * nm;
         if (!plan) {
             fisher_mul_kernel<<<nblk(n_rays), kThreads, 0, s>>>(nm, nprobe, n_rays, F, v, out);
@@ -476,7 +481,11 @@ struct HessOp {
         PSPS_TRY(project(plan, v, l.p, ch, s));
         fisher_mul_kernel<<<nblk(n_rays), kThreads, 0, s>>>(nm, nprobe, n_rays, F, l.p, u.p);
         PSPS_LAUNCH_CHECK();
-        PSPS_TRY(backproject(plan, u.p, out, ch, 0, s));
+        const int mode = plan->back_mode;
+        if (precise && plan->g.kind != MBIR_CONE3D && mode == 0) plan->back_mode = 1;
+        const mbir_status bs = backproject(plan, u.p, out, ch, 0, s);
+        plan->back_mode = mode;
+        PSPS_TRY(bs);
         if (has_pen)
             for (int p = 0; p < nprobe; ++p)
                 PSPS_TRY(launch_penalty(pd, plan->g.nx, plan->g.ny, plan->g.nz, v + (int64_t)p * nm * n, nullptr,
@@ -506,7 +515,7 @@ mbir_status finish_scalar(psps_precond *pc, float *lam, bool fourier, cudaStream
         float *imp = pc->tmp.p, *k = pc->tmp.p + pc->n;
         PSPS_CUDA(cudaMemsetAsync(imp, 0, sizeof(float) * pc->n, s));
         set_value_kernel<<<1, 1, 0, s>>>(imp, 0, 1.f);
-        PSPS_TRY(pc->fft.filter(1, imp, pc->Z.p, k, nullptr, pc->s.p, s));
+        PSPS_TRY(pc->fft.filter(1, imp, pc->Z.p, k, nullptr, nullptr, pc->s.p, s));
         abs_kernel<<<gs(pc->n), kThreads, 0, s>>>(k, pc->n);
         PSPS_TRY(pc->fft.forward(1, k, pc->Z.p, s));
         real_part_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->Z.p, pc->s_abs.p, pc->n);
@@ -549,7 +558,7 @@ mbir_status finish_cross_fourier(psps_precond *pc, const float *P, const float *
     for (int ab = 0; ab < nm * nm; ++ab) {
         PSPS_CUDA(cudaMemsetAsync(imp, 0, sizeof(float) * n, s));
         set_value_kernel<<<1, 1, 0, s>>>(imp, 0, 1.f);
-        PSPS_TRY(pc->fft.filter(1, imp, pc->Z.p, k, nullptr, pc->Li.p + (int64_t)ab * n, s));
+        PSPS_TRY(pc->fft.filter(1, imp, pc->Z.p, k, nullptr, nullptr, pc->Li.p + (int64_t)ab * n, s));
         abs_kernel<<<gs(n), kThreads, 0, s>>>(k, n);
         PSPS_TRY(pc->fft.forward(1, k, pc->Z.p, s));
         real_part_kernel<<<gs(n), kThreads, 0, s>>>(pc->Z.p, pc->Li_abs.p + (int64_t)ab * n, n);
@@ -606,53 +615,74 @@ mbir_status precond_apply(psps_precond *pc, int op, const float *in, float *out,
     const bool absm = (op == PSPS_APPLY_ABS_M || op == PSPS_APPLY_ABS_MT);
     const bool tr = (op == PSPS_APPLY_MT || op == PSPS_APPLY_ABS_MT);
     const int64_t tot = pc->n * pc->nm;
+    // Where M0 enters the Fourier and wavelet kinds: one-sided M = M0 C
+    // (M^T = C^T M0^T: M0 before the transform for M^T, after it for M) or
+    // the literal two-sided M0^T C M0 (both).
+    const bool m0_before = pc->sides == 2 || tr;
+    const bool m0_after = pc->sides == 2 || !tr;
     switch (pc->kind) {
         case PSPS_PRECOND_NONE:
             if (in != out) PSPS_CUDA(cudaMemcpyAsync(out, in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, s));
             return MBIR_OK;
         case PSPS_PRECOND_FOURIER:
-        case PSPS_PRECOND_MOD_FOURIER:
-            // symmetric: M^T = M, |M|^T = |M|
-            return pc->fft.filter(pc->nm, in, pc->Z.p, out, pc->kind == PSPS_PRECOND_MOD_FOURIER ? pc->m0.p : nullptr,
+        case PSPS_PRECOND_MOD_FOURIER: {
+            // C and |C| are symmetric circulants
+            const float *m0 = pc->kind == PSPS_PRECOND_MOD_FOURIER ? pc->m0.p : nullptr;
+            return pc->fft.filter(pc->nm, in, pc->Z.p, out, m0_before ? m0 : nullptr, m0_after ? m0 : nullptr,
                                   absm ? pc->s_abs.p : pc->s.p, s);
+        }
         case PSPS_PRECOND_HAAR:
-            return haar_apply(pc->nx, pc->nm, in, pc->tmp.p, out, pc->m0.p, pc->s.p, absm ? 0xffffffffu : 0u, s,
-                              pc->nz);
+            return haar_apply(pc->nx, pc->nm, in, pc->tmp.p, out, m0_before ? pc->m0.p : nullptr,
+                              m0_after ? pc->m0.p : nullptr, pc->s.p, absm ? 0xffffffffu : 0u, s, pc->nz);
         case PSPS_PRECOND_BLOCK:
             block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Babs.p : pc->B.p, in, out,
                                                               tr ? 1 : 0);
             PSPS_LAUNCH_CHECK();
             return MBIR_OK;
         case PSPS_PRECOND_BLOCK_FOURIER: {
-            // M = M0^T U^H L^-1/2 U M0 (Eq. 57); every factor is symmetric, so
-            // M^T = M; |M| uses |M0| and the absolute-kernel spectra.
+            // M = M0^T C M0 (Eq. 57) or M0^T C with C = U^H L^-1/2 U; the
+            // per-frequency blocks are symmetric, so C^T = C; |M| uses |M0|
+            // and the absolute-kernel spectra.  M^T applies M0 first.
             const float *Bm = absm ? pc->Babs.p : pc->B.p;
             float *t0 = pc->tmp.p, *t1 = pc->tmp.p + pc->n * pc->nm;
-            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
-            PSPS_LAUNCH_CHECK();
-            PSPS_TRY(pc->fft.forward(pc->nm, t0, pc->Z.p, s));
+            const float *src = in;
+            if (m0_before) {
+                block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
+                PSPS_LAUNCH_CHECK();
+                src = t0;
+            }
+            PSPS_TRY(pc->fft.forward(pc->nm, src, pc->Z.p, s));
             mix_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Li_abs.p : pc->Li.p, pc->Z.p);
             PSPS_LAUNCH_CHECK();
-            PSPS_TRY(pc->fft.inverse(pc->nm, pc->Z.p, t1, nullptr, s));
-            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
-            PSPS_LAUNCH_CHECK();
+            PSPS_TRY(pc->fft.inverse(pc->nm, pc->Z.p, m0_after ? t1 : out, nullptr, s));
+            if (m0_after) {
+                block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
+                PSPS_LAUNCH_CHECK();
+            }
             return MBIR_OK;
         }
         case PSPS_PRECOND_BLOCK_HAAR: {
-            // M = M0^T U^T K^-1/2 U M0 (Eq. 61), U per material; M^T swaps
-            // the blocks of K^-1/2; |M| uses |M0|, |U| and |K^-1/2|.
+            // M = M0^T U^T K^-1/2 U M0 (Eq. 61) or M0^T U^T K^-1/2 U, U per
+            // material; M^T swaps the blocks of K^-1/2 and applies M0 first;
+            // |M| uses |M0|, |U| and |K^-1/2|.
             const float *Bm = absm ? pc->Babs.p : pc->B.p;
             const unsigned amask = absm ? 0xffffffffu : 0u;
             float *t0 = pc->tmp.p, *t1 = pc->tmp.p + pc->n * pc->nm;
-            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
-            PSPS_LAUNCH_CHECK();
-            PSPS_TRY(haar_forward(pc->nx, pc->nm, t0, t1, nullptr, nullptr, amask, s, pc->nz));
+            const float *src = in;
+            if (m0_before) {
+                block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, in, t0, 0);
+                PSPS_LAUNCH_CHECK();
+                src = t0;
+            }
+            PSPS_TRY(haar_forward(pc->nx, pc->nm, src, t1, nullptr, nullptr, amask, s, pc->nz));
             block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, absm ? pc->Li_abs.p : pc->Li.p, t1, t0,
                                                               tr ? 1 : 0);
             PSPS_LAUNCH_CHECK();
-            PSPS_TRY(haar_inverse(pc->nx, pc->nm, t0, t1, nullptr, amask, s, pc->nz));
-            block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
-            PSPS_LAUNCH_CHECK();
+            PSPS_TRY(haar_inverse(pc->nx, pc->nm, t0, m0_after ? t1 : out, nullptr, amask, s, pc->nz));
+            if (m0_after) {
+                block_apply_kernel<<<gs(pc->n), kThreads, 0, s>>>(pc->nm, pc->n, Bm, t1, out, 1);
+                PSPS_LAUNCH_CHECK();
+            }
             return MBIR_OK;
         }
         default:
@@ -738,13 +768,14 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_LAUNCH_CHECK();
         // all nm probes at once when the plan has the channels, else one by one
         if (!plan || nm * nm <= max_ch) {
-            PSPS_TRY(H.apply(ones.p, Hcols.p, nm, s));
+            PSPS_TRY(H.apply(ones.p, Hcols.p, nm, s, true));
         } else {
             for (int k = 0; k < nm; ++k)
-                PSPS_TRY(H.apply(ones.p + (int64_t)k * nm * n, Hcols.p + (int64_t)k * nm * n, 1, s));
+                PSPS_TRY(H.apply(ones.p + (int64_t)k * nm * n, Hcols.p + (int64_t)k * nm * n, 1, s, true));
         }
         // Hcols[k][m][j] = (H 1_k)_m(j) = block[m][k] -> reorder to [m][k][j]
-        DBuf<float> Hb;
+        // (kept with the preconditioner for psps_precondition_export)
+        DBuf<float> &Hb = pc->Hblk;
         PSPS_TRY(Hb.alloc((size_t)nm * nm * n));
         for (int k = 0; k < nm; ++k)
             for (int m = 0; m < nm; ++m)
@@ -781,7 +812,7 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
             PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * nm * n, s));
             set_value_kernel<<<1, 1, 0, s>>>(d.p, (int64_t)k * n + centre, 1.f);
             PSPS_TRY(launch_block_apply(nm, n, pc->B.p, d.p, v.p, 0, s));
-            PSPS_TRY(H.apply(v.p, hv.p, 1, s));
+            PSPS_TRY(H.apply(v.p, hv.p, 1, s, true));
             PSPS_TRY(launch_block_apply(nm, n, pc->B.p, hv.p, v.p, 1, s));
             PSPS_TRY(pc->fft.forward(nm, v.p, pc->Z.p, s));
             PSPS_TRY(launch_phase(nm, pc->nx, pc->ny, pc->nz, pc->Z.p, k, Lc.p, s));
@@ -789,6 +820,8 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_TRY(P.alloc((size_t)nm * nm * n));
         PSPS_TRY(lmax.alloc(n));
         PSPS_TRY(launch_polar(nm, n, Lc.p, P.p, lmax.p, s));
+        PSPS_TRY(pc->est.alloc(P.n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->est.p, P.p, sizeof(float) * P.n, cudaMemcpyDeviceToDevice, s));
         return finish_cross_fourier(pc, P.p, lmax.p, s);
     }
     if (kind == PSPS_PRECOND_BLOCK_HAAR) {
@@ -839,6 +872,8 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
             }
             PSPS_LAUNCH_CHECK();
         }
+        PSPS_TRY(pc->est.alloc(K.n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->est.p, K.p, sizeof(float) * K.n, cudaMemcpyDeviceToDevice, s));
         DBuf<float2> Kc;
         DBuf<float> P, lmax;
         PSPS_TRY(Kc.alloc((size_t)nm * nm * n));
@@ -859,11 +894,11 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
     const float *m0 = pc->m0.p;
     const int nx = pc->nx;
     // N v = m0 .* H (m0 .* v)
-    auto applyN = [&](const float *v, float *out, int nprobe) -> mbir_status {
+    auto applyN = [&](const float *v, float *out, int nprobe, bool precise) -> mbir_status {
         float *w = pc->tmp.p;  // nprobe * n
         mul_bcast_kernel<<<gs(n * nprobe), kThreads, 0, s>>>(v, m0, w, n, nprobe);
         PSPS_LAUNCH_CHECK();
-        PSPS_TRY(H.apply(w, out, nprobe, s));
+        PSPS_TRY(H.apply(w, out, nprobe, s, precise));
         mul_bcast_kernel<<<gs(n * nprobe), kThreads, 0, s>>>(out, m0, out, n, nprobe);
         PSPS_LAUNCH_CHECK();
         return MBIR_OK;
@@ -876,10 +911,12 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
         PSPS_TRY(r.alloc(n));
         PSPS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * n, s));
         set_value_kernel<<<1, 1, 0, s>>>(d.p, centre, 1.f);
-        PSPS_TRY(applyN(d.p, r.p, 1));
+        PSPS_TRY(applyN(d.p, r.p, 1, true));
         PSPS_TRY(pc->fft.forward(1, r.p, pc->Z.p, s));
         modulus_kernel<<<gs(n), kThreads, 0, s>>>(pc->Z.p, lam.p, n);
         PSPS_LAUNCH_CHECK();
+        PSPS_TRY(pc->est.alloc(n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->est.p, lam.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
         PSPS_TRY(finish_scalar(pc, lam.p, true, s));
         PSPS_CUDA(cudaStreamSynchronize(s));
         return MBIR_OK;
@@ -906,7 +943,7 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
             // dx = U^T xi  (haar_inverse uses its coefficient input as scratch)
             PSPS_CUDA(cudaMemcpyAsync(coef.p, mask.p, sizeof(float) * nb * n, cudaMemcpyDeviceToDevice, s));
             PSPS_TRY(haar_inverse(nx, nb, coef.p, dx.p, nullptr, 0u, s, nz));
-            PSPS_TRY(applyN(dx.p, tmp2.p, nb));
+            PSPS_TRY(applyN(dx.p, tmp2.p, nb, false));
             PSPS_TRY(haar_forward(nx, nb, tmp2.p, r.p, nullptr, nullptr, 0u, s, nz));
             PSPS_TRY(haar_forward(nx, nb, dx.p, den.p, nullptr, nullptr, 0u, s, nz));
             for (int b = 0; b < nb; ++b)
@@ -914,6 +951,8 @@ mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, con
                                                                den.p + (int64_t)b * n, lam.p, n);
             PSPS_LAUNCH_CHECK();
         }
+        PSPS_TRY(pc->est.alloc(n));
+        PSPS_CUDA(cudaMemcpyAsync(pc->est.p, lam.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
         PSPS_TRY(finish_scalar(pc, lam.p, false, s));
         PSPS_CUDA(cudaStreamSynchronize(s));
     }
@@ -1048,4 +1087,37 @@ extern "C" mbir_status psps_precondition(psps_precond *pc, int op, const float *
     if (op < PSPS_APPLY_M || op > PSPS_APPLY_ABS_MT) return fail(MBIR_ERR_ARG, "psps_precondition: bad op %d", op);
     if (in == out) return fail(MBIR_ERR_ARG, "psps_precondition: in and out must not alias");
     return precond_apply(pc, op, in, out, (cudaStream_t)s);
+}
+
+extern "C" mbir_status psps_precondition_export(psps_precond *pc, int what, float *out, int64_t n_out,
+                                                mbir_stream stream) {
+    if (!pc || !out) return fail(MBIR_ERR_ARG, "psps_precondition_export: null argument");
+    const psps::DBuf<float> *src = nullptr;
+    const bool cross = pc->kind == PSPS_PRECOND_BLOCK_FOURIER || pc->kind == PSPS_PRECOND_BLOCK_HAAR;
+    switch (what) {
+        case PSPS_EXPORT_SCALES: src = cross ? &pc->Li : &pc->s; break;
+        case PSPS_EXPORT_BLOCKS: src = &pc->B; break;
+        case PSPS_EXPORT_M0: src = &pc->m0; break;
+        case PSPS_EXPORT_HBLOCKS: src = &pc->Hblk; break;
+        case PSPS_EXPORT_ESTIMATE: src = &pc->est; break;
+        default: return fail(MBIR_ERR_ARG, "psps_precondition_export: unknown array %d", what);
+    }
+    if (!src->p || src->n == 0)
+        return fail(MBIR_ERR_ARG, "psps_precondition_export: preconditioner kind %d has no array %d", pc->kind, what);
+    // the scalar kinds' scratch may be longer than the array itself
+    const bool block_shaped = what == PSPS_EXPORT_BLOCKS || what == PSPS_EXPORT_HBLOCKS ||
+                              ((what == PSPS_EXPORT_SCALES || what == PSPS_EXPORT_ESTIMATE) && cross);
+    const int64_t n = block_shaped ? (int64_t)pc->nm * pc->nm * pc->n : pc->n;
+    if (n_out != n)
+        return fail(MBIR_ERR_ARG, "psps_precondition_export: array %d holds %lld values, n_out is %lld", what,
+                    (long long)n, (long long)n_out);
+    PSPS_CUDA(cudaMemcpyAsync(out, src->p, sizeof(float) * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return MBIR_OK;
+}
+
+extern "C" mbir_status psps_precondition_set_sides(psps_precond *pc, int sides) {
+    if (!pc) return fail(MBIR_ERR_ARG, "psps_precondition_set_sides: null preconditioner");
+    if (sides != 1 && sides != 2) return fail(MBIR_ERR_ARG, "psps_precondition_set_sides: sides must be 1 or 2");
+    pc->sides = sides;
+    return MBIR_OK;
 }

@@ -9,10 +9,13 @@ struct psps_precond {
     bool image = true;       // false: projection-domain unknowns [nm][n_rays]
     int nx = 1, ny = 1, nz = 1;  // image grid (nz = 1: 2-D)
     int64_t n = 0;           // unknowns per material
+    int sides = 1;           // Fourier / wavelet kinds: M = M0 C (1) or M0^T C M0 (2)
     psps::DBuf<float> m0;    // diagonal zero-frequency normalisation (one material)
     psps::DBuf<float> s, s_abs;  // spectra / wavelet-domain scales
     psps::DBuf<float> B, Babs;   // blocks [nm][nm][n]
     psps::DBuf<float> Li, Li_abs;  // cross-material Fourier: per-frequency blocks [nm][nm][n]
+    psps::DBuf<float> Hblk;      // built: the (F+R)1_k blocks of Eqs. 30, 53-54, [nm][nm][n]
+    psps::DBuf<float> est;       // built: Eq. 18 estimates before the floor ([n] or [nm][nm][n])
     psps::DBuf<float> tmp;       // scratch (n * nm * 2)
     psps::DBuf<float2> Z;        // FFT scratch (n * nm * 2 complex)
     psps::FftPlan fft;

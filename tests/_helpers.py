@@ -59,7 +59,7 @@ def phantom(geom, seed=0, nm=1):
     return np.stack(out)
 
 
-def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None):
+def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None, sides=1):
     """Oracle preconditioner for a problem plus the data that defines it
     (eigenvalues, m0, blocks in the library's [m][k][n] layout).  blur: an
     ``oracle.model.Blur`` in the outer operator (the preconditioners use the
@@ -83,29 +83,29 @@ def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None):
         L = precond.cross_fourier_blocks(aH, M0, st.shape, st.nm)
         P = precond.polar_real(L)
         lam = np.ascontiguousarray(np.transpose(P.reshape(-1, st.nm, st.nm), (1, 2, 0)))
-        return st, precond.CrossFourier(L, M0), {"lam": lam, "blocks": blocks}
+        return st, precond.CrossFourier(L, M0, sides), {"lam": lam, "blocks": blocks}
     if kind == "block_haar":
         M0 = precond.Block(B, st.shape)
         K = precond.cross_haar_blocks(aH, M0, st.shape, st.nm, lattice)
         P = precond.polar_real(K)
         lam = np.ascontiguousarray(np.transpose(P.reshape(-1, st.nm, st.nm), (1, 2, 0)))
-        return st, precond.CrossHaar(K, M0), {"lam": lam, "blocks": blocks}
+        return st, precond.CrossHaar(K, M0, sides), {"lam": lam, "blocks": blocks}
     m0 = B[:, 0, 0].reshape(st.shape)
 
     def aN(v):
         return m0[None] * aH(m0[None] * v)
     if kind == "mod_fourier":
         lam = precond.fourier_eigenvalues(aN, st.shape)
-        return st, precond.Fourier(lam, m0), {"lam": lam, "m0": m0}
+        return st, precond.Fourier(lam, m0, sides), {"lam": lam, "m0": m0}
     if kind == "haar":
         lam = precond.haar_eigenvalues(aN, st.shape, lattice=lattice)
-        return st, precond.Haar(lam, m0), {"lam": lam, "m0": m0}
+        return st, precond.Haar(lam, m0, sides), {"lam": lam, "m0": m0}
     raise ValueError(kind)
 
 
-def gpu_precond_from(psps, plan, spec, kind, data):
+def gpu_precond_from(psps, plan, spec, kind, data, sides=1):
     """The library's preconditioner created from the oracle's data."""
     if kind == "none":
         return None
     kw = {k: to_dev(v) for k, v in data.items()}
-    return psps.Precond(plan, spec, kind, **kw)
+    return psps.Precond(plan, spec, kind, sides=sides, **kw)

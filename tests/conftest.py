@@ -18,3 +18,32 @@ def oracle_lib():
     import oracle
     oracle.build_c()
     return oracle
+
+
+class ErrorLog:
+    """Measured errors against the oracle, one record per (test, quantity):
+    written as JSON at the end of the session when PSPS_ERROR_LOG names a
+    file (the table of errors per result and configuration is made from it)."""
+
+    def __init__(self):
+        self.rows = []
+
+    def add(self, test: str, quantity: str, error: float, bound: float, **extra):
+        self.rows.append({"test": test, "quantity": quantity, "error": float(error), "bound": float(bound),
+                          **{k: (float(v) if isinstance(v, (int, float)) else v) for k, v in extra.items()}})
+
+
+_ERRORS = ErrorLog()
+
+
+@pytest.fixture(scope="session")
+def error_log():
+    return _ERRORS
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("PSPS_ERROR_LOG")
+    if path and _ERRORS.rows:
+        import json
+        with open(path, "w") as f:
+            json.dump(_ERRORS.rows, f, indent=1)

@@ -52,6 +52,18 @@ def test_apply_parity(psps, oracle_lib, pname, kind):
 
 
 @pytest.mark.parametrize("pname", ["c1", "c2_64"])
+@pytest.mark.parametrize("kind", ["mod_fourier", "haar", "block_fourier", "block_haar"])
+def test_two_sided_apply_parity(psps, oracle_lib, pname, kind):
+    """The literal two-sided M0^T C M0 of Eqs. 33, 34, 57, 61
+    (psps_precondition_set_sides(pc, 2)) against the oracle's sides=2."""
+    prob = problems()[pname] if kind in ("mod_fourier", "haar") else synth.config4_slice(nx=64, n_views=90, n_u=111)
+    st, P, data = oracle_precond(oracle_lib, prob, kind, sides=2)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    pc = gpu_precond_from(psps, plan, spec, kind, data, sides=2)
+    check_ops(psps, pc, P, (st.nm,) + prob.geom.image_shape, APPLY_TOL)
+
+
+@pytest.mark.parametrize("pname", ["c1", "c2_64"])
 @pytest.mark.parametrize("kind", ["fourier", "mod_fourier", "haar", "block"])
 def test_build_parity(psps, oracle_lib, pname, kind):
     prob = problems()[pname]

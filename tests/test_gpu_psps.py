@@ -289,3 +289,49 @@ def test_zero_iterations(psps):
     h = psps.psps_step(st, 0)
     assert h.shape == (1,) and np.isfinite(h[0]) and h[0] > 0
     assert np.array_equal(psps.psps_step(st, 0), h)
+
+
+FULL_SIZE = {
+    # the benchmark's workloads at their own sizes, preconditioners built on
+    # the GPU the way bench.py builds them
+    "c2_512-haar": (lambda: synth.config2(), "haar"),
+    "c4_512-block_fourier": (lambda: synth.config4_slice(), "block_fourier"),
+    "c5_64-block_fourier": (lambda: synth.config5(n=64, n_views=90, n_u=128, n_v=96), "block_fourier"),
+}
+
+
+@pytest.mark.parametrize("case", list(FULL_SIZE))
+def test_full_size_gpu_built_step(psps, oracle_lib, error_log, case):
+    """Line-searched step parity at the workload's own size with the GPU-built
+    preconditioner (autotuned plan, as timed by the benchmark): from the
+    oracle's iterates x_0 = 0 and x_4, one GPU iteration against one oracle
+    iteration with the oracle's FP64-built preconditioner.  Objective before
+    and after to 1e-5, alpha and the image to 1e-4."""
+    from oracle import psps as opsps
+    mk, kind = FULL_SIZE[case]
+    prob = mk()
+    st, P, data = oracle_precond(oracle_lib, prob, kind)
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
+    plan.autotune(2 * st.nm)
+    yd = to_dev(prob.y)
+    pc = psps.Precond(plan, spec, kind, yd, prob.beta)
+    xk = st.zeros()
+    done = 0
+    for k in [0, 4]:
+        if k > done:
+            xk, _ = opsps.run(st, P, k - done, opsps.LineSearch(), x0=xk)
+            done = k
+        x1o, h1o, a1o = opsps.run(st, P, 1, opsps.LineSearch(), x0=xk, return_alphas=True)
+        state = psps.State(plan, spec, pc, yd, prob.beta, x0=to_dev(xk), line_search=True, graph=True)
+        h1g = psps.psps_step(state, 1)
+        a1g = psps.psps_get_alphas(state, 1)
+        x1g = to_host(psps.psps_get_image(state))
+        eo = [abs(h1g[i] - h1o[i]) / abs(h1o[i]) for i in (0, 1)]
+        ea = abs(a1g[0] - a1o[0]) / abs(a1o[0])
+        ex = rel_l2(x1g, x1o)
+        error_log.add(f"full-size step {case} k={k}", "objective before/after", max(eo), OBJ_TOL)
+        error_log.add(f"full-size step {case} k={k}", "alpha", ea, 1e-4)
+        error_log.add(f"full-size step {case} k={k}", "image", ex, IMG_TOL)
+        assert max(eo) <= OBJ_TOL, (k, eo)
+        assert ea <= 1e-4, (k, a1g, a1o)
+        assert ex < IMG_TOL, (k, ex)

@@ -66,3 +66,28 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
     st = _call_noalloc(lib, Q, S, l, y, out, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == -1
     assert b"static scratch" in lib.mbir_last_error()
+
+
+def test_noalloc_rejects_a_capturing_stream():
+    """The call stages its table with a pageable host copy, which a CUDA graph
+    would replay from a stack buffer that no longer exists; made on a stream
+    that is capturing, it returns MBIR_ERR_ARG and enqueues nothing."""
+    import torch
+
+    import paper_2010_01371_gb300 as p
+    lib = p.lib()
+    Q, S = np.ones((1, 1)), np.full((1, 1), 1e4)
+    l = torch.zeros((1, 8), device="cuda")
+    y = torch.ones((1, 8), device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        out.fill_(1.0)
+        st = _call_noalloc(lib, Q, S, l, y, out, ctypes.c_void_p(side.cuda_stream))
+    assert st == -1
+    assert b"capturing" in lib.mbir_last_error()
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(out.item()) == 1.0
