@@ -386,11 +386,17 @@ def _haar_test_sets3(shape, lattice: int):
     return sets
 
 
-def haar_eigenvalues(apply_H, shape, lattice: int = 3) -> np.ndarray:
+def haar_eigenvalues(apply_H, shape, lattice: int = 3, part=None) -> np.ndarray:
     """Eq. 18 with wavelet test functions dx = U^T xi (Sec. II-D-3):
-    Lambda~_k = [U H dx]_k / [U dx]_k for the coefficients k that xi excites."""
+    Lambda~_k = [U H dx]_k / [U dx]_k for the coefficients k that xi excites.
+    part = (i, n): only every n-th test set from the i-th (the other
+    coefficients stay 0), so that the sets can be split among processes; the
+    n parts add up to the whole estimate."""
     lam = np.zeros(shape)
-    for sel in haar_test_sets(shape, lattice):
+    sets = haar_test_sets(shape, lattice)
+    if part is not None:
+        sets = sets[part[0]::part[1]]
+    for sel in sets:
         dx = haar.transpose(sel.astype(np.float64))
         r = haar.forward(apply_H(dx[None])[0])
         den = haar.forward(dx)

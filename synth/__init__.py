@@ -468,12 +468,15 @@ def config4(n_slices: int = 16, n_views: int = 720, shrink: int = 1) -> list:
 CONFIG5_BETA = np.array([[0.5, 3.0], [3.0, 2000.0]])
 
 
-def config5(n: int = 256, n_views: int = 360, n_u: int = 512, n_v: int = 384, rays: bool = True) -> Problem:
+def config5(n: int = 256, n_views: int = 360, n_u: int = 512, n_v: int = 384, rays: bool = True,
+            first_views: int | None = None) -> Problem:
     """3-D cone-beam one-step MBMD: 2 materials (water, iodine-like), 80/140 kVp
     dual-energy channels (each normalised to I0 = 5e4), 256^3 at 0.5 mm, 360
     views over 360 deg onto a 512 x 384 flat detector of 0.8 mm pixels, SID 600,
     SDD 1200; seeded ellipsoid phantom; per-voxel 2x2 blocks.  Smaller n /
-    views / detector scale the same scan down (same field of view).  beta in
+    views / detector scale the same scan down (same field of view);
+    first_views keeps only the first views of the orbit (same volume, same
+    view spacing: a bounded part of the scan).  beta in
     density units: the water and iodine strengths of CONFIG4_BETA (rounded)
     with the cross term 0.1 sqrt(beta_11 beta_22)."""
     E = np.arange(20.0, 141.0)
@@ -481,7 +484,10 @@ def config5(n: int = 256, n_views: int = 360, n_u: int = 512, n_v: int = 384, ra
     I0 = 5e4
     S = np.stack([I0 * kramers(E, 80.0), I0 * kramers(E, 140.0)])
     scale = 256.0 / n
-    geom = Geometry(CONE3D, n, n, n, 0.5 * scale, 0.5 * scale, 0.5 * scale, n_views, 0.0, 2 * math.pi, n_u, n_v,
+    nv, span = n_views, 2 * math.pi
+    if first_views is not None and first_views < n_views:
+        nv, span = first_views, 2 * math.pi * first_views / n_views
+    geom = Geometry(CONE3D, n, n, n, 0.5 * scale, 0.5 * scale, 0.5 * scale, nv, 0.0, span, n_u, n_v,
                     0.8 * 512 / n_u, 0.8 * 384 / n_v, 600.0, 1200.0)
     g = rng(5, "phantom")
     water = [Ellipsoid(0.0, 0.0, 0.0, 55.0, 45.0, 50.0, 0.0, 1.0)]

@@ -11,7 +11,13 @@ from synth import FAN2D, PAR2D, Geometry
 def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    e = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    try:                      # the session's error log (tests/conftest.py)
+        import conftest
+        conftest._ERRORS.note(e)
+    except Exception:
+        pass
+    return e
 
 
 def to_dev(a):
@@ -109,3 +115,47 @@ def gpu_precond_from(psps, plan, spec, kind, data, sides=1):
         return None
     kw = {k: to_dev(v) for k, v in data.items()}
     return psps.Precond(plan, spec, kind, sides=sides, **kw)
+
+
+def _haar_part(job):
+    """Worker: one share of the oracle's Haar test sets for a seeded problem
+    (rebuilt here from its synth builder and keywords)."""
+    builder, kw, i, n = job
+    import oracle
+    from oracle import build, precond, psps as opsps
+    oracle.build_c()
+    prob = getattr(synth, builder)(**kw)
+    st = opsps.Setup(oracle.Projector(prob.geom), prob.Q, prob.S, prob.y, prob.beta)
+    F = build.fisher(st)
+    aH = build.make_apply_H(st, F)
+    m0 = build.m0_blocks(st, F)[:, 0, 0].reshape(st.shape)
+    return precond.haar_eigenvalues(lambda v: m0[None] * aH(m0[None] * v), st.shape, part=(i, n))
+
+
+def oracle_haar_parallel(oracle_lib, builder, kw, processes=None):
+    """The oracle's Haar preconditioner (Eq. 34 with the lattice test
+    functions) of a seeded problem, its test sets evaluated in spawned
+    processes (single-threaded BLAS each); returns (Setup, preconditioner)."""
+    import multiprocessing as mp
+    import os
+    from oracle import build, precond, psps as opsps
+    prob = getattr(synth, builder)(**kw)
+    st = opsps.Setup(oracle_lib.Projector(prob.geom), prob.Q, prob.S, prob.y, prob.beta)
+    m0 = build.m0_blocks(st, build.fisher(st))[:, 0, 0].reshape(st.shape)
+    try:
+        n = processes or len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = processes or (os.cpu_count() or 1)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(n) as pool:
+            parts = pool.map(_haar_part, [(builder, kw, i, n) for i in range(n)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return st, precond.Haar(sum(parts), m0)

@@ -27,9 +27,15 @@ class ErrorLog:
 
     def __init__(self):
         self.rows = []
+        self.current = ""
+
+    def note(self, error: float):
+        """A relative L2 error computed by the current test (every parity
+        comparison goes through _helpers.rel_l2)."""
+        self.rows.append({"test": self.current, "quantity": "rel_l2", "error": float(error)})
 
     def add(self, test: str, quantity: str, error: float, bound: float, **extra):
-        self.rows.append({"test": test, "quantity": quantity, "error": float(error), "bound": float(bound),
+        self.rows.append({"test": test or self.current, "quantity": quantity, "error": float(error), "bound": float(bound),
                           **{k: (float(v) if isinstance(v, (int, float)) else v) for k, v in extra.items()}})
 
 
@@ -39,6 +45,12 @@ _ERRORS = ErrorLog()
 @pytest.fixture(scope="session")
 def error_log():
     return _ERRORS
+
+
+@pytest.fixture(autouse=True)
+def _error_log_context(request):
+    _ERRORS.current = request.node.nodeid
+    yield
 
 
 def pytest_sessionfinish(session, exitstatus):

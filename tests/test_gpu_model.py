@@ -103,6 +103,59 @@ def test_autograd_adjoint(psps, oracle_lib):
     assert abs(fd - an) <= 1e-3 * abs(an)
 
 
+AUTOGRAD_CASES = {
+    # one-step MBMD, 3 materials x 4 photon-counting channels (101 energies)
+    "c4_64_3mat": lambda: synth.config4_slice(nx=64, n_views=90, n_u=111),
+    # cone-beam one-step MBMD, 2 materials x 2 kVp, 32^3 (the scan scaled down)
+    "c5_32_cone": lambda: synth.config5(n=32, n_views=24, n_u=64, n_v=48),
+}
+
+
+@pytest.mark.parametrize("case", list(AUTOGRAD_CASES))
+def test_autograd_basis_images(psps, oracle_lib, error_log, case):
+    """MBMDData over several basis images (Sec. II-F, Eqs. 43-48): the
+    backward (mbmd_gradient) against the oracle gradient (1e-5), its
+    directional derivative against a central finite difference of the FP64
+    oracle objective (1e-5) and of the GPU forward (1e-3: FP32 objective),
+    and the graph saves only x and y -- l = A x and exp(-Q l) are recomputed
+    in backward, never stored."""
+    import torch
+    from oracle import model
+    prob = AUTOGRAD_CASES[case]()
+    A = oracle_lib.Projector(prob.geom)
+    Q, S, y = prob.Q, prob.S, prob.y
+    x0 = 0.8 * prob.truth
+    plan, spec = psps.Plan(prob.geom), psps.Spectrum(Q, S)
+    yd = to_dev(y)
+    x = to_dev(x0).requires_grad_(True)
+    saved = []
+    with torch.autograd.graph.saved_tensors_hooks(lambda t: saved.append(t.numel()) or t, lambda t: t):
+        L = psps.MBMDData.apply(x, plan, spec, yd)
+    assert sum(saved) <= x.numel() + yd.numel(), saved
+    want_L = model.data_objective(Q, S, A.project(x0), y)
+    assert abs(float(L) - want_L) <= 1e-5 * abs(want_L)
+    L.backward()
+    want = A.backproject(model.data_grad_l(Q, S, A.project(x0), y))
+    e = rel_l2(to_host(x.grad), want)
+    error_log.add(f"autograd {case}", "gradient vs oracle", e, 1e-5)
+    assert e < 1e-5, e
+    v = np.random.default_rng(9).standard_normal(x0.shape) * (np.abs(x0).max(axis=tuple(range(1, x0.ndim)),
+                                                                              keepdims=True) + 1e-3)
+    dg = float(np.sum(to_host(x.grad) * v))
+    h = 1e-4
+    fd_o = (model.data_objective(Q, S, A.project(x0 + h * v), y)
+            - model.data_objective(Q, S, A.project(x0 - h * v), y)) / (2 * h)
+    error_log.add(f"autograd {case}", "directional derivative vs oracle central difference",
+                  abs(dg - fd_o) / abs(fd_o), 1e-5)
+    assert abs(dg - fd_o) <= 1e-5 * abs(fd_o), (dg, fd_o)
+    h = 1e-2
+    with torch.no_grad():
+        fp = float(psps.MBMDData.apply(to_dev(x0 + h * v), plan, spec, yd))
+        fm = float(psps.MBMDData.apply(to_dev(x0 - h * v), plan, spec, yd))
+    fd_g = (fp - fm) / (2 * h)
+    assert abs(dg - fd_g) <= 1e-3 * abs(dg), (dg, fd_g)
+
+
 def test_full_size_projection_domain(psps, oracle_lib):
     """Full projection-domain workload (720 x 888 rays, 2 materials x 2 kVp,
     121 energies): the per-ray gradient numerators of every ray and the data

@@ -33,11 +33,13 @@ def problems():
 OPS = ["M", "MT", "absM", "absMT"]
 
 
-def check_ops(psps, pc, P, shape, tol, seed=3):
+def check_ops(psps, pc, P, shape, tol, seed=3, log=None, name=""):
     v = np.random.default_rng(seed).standard_normal(shape)
     for op in OPS:
         got = to_host(psps.psps_precondition(pc, op, to_dev(v)))
         want = getattr(P, op)(v)
+        if log is not None:
+            log.add(name, f"apply {op}", rel_l2(got, want), tol)
         assert rel_l2(got, want) < tol, (op, rel_l2(got, want))
 
 
@@ -65,16 +67,17 @@ def test_two_sided_apply_parity(psps, oracle_lib, pname, kind):
 
 @pytest.mark.parametrize("pname", ["c1", "c2_64"])
 @pytest.mark.parametrize("kind", ["fourier", "mod_fourier", "haar", "block"])
-def test_build_parity(psps, oracle_lib, pname, kind):
+def test_build_parity(psps, oracle_lib, error_log, pname, kind):
     prob = problems()[pname]
     st, P, _ = oracle_precond(oracle_lib, prob, kind)
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     pc = psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta)
-    check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOL)
+    check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOL, log=error_log,
+              name=f"GPU-built {pname} {kind}")
 
 
 @pytest.mark.parametrize("kind", ["block", "block_fourier", "block_haar"])
-def test_mbmd_apply_and_build(psps, oracle_lib, kind):
+def test_mbmd_apply_and_build(psps, oracle_lib, error_log, kind):
     """One-step MBMD (3 materials): per-pixel 3x3 blocks, the cross-material
     Fourier (Eq. 57) and the cross-material wavelet (Eq. 61) preconditioners,
     created from the oracle's data (apply tolerance) and built on the GPU
@@ -84,7 +87,8 @@ def test_mbmd_apply_and_build(psps, oracle_lib, kind):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (3,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL,
+              log=error_log, name=f"GPU-built c4_64 {kind}")
 
 
 def test_projection_domain_block(psps, oracle_lib):

@@ -422,3 +422,19 @@ def test_abs_bounds_dominate_3d(oracle_lib):
         Ad = dense(P.absM, st.shape)
         assert np.allclose(dense(P.MT, st.shape), Md.T, atol=1e-12 * np.abs(Md).max())
         assert (Ad >= np.abs(Md) - 1e-12 * np.abs(Md).max()).all(), kind
+
+
+def test_haar_eigenvalue_parts_add_up():
+    """Splitting the Haar test sets among processes (part = (i, n)) gives
+    the whole estimate once the parts are added."""
+    from oracle import haar, precond
+    shape = (16, 16)
+    rng = np.random.default_rng(13)
+    A = rng.standard_normal((256, 256))
+    Hd = A @ A.T + 256 * np.eye(256)
+
+    def apply_H(v):
+        return (Hd @ v.reshape(v.shape[0], -1).T).T.reshape(v.shape)
+    whole = precond.haar_eigenvalues(apply_H, shape)
+    parts = sum(precond.haar_eigenvalues(apply_H, shape, part=(i, 3)) for i in range(3))
+    assert np.array_equal(parts, whole)
