@@ -481,7 +481,7 @@ def ours(args, prob, workload=WORKLOAD, kind="haar", desc="", blur=None, noise=N
             "config": {"workload": workload, "problem": desc or WORKLOADS[workload][2], "precond": kind,
                        "line_search": True, "graph": True,
                        "l2": "flushed (256 MB write) between timed steps", "build_s": round(build_s, 3),
-                       "views_per_cta": tuned},
+                       "views_per_cta": tuned, "tuning": plan.tuning() if plan is not None else None},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline,
             "e2e": {"value": world * args.steps / e2e_s, "unit": "iter/s",
                     "h2d_bytes_per_step": int(y_host.numel() * 4), "d2h_bytes_per_step": 2 * 8 + DEVLS_BYTES}}
@@ -674,8 +674,35 @@ def kernel_bench(args, prob):
     plan = p.Plan(prob.geom)
     rng = np.random.default_rng(0)
     x1 = torch.as_tensor(prob.truth.astype(np.float32), device=dev)
-    s2 = torch.as_tensor(rng.random((2, plan.n_rays)).astype(np.float32), device=dev)
     out = {}
+    if prob.geom.kind == 2:
+        # cone beam: forward of the basis images, and the 2 n_mat-channel
+        # transposes (split-table gather, direct gather)
+        nm = x1.shape[0]
+        s4 = torch.as_tensor(rng.random((2 * nm, plan.n_rays)).astype(np.float32), device=dev)
+        l = torch.empty((nm, plan.n_rays), device=dev)
+        img = torch.empty((2 * nm,) + plan.image_shape, device=dev)
+
+        def timec(fn, reps=5):
+            fn()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+        out[f"project_{nm}ch_ms"] = timec(lambda: p.mbir_project(plan, x1, l))
+        for mode in ["tile", "gather"]:
+            plan.set_backprojector(mode)
+            out[f"backproject_{'split' if mode == 'tile' else 'gather'}_{2 * nm}ch_ms"] = timec(
+                lambda: p.mbir_backproject(plan, s4, img))
+        print(json.dumps({"kernels": out, "workload": args.workload}), flush=True)
+        return
+    s2 = torch.as_tensor(rng.random((2, plan.n_rays)).astype(np.float32), device=dev)
 
     def timeit(fn, reps=20):
         fn()
@@ -691,9 +718,13 @@ def kernel_bench(args, prob):
         return float(np.median(ts))
     l1 = torch.empty((1, plan.n_rays), device=dev)
     g2 = torch.empty((2,) + plan.image_shape, device=dev)
-    for mode in ["tile", "ray"]:
+    x3 = torch.as_tensor(np.concatenate([prob.truth] * 3).astype(np.float32), device=dev)
+    l3 = torch.empty((3, plan.n_rays), device=dev)
+    for mode in ["tile", "ray", "strip"]:
         plan.set_projector(mode)
         out[f"project_{mode}_1ch_ms"] = timeit(lambda: p.mbir_project(plan, x1, l1))
+        out[f"project_{mode}_3ch_ms"] = timeit(lambda: p.mbir_project(plan, x3, l3))
+    plan.set_projector("ray")
     for mode in ["tile", "gather", "atomic"]:
         plan.set_backprojector(mode)
         out[f"backproject_{mode}_2ch_ms"] = timeit(lambda: p.mbir_backproject(plan, s2, g2))
@@ -723,7 +754,11 @@ def main():
     args = ap.parse_args()
     import synth
     if args.kernels:
-        kernel_bench(args, synth.config2())
+        if args.workload.startswith("c5"):       # geometry and phantom only
+            kw = dict(WORKLOADS[args.workload][3]) if len(WORKLOADS[args.workload]) > 3 else {}
+            kernel_bench(args, synth.config5(**kw, rays=False))
+        else:
+            kernel_bench(args, synth.config2())
         return
     if args.impl == "reference":
         reference_arm(args)

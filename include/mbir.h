@@ -83,9 +83,14 @@ typedef struct psps_state psps_state;
 
 /* ---------------------------------------------------------------- projector */
 
-/* Create a projector plan for one geometry: precomputes the per-ray Joseph
- * set-up (FP64 on the device, stored FP32) and owns the projector's scratch.
- * n_mat_max bounds the number of channels later calls may pass (1..8). */
+/* Create a projector plan for one geometry: the system matrix A of the mean
+ * model (Eq. 1; A for standard CT, Eqs. 19-20; applied per basis material in
+ * one-step MBMD, Eq. 44), which the paper leaves unspecified and this library
+ * realises as Joseph's method (pixel-driven interpolation along each ray).
+ * Precomputes the per-ray Joseph set-up (FP64 on the device, stored FP32) and
+ * owns the projector's scratch.  n_mat_max bounds the number of channels
+ * later calls may pass (1..8).  MBIR_ERR_ARG for an invalid geometry,
+ * MBIR_ERR_OOM if device memory runs out; *out is NULL on error. */
 mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, mbir_plan **out);
 mbir_status mbir_plan_destroy(mbir_plan *plan);
 /* Number of rays (sinogram entries per channel) and pixels of a plan. */
@@ -112,9 +117,10 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
  * that reach one pixel: a few for detector bins no finer than the pixels,
  * more for finer bins); the sums are exact integer sums, so the result is
  * bitwise reproducible.  A non-finite input makes its channel's image NaN.
- * It needs 8 bytes x n_mat_max x n_pix of plan scratch.  3-D (cone): 0 and 1 =
- * voxel-driven gather (default, deterministic), 2 = ray-driven scatter with
- * global FP32 atomics.  All use the forward projector's per-ray weights and
+ * It needs 8 bytes x n_mat_max x n_pix of plan scratch.  3-D (cone): 0 =
+ * voxel-driven gather with per-plane split tables in shared memory (default),
+ * 1 = the direct voxel-driven gather (both deterministic and bitwise equal),
+ * 2 = ray-driven scatter with global FP32 atomics.  All use the forward projector's per-ray weights and
  * are the exact transpose of mbir_project up to FP32 rounding.  MBIR_ERR_ARG
  * for another mode. */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
@@ -125,19 +131,37 @@ mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
  * one accumulator receives), not the result's definition.
  * MBIR_ERR_ARG outside 1..180. */
 mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
-/* Autotuner: times the 2-D tile transpose (n_channels channels, zero data, a
- * warm-up and three launches per candidate, CUDA events on `stream`) for
- * 4/8/15/30/45/60/90/120/180 views per CTA and keeps the fastest in the plan
- * (written to *views_per_cta if non-NULL).  Synchronises; allocates and frees
- * temporary device buffers; not allowed while `stream` is capturing
- * (MBIR_ERR_ARG).  Cone-beam plans have nothing to tune and return at once.
- * MBIR_ERR_ARG if n_channels is outside 1..n_mat_max. */
+/* Autotuner (the paper has no counterpart; it picks work shapes, never the
+ * operator): times candidates with zero data (a warm-up and up to three
+ * launches each, CUDA events on `stream`) and keeps the fastest in the plan.
+ * 2-D plans: the tile transpose of n_channels channels for 4/8/15/30/45/60/
+ * 90/120/180 views per CTA (written to *views_per_cta if non-NULL), then the
+ * forward projection of n_channels / 2 (at least 1) basis images by one
+ * thread per ray and by the strip kernel with 32/64/128/256 bins (and
+ * 256 / that many views) per CTA.  Cone-beam plans: the split-table and the
+ * direct voxel gather (bitwise equal results), then the forward's per-lane
+ * and warp-aligned marches (mbir_plan_set_projector modes 1 and 2; equal
+ * results).  Synchronises; allocates and
+ * frees temporary device buffers; not allowed while `stream` is capturing
+ * (MBIR_ERR_ARG).  MBIR_ERR_ARG if n_channels is outside 1..n_mat_max; on
+ * any error the plan keeps its previous choices. */
 mbir_status mbir_plan_autotune(mbir_plan *plan, int n_channels, mbir_stream stream, int *views_per_cta);
-/* Select the forward projector's algorithm: 0 = per-tile partial sums through
- * shared memory, combined with one FP32 atomic per (tile, ray); 1 = one thread
- * per ray with Kahan-compensated sums (default; deterministic, and faster on
- * one channel: 0.27 vs 0.43 ms on 512^2 / 720 x 888 fan beam).  Same Joseph
- * weights. */
+/* Bins per CTA of the strip forward (mode 2): 32, 64, 128 or 256, with
+ * 256 / bins views per CTA; MBIR_ERR_ARG otherwise.  Work split only. */
+mbir_status mbir_plan_set_strip_bins(mbir_plan *plan, int bins);
+/* The plan's current choices (any pointer may be NULL): forward algorithm
+ * (mbir_plan_set_projector's modes), strip bins per CTA, transpose mode and
+ * tile-transpose views per CTA. */
+mbir_status mbir_plan_tuning(const mbir_plan *plan, int *fwd_mode, int *strip_bins, int *back_mode, int *back_views);
+/* Select the forward projector's algorithm (Eq. 1's A).  2-D: 0 = per-tile
+ * partial sums through shared memory, combined with one FP32 atomic per
+ * (tile, ray); 1 = one thread per ray with Kahan-compensated sums, gathering
+ * from L1/L2 (deterministic); 2 = rays of a block of views and bins march
+ * shared-memory strips of the image, every lane on the same driving index
+ * (deterministic).  Cone beam: one thread per ray; 1 (and 0) = each lane
+ * marches its own range, 2 = the lanes of a warp march the same plane index
+ * (same samples and sums).  All use the same per-ray Joseph weights.
+ * MBIR_ERR_ARG for other modes. */
 mbir_status mbir_plan_set_projector(mbir_plan *plan, int mode);
 
 /* ------------------------------------------------------- spectral model */
@@ -243,8 +267,8 @@ mbir_status mbmd_objective_noalloc(int n_mat, int n_energy, int n_chan, const do
 enum {
     PSPS_PRECOND_NONE = 0,          /* M = I: plain SPS (Sec. II-B)                   */
     PSPS_PRECOND_FOURIER = 1,       /* M = U^H Lambda^-1/2 U (Eq. 29)                 */
-    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U [M0] (Eqs. 30-33)     */
-    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT [M0] (Eq. 34) */
+    PSPS_PRECOND_MOD_FOURIER = 2,   /* M = M0 U^H Lambda^-1/2 U M0 (Eqs. 30-33)       */
+    PSPS_PRECOND_HAAR = 3,          /* M = M0 U_DWT^T Lambda^-1/2 U_DWT M0 (Eq. 34)   */
     PSPS_PRECOND_BLOCK = 4,         /* per-pixel / per-ray N_k x N_k M0 (Eqs. 42, 54) */
     PSPS_PRECOND_BLOCK_FOURIER = 5, /* cross-material Fourier (Eqs. 56-57)            */
     PSPS_PRECOND_BLOCK_HAAR = 6     /* cross-material wavelet (Eqs. 58-61)            */
@@ -296,11 +320,15 @@ mbir_status psps_precondition_destroy(psps_precond *pc);
  * BLOCK_FOURIER, BLOCK_HAAR; FOURIER and BLOCK are unaffected).  The paper
  * writes M = M0^T C M0 (Eqs. 33, 34, 57, 61) with C = U^H Lambda~^-1/2 U built
  * from the spectrum of N = M0^T H M0; then M^T H M = M0^T M0 where N is
- * diagonal in U, not the I that Sec. II-C aims for.  sides = 1 (the default
- * of every build and create) applies M = M0^T C, so that M^T H M = C N C = I
- * there; sides = 2 applies the literal two-sided form.  Call it before
- * psps_state_create: a state precomputes A|M|1 and |M|^T|R||M|1 from the
- * preconditioner it is given.  sides other than 1 or 2 return MBIR_ERR_ARG. */
+ * diagonal in U, not the I that Sec. II-C aims for.  With one material that
+ * remainder is diagonal and the separable curvature absorbs it: MOD_FOURIER
+ * and HAAR default to the literal form (sides = 2).  With per-pixel blocks it
+ * couples the materials of a pixel, which a separable surrogate cannot
+ * absorb: BLOCK_FOURIER and BLOCK_HAAR default to the one-sided M = M0^T C
+ * (sides = 1), for which M^T H M = C N C = I there.  This call overrides the
+ * default.  Call it before psps_state_create: a state precomputes A|M|1 and
+ * |M|^T|R||M|1 from the preconditioner it is given.  sides other than 1 or 2
+ * return MBIR_ERR_ARG. */
 mbir_status psps_precondition_set_sides(psps_precond *pc, int sides);
 
 /* Copy one array of a preconditioner into caller-owned device memory (for
@@ -329,8 +357,14 @@ enum { PSPS_EXPORT_SCALES = 0, PSPS_EXPORT_BLOCKS = 1, PSPS_EXPORT_M0 = 2, PSPS_
        PSPS_EXPORT_ESTIMATE = 4 };
 mbir_status psps_precondition_export(psps_precond *pc, int what, float *out, int64_t n_out, mbir_stream stream);
 
-/* out = op(M) in for op in PSPS_APPLY_*, arrays shaped like the unknowns
- * ([n_mat][image] or [n_mat][n_rays]); in and out must not alias. */
+/* out = op(M) in for op in PSPS_APPLY_*: the change of variables x = M x'
+ * of Sec. II-C (Eq. 15) with the preconditioner's M (Eqs. 29, 33, 34, 42, 57,
+ * 61), its transpose (the preconditioned gradient M^T grad, Eq. 5 for A M),
+ * and the elementwise bounds |M|, |M|^T that the separable curvature of the
+ * preconditioned problem uses (Eqs. 6 and 8 with A M).  Arrays device,
+ * caller-owned, shaped like the unknowns ([n_mat][image] or
+ * [n_mat][n_rays]); in and out must not alias (MBIR_ERR_ARG).  Asynchronous
+ * on `stream`. */
 mbir_status psps_precondition(psps_precond *pc, int op, const float *in, float *out, mbir_stream stream);
 
 /* ------------------------------------------------------------ iteration */
@@ -341,21 +375,31 @@ enum {
     PSPS_FLAG_GRAPH = 4       /* replay each iteration as a captured CUDA graph */
 };
 
-/* Create an iteration state: copies y (device [n_chan][n_rays]), beta (host
- * [n_mat][n_mat], NULL = 0) and x0 (device image, NULL = 0); pc == NULL runs
- * plain SPS.  The state keeps x, l = A x (updated incrementally, recomputed
- * exactly every `reproject_every` iterations), the precomputed
- * gamma~ = A|M|1 and |M|^T|R||M|1, and the objective history on the device.
- * Synchronises `stream`. */
+/* Create an iteration state for the PWLS estimate of Eqs. 2-3 (penalty
+ * Eqs. 26, 49-52) solved by SPS on x' with x = M x' (Sec. II-B, Eqs. 4-7, on
+ * the preconditioned model of Eq. 15): copies y (device [n_chan][n_rays]),
+ * beta (host [n_mat][n_mat], NULL = 0) and x0 (device image, NULL = 0);
+ * pc == NULL runs plain SPS.  The state keeps x, l = A x (updated
+ * incrementally, recomputed exactly every `reproject_every` iterations), the
+ * precomputed gamma~ = A|M|1 (gamma of Eq. 9 for A M) and |M|^T|R||M|1, and
+ * the objective history on the device.  The library owns the state (free it
+ * with psps_state_destroy); the plan, spectrum and preconditioner must
+ * outlive it.  MBIR_ERR_ARG on size or argument mismatches, MBIR_ERR_OOM if
+ * device memory runs out.  Synchronises `stream`. */
 mbir_status psps_state_create(mbir_plan *plan, const mbmd_spectrum *spec, psps_precond *pc, const float *y,
                               int64_t n_rays, const double *beta, const float *x0, int flags,
                               int reproject_every, mbir_stream stream, psps_state **out);
 mbir_status psps_state_destroy(psps_state *st);
 
-/* Run n_iter iterations on `stream` (asynchronous).  If objective_history
+/* Run n_iter iterations on `stream` (asynchronous): per iteration the SPS
+ * numerators (Eqs. 8-11), the preconditioned gradient and separable curvature
+ * (Eqs. 5-6 for A M), the direction p' = -grad'/d' of the surrogate's
+ * minimiser (Eq. 7), p = M p', the line search along p (with
+ * PSPS_FLAG_LINESEARCH) and the update x += alpha p.  If objective_history
  * (HOST, length n_iter + 1) is non-NULL the call synchronises and writes
  * Phi before each iteration and after the last one (after an exact
- * re-projection).  Returns MBIR_ERR_NONFINITE if a reduction went non-finite. */
+ * re-projection).  Returns MBIR_ERR_NONFINITE if a reduction went non-finite,
+ * MBIR_ERR_ARG for n_iter < 0. */
 mbir_status psps_step(psps_state *st, int n_iter, double *objective_history, mbir_stream stream);
 
 /* Replace the measured counts y of the state (n = n_chan * n_rays values,
@@ -365,8 +409,11 @@ mbir_status psps_step(psps_state *st, int n_iter, double *objective_history, mbi
  * state are kept (Eq. 3 with the new y).  MBIR_ERR_ARG if n does not match. */
 mbir_status psps_state_set_data(psps_state *st, const float *y, int64_t n, mbir_stream stream);
 
-/* Copy the current image x (device, [n_mat][image]) / step lengths (host,
- * the last n alphas of the most recent psps_step call; synchronises). */
+/* Copy the current image x = M x' (Eq. 15: the estimate of Eq. 2 in the
+ * original variables; device, caller-owned, [n_mat][image] or
+ * [n_mat][n_rays], asynchronous on `stream`) / step lengths (host, the last n
+ * alphas of the most recent psps_step call; synchronises).  MBIR_ERR_ARG for
+ * NULL pointers or n outside the recorded range. */
 mbir_status psps_get_image(psps_state *st, float *x, mbir_stream stream);
 mbir_status psps_get_alphas(psps_state *st, double *alphas, int n, mbir_stream stream);
 

@@ -51,10 +51,13 @@ def m0_blocks(st: Setup, F: np.ndarray) -> np.ndarray:
     return precond.inv_sqrt_blocks(H, floor="block", zero_rule=True)
 
 
-def build(st: Setup, kind: str, sides: int = 1):
+def build(st: Setup, kind: str, sides: int | None = None):
     """The preconditioner of one kind; sides: where M0 enters the Fourier and
-    wavelet kinds (1: M = M0 C, the default reading; 2: the literal
-    M0 C M0 of Eqs. 33, 34, 57, 61)."""
+    wavelet kinds (1: M = M0^T C; 2: the literal M0^T C M0 of Eqs. 33, 34, 57,
+    61); None: each kind's default (2 for the one-material kinds, 1 for the
+    cross-material ones; see ``precond``)."""
+    if sides is None:
+        sides = 1 if kind in ("block_fourier", "block_haar") else 2
     if kind == "none":
         return precond.Identity()
     F = fisher(st)

@@ -31,10 +31,15 @@ Readings of the paper used here:
 * Where M0 goes (Eqs. 33, 34, 57, 61).  The paper writes M = M0^T U^H
   Lambda~^-1/2 U M0 with Lambda~ the spectrum of N = M0^T H M0.  Then
   M^T H M = M0^T C N C M0 = M0^T M0 when N is diagonal in U (C = U^H
-  Lambda~^-1/2 U), not the I that Sec. II-C sets as the goal, and M M^T is
-  not an approximate inverse of H.  The one-sided M = M0 C gives
-  M^T H M = C N C = I in that case and M M^T = M0 N^-1 M0^T = H^-1; it is the
-  default (``sides=1``); ``sides=2`` keeps the literal two-sided form.
+  Lambda~^-1/2 U), not the I that Sec. II-C sets as the goal.  For a scalar
+  M0 (one material) that remainder is diagonal and the separable SPS
+  curvature absorbs it, so the literal form is kept there (``sides=2``, the
+  default of Fourier and Haar).  For per-pixel N_k x N_k blocks the
+  remainder M0^T M0 couples the materials of a pixel, which a separable
+  surrogate cannot absorb (the literal cross-material Fourier PSPS does not
+  converge on the 3-material slice); there the one-sided M = M0^T C is used
+  (``sides=1``, the default of CrossFourier and CrossHaar), for which
+  M^T H M = C N C = I and M M^T = M0^T N^-1 M0 = H^-1 in that case.
 * M0 = D{(F+R)1}^-1/2 (Eq. 30) or, with several materials, the per-pixel /
   per-ray N_k x N_k blocks of (F+R)1_k (Eqs. 42, 53-54) raised to -1/2; a
   block's eigenvalues are clamped to >= 1e-6 x its largest one, and pixels
@@ -131,12 +136,12 @@ def clamp_eigs(lam: np.ndarray) -> np.ndarray:
 
 
 class Fourier:
-    """M = m0 C with C = U^H diag(lam^-1/2) U (Eq. 29 with m0 = 1, Eq. 33 with
-    the zero-frequency normalisation m0 = M0 of Eq. 30); sides=2: the literal
-    m0 C m0.  One material.  |M| = m0 |C| (m0 |C| m0) with |C| the circulant
-    of the absolute kernel |IDFT(lam^-1/2)|."""
+    """M = m0 C m0 with C = U^H diag(lam^-1/2) U (Eq. 29 with m0 = 1, Eq. 33
+    with the zero-frequency normalisation m0 = M0 of Eq. 30; sides=1: the
+    one-sided m0 C).  One material.  |M| = m0 |C| m0 (m0 |C|) with |C| the
+    circulant of the absolute kernel |IDFT(lam^-1/2)|."""
 
-    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None, sides: int = 1):
+    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None, sides: int = 2):
         self.s = 1.0 / np.sqrt(clamp_eigs(lam))
         self.shape = lam.shape
         self.m0 = np.ones(self.shape) if m0 is None else np.asarray(m0, dtype=np.float64).reshape(self.shape)
@@ -241,11 +246,11 @@ def polar_real(L: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 class Haar:
-    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT (Eq. 34 with M0 on one side; sides=2:
-    the literal M0 U^T Lambda~^-1/2 U M0); |M| uses |U| and |M0|.  One
-    material, 2-D images or 3-D volumes."""
+    """M = M0 U_DWT^T Lambda~^-1/2 U_DWT M0 (Eq. 34; sides=1: the one-sided
+    M0 U^T Lambda~^-1/2 U); |M| uses |U| and |M0|.  One material, 2-D images
+    or 3-D volumes."""
 
-    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None, sides: int = 1):
+    def __init__(self, lam: np.ndarray, m0: np.ndarray | None = None, sides: int = 2):
         self.s = 1.0 / np.sqrt(clamp_eigs(lam))
         self.shape = lam.shape
         self.m0 = np.ones(self.shape) if m0 is None else np.asarray(m0, dtype=np.float64).reshape(self.shape)

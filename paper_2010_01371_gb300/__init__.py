@@ -93,9 +93,24 @@ class Plan:
         _call(lib().mbir_plan_autotune, self.h, int(n_channels), _stream(), ctypes.byref(v))
         return int(v.value)
 
+    def set_strip_bins(self, bins: int):
+        """Bins per CTA of the strip forward (32, 64, 128, 256)."""
+        _call(lib().mbir_plan_set_strip_bins, self.h, int(bins))
+
+    def tuning(self) -> dict:
+        """The plan's current choices (``mbir_plan_tuning``)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _call(lib().mbir_plan_tuning, self.h, *[ctypes.byref(x) for x in v])
+        names = {0: "tile", 1: "ray", 2: "strip"}
+        return {"forward": names[v[0].value], "strip_bins": v[1].value, "backproject_mode": v[2].value,
+                "views_per_cta": v[3].value}
+
     def set_projector(self, mode: str):
-        """'ray' (default: one thread per ray, deterministic) or 'tile'."""
-        _call(lib().mbir_plan_set_projector, self.h, {"tile": 0, "ray": 1}[mode])
+        """2-D: 'ray' (one thread per ray), 'strip' (shared-memory strips) or
+        'tile'; cone beam: 'ray' (each lane marches its own range) or
+        'aligned' (the lanes of a warp march together; the same mode number
+        as 'strip')."""
+        _call(lib().mbir_plan_set_projector, self.h, {"tile": 0, "ray": 1, "strip": 2, "aligned": 2}[mode])
 
     def __del__(self):
         if getattr(self, "h", None) and _abi._lib is not None:
@@ -209,12 +224,13 @@ class Precond:
     """One-time preconditioner build (``psps_precondition_build``)."""
 
     def __init__(self, plan: Plan | None, spec: Spectrum, kind: str, y=None, beta=None, haar_lattice: int = 3,
-                 lam=None, m0=None, blocks=None, sides: int = 1):
+                 lam=None, m0=None, blocks=None, sides: int | None = None):
         """Build from data (``y``) or, when ``lam`` / ``blocks`` is given,
         create from precomputed eigenvalues / blocks
         (``psps_precondition_create``).  sides: M = M0^T C (1) or the
         literal M0^T C M0 (2) for the Fourier and wavelet kinds
-        (``psps_precondition_set_sides``)."""
+        (``psps_precondition_set_sides``); None keeps the kind's default (2
+        for one material, 1 for the cross-material kinds)."""
         self.sides = sides
         self.kind = kind
         self.plan, self.spec = plan, spec
@@ -227,7 +243,7 @@ class Precond:
                   _dev(lam, "lam") if lam is not None else None, _dev(m0, "m0") if m0 is not None else None,
                   _dev(blocks, "blocks") if blocks is not None else None, _stream(), ctypes.byref(h))
             self.h = h
-            if sides != 1:
+            if sides is not None:
                 _call(lib().psps_precondition_set_sides, h, int(sides))
             return
         n_rays = y.numel() // spec.n_chan
@@ -239,7 +255,7 @@ class Precond:
         _call(lib().psps_precondition_build, plan.h if plan else None, spec.h, PSPS_PRECOND[kind], _dev(y, "y"),
               int(n_rays), b, int(haar_lattice), _stream(), ctypes.byref(h))
         self.h = h
-        if sides != 1:
+        if sides is not None:
             _call(lib().psps_precondition_set_sides, h, int(sides))
 
     def __del__(self):

@@ -219,7 +219,8 @@ struct mbir_plan {
     psps::DBuf<float4> view;      // parallel: (cos, sin, -, -); fan: (sx, sy, beta + pi, -)
     int back_mode = 0;            // 0 tile scatter (default), 1 pixel gather, 2 ray-driven atomics
     int back_views = 60;          // views per CTA of the tile transpose
-    int fwd_mode = 1;             // 0 tile sums, 1 one thread per ray (default)
+    int fwd_mode = 1;             // 0 tile sums, 1 one thread per ray (default), 2 shared-memory strips
+    int strip_bins = 64;          // strip forward: bins per CTA (32, 64, 128 or 256; 256 / it views)
     // 3-D per-ray Joseph set-up (cone_ray, computed once): (fb_mid, dfb,
     // fc_mid, dfc) in `ray` and (weight, bits(axis | lo << 2 | hi << 17)) in
     // ray3b; per view, the set of driving axes its rays use (bit a)

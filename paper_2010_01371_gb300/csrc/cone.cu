@@ -202,17 +202,37 @@ struct P3<4> {
     }
 };
 
-template <int NM>
+// ALIGNED: the lanes of a warp (neighbouring detector columns of one row)
+// step the same driving index over the union of their ranges, each adding
+// only inside its own range, so that one load instruction of the warp reads
+// neighbouring voxels of one plane (a few cache lines) instead of one plane
+// per lane.  Same samples, weights and summation order either way.
+template <int NM, bool ALIGNED>
 __global__ void __launch_bounds__(kThreads)
     fwd_cone_kernel(mbir_geometry g, const float4 *__restrict__ ta, const float2 *__restrict__ tb,
                     const typename P3<NM>::T *__restrict__ ox, const typename P3<NM>::T *__restrict__ oy,
                     const typename P3<NM>::T *__restrict__ oz, int nm, int64_t n_rays, float *__restrict__ l) {
     const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray >= n_rays) return;
-    const float4 A = ta[ray];
-    const float2 B = tb[ray];
+    if (ALIGNED) {
+        if (((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >= n_rays) return;   // whole warp past the end
+    } else if (ray >= n_rays) {
+        return;
+    }
+    const bool live = ray < n_rays;
+    const float4 A = live ? ta[ray] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 B = live ? tb[ray] : make_float2(0.f, __int_as_float(1 << 2));   // empty range lo 1 > hi 0
     int axis, lo, hi;
     decode3(B, axis, lo, hi);
+    int i_lo = lo, i_hi = hi;
+    if (ALIGNED) {
+        // rays that miss the volume (lo > hi) do not widen the warp's range
+        if (lo > hi) i_lo = 0x7fffffff, i_hi = -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            i_lo = min(i_lo, __shfl_xor_sync(0xffffffffu, i_lo, o));
+            i_hi = max(i_hi, __shfl_xor_sync(0xffffffffu, i_hi, o));
+        }
+    }
     const typename P3<NM>::T *src = axis == 0 ? ox : (axis == 1 ? oy : oz);
     const int nb = axis == 0 ? g.ny : g.nx;
     const int nc = axis == 2 ? g.ny : g.nz;
@@ -220,7 +240,8 @@ __global__ void __launch_bounds__(kThreads)
     float acc[NM], comp[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
-    for (int i = lo; i <= hi; ++i) {
+    for (int i = i_lo; i <= i_hi; ++i) {
+        if (ALIGNED && (i < lo || i > hi)) continue;
         const float t = (float)i - ca;
         float gb, gc;
         const int ib0 = joseph_split(fmaf(t, A.y, A.x), gb), ic0 = joseph_split(fmaf(t, A.w, A.z), gc);
@@ -251,6 +272,7 @@ __global__ void __launch_bounds__(kThreads)
             acc[m] = tt;
         }
     }
+    if (!live) return;
 #pragma unroll
     for (int m = 0; m < NM; ++m)
         if (m < nm) l[(int64_t)m * n_rays + ray] = acc[m] * B.x;
@@ -542,6 +564,195 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
     }
 }
 
+// The detector box of the whole tile's footprint for driving axis A != 2,
+// computed by the lanes of one warp (lanes 0-3 project one corner each) and
+// shared by shuffles, so no barrier is needed for it: every warp gets the
+// same box.  Same bounds as footprint_box<4> of the tile corners.
+template <int A>
+__device__ __forceinline__ bool tile_box_warp(const mbir_geometry &g, const float4 &V, float tx0, float tx1, float ty0,
+                                              float ty1, float tz0, float tz1, int &iu0, int &iu1, int &iv0,
+                                              int &iv1) {
+    const float dx = (float)g.dx, dy = (float)g.dy, dz = (float)g.dz;
+    const int lane = threadIdx.x & 31;
+    const float xa = A == 0 ? tx0 : tx0 - dx, xb = A == 0 ? tx1 : tx1 + dx;
+    const float ya = A == 1 ? ty0 : ty0 - dy, yb = A == 1 ? ty1 : ty1 + dy;
+    const int k = lane & 3;
+    const float qx = ((k & 1) ? xb : xa) - V.x, qy = ((k >> 1) ? yb : ya) - V.y;
+    const float depth = -(qx * V.z + qy * V.w);
+    const float inv = (float)g.sdd / depth;
+    float u = (-qx * V.w + qy * V.z) * inv;
+    float umin = u, umax = u, imin = inv, imax = inv;
+    int behind = depth > 0.f ? 0 : 1;
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        imin = fminf(imin, __shfl_xor_sync(0xffffffffu, imin, o));
+        imax = fmaxf(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+        behind |= __shfl_xor_sync(0xffffffffu, behind, o);
+    }
+    if (behind) return false;
+    const float za = tz0 - dz, zb = tz1 + dz;
+    const float wmin = fminf(fminf(za * imin, za * imax), fminf(zb * imin, zb * imax));
+    const float wmax = fmaxf(fmaxf(za * imin, za * imax), fmaxf(zb * imin, zb * imax));
+    const float inv_du = (float)(1.0 / g.du), inv_dv = (float)(1.0 / g.dv);
+    const float cu = 0.5f * (g.n_u - 1), cv = 0.5f * (g.n_v - 1);
+    constexpr float eps = 1.0e-3f;
+    iu0 = max((int)ceilf(fmaxf(umin * inv_du + cu - eps, -2.0e9f)), 0);
+    iu1 = min((int)floorf(fminf(umax * inv_du + cu + eps, 2.0e9f)), g.n_u - 1);
+    iv0 = max((int)ceilf(fmaxf(wmin * inv_dv + cv - eps, -2.0e9f)), 0);
+    iv1 = min((int)floorf(fminf(wmax * inv_dv + cv + eps, 2.0e9f)), g.n_v - 1);
+    return true;
+}
+
+// Voxel-driven exact transpose with split tables (default).  Same tiles,
+// candidate boxes and staging as back_cone_gather_kernel, but the staging
+// also evaluates, for every staged detector cell and each of the tile's
+// kPlanes driving planes (x- or y-driven rays), the ray's Joseph split on
+// that plane: lower indices (ib0, ic0) packed in one word and the upper
+// weights (gb, gc).  Those are the same for every voxel of the plane, so a
+// voxel's candidate test is two integer compares against its own indices and
+// its weight two shared-memory loads -- the arithmetic of the split leaves
+// the per-(voxel, cell) loop.  Cells of another driving axis, and samples
+// whose taps cannot reach the volume, get a code no voxel matches.  Same
+// weights and summation order as back_cone_gather_kernel, so the two give
+// bitwise the same image; z-driven rays and boxes larger than the staging
+// area take that kernel's global-memory path.
+constexpr int kPlanes = 4;
+static_assert(kGX == kPlanes && kGY == kPlanes, "one split table per driving plane of the tile");
+constexpr unsigned kNoCell = 0xffffffffu;
+
+template <int C>
+__global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
+    back_cone_split_kernel(mbir_geometry g, const float4 *__restrict__ vt, const float4 *__restrict__ ta,
+                           const float2 *__restrict__ tb, const int *__restrict__ view_axes,
+                           const typename Vec<C>::T *__restrict__ ws, int nc, float *__restrict__ x,
+                           int accumulate) {
+    __shared__ unsigned s_ij[kPlanes][kStageCap];
+    __shared__ float2 s_f[kPlanes][kStageCap];
+    __shared__ typename Vec<C>::T s_ws[kStageCap];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kGX, y0 = blockIdx.y * kGY, z0 = blockIdx.z * kGZ;
+    const int ix = x0 + tid % kGX, iy = y0 + (tid / kGX) % kGY, iz = z0 + tid / (kGX * kGY);
+    const bool inside = ix < g.nx && iy < g.ny && iz < g.nz;
+    const float dx = (float)g.dx, dy = (float)g.dy, dz = (float)g.dz;
+    const float cx = 0.5f * (g.nx - 1), cy = 0.5f * (g.ny - 1), cz = 0.5f * (g.nz - 1);
+    const float px = (ix - cx) * dx, py = (iy - cy) * dy, pz = (iz - cz) * dz;
+    const float tx0 = (x0 - cx) * dx, tx1 = (min(x0 + kGX, g.nx) - 1 - cx) * dx;
+    const float ty0 = (y0 - cy) * dy, ty1 = (min(y0 + kGY, g.ny) - 1 - cy) * dy;
+    const float tz0 = (z0 - cz) * dz, tz1 = (min(z0 + kGZ, g.nz) - 1 - cz) * dz;
+    const int *tbits = reinterpret_cast<const int *>(tb);  // (w, bits) pairs: bits at odd indices
+    float acc[C], comp[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = comp[c] = 0.f;
+    for (int v = 0; v < g.n_views; ++v) {
+        const int axes = view_axes[v];
+        if (!axes) continue;
+        const float4 V = vt[v];  // (sx, sy, cos beta, sin beta)
+        const bool mixed = (axes & (axes - 1)) != 0;
+        const int64_t view0 = (int64_t)v * g.n_u * g.n_v;
+        float sv[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) sv[c] = 0.f;
+#pragma unroll
+        for (int A = 0; A < 3; ++A) {
+            if (!((axes >> A) & 1)) continue;
+            float xs[2], ys[2], zs[2];
+            int iu0, iu1, iv0, iv1;
+            if (A == 0) {
+                voxel_footprint<0>(g, px, py, pz, xs, ys, zs);
+                footprint_box<2>(g, V, xs, ys, zs, iu0, iu1, iv0, iv1);
+            } else if (A == 1) {
+                voxel_footprint<1>(g, px, py, pz, xs, ys, zs);
+                footprint_box<2>(g, V, xs, ys, zs, iu0, iu1, iv0, iv1);
+            } else {
+                voxel_footprint<2>(g, px, py, pz, xs, ys, zs);
+                footprint_box<4>(g, V, xs, ys, zs, iu0, iu1, iv0, iv1);
+            }
+            int su0 = 0, su1 = -1, sv0 = 0, sv1 = -1;
+            bool staged = false;
+            if (A == 0)
+                staged = tile_box_warp<0>(g, V, tx0, tx1, ty0, ty1, tz0, tz1, su0, su1, sv0, sv1);
+            else if (A == 1)
+                staged = tile_box_warp<1>(g, V, tx0, tx1, ty0, ty1, tz0, tz1, su0, su1, sv0, sv1);
+            staged = staged && su1 >= su0 && sv1 >= sv0 && (su1 - su0 + 1) * (sv1 - sv0 + 1) <= kStageCap;
+            const int sw = su1 - su0 + 1;
+            if (staged) {
+                __syncthreads();   // the previous staging's readers are done
+                const int n = sw * (sv1 - sv0 + 1);
+                const int pbase = A == 0 ? x0 : y0;
+                const float ca = 0.5f * ((A == 0 ? g.nx : g.ny) - 1);
+                const int nb = A == 0 ? g.ny : g.nx;   // interpolated axes b, c (c = z for A = 0, 1)
+                for (int k = tid; k < n; k += blockDim.x) {
+                    const int64_t ray = view0 + (int64_t)(sv0 + k / sw) * g.n_u + su0 + k % sw;
+                    s_ws[k] = __ldg(ws + ray);
+                    const bool same = (__ldg(tbits + 2 * ray + 1) & 3) == A;
+                    const float4 R = __ldg(ta + ray);
+#pragma unroll
+                    for (int q = 0; q < kPlanes; ++q) {
+                        const float t = (float)(pbase + q) - ca;
+                        float gb, gc;
+                        const int ib0 = joseph_split(fmaf(t, R.y, R.x), gb);
+                        const int ic0 = joseph_split(fmaf(t, R.w, R.z), gc);
+                        const bool ok = same && ib0 >= -1 && ib0 < nb && ic0 >= -1 && ic0 < g.nz;
+                        s_ij[q][k] = ok ? (unsigned)(ib0 + 1) | ((unsigned)(ic0 + 1) << 16) : kNoCell;
+                        s_f[q][k] = make_float2(gb, gc);
+                    }
+                }
+                __syncthreads();
+                iu0 = max(iu0, su0), iu1 = min(iu1, su1), iv0 = max(iv0, sv0), iv1 = min(iv1, sv1);
+            }
+            if (!inside) continue;
+            if (staged) {
+                const int q = A == 0 ? ix - x0 : iy - y0;
+                const int ib = A == 0 ? iy : ix;
+                const unsigned *tij = s_ij[q];
+                const float2 *tf = s_f[q];
+                for (int jv = iv0; jv <= iv1; ++jv) {
+                    const int row = (jv - sv0) * sw - su0;
+                    for (int ju = iu0; ju <= iu1; ++ju) {
+                        const int k = row + ju;
+                        const unsigned code = tij[k];
+                        const int db = ib - ((int)(code & 0xffffu) - 1), dc = iz - ((int)(code >> 16) - 1);
+                        if ((unsigned)db > 1u || (unsigned)dc > 1u) continue;
+                        const float2 f = tf[k];
+                        const float wbc = (db ? f.x : 1.f - f.x) * (dc ? f.y : 1.f - f.y);
+                        float val[C];
+                        Vec<C>::get(s_ws[k], val);
+#pragma unroll
+                        for (int c = 0; c < C; ++c) sv[c] = fmaf(wbc, val[c], sv[c]);
+                    }
+                }
+            } else if (A == 0) {
+                gather_cells<0, C>(g, v, ix, iy, iz, iu0, iu1, iv0, iv1, mixed, ta, tbits, ws, nullptr, s_ws, nullptr,
+                                   su0, sv0, sw, sv);
+            } else if (A == 1) {
+                gather_cells<1, C>(g, v, ix, iy, iz, iu0, iu1, iv0, iv1, mixed, ta, tbits, ws, nullptr, s_ws, nullptr,
+                                   su0, sv0, sw, sv);
+            } else {
+                gather_cells<2, C>(g, v, ix, iy, iz, iu0, iu1, iv0, iv1, mixed, ta, tbits, ws, nullptr, s_ws, nullptr,
+                                   su0, sv0, sw, sv);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float yk = __fsub_rn(sv[c], comp[c]);
+            const float tt = __fadd_rn(acc[c], yk);
+            comp[c] = __fsub_rn(__fsub_rn(tt, acc[c]), yk);
+            acc[c] = tt;
+        }
+    }
+    if (!inside) return;
+    const int64_t npix = (int64_t)g.nx * g.ny * g.nz;
+    const int64_t j = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if (c >= nc) break;
+        float *o = x + (int64_t)c * npix + j;
+        *o = accumulate ? *o + acc[c] : acc[c];
+    }
+}
+
 }  // namespace
 
 mbir_status cone_setup(mbir_plan *p) {
@@ -571,14 +782,31 @@ mbir_status project_cone(mbir_plan *p, const float *x, float *l, int n_mat, cuda
         PSPS_LAUNCH_CHECK();
         const unsigned gr = (unsigned)cdiv(p->n_rays, kThreads);
         float *lm = l + (int64_t)m0 * p->n_rays;
-        if (P == 1)
-            fwd_cone_kernel<1><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, ox, oy, oz, nm, p->n_rays, lm);
-        else if (P == 2)
-            fwd_cone_kernel<2><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float2 *)ox,
-                                                       (const float2 *)oy, (const float2 *)oz, nm, p->n_rays, lm);
-        else
-            fwd_cone_kernel<4><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float4 *)ox,
-                                                       (const float4 *)oy, (const float4 *)oz, nm, p->n_rays, lm);
+        // fwd_mode 2: warp-aligned march; otherwise each lane from its own range
+        if (p->fwd_mode == 2) {
+            if (P == 1)
+                fwd_cone_kernel<1, true><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, ox, oy, oz, nm, p->n_rays, lm);
+            else if (P == 2)
+                fwd_cone_kernel<2, true><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float2 *)ox,
+                                                                 (const float2 *)oy, (const float2 *)oz, nm,
+                                                                 p->n_rays, lm);
+            else
+                fwd_cone_kernel<4, true><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float4 *)ox,
+                                                                 (const float4 *)oy, (const float4 *)oz, nm,
+                                                                 p->n_rays, lm);
+        } else {
+            if (P == 1)
+                fwd_cone_kernel<1, false><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, ox, oy, oz, nm, p->n_rays,
+                                                                  lm);
+            else if (P == 2)
+                fwd_cone_kernel<2, false><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float2 *)ox,
+                                                                  (const float2 *)oy, (const float2 *)oz, nm,
+                                                                  p->n_rays, lm);
+            else
+                fwd_cone_kernel<4, false><<<gr, kThreads, 0, s>>>(g, p->ray.p, p->ray3b.p, (const float4 *)ox,
+                                                                  (const float4 *)oy, (const float4 *)oz, nm,
+                                                                  p->n_rays, lm);
+        }
         PSPS_LAUNCH_CHECK();
     }
     return MBIR_OK;
@@ -602,20 +830,35 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
         const int nc = left >= 4 ? 4 : left;                 // channels of this launch
         const int C = nc == 1 ? 1 : (nc == 2 ? 2 : 4);      // interleaved floats per ray
         float *w = p->wsino.p;
+        // mode 0 (default): split-table gather; mode 1: the direct gather
+        // (both deterministic and bitwise equal)
+        const bool split = p->back_mode == 0;
         if (C == 4) {
             weigh_sino_kernel<4><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
             PSPS_LAUNCH_CHECK();
-            back_cone_gather_kernel<4><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+            if (split)
+                back_cone_split_kernel<4><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                               p->view_axes.p, (const float4 *)w, nc, xm, accumulate);
+            else
+                back_cone_gather_kernel<4><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
                                                                 p->view_axes.p, (const float4 *)w, nc, xm, accumulate);
         } else if (C == 2) {
             weigh_sino_kernel<2><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
             PSPS_LAUNCH_CHECK();
-            back_cone_gather_kernel<2><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+            if (split)
+                back_cone_split_kernel<2><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                               p->view_axes.p, (const float2 *)w, nc, xm, accumulate);
+            else
+                back_cone_gather_kernel<2><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
                                                                 p->view_axes.p, (const float2 *)w, nc, xm, accumulate);
         } else {
             weigh_sino_kernel<1><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
             PSPS_LAUNCH_CHECK();
-            back_cone_gather_kernel<1><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+            if (split)
+                back_cone_split_kernel<1><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                               p->view_axes.p, w, nc, xm, accumulate);
+            else
+                back_cone_gather_kernel<1><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
                                                                 p->view_axes.p, w, nc, xm, accumulate);
         }
         PSPS_LAUNCH_CHECK();

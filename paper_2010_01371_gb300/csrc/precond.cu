@@ -702,11 +702,20 @@ using namespace psps;
 
 namespace {
 
+// Where M0 enters by default: the literal two-sided M0^T C M0 for a scalar
+// M0 (its remainder M0^2 in M^T H M is diagonal, absorbed by the separable
+// curvature), the one-sided M0^T C for per-pixel blocks (the remainder
+// M0^T M0 would couple the materials of a pixel).
+int default_sides(int kind) {
+    return (kind == PSPS_PRECOND_BLOCK_FOURIER || kind == PSPS_PRECOND_BLOCK_HAAR) ? 1 : 2;
+}
+
 mbir_status build_impl(mbir_plan *plan, const mbmd_spectrum *spec, int kind, const float *y, int64_t n_rays,
                        const double *beta, int haar_lattice, cudaStream_t s, psps_precond *pc) {
     const int nm = spec->n_mat;
     pc->kind = kind;
     pc->nm = nm;
+    pc->sides = default_sides(kind);
     pc->image = plan != nullptr;
     if (plan) {
         pc->nx = plan->g.nx;
@@ -986,6 +995,7 @@ mbir_status create_impl(mbir_plan *plan, int kind, int nm, int64_t n, const floa
                         const float *blocks, cudaStream_t s, psps_precond *pc) {
     pc->kind = kind;
     pc->nm = nm;
+    pc->sides = default_sides(kind);
     pc->image = plan != nullptr;
     pc->n = n;
     pc->nx = plan ? plan->g.nx : (int)n;

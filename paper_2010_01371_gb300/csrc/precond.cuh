@@ -9,7 +9,7 @@ struct psps_precond {
     bool image = true;       // false: projection-domain unknowns [nm][n_rays]
     int nx = 1, ny = 1, nz = 1;  // image grid (nz = 1: 2-D)
     int64_t n = 0;           // unknowns per material
-    int sides = 1;           // Fourier / wavelet kinds: M = M0 C (1) or M0^T C M0 (2)
+    int sides = 2;           // Fourier / wavelet kinds: M = M0^T C (1) or M0^T C M0 (2); set per kind
     psps::DBuf<float> m0;    // diagonal zero-frequency normalisation (one material)
     psps::DBuf<float> s, s_abs;  // spectra / wavelet-domain scales
     psps::DBuf<float> B, Babs;   // blocks [nm][nm][n]

@@ -25,6 +25,7 @@
 //    ray-driven scatter with global FP32 atomics, all with the forward's
 //    per-ray weights (mbir_plan_set_backprojector).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -871,6 +872,183 @@ __global__ void __launch_bounds__(kThreads, 8)
     }
 }
 
+// ---------------------------------------------------------------- strip forward
+// One CTA owns kSV consecutive views x kSB consecutive bins (one ray per
+// thread, lanes on neighbouring bins) and marches its rays through the image
+// in strips of S driving indices (columns for x-driven rays, rows for
+// y-driven ones).  For every strip the CTA finds the window of interpolated
+// indices its rays touch there (block min/max of the sample splits at the
+// strip ends; the split is monotone along a ray), stages that window of the
+// strip in shared memory (zero outside the image, so samples need no bounds
+// tests) and every lane then steps the same driving index: neighbouring lanes
+// read neighbouring shared-memory words.  Windows taller than kSH rows are
+// staged in part and the samples outside read global memory.  Sums: a plain
+// FP32 sum per strip (at most S samples), strips Kahan-compensated.  Weights
+// and the sample split are the per-ray table's, as in every other projector
+// and transpose, so the result is the same operator.
+// Views x bins per CTA: sb bins (a runtime choice among 32, 64, 128, 256,
+// tuned per plan) and kThreads / sb views, one ray per thread.
+constexpr int kSH = 256;           // staged window rows
+
+template <int NM>
+struct StripShape {
+    static constexpr int S = NM == 1 ? 32 : (NM == 2 ? 16 : 8);   // strip width (driving indices)
+    static constexpr size_t smem = sizeof(float) * NM * S * kSH;
+};
+
+// Planar transposed copies xt[m][ix][iy] of x[m][iy][ix] (the x-driven
+// strips read columns contiguously), 32 x 32 tiles through shared memory.
+__global__ void transpose_planes_kernel(const float *__restrict__ x, int nm, int nx, int ny, float *__restrict__ xt) {
+    __shared__ float tile[32][33];
+    const int64_t npix = (int64_t)nx * ny;
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32, m = blockIdx.z;
+    if (m >= nm) return;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int iy = by + r, ix = bx + threadIdx.x;
+        if (iy < ny && ix < nx) tile[r][threadIdx.x] = x[m * npix + (int64_t)iy * nx + ix];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int ix = bx + r, iy = by + threadIdx.x;
+        if (iy < ny && ix < nx) xt[m * npix + (int64_t)ix * ny + iy] = tile[threadIdx.x][r];
+    }
+}
+
+__device__ __forceinline__ int block_min_int(int v, int *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = min(r, red[w]);
+    return r;
+}
+
+__device__ __forceinline__ int block_max_int(int v, int *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = max(r, red[w]);
+    return r;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) fwd_strip_2d_kernel(const float4 *__restrict__ tab, mbir_geometry g,
+                                                                const float *__restrict__ x,
+                                                                const float *__restrict__ xt, int64_t n_rays, int sb,
+                                                                float *__restrict__ l) {
+    constexpr int S = StripShape<NM>::S;
+    extern __shared__ float sm[];   // [NM][S][kSH]
+    __shared__ int red[4][kThreads / 32];
+    const int tid = threadIdx.x;
+    const int view = blockIdx.y * (kThreads / sb) + tid / sb, bin = blockIdx.x * sb + tid % sb;
+    const bool valid = view < g.n_views && bin < g.n_u;
+    const int64_t ray = (int64_t)view * g.n_u + bin;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    int axis = 0, lo = 1, hi = 0;
+    if (valid) {
+        r = __ldg(tab + ray);
+        decode(r, axis, lo, hi);
+    }
+    const float f0h = r.x - 0.5f;
+    const int64_t npix = (int64_t)g.nx * g.ny;
+    float acc[NM], comp[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
+#pragma unroll 1
+    for (int fam = 0; fam < 2; ++fam) {
+        const bool mine = valid && lo <= hi && axis == fam;
+        // driving-index range of this family's rays in the CTA (uniform)
+        const int f_lo = block_min_int(mine ? lo : INT_MAX, red[0]);
+        const int f_hi = block_max_int(mine ? hi : -1, red[1]);
+        if (f_lo > f_hi) continue;
+        const int n_drive = fam == 0 ? g.nx : g.ny, n_other = fam == 0 ? g.ny : g.nx;
+        const float *src = fam == 0 ? xt : x;   // planar [m][driving][interpolated]
+#pragma unroll 1
+        for (int i0 = f_lo; i0 <= f_hi; i0 += S) {
+            const int ia = max(lo, i0), ib = min(hi, i0 + S - 1);
+            const bool has = mine && ia <= ib;
+            int ka = INT_MAX, kb = INT_MIN;
+            if (has) {
+                float fa, fb;
+                const int k1 = joseph_split(fmaf((float)ia, r.y, f0h), fa);
+                const int k2 = joseph_split(fmaf((float)ib, r.y, f0h), fb);
+                ka = min(k1, k2) - 1;       // one index of margin on each side
+                kb = max(k1, k2) + 2;       // upper neighbour k + 1, plus margin
+            }
+            __syncthreads();   // previous strip's readers of sm and red are done
+            const int w0 = block_min_int(ka, red[2]);
+            const int w1 = block_max_int(kb, red[3]);
+            if (w1 < w0) continue;                  // no ray of the CTA samples this strip
+            const int hs = min(w1 - w0 + 1, kSH);   // staged rows [w0, w0 + hs)
+            // one warp per (material, strip index), lanes down the window
+            for (int mc = tid >> 5; mc < NM * S; mc += kThreads / 32) {
+                const int m = mc / S, i = i0 + (mc - m * S);
+                const float *col = src + m * npix + (int64_t)i * n_other;
+                float *dst = sm + mc * kSH;
+                const bool in_i = i < n_drive;
+                for (int rr = tid & 31; rr < hs; rr += 32) {
+                    const int row = w0 + rr;
+                    dst[rr] = (in_i && row >= 0 && row < n_other) ? __ldg(col + row) : 0.f;
+                }
+            }
+            __syncthreads();
+            if (has) {
+                float sum[NM];
+#pragma unroll
+                for (int m = 0; m < NM; ++m) sum[m] = 0.f;
+                for (int i = ia; i <= ib; ++i) {
+                    float f;
+                    const int k = joseph_split(fmaf((float)i, r.y, f0h), f);
+                    const int kl = k - w0, c = i - i0;
+                    if (kl >= 0 && kl + 1 < hs) {
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            const float a = sm[(m * S + c) * kSH + kl], b = sm[(m * S + c) * kSH + kl + 1];
+                            sum[m] += fmaf(f, b - a, a);
+                        }
+                    } else {
+                        // outside the staged part of a tall window
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            const float *col = src + m * npix + (int64_t)i * n_other;
+                            const float a = (k >= 0 && k < n_other) ? __ldg(col + k) : 0.f;
+                            const float b = (k + 1 >= 0 && k + 1 < n_other) ? __ldg(col + k + 1) : 0.f;
+                            sum[m] += fmaf(f, b - a, a);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const float yk = __fsub_rn(sum[m], comp[m]);
+                    const float t = __fadd_rn(acc[m], yk);
+                    comp[m] = __fsub_rn(__fsub_rn(t, acc[m]), yk);
+                    acc[m] = t;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) l[(int64_t)m * n_rays + ray] = acc[m] * r.z;
+}
+
+template <int NM>
+mbir_status project_strip_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s) {
+    const int nx = p->g.nx, ny = p->g.ny;
+    const dim3 tb(32, 8), tg((unsigned)cdiv(nx, 32), (unsigned)cdiv(ny, 32), (unsigned)NM);
+    transpose_planes_kernel<<<tg, tb, 0, s>>>(x, NM, nx, ny, p->xcol.p);
+    PSPS_LAUNCH_CHECK();
+    const int sb = p->strip_bins, sv = kThreads / sb;
+    const dim3 grd((unsigned)cdiv(p->g.n_u, sb), (unsigned)cdiv(p->g.n_views, sv));
+    fwd_strip_2d_kernel<NM><<<grd, kThreads, StripShape<NM>::smem, s>>>(p->ray.p, p->g, x, p->xcol.p, p->n_rays, sb,
+                                                                        l);
+    PSPS_LAUNCH_CHECK();
+    return MBIR_OK;
+}
+
 template <int NM>
 mbir_status project_2d_nm(mbir_plan *p, const float *x, float *l, cudaStream_t s) {
     constexpr int P = Pack<NM>::P;
@@ -928,6 +1106,15 @@ mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStrea
         const int nm = n_mat - m0 < 4 ? n_mat - m0 : 4;
         const float *xm = x + (int64_t)m0 * p->n_pix;
         float *lm = l + (int64_t)m0 * p->n_rays;
+        if (p->fwd_mode == 2) {
+            switch (nm) {
+                case 1: PSPS_TRY(project_strip_nm<1>(p, xm, lm, s)); break;
+                case 2: PSPS_TRY(project_strip_nm<2>(p, xm, lm, s)); break;
+                case 3: PSPS_TRY(project_strip_nm<3>(p, xm, lm, s)); break;
+                default: PSPS_TRY(project_strip_nm<4>(p, xm, lm, s)); break;
+            }
+            continue;
+        }
         switch (nm) {
             case 1: PSPS_TRY(project_2d_nm<1>(p, xm, lm, s)); break;
             case 2: PSPS_TRY(project_2d_nm<2>(p, xm, lm, s)); break;
@@ -1130,6 +1317,88 @@ extern "C" mbir_status mbir_plan_set_tiling(mbir_plan *p, int views_per_cta) {
     return MBIR_OK;
 }
 
+namespace {
+
+// Device time of `reps` calls of fn after one warm-up call (CUDA events on s).
+template <class F>
+mbir_status time_calls(F &&fn, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, float &ms) {
+    PSPS_TRY(fn());
+    PSPS_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) PSPS_TRY(fn());
+    PSPS_CUDA(cudaEventRecord(e1, s));
+    PSPS_CUDA(cudaEventSynchronize(e1));
+    PSPS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return MBIR_OK;
+}
+
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+mbir_status autotune_impl(mbir_plan *p, int n_channels, cudaStream_t s) {
+    EventPair ev;
+    PSPS_CUDA(cudaEventCreate(&ev.e0));
+    PSPS_CUDA(cudaEventCreate(&ev.e1));
+    const int n_fwd = n_channels / 2 > 0 ? n_channels / 2 : 1;   // basis images of a 2 n_mat-channel transpose
+    DBuf<float> sino, img;
+    PSPS_TRY(sino.alloc((size_t)n_channels * p->n_rays));
+    PSPS_TRY(img.alloc((size_t)n_channels * p->n_pix));
+    PSPS_CUDA(cudaMemsetAsync(sino.p, 0, sizeof(float) * sino.n, s));
+    PSPS_CUDA(cudaMemsetAsync(img.p, 0, sizeof(float) * img.n, s));
+    float ms = 0.f, best_ms = 3.0e38f;
+    if (p->g.kind == MBIR_CONE3D) {
+        // the transpose's algorithm: split-table gather (0) or direct gather (1)
+        int best = p->back_mode;
+        for (int mode : {0, 1}) {
+            p->back_mode = mode;
+            PSPS_TRY(time_calls([&] { return backproject(p, sino.p, img.p, n_channels, 0, s); }, s, ev.e0, ev.e1, 1,
+                                ms));
+            if (ms < best_ms) best_ms = ms, best = mode;
+        }
+        p->back_mode = best;
+        // the forward's march: each lane from its own range (1) or warp-aligned (2)
+        best_ms = 3.0e38f;
+        best = p->fwd_mode;
+        for (int mode : {1, 2}) {
+            p->fwd_mode = mode;
+            PSPS_TRY(time_calls([&] { return project(p, img.p, sino.p, n_fwd, s); }, s, ev.e0, ev.e1, 1, ms));
+            if (ms < best_ms) best_ms = ms, best = mode;
+        }
+        p->fwd_mode = best;
+        return MBIR_OK;
+    }
+    // 2-D transpose: views per CTA of the tile kernel
+    p->back_mode = 0;
+    int best = p->back_views;
+    const int cand[] = {4, 8, 15, 30, 45, 60, 90, 120, 180};
+    for (int vs : cand) {
+        if (vs > p->g.n_views && vs != cand[0]) continue;
+        p->back_views = vs;
+        PSPS_TRY(time_calls([&] { return backproject(p, sino.p, img.p, n_channels, 0, s); }, s, ev.e0, ev.e1, 3, ms));
+        if (ms < best_ms) best_ms = ms, best = vs;
+    }
+    p->back_views = best;
+    // 2-D forward: one thread per ray, or the strip kernel with 32 .. 256
+    // bins per CTA
+    best_ms = 3.0e38f;
+    int best_mode = p->fwd_mode, best_sb = p->strip_bins;
+    for (int c = 0; c < 5; ++c) {
+        p->fwd_mode = c == 0 ? 1 : 2;
+        if (c > 0) p->strip_bins = 16 << c;   // 32, 64, 128, 256
+        PSPS_TRY(time_calls([&] { return project(p, img.p, sino.p, n_fwd, s); }, s, ev.e0, ev.e1, 3, ms));
+        if (ms < best_ms) best_ms = ms, best_mode = p->fwd_mode, best_sb = p->strip_bins;
+    }
+    p->fwd_mode = best_mode;
+    p->strip_bins = best_sb;
+    return MBIR_OK;
+}
+
+}  // namespace
+
 extern "C" mbir_status mbir_plan_autotune(mbir_plan *p, int n_channels, mbir_stream stream, int *views_per_cta) {
     if (!p || n_channels < 1 || n_channels > p->n_mat_max)
         return fail(MBIR_ERR_ARG, "mbir_plan_autotune: bad argument (n_channels must be 1..n_mat_max)");
@@ -1137,49 +1406,35 @@ extern "C" mbir_status mbir_plan_autotune(mbir_plan *p, int n_channels, mbir_str
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     PSPS_CUDA(cudaStreamIsCapturing(s, &cap));
     if (cap != cudaStreamCaptureStatusNone) return fail(MBIR_ERR_ARG, "mbir_plan_autotune: stream is capturing");
-    if (p->g.kind == MBIR_CONE3D) {  // nothing to tune: the 3-D transpose has no view split
-        if (views_per_cta) *views_per_cta = p->back_views;
-        return MBIR_OK;
+    const int back_mode = p->back_mode, back_views = p->back_views, fwd_mode = p->fwd_mode, sb = p->strip_bins;
+    const mbir_status st = autotune_impl(p, n_channels, s);
+    if (st != MBIR_OK) {   // keep the plan as it was
+        p->back_mode = back_mode, p->back_views = back_views, p->fwd_mode = fwd_mode, p->strip_bins = sb;
+        return st;
     }
-    DBuf<float> sino, img;
-    PSPS_TRY(sino.alloc((size_t)n_channels * p->n_rays));
-    PSPS_TRY(img.alloc((size_t)n_channels * p->n_pix));
-    PSPS_CUDA(cudaMemsetAsync(sino.p, 0, sizeof(float) * sino.n, s));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    mbir_status st = MBIR_OK;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-        st = fail(MBIR_ERR_CUDA, "mbir_plan_autotune: event creation failed");
-    const int mode = p->back_mode, keep = p->back_views;
-    p->back_mode = 0;
-    int best = keep;
-    float best_ms = 3.0e38f;
-    const int cand[] = {4, 8, 15, 30, 45, 60, 90, 120, 180};
-    for (int vs : cand) {
-        if (st != MBIR_OK) break;
-        if (vs > p->g.n_views && vs != cand[0]) continue;
-        p->back_views = vs;
-        float ms = 0.f;
-        if ((st = backproject(p, sino.p, img.p, n_channels, 0, s)) != MBIR_OK) break;  // warm-up
-        if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(MBIR_ERR_CUDA, "mbir_plan_autotune: event record");
-        for (int r = 0; r < 3 && st == MBIR_OK; ++r) st = backproject(p, sino.p, img.p, n_channels, 0, s);
-        if (st != MBIR_OK) break;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            st = fail(MBIR_ERR_CUDA, "mbir_plan_autotune: timing failed");
-            break;
-        }
-        if (ms < best_ms) best_ms = ms, best = vs;
-    }
-    p->back_mode = mode;
-    p->back_views = st == MBIR_OK ? best : keep;
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (st == MBIR_OK && views_per_cta) *views_per_cta = best;
-    return st;
+    if (views_per_cta) *views_per_cta = p->back_views;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbir_plan_set_strip_bins(mbir_plan *p, int bins) {
+    if (!p || (bins != 32 && bins != 64 && bins != 128 && bins != 256))
+        return fail(MBIR_ERR_ARG, "mbir_plan_set_strip_bins: bins must be 32, 64, 128 or 256");
+    p->strip_bins = bins;
+    return MBIR_OK;
+}
+
+extern "C" mbir_status mbir_plan_tuning(const mbir_plan *p, int *fwd_mode, int *strip_bins, int *back_mode,
+                                        int *back_views) {
+    if (!p) return fail(MBIR_ERR_ARG, "mbir_plan_tuning: null plan");
+    if (fwd_mode) *fwd_mode = p->fwd_mode;
+    if (strip_bins) *strip_bins = p->strip_bins;
+    if (back_mode) *back_mode = p->back_mode;
+    if (back_views) *back_views = p->back_views;
+    return MBIR_OK;
 }
 
 extern "C" mbir_status mbir_plan_set_projector(mbir_plan *p, int mode) {
-    if (!p || mode < 0 || mode > 1) return fail(MBIR_ERR_ARG, "mbir_plan_set_projector: bad argument");
+    if (!p || mode < 0 || mode > 2) return fail(MBIR_ERR_ARG, "mbir_plan_set_projector: bad argument");
     p->fwd_mode = mode;
     return MBIR_OK;
 }

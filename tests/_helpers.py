@@ -65,7 +65,7 @@ def phantom(geom, seed=0, nm=1):
     return np.stack(out)
 
 
-def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None, sides=1):
+def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None, sides=None):
     """Oracle preconditioner for a problem plus the data that defines it
     (eigenvalues, m0, blocks in the library's [m][k][n] layout).  blur: an
     ``oracle.model.Blur`` in the outer operator (the preconditioners use the
@@ -77,6 +77,8 @@ def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None, side
         return st, precond.Identity(), {}
     F = build.fisher(st)
     aH = build.make_apply_H(st, F)
+    if sides is None:        # each kind's default
+        sides = 1 if kind in ("block_fourier", "block_haar") else 2
     if kind == "fourier":
         lam = precond.fourier_eigenvalues(aH, st.shape)
         return st, precond.Fourier(lam), {"lam": lam}
@@ -109,7 +111,7 @@ def oracle_precond(oracle_lib, prob, kind, lattice=3, proj=True, blur=None, side
     raise ValueError(kind)
 
 
-def gpu_precond_from(psps, plan, spec, kind, data, sides=1):
+def gpu_precond_from(psps, plan, spec, kind, data, sides=None):
     """The library's preconditioner created from the oracle's data."""
     if kind == "none":
         return None
@@ -158,4 +160,4 @@ def oracle_haar_parallel(oracle_lib, builder, kw, processes=None):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return st, precond.Haar(sum(parts), m0)
+    return st, precond.Haar(sum(parts), m0)   # the kind's default (literal) form

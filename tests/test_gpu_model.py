@@ -139,8 +139,10 @@ def test_autograd_basis_images(psps, oracle_lib, error_log, case):
     e = rel_l2(to_host(x.grad), want)
     error_log.add(f"autograd {case}", "gradient vs oracle", e, 1e-5)
     assert e < 1e-5, e
-    v = np.random.default_rng(9).standard_normal(x0.shape) * (np.abs(x0).max(axis=tuple(range(1, x0.ndim)),
-                                                                              keepdims=True) + 1e-3)
+    # direction: the oracle gradient scaled to the image's norm (a random
+    # direction makes g . v a sum with cancellation, whose relative error is
+    # the gradient's times ||g|| ||v|| / |g . v|)
+    v = want * (np.linalg.norm(x0) / np.linalg.norm(want))
     dg = float(np.sum(to_host(x.grad) * v))
     h = 1e-4
     fd_o = (model.data_objective(Q, S, A.project(x0 + h * v), y)
@@ -148,11 +150,15 @@ def test_autograd_basis_images(psps, oracle_lib, error_log, case):
     error_log.add(f"autograd {case}", "directional derivative vs oracle central difference",
                   abs(dg - fd_o) / abs(fd_o), 1e-5)
     assert abs(dg - fd_o) <= 1e-5 * abs(fd_o), (dg, fd_o)
-    h = 1e-2
+    # central difference of the GPU forward itself (FP32 data term, double-
+    # float sum): checks the autograd plumbing, not the precision
+    h = 1e-3
     with torch.no_grad():
         fp = float(psps.MBMDData.apply(to_dev(x0 + h * v), plan, spec, yd))
         fm = float(psps.MBMDData.apply(to_dev(x0 - h * v), plan, spec, yd))
     fd_g = (fp - fm) / (2 * h)
+    error_log.add(f"autograd {case}", "directional derivative vs GPU central difference", abs(dg - fd_g) / abs(dg),
+                  1e-3)
     assert abs(dg - fd_g) <= 1e-3 * abs(dg), (dg, fd_g)
 
 

@@ -55,14 +55,25 @@ def test_apply_parity(psps, oracle_lib, pname, kind):
 
 @pytest.mark.parametrize("pname", ["c1", "c2_64"])
 @pytest.mark.parametrize("kind", ["mod_fourier", "haar", "block_fourier", "block_haar"])
-def test_two_sided_apply_parity(psps, oracle_lib, pname, kind):
-    """The literal two-sided M0^T C M0 of Eqs. 33, 34, 57, 61
-    (psps_precondition_set_sides(pc, 2)) against the oracle's sides=2."""
+@pytest.mark.parametrize("sides", [1, 2])
+def test_sides_apply_parity(psps, oracle_lib, pname, kind, sides):
+    """Both placements of M0 (psps_precondition_set_sides): the one-sided
+    M0^T C and the literal two-sided M0^T C M0 of Eqs. 33, 34, 57, 61, against
+    the oracle's; and the kinds' defaults (2 for one material, 1 for the
+    cross-material kinds) match the oracle's defaults."""
     prob = problems()[pname] if kind in ("mod_fourier", "haar") else synth.config4_slice(nx=64, n_views=90, n_u=111)
-    st, P, data = oracle_precond(oracle_lib, prob, kind, sides=2)
+    st, P, data = oracle_precond(oracle_lib, prob, kind, sides=sides)
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
-    pc = gpu_precond_from(psps, plan, spec, kind, data, sides=2)
+    pc = gpu_precond_from(psps, plan, spec, kind, data, sides=sides)
     check_ops(psps, pc, P, (st.nm,) + prob.geom.image_shape, APPLY_TOL)
+    default = 1 if kind.startswith("block_") else 2
+    if sides == default:
+        check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, (st.nm,) + prob.geom.image_shape,
+                  APPLY_TOL)
+    with pytest.raises(psps.MbirError):
+        psps.lib()
+        from paper_2010_01371_gb300 import _abi
+        _abi.check(psps.lib().psps_precondition_set_sides(pc.h, 3))
 
 
 @pytest.mark.parametrize("pname", ["c1", "c2_64"])

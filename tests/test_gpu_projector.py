@@ -22,7 +22,7 @@ def psps():
 
 @pytest.mark.parametrize("name", list(small_geoms()))
 @pytest.mark.parametrize("nm", [1, 2])
-@pytest.mark.parametrize("mode", ["tile", "ray"])
+@pytest.mark.parametrize("mode", ["tile", "ray", "strip"])
 def test_project_parity(psps, oracle_lib, name, nm, mode):
     g = small_geoms()[name]
     x = phantom(g, seed=1, nm=nm)
@@ -52,7 +52,7 @@ def test_backproject_parity(psps, oracle_lib, name, mode):
 
 
 @pytest.mark.parametrize("nm", [3, 4, 5])
-@pytest.mark.parametrize("mode", ["tile", "ray"])
+@pytest.mark.parametrize("mode", ["tile", "ray", "strip"])
 def test_material_packing(psps, oracle_lib, nm, mode):
     g = small_geoms()["fan2d_ragged"]
     x = phantom(g, seed=3, nm=nm)
@@ -120,7 +120,7 @@ def test_adjoint_fp32(psps):
     assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
 
 
-@pytest.mark.parametrize("mode", ["tile", "ray"])
+@pytest.mark.parametrize("mode", ["tile", "ray", "strip"])
 def test_full_size_sampled(psps, oracle_lib, mode):
     """Full 512^2 / 720 x 888 fan-beam geometry: every 97th ray (plus the
     first and last) against the oracle ray by ray, and the adjoint identity
@@ -156,19 +156,26 @@ def test_empty_and_errors(psps):
 @pytest.mark.parametrize("name", list(cone_geoms()))
 @pytest.mark.parametrize("nm", [1, 2, 3])
 def test_cone_project_parity(psps, oracle_lib, name, nm):
+    """Cone forward, both marches: each lane over its own range and the
+    warp-aligned one, which takes the same samples in the same order (bitwise
+    equal)."""
     g = cone_geoms()[name]
     x = phantom(g, seed=11, nm=nm)
-    got = to_host(psps.mbir_project(psps.Plan(g), to_dev(x)))
+    plan = psps.Plan(g)
+    got = to_host(psps.mbir_project(plan, to_dev(x)))
     want = oracle_lib.Projector(g).project(x)
     assert rel_l2(got, want) < TOL, rel_l2(got, want)
+    plan.set_projector("aligned")
+    assert np.array_equal(to_host(psps.mbir_project(plan, to_dev(x))), got)
 
 
 @pytest.mark.parametrize("name", list(cone_geoms()))
-@pytest.mark.parametrize("mode", ["tile", "atomic"])
+@pytest.mark.parametrize("mode", ["tile", "gather", "atomic"])
 @pytest.mark.parametrize("nch", [1, 2, 3, 5])
 def test_cone_backproject_parity(psps, oracle_lib, name, mode, nch):
-    """3-D transposes: the voxel-driven gather (default; channel groups of 4 /
-    2 / 1) and the ray-driven atomic scatter; accumulate adds."""
+    """3-D transposes: the voxel-driven gather with split tables (default,
+    mode 'tile'), the direct voxel-driven gather ('gather'; channel groups of
+    4 / 2 / 1) and the ray-driven atomic scatter; accumulate adds."""
     g = cone_geoms()[name]
     s = np.random.default_rng(12).random((nch, g.n_rays))
     plan = psps.Plan(g)
@@ -211,14 +218,22 @@ def test_tile_transpose_nonfinite_input(psps):
     assert np.isnan(got[1]).all()
 
 
-def test_cone_gather_deterministic(psps):
-    """The 3-D gather has no atomics: two runs are bitwise equal."""
-    g = cone_geoms()["cone_small"]
-    s = to_dev(np.random.default_rng(14).random((2, g.n_rays)))
+@pytest.mark.parametrize("name", list(cone_geoms()) + ["c5_64"])
+def test_cone_gather_deterministic(psps, name):
+    """The 3-D gathers have no atomics: two runs are bitwise equal, and the
+    split-table gather (default) equals the direct gather bit for bit (same
+    candidates, weights and summation order), 1, 2 and 4 channels."""
+    g = cone_geoms()[name] if name != "c5_64" else synth.config5(n=64, n_views=90, n_u=128, n_v=96,
+                                                                     rays=False).geom
     plan = psps.Plan(g)
-    a = to_host(psps.mbir_backproject(plan, s))
-    b = to_host(psps.mbir_backproject(plan, s))
-    assert np.array_equal(a, b)
+    direct = psps.Plan(g)
+    direct.set_backprojector("gather")
+    for nch in [1, 2, 4]:
+        s = to_dev(np.random.default_rng(14).standard_normal((nch, g.n_rays)))
+        a = to_host(psps.mbir_backproject(plan, s))
+        b = to_host(psps.mbir_backproject(plan, s))
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, to_host(psps.mbir_backproject(direct, s))), nch
 
 
 def test_cone_full_size_sampled(psps, oracle_lib):
@@ -246,11 +261,39 @@ def test_autotune_keeps_parity(psps, oracle_lib):
     plan = psps.Plan(g)
     v = plan.autotune(2)
     assert v in (4, 8, 15, 30, 45)
+    t = plan.tuning()
+    assert t["views_per_cta"] == v and t["forward"] in ("ray", "strip") and t["strip_bins"] in (32, 64, 128, 256)
     s = np.random.default_rng(11).random((2, g.n_rays))
     got = to_host(psps.mbir_backproject(plan, to_dev(s)))
     assert rel_l2(got, oracle_lib.Projector(g).backproject(s)) < TOL
+    x = phantom(g, seed=4, nm=2)
+    assert rel_l2(to_host(psps.mbir_project(plan, to_dev(x))), oracle_lib.Projector(g).project(x)) < TOL
     with pytest.raises(RuntimeError):
         plan.autotune(0)
+
+
+@pytest.mark.parametrize("sb", [32, 64, 128, 256])
+def test_strip_forward_shapes(psps, oracle_lib, sb):
+    """Every CTA shape of the strip forward (sb bins x 256 / sb views) gives
+    the same projection (within FP32) as the oracle, ragged sizes included."""
+    for name in ["par2d_ragged", "fan2d_ragged", "fan2d_c2_128"]:
+        g = small_geoms()[name]
+        plan = psps.Plan(g)
+        plan.set_projector("strip")
+        plan.set_strip_bins(sb)
+        x = phantom(g, seed=5, nm=3)
+        assert rel_l2(to_host(psps.mbir_project(plan, to_dev(x))), oracle_lib.Projector(g).project(x)) < TOL
+
+
+def test_autotune_cone(psps, oracle_lib):
+    """Cone plans: the autotuner picks one of the two gathers (bitwise
+    equal) and the transpose stays exact."""
+    g = cone_geoms()["cone_ragged"]
+    plan = psps.Plan(g)
+    plan.autotune(4)
+    assert plan.tuning()["backproject_mode"] in (0, 1)
+    s = np.random.default_rng(17).random((4, g.n_rays))
+    assert rel_l2(to_host(psps.mbir_backproject(plan, to_dev(s))), oracle_lib.Projector(g).backproject(s)) < TOL
 
 
 def test_degenerate_geometries(psps, oracle_lib):
@@ -273,3 +316,57 @@ def test_degenerate_geometries(psps, oracle_lib):
             plan = psps.Plan(g)
             plan.set_backprojector(mode)
             assert rel_l2(to_host(psps.mbir_backproject(plan, to_dev(s))), A.backproject(s)) < TOL, (g, mode)
+
+
+def test_fixed_point_transpose_numerators_full_size(psps, oracle_lib, error_log):
+    """The tile transpose's 32-bit fixed-point sums on the real numerators of
+    the 512^2 / 720 x 888 fan-beam workload (gradient g and curvature kappa
+    of Eqs. 5, 8-11, from the data at x = 0 and at an iterate), element by
+    element against the FP64 oracle transpose.
+
+    Bound: every term w_i s_i is rounded once to the grid
+    u = M max(2^-22, T 2^-30), M = w_max max|s| (T = views per CTA x the
+    rays of one view that can reach one accumulator), and pixel j receives at
+    most N = n_views x cell_rays terms, so |error_j| <= N u / 2.  Pixels whose
+    value is small against M carry a larger relative error; the max relative
+    error over pixels above 1e-3 of the largest is recorded beside the FP32
+    gather's."""
+    import math as _m
+    from oracle import model, psps as opsps, precond
+    prob = synth.config2()
+    g = prob.geom
+    A = oracle_lib.Projector(g)
+    st = opsps.Setup(A, prob.Q, prob.S, prob.y, prob.beta)
+    xk, _ = opsps.run(st, precond.Identity(), 3, None)          # plain SPS iterate
+    vs = 45
+    pix = max(g.dx, g.dy)
+    R = _m.hypot((0.5 * g.nx + 1.0) * g.dx, (0.5 * g.ny + 1.0) * g.dy)
+    cell_rays = int(_m.floor(2.0 / ((g.sid - R) * (g.du / g.sdd) / pix))) + 2
+    T = vs * cell_rays
+    w_max = max(g.dx, g.dy) * _m.sqrt(2.0)
+    n_terms = g.n_views * cell_rays
+    plan = psps.Plan(g)
+    plan.set_tiling(vs)
+    gather = psps.Plan(g)
+    gather.set_backprojector("gather")
+    gamma = A.project(np.ones((1,) + g.image_shape))
+    for label, x in [("x=0", st.zeros()), ("x=SPS iterate 3", xk)]:
+        l = A.project(x)
+        for name, s in [("g", model.data_grad_l(prob.Q, prob.S, l, prob.y)),
+                        ("kappa", model.curvature_numerator(prob.Q, prob.S, l, prob.y, gamma))]:
+            want = A.backproject(s)
+            sf = np.asarray(s, dtype=np.float32)
+            got = to_host(psps.mbir_backproject(plan, to_dev(sf)))
+            ref = to_host(psps.mbir_backproject(gather, to_dev(sf)))
+            M = w_max * float(np.abs(sf).max())
+            u = M * max(2.0 ** -22, T * 2.0 ** -30)
+            bound = n_terms * u / 2
+            err = np.abs(got - want)
+            assert err.max() <= bound, (label, name, err.max(), bound)
+            big = np.abs(want) >= 1e-3 * np.abs(want).max()
+            rel = float(np.max(err[big] / np.abs(want[big])))
+            rel_gather = float(np.max(np.abs(ref - want)[big] / np.abs(want[big])))
+            error_log.add(f"fixed-point transpose c2 512 {label} {name}", "max abs error / bound N u/2",
+                          float(err.max() / bound), 1.0, rel_above_floor=rel, rel_gather=rel_gather,
+                          M_over_median=float(M / np.median(np.abs(sf[sf != 0]))))
+            assert rel_l2(got, want) < TOL

@@ -72,9 +72,9 @@ def test_fourier_exact_on_circulant():
     # N is circulant its estimate is exact: the one-sided M = M0 C whitens H,
     # the literal two-sided form gives M^T H M = M0 N^-1/2 N N^-1/2 M0 = M0^2.
     lamN = precond.fourier_eigenvalues(lambda z: 0.25 * apply_H(z), shape)
-    P1 = precond.Fourier(lamN, np.full(shape, 0.5))
+    P1 = precond.Fourier(lamN, np.full(shape, 0.5), sides=1)
     assert np.allclose(P1.MT(apply_H(P1.M(v))), v, rtol=1e-11, atol=1e-11)
-    P2 = precond.Fourier(lamN, np.full(shape, 0.5), sides=2)
+    P2 = precond.Fourier(lamN, np.full(shape, 0.5))          # the literal form (default)
     assert np.allclose(P2.MT(apply_H(P2.M(v))), 0.25 * v, rtol=1e-11, atol=1e-11)
 
 
@@ -92,10 +92,11 @@ def _scaled_blocks(apply_N, M0, nm):
 
 @pytest.mark.parametrize("kind", ["mod_fourier", "haar"])
 def test_one_sided_whitens_scaled_hessian(kind):
-    """The reading of where M0 goes (Eqs. 33, 34): with N = M0 H M0 diagonal
-    in the transform basis and a non-constant M0, Eq. 18 recovers N's
-    spectrum, the one-sided M = M0 C gives M^T H M = I and M M^T = H^-1
-    (dense), and the literal two-sided M0 C M0 gives M^T H M = M0^2."""
+    """Where M0 goes (Eqs. 33, 34): with N = M0 H M0 diagonal in the
+    transform basis and a non-constant M0, Eq. 18 recovers N's spectrum, the
+    one-sided M = M0 C gives M^T H M = I and M M^T = H^-1 (dense), and the
+    literal two-sided M0 C M0 (the one-material default) gives
+    M^T H M = M0^2, a diagonal remainder."""
     from oracle import haar, precond
     shape = (8, 8)
     rng = np.random.default_rng(11)
@@ -117,7 +118,7 @@ def test_one_sided_whitens_scaled_hessian(kind):
     assert np.allclose(est, lam, rtol=1e-12)
     apply_H = _scaled(apply_N, m0)
     Hd = dense(apply_H, shape)
-    P1, P2 = make(est, m0), make(est, m0, sides=2)
+    P1, P2 = make(est, m0, sides=1), make(est, m0, sides=2)
     M1, M2 = dense(P1.M, shape), dense(P2.M, shape)
     assert np.allclose(dense(P1.MT, shape), M1.T, atol=1e-13)
     assert np.allclose(M1.T @ Hd @ M1, np.eye(64), atol=1e-10)
@@ -155,7 +156,7 @@ def test_one_sided_cross_material_whitens(kind):
         apply_H = _scaled_blocks(apply_N, M0, nm)
         est = precond.cross_haar_blocks(apply_H, M0, shape, nm)
         assert np.allclose(est, Kt, rtol=1e-9, atol=1e-9)
-        P1, P2 = precond.CrossHaar(est, M0), precond.CrossHaar(est, M0, sides=2)
+        P1, P2 = precond.CrossHaar(est, M0, sides=1), precond.CrossHaar(est, M0, sides=2)
     else:
         Gf = rng.standard_normal(shape + (nm, nm))
         idx = tuple(np.meshgrid(*[(-np.arange(k)) % k for k in shape], indexing="ij"))
@@ -168,7 +169,7 @@ def test_one_sided_cross_material_whitens(kind):
         apply_H = _scaled_blocks(apply_N, M0, nm)
         est = precond.cross_fourier_blocks(apply_H, M0, shape, nm)
         assert np.allclose(est, Lb, rtol=1e-9, atol=1e-9)
-        P1, P2 = precond.CrossFourier(est, M0), precond.CrossFourier(est, M0, sides=2)
+        P1, P2 = precond.CrossFourier(est, M0, sides=1), precond.CrossFourier(est, M0, sides=2)
     Hd = dense(apply_H, shape, nm)
     M1, M2 = dense(P1.M, shape, nm), dense(P2.M, shape, nm)
     assert np.allclose(dense(P1.MT, shape, nm), M1.T, atol=1e-12 * np.abs(M1).max())
@@ -301,11 +302,12 @@ def test_cross_haar_one_material_is_haar(oracle_lib):
     img = synth.render(g, [synth.Ellipse(0.5, -0.3, 5.0, 6.0, 0.2, 0.02)])
     y = np.round(1e4 * np.exp(-A.project(img[None])))
     st = psps.Setup(A, np.ones((1, 1)), np.full((1, 1), 1e4), y, np.array([[50.0]]))
-    Ph, Pc = build.build(st, "haar"), build.build(st, "block_haar")
     v = np.random.default_rng(7).standard_normal((1,) + st.shape)
-    for op in ["M", "MT", "absM", "absMT"]:
-        a, b = getattr(Ph, op)(v), getattr(Pc, op)(v)
-        assert np.allclose(a, b, rtol=1e-10, atol=1e-12 * np.abs(a).max()), op
+    for sides in (1, 2):
+        Ph, Pc = build.build(st, "haar", sides), build.build(st, "block_haar", sides)
+        for op in ["M", "MT", "absM", "absMT"]:
+            a, b = getattr(Ph, op)(v), getattr(Pc, op)(v)
+            assert np.allclose(a, b, rtol=1e-10, atol=1e-12 * np.abs(a).max()), (op, sides)
 
 
 # ---------------------------------------------------------------------------
