@@ -695,7 +695,9 @@ def kernel_bench(args, prob):
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
             return float(np.median(ts))
-        out[f"project_{nm}ch_ms"] = timec(lambda: p.mbir_project(plan, x1, l))
+        for mode in ["ray", "aligned"]:
+            plan.set_projector(mode)
+            out[f"project_{mode}_{nm}ch_ms"] = timec(lambda: p.mbir_project(plan, x1, l))
         for mode in ["tile", "gather"]:
             plan.set_backprojector(mode)
             out[f"backproject_{'split' if mode == 'tile' else 'gather'}_{2 * nm}ch_ms"] = timec(

@@ -300,7 +300,7 @@ FULL_SIZE = {
     # the GPU the way bench.py builds them: (synth builder, keywords, kind)
     "c2_512-haar": ("config2", {}, "haar"),
     "c4_512-block_fourier": ("config4_slice", {}, "block_fourier"),
-    "c5_64-block_fourier": ("config5", {"n": 64, "n_views": 90, "n_u": 128, "n_v": 96}, "block_fourier"),
+    "c5_64-block": ("config5", {"n": 64, "n_views": 90, "n_u": 128, "n_v": 96}, "block"),
 }
 
 
