@@ -240,7 +240,54 @@ __global__ void __launch_bounds__(kThreads)
     float acc[NM], comp[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
-    for (int i = i_lo; i <= i_hi; ++i) {
+    int i = i_lo;
+    if (!ALIGNED) {
+        // Two samples per step: their eight tap loads (addresses clamped into
+        // the volume, values zeroed outside it) are issued before use; the
+        // taps and samples are then added in the one-at-a-time order.
+        using T = typename P3<NM>::T;
+        for (; i + 1 <= i_hi; i += 2) {
+            T v[2][4];
+            float gb[2], gc[2];
+            bool ok[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float t = (float)(i + u) - ca;
+                const int ib0 = joseph_split(fmaf(t, A.y, A.x), gb[u]), ic0 = joseph_split(fmaf(t, A.w, A.z), gc[u]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ic = ic0 + (q >> 1), ib = ib0 + (q & 1);
+                    ok[u][q] = ic >= 0 && ic < nc && ib >= 0 && ib < nb;
+                    const int icc = min(max(ic, 0), nc - 1), ibc = min(max(ib, 0), nb - 1);
+                    v[u][q] = __ldg(src + ((int64_t)(i + u) * nc + icc) * nb + ibc);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                float sm[NM];
+#pragma unroll
+                for (int m = 0; m < NM; ++m) sm[m] = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!ok[u][q]) continue;
+                    const float wc = (q >> 1) ? gc[u] : 1.f - gc[u];
+                    const float wbc = ((q & 1) ? gb[u] : 1.f - gb[u]) * wc;
+                    float val[NM];
+                    P3<NM>::get(v[u][q], val);
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) sm[m] = fmaf(wbc, val[m], sm[m]);
+                }
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const float yk = __fsub_rn(sm[m], comp[m]);
+                    const float tt = __fadd_rn(acc[m], yk);
+                    comp[m] = __fsub_rn(__fsub_rn(tt, acc[m]), yk);
+                    acc[m] = tt;
+                }
+            }
+        }
+    }
+    for (; i <= i_hi; ++i) {
         if (ALIGNED && (i < lo || i > hi)) continue;
         const float t = (float)i - ca;
         float gb, gc;

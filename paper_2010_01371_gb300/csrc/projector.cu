@@ -254,7 +254,41 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restri
     float acc[NM], comp[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
-    for (int i = lo; i <= hi; ++i) {
+    // Two samples per step, their four loads issued before use (addresses
+    // clamped into the grid, values zeroed outside it); the samples are then
+    // added in order, exactly as one at a time.
+    using T = typename Pack<NM>::T;
+    int i = lo;
+    for (; i + 1 <= hi; i += 2) {
+        T va[2], vb[2];
+        float f[2];
+        bool oa[2], ob[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i0 = joseph_split(fmaf((float)(i + u), r.y, f0h), f[u]);
+            const T *base = src + (int64_t)(i + u) * n_other;
+            oa[u] = i0 >= 0 && i0 < n_other;
+            ob[u] = i0 + 1 >= 0 && i0 + 1 < n_other;
+            va[u] = __ldg(base + min(max(i0, 0), n_other - 1));
+            vb[u] = __ldg(base + min(max(i0 + 1, 0), n_other - 1));
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float a[NM], b[NM];
+            Pack<NM>::get(va[u], a);
+            Pack<NM>::get(vb[u], b);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const float am = oa[u] ? a[m] : 0.f, bm = ob[u] ? b[m] : 0.f;
+                const float v = __fadd_rn(__fmul_rn(1.f - f[u], am), __fmul_rn(f[u], bm));
+                const float yk = __fsub_rn(v, comp[m]);
+                const float t = __fadd_rn(acc[m], yk);
+                comp[m] = __fsub_rn(__fsub_rn(t, acc[m]), yk);
+                acc[m] = t;
+            }
+        }
+    }
+    for (; i <= hi; ++i) {
         float f;
         const int i0 = joseph_split(fmaf((float)i, r.y, f0h), f);
         const typename Pack<NM>::T *base = src + (int64_t)i * n_other;
@@ -291,7 +325,35 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_pair_kernel(const float4 *__r
     const int rel = __float_as_int(kSplitMagic) - 1;
     const float2 *row = (axis == 0 ? pc : pr) + (int64_t)lo * stride;
     float acc = 0.f, comp = 0.f, fi = (float)lo;
-    for (int i = lo; i <= hi; ++i, fi += 1.f, row += stride) {
+    // Four samples per step: their neighbour-pair loads are issued before any
+    // is consumed, so a lane keeps four independent gathers in flight; the
+    // samples are then added in order, exactly as one at a time.
+    constexpr int U = 4;
+    int i = lo;
+    for (; i + U - 1 <= hi; i += U, fi += (float)U, row += U * stride) {
+        float2 ab[U];
+        float f[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float h = fmaf(fi + (float)u, r.y, f0h);
+            const float rn = h + kSplitMagic;
+            const int k = __float_as_int(rn) - rel;
+            ok[u] = (unsigned)k <= (unsigned)n_other;   // else both pixels are off the grid
+            f[u] = (h - (rn - kSplitMagic)) + 0.5f;
+            ab[u] = __ldg(row + u * stride + (ok[u] ? k : 0));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ok[u]) continue;
+            const float v = fmaf(f[u], ab[u].y - ab[u].x, ab[u].x);
+            const float yk = __fsub_rn(v, comp);
+            const float t = __fadd_rn(acc, yk);
+            comp = __fsub_rn(__fsub_rn(t, acc), yk);
+            acc = t;
+        }
+    }
+    for (; i <= hi; ++i, fi += 1.f, row += stride) {
         const float h = fmaf(fi, r.y, f0h);
         const float rn = h + kSplitMagic;
         const int k = __float_as_int(rn) - rel;

@@ -2,10 +2,14 @@
 
 Applies are checked with the preconditioner created from the oracle's own
 eigenvalues / blocks (tolerance 1e-5: the FP32 FFT and Haar kernels).  The
-GPU build itself runs in FP32 (impulse responses through the FP32 projector,
-FP32 FFT) and is checked against the FP64 build at 1e-3: the eigenvalues at
-the smallest frequencies are differences of large responses, where FP32
-rounding of ~1e-7 of the largest response becomes ~1e-4 of the smallest.
+GPU build itself applies the Hessian in FP32; its arrays are bounded element
+by element in test_gpu_build.py (Weyl: an eigenvalue estimate moves by up to
+eps_b lambda_max, eps_b ~ 8 n 2^-24).  Here the built preconditioner's
+operators M, M^T, |M|, |M|^T are compared with the FP64 build's, in relative
+L2, at a tolerance per kind a few times the measured error: plain Fourier
+1e-3 (its spectrum spans about three and a half decades, so its smallest
+eigenvalues carry ~1e-4..1e-3), modified Fourier and the cross-material kinds
+1e-4, Haar and the blocks 1e-5.
 """
 import numpy as np
 import pytest
@@ -16,7 +20,8 @@ from _helpers import gpu_precond_from, oracle_precond, rel_l2, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 APPLY_TOL = 1e-5
-BUILD_TOL = 1e-3
+BUILD_TOLS = {"fourier": 1e-3, "mod_fourier": 1e-4, "haar": 1e-5, "block": 1e-5, "block_fourier": 1e-4,
+              "block_haar": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +88,7 @@ def test_build_parity(psps, oracle_lib, error_log, pname, kind):
     st, P, _ = oracle_precond(oracle_lib, prob, kind)
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     pc = psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta)
-    check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOL, log=error_log,
+    check_ops(psps, pc, P, (1,) + prob.geom.image_shape, BUILD_TOLS[kind], log=error_log,
               name=f"GPU-built {pname} {kind}")
 
 
@@ -98,7 +103,7 @@ def test_mbmd_apply_and_build(psps, oracle_lib, error_log, kind):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (3,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL,
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOLS[kind],
               log=error_log, name=f"GPU-built c4_64 {kind}")
 
 
@@ -142,7 +147,7 @@ def test_mixed_radix_fourier(psps, oracle_lib, kind):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (1,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOLS[kind])
 
 
 @pytest.mark.parametrize("n", [40, 48, 56])
@@ -154,7 +159,8 @@ def test_mixed_radix_cross_material(psps, oracle_lib, n):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (3,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, "block_fourier", data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape,
+              BUILD_TOLS["block_fourier"])
 
 
 def cone_mbir_problem():
@@ -174,7 +180,7 @@ def test_3d_fourier(psps, oracle_lib, kind):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (1,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, kind, data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, kind, to_dev(prob.y), prob.beta), P, shape, BUILD_TOLS[kind])
 
 
 def test_3d_cross_material_fourier(psps, oracle_lib):
@@ -185,7 +191,8 @@ def test_3d_cross_material_fourier(psps, oracle_lib):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (2,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, "block_fourier", data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "block_fourier", to_dev(prob.y), prob.beta), P, shape,
+              BUILD_TOLS["block_fourier"])
 
 
 def cone_haar_problem(n=16):
@@ -242,7 +249,7 @@ def test_3d_haar_build(psps, oracle_lib):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (1,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, "haar", data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, "haar", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "haar", to_dev(prob.y), prob.beta), P, shape, BUILD_TOLS["haar"])
 
 
 def test_3d_cross_material_wavelet_build(psps, oracle_lib):
@@ -254,7 +261,8 @@ def test_3d_cross_material_wavelet_build(psps, oracle_lib):
     plan, spec = psps.Plan(prob.geom), psps.Spectrum(prob.Q, prob.S)
     shape = (2,) + prob.geom.image_shape
     check_ops(psps, gpu_precond_from(psps, plan, spec, "block_haar", data), P, shape, APPLY_TOL)
-    check_ops(psps, psps.Precond(plan, spec, "block_haar", to_dev(prob.y), prob.beta), P, shape, BUILD_TOL)
+    check_ops(psps, psps.Precond(plan, spec, "block_haar", to_dev(prob.y), prob.beta), P, shape,
+              BUILD_TOLS["block_haar"])
 
 
 def test_3d_haar_rejects_non_cubes(psps):

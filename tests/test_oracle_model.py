@@ -390,3 +390,103 @@ def test_correlated_surrogate_majorises():
         return float(np.sum(0.5 * e * np.exp(-2 * zz) + rh * np.exp(-zz)))
     assert L1(z) - L1(z0) <= Hs(eta1, rho1, z) - Hs(eta1, rho1, z0) + 1e-9 * abs(L1(z0))
     assert L1(z) - L1(z0) > Hs(eta_w, rho_w, z) - Hs(eta_w, rho_w, z0) + 1e-6 * abs(L1(z) - L1(z0))
+
+
+@pytest.mark.parametrize("with_blur", [False, True])
+def test_line_terms_derivatives(with_blur):
+    """phi, phi', phi'' of the data term along a direction (diagonal
+    Sigma_y, with and without a detector blur) equal the objective and its
+    central differences."""
+    from oracle import model
+    Q, S, blur, l, y, n = _blur_case(seed=31)
+    blur = blur if with_blur else None
+    q = np.random.default_rng(32).normal(0.0, 1.0, l.shape)
+    a, h = 0.3, 1e-4
+    f, f1, f2 = model.line_terms(Q, S, l, q, y, a, blur)
+    phi = lambda t: model.data_objective(Q, S, l + t * q, y, blur)  # noqa: E731
+    assert abs(f - phi(a)) <= 1e-12 * abs(f)
+    assert abs(f1 - (phi(a + h) - phi(a - h)) / (2 * h)) <= 1e-6 * abs(f1) + 1e-9 * abs(f)
+    assert abs(f2 - (phi(a + h) - 2 * phi(a) + phi(a - h)) / h ** 2) <= 1e-4 * abs(f2) + 1e-7 * abs(f)
+
+
+def test_line_terms_one_ray_closed_form():
+    """One ray, one energy (Beer-Lambert): phi(a) = 1/2 w (I0 e^-(l + a q) - y)^2
+    with w = 1 / y, so phi' = -w r I0 q e^-z and
+    phi'' = w I0^2 q^2 e^-2z + w r I0 q^2 e^-z (r = I0 e^-z - y, z = l + a q)."""
+    from oracle import model
+    I0, l0, q, y, a = 1.0e4, 0.7, 0.013, 3100.0, 11.0
+    z = l0 + a * q
+    r = I0 * math.exp(-z) - y
+    w = 1.0 / y
+    f, f1, f2 = model.line_terms(np.ones((1, 1)), np.full((1, 1), I0), np.array([[l0]]), np.array([[q]]),
+                                 np.array([[y]]), a)
+    assert abs(f - 0.5 * w * r * r) <= 1e-13 * abs(f)
+    assert abs(f1 - (-w * r * I0 * q * math.exp(-z))) <= 1e-13 * abs(f1)
+    assert abs(f2 - (w * (I0 * q * math.exp(-z)) ** 2 + w * r * I0 * q * q * math.exp(-z))) <= 1e-13 * abs(f2)
+
+
+def _rule(phi, dphi, d2phi, a0, n_ls=3, n_halve=8, trust=8.0, alpha_max=1e12):
+    """The line-search rule as stated (reading R8), written out for a scalar
+    phi given in closed form: n_ls evaluations starting at a0, each followed
+    (but the last) by a Newton step kept within [a / trust, a trust] and
+    below alpha_max (a kept when phi'' <= 0); accept the last evaluated a if
+    phi(a) <= phi(0), else halve up to n_halve times, else 0.  Returns
+    (alpha, evaluated points, clipped, halvings)."""
+    a, pts, clipped = a0, [], False
+    for k in range(n_ls):
+        pts.append(a)
+        if k + 1 < n_ls:
+            if d2phi(a) > 0:
+                newton = a - dphi(a) / d2phi(a)
+                an = min(max(newton, a / trust), a * trust)
+                clipped |= an != newton
+            else:
+                an = a
+            a = min(an, alpha_max)
+    if phi(a) <= phi(0.0):
+        return a, pts, clipped, 0
+    for h in range(1, n_halve + 1):
+        a = 0.5 * a
+        if phi(a) <= phi(0.0):
+            return a, pts, clipped, h
+    return 0.0, pts, clipped, n_halve + 1
+
+
+@pytest.mark.parametrize("case", ["newton_inside", "clipped", "halved"])
+def test_line_search_worked_example(case):
+    """The oracle's safeguarded line search against the stated rule on a
+    one-ray problem whose phi is known in closed form (projection domain,
+    one material and energy, no penalty): a Newton step inside the trust
+    region, steps clipped by the factor-8 trust bound (the minimiser far
+    out), and an overshooting warm start that needs halvings.  A different
+    trust factor, halving count or acceptance test changes alpha."""
+    import oracle
+    from oracle import psps as opsps
+    I0, q = 1.0e4, 1.0e-3
+    y_of = {"newton_inside": I0 * math.exp(-3.0 * q), "clipped": I0 * math.exp(-500.0 * q),
+            "halved": 0.9 * I0}
+    a0 = {"newton_inside": 1.0, "clipped": 1.0, "halved": 4000.0}[case]
+    y = y_of[case]
+    st = opsps.Setup(oracle.IdentityProjector(1), np.ones((1, 1)), np.full((1, 1), I0), np.array([[y]]), None)
+    x = np.zeros((1, 1))
+    p = np.full((1, 1), q)
+    w = 1.0 / y
+
+    def phi(a):
+        return 0.5 * w * (I0 * math.exp(-a * q) - y) ** 2
+
+    def dphi(a):
+        return -w * (I0 * math.exp(-a * q) - y) * I0 * q * math.exp(-a * q)
+
+    def d2phi(a):
+        e = math.exp(-a * q)
+        return w * (I0 * q * e) ** 2 + w * (I0 * e - y) * I0 * q * q * e
+    want, pts, clipped, halvings = _rule(phi, dphi, d2phi, a0)
+    got, f, _ = opsps.line_search(st, x, p, np.zeros((1, 1)), p.copy(), phi(0.0), opsps.LineSearch(), a0)
+    assert abs(got - want) <= 1e-12 * max(abs(want), 1.0), (case, got, want, pts)
+    if case == "clipped":
+        assert clipped and want == 64.0
+    if case == "halved":
+        assert halvings >= 1
+    if case == "newton_inside":
+        assert not clipped and abs(want - 3.0) < 0.5
