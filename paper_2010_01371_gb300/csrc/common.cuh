@@ -266,6 +266,9 @@ mbir_status project(mbir_plan *p, const float *x, float *l, int n_mat, cudaStrea
 mbir_status backproject(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s);
 // cone-beam (cone.cu)
 mbir_status cone_setup(mbir_plan *p);
+// Floats of each zero-bordered packed volume copy the cone forward reads
+// (4 per voxel, the largest of the three driving-axis layouts).
+int64_t cone_pack_floats(const mbir_geometry &g);
 mbir_status project_cone(mbir_plan *p, const float *x, float *l, int n_mat, cudaStream_t s);
 mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_mat, int accumulate, cudaStream_t s);
 }  // namespace psps

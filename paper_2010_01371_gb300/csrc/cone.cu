@@ -156,17 +156,50 @@ __device__ __forceinline__ void decode3(float2 b, int &axis, int &lo, int &hi) {
 }
 
 // Packed copies of x[m][z][y][x] for the three driving axes, materials
-// innermost with stride P: layout[a][c][b][m] (see the file comment).
+// innermost with stride P: layout[a][c][b][m] (see the file comment), each
+// plane of the driving axis with kPad zero cells on both sides of b and c,
+// so that every tap of every sample a ray's range can take lies inside the
+// copy and reads the value or a zero (no bounds tests in the forward).
+constexpr int kPad = 2;
+
+__host__ __device__ inline int64_t pack3d_floats(int nx, int ny, int nz) {
+    const int64_t a = (int64_t)nx * (nz + 2 * kPad) * (ny + 2 * kPad);   // a = x: [ix][iz][iy]
+    const int64_t b = (int64_t)ny * (nz + 2 * kPad) * (nx + 2 * kPad);   // a = y: [iy][iz][ix]
+    const int64_t c = (int64_t)nz * (ny + 2 * kPad) * (nx + 2 * kPad);   // a = z: [iz][iy][ix]
+    return 4 * (a > b ? (a > c ? a : c) : (b > c ? b : c));
+}
+
+// Zero the kPad-wide borders of the three packed copies (the interiors are
+// written by pack3d_kernel), P floats per cell.
+__global__ void pack3d_border_kernel(int P, int nx, int ny, int nz, float *__restrict__ ox, float *__restrict__ oy,
+                                     float *__restrict__ oz) {
+    const int W = 2 * kPad;
+    for (int a = 0; a < 3; ++a) {
+        const int na = a == 0 ? nx : (a == 1 ? ny : nz);
+        const int nb = a == 0 ? ny : nx, nc = a == 2 ? ny : nz;
+        const int64_t plane = (int64_t)(nc + W) * (nb + W);
+        float *o = a == 0 ? ox : (a == 1 ? oy : oz);
+        const int64_t n = (int64_t)na * plane;
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+            const int rem = (int)(k % plane);
+            const int c = rem / (nb + W), b = rem % (nb + W);
+            if (c >= kPad && c < nc + kPad && b >= kPad && b < nb + kPad) continue;
+            for (int m = 0; m < P; ++m) o[k * P + m] = 0.f;
+        }
+    }
+}
+
 __global__ void pack3d_kernel(const float *__restrict__ x, int nm, int P, int nx, int ny, int nz,
                               float *__restrict__ ox, float *__restrict__ oy, float *__restrict__ oz) {
     const int64_t n = (int64_t)nx * ny * nz;
+    const int W = 2 * kPad;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(j % nx);
         const int iy = (int)((j / nx) % ny);
         const int iz = (int)(j / ((int64_t)nx * ny));
-        const int64_t px = (((int64_t)ix * nz + iz) * ny + iy) * P;   // a = x: [ix][iz][iy]
-        const int64_t py = (((int64_t)iy * nz + iz) * nx + ix) * P;   // a = y: [iy][iz][ix]
-        const int64_t pz = (((int64_t)iz * ny + iy) * nx + ix) * P;   // a = z: [iz][iy][ix]
+        const int64_t px = (((int64_t)ix * (nz + W) + iz + kPad) * (ny + W) + iy + kPad) * P;   // [ix][iz][iy]
+        const int64_t py = (((int64_t)iy * (nz + W) + iz + kPad) * (nx + W) + ix + kPad) * P;   // [iy][iz][ix]
+        const int64_t pz = (((int64_t)iz * (ny + W) + iy + kPad) * (nx + W) + ix + kPad) * P;   // [iz][iy][ix]
         for (int m = 0; m < P; ++m) {
             const float v = m < nm ? x[m * n + j] : 0.f;
             ox[px + m] = v;
@@ -234,8 +267,13 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
     const typename P3<NM>::T *src = axis == 0 ? ox : (axis == 1 ? oy : oz);
-    const int nb = axis == 0 ? g.ny : g.nx;
-    const int nc = axis == 2 ? g.ny : g.nz;
+    // padded plane: (nc + 2 kPad) rows of (nb + 2 kPad) cells.  A sample's
+    // lower tap indices are clamped to [-kPad, n + kPad - 2]: a sample the
+    // clamp moves lies wholly outside the volume (its taps are at <= -2 or
+    // >= n), and the clamped taps then read border zeros, as the true ones
+    // are; every other sample reads its own taps.
+    const int nb = axis == 0 ? g.ny : g.nx, nc = axis == 2 ? g.ny : g.nz;
+    const int nbp = nb + 2 * kPad, ncp = nc + 2 * kPad;
     const float ca = 0.5f * ((axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz)) - 1);
     float acc[NM], comp[NM];
 #pragma unroll
@@ -249,18 +287,16 @@ __global__ void __launch_bounds__(kThreads)
         for (; i + 1 <= i_hi; i += 2) {
             T v[2][4];
             float gb[2], gc[2];
-            bool ok[2][4];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const float t = (float)(i + u) - ca;
                 const int ib0 = joseph_split(fmaf(t, A.y, A.x), gb[u]), ic0 = joseph_split(fmaf(t, A.w, A.z), gc[u]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int ic = ic0 + (q >> 1), ib = ib0 + (q & 1);
-                    ok[u][q] = ic >= 0 && ic < nc && ib >= 0 && ib < nb;
-                    const int icc = min(max(ic, 0), nc - 1), ibc = min(max(ib, 0), nb - 1);
-                    v[u][q] = __ldg(src + ((int64_t)(i + u) * nc + icc) * nb + ibc);
-                }
+                const int ibc = min(max(ib0, -kPad), nb + kPad - 2), icc = min(max(ic0, -kPad), nc + kPad - 2);
+                const T *tap = src + ((int64_t)(i + u) * ncp + icc + kPad) * nbp + ibc + kPad;
+                v[u][0] = __ldg(tap);
+                v[u][1] = __ldg(tap + 1);
+                v[u][2] = __ldg(tap + nbp);
+                v[u][3] = __ldg(tap + nbp + 1);
             }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -269,7 +305,6 @@ __global__ void __launch_bounds__(kThreads)
                 for (int m = 0; m < NM; ++m) sm[m] = 0.f;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (!ok[u][q]) continue;
                     const float wc = (q >> 1) ? gc[u] : 1.f - gc[u];
                     const float wbc = ((q & 1) ? gb[u] : 1.f - gb[u]) * wc;
                     float val[NM];
@@ -295,18 +330,16 @@ __global__ void __launch_bounds__(kThreads)
         float s[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) s[m] = 0.f;
+        const int ibc = min(max(ib0, -kPad), nb + kPad - 2), icc = min(max(ic0, -kPad), nc + kPad - 2);
+        const typename P3<NM>::T *tap = src + ((int64_t)i * ncp + icc + kPad) * nbp + ibc + kPad;
 #pragma unroll
         for (int jc = 0; jc < 2; ++jc) {
-            const int ic = ic0 + jc;
-            if (ic < 0 || ic >= nc) continue;
             const float wc = jc ? gc : 1.f - gc;
 #pragma unroll
             for (int jb = 0; jb < 2; ++jb) {
-                const int ib = ib0 + jb;
-                if (ib < 0 || ib >= nb) continue;
                 const float wbc = (jb ? gb : 1.f - gb) * wc;
                 float val[NM];
-                P3<NM>::get(__ldg(src + ((int64_t)i * nc + ic) * nb + ib), val);
+                P3<NM>::get(__ldg(tap + jc * nbp + jb), val);
 #pragma unroll
                 for (int m = 0; m < NM; ++m) s[m] = fmaf(wbc, val[m], s[m]);
             }
@@ -802,6 +835,8 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
 
 }  // namespace
 
+int64_t cone_pack_floats(const mbir_geometry &g) { return pack3d_floats(g.nx, g.ny, g.nz); }
+
 mbir_status cone_setup(mbir_plan *p) {
     PSPS_TRY(p->view.alloc(p->g.n_views));
     PSPS_TRY(p->ray.alloc(p->n_rays));
@@ -825,6 +860,8 @@ mbir_status project_cone(mbir_plan *p, const float *x, float *l, int n_mat, cuda
         const int P = nm == 1 ? 1 : (nm == 2 ? 2 : 4);
         float *ox = p->xcol.p, *oy = p->xrow.p, *oz = p->xcol3.p;
         const int64_t grid = cdiv(n, kThreads) < 65535 * 8 ? cdiv(n, kThreads) : 65535 * 8;
+        pack3d_border_kernel<<<1024, kThreads, 0, s>>>(P, g.nx, g.ny, g.nz, ox, oy, oz);
+        PSPS_LAUNCH_CHECK();
         pack3d_kernel<<<(unsigned)grid, kThreads, 0, s>>>(x + m0 * n, nm, P, g.nx, g.ny, g.nz, ox, oy, oz);
         PSPS_LAUNCH_CHECK();
         const unsigned gr = (unsigned)cdiv(p->n_rays, kThreads);

@@ -254,41 +254,7 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_kernel(const float4 *__restri
     float acc[NM], comp[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = comp[m] = 0.f;
-    // Two samples per step, their four loads issued before use (addresses
-    // clamped into the grid, values zeroed outside it); the samples are then
-    // added in order, exactly as one at a time.
-    using T = typename Pack<NM>::T;
-    int i = lo;
-    for (; i + 1 <= hi; i += 2) {
-        T va[2], vb[2];
-        float f[2];
-        bool oa[2], ob[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int i0 = joseph_split(fmaf((float)(i + u), r.y, f0h), f[u]);
-            const T *base = src + (int64_t)(i + u) * n_other;
-            oa[u] = i0 >= 0 && i0 < n_other;
-            ob[u] = i0 + 1 >= 0 && i0 + 1 < n_other;
-            va[u] = __ldg(base + min(max(i0, 0), n_other - 1));
-            vb[u] = __ldg(base + min(max(i0 + 1, 0), n_other - 1));
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            float a[NM], b[NM];
-            Pack<NM>::get(va[u], a);
-            Pack<NM>::get(vb[u], b);
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                const float am = oa[u] ? a[m] : 0.f, bm = ob[u] ? b[m] : 0.f;
-                const float v = __fadd_rn(__fmul_rn(1.f - f[u], am), __fmul_rn(f[u], bm));
-                const float yk = __fsub_rn(v, comp[m]);
-                const float t = __fadd_rn(acc[m], yk);
-                comp[m] = __fsub_rn(__fsub_rn(t, acc[m]), yk);
-                acc[m] = t;
-            }
-        }
-    }
-    for (; i <= hi; ++i) {
+    for (int i = lo; i <= hi; ++i) {
         float f;
         const int i0 = joseph_split(fmaf((float)i, r.y, f0h), f);
         const typename Pack<NM>::T *base = src + (int64_t)i * n_other;
@@ -1281,8 +1247,9 @@ extern "C" mbir_status mbir_plan_create(const mbir_geometry *g, int n_mat_max, m
     p->n_rays = (int64_t)p->g.n_views * p->g.n_u * p->g.n_v;
     p->n_pix = (int64_t)p->g.nx * p->g.ny * p->g.nz;
     mbir_status st;
-    if ((st = p->xcol.alloc(p->n_pix * 4)) != MBIR_OK || (st = p->xrow.alloc(p->n_pix * 4)) != MBIR_OK ||
-        (cone && (st = p->xcol3.alloc(p->n_pix * 4)) != MBIR_OK)) {
+    const int64_t copy = cone ? std::max<int64_t>(p->n_pix * 4, cone_pack_floats(p->g)) : p->n_pix * 4;
+    if ((st = p->xcol.alloc(copy)) != MBIR_OK || (st = p->xrow.alloc(copy)) != MBIR_OK ||
+        (cone && (st = p->xcol3.alloc(copy)) != MBIR_OK)) {
         delete p;
         return st;
     }
