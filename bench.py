@@ -677,7 +677,7 @@ def kernel_bench(args, prob):
     out = {}
     if prob.geom.kind == 2:
         # cone beam: forward of the basis images, and the 2 n_mat-channel
-        # transposes (split-table gather, direct gather)
+        # transposes (fixed-point tile scatter, direct and split-table gathers)
         nm = x1.shape[0]
         s4 = torch.as_tensor(rng.random((2 * nm, plan.n_rays)).astype(np.float32), device=dev)
         l = torch.empty((nm, plan.n_rays), device=dev)
@@ -698,10 +698,9 @@ def kernel_bench(args, prob):
         for mode in ["ray", "aligned"]:
             plan.set_projector(mode)
             out[f"project_{mode}_{nm}ch_ms"] = timec(lambda: p.mbir_project(plan, x1, l))
-        for mode in ["tile", "gather"]:
+        for mode in ["tile", "gather", "split"]:
             plan.set_backprojector(mode)
-            out[f"backproject_{'split' if mode == 'tile' else 'gather'}_{2 * nm}ch_ms"] = timec(
-                lambda: p.mbir_backproject(plan, s4, img))
+            out[f"backproject_{mode}_{2 * nm}ch_ms"] = timec(lambda: p.mbir_backproject(plan, s4, img))
         print(json.dumps({"kernels": out, "workload": args.workload}), flush=True)
         return
     s2 = torch.as_tensor(rng.random((2, plan.n_rays)).astype(np.float32), device=dev)

@@ -118,11 +118,21 @@ mbir_status mbir_backproject(mbir_plan *plan, const float *s, float *x, int n_ma
  * more for finer bins); the sums are exact integer sums, so the result is
  * bitwise reproducible.  A non-finite input makes its channel's image NaN.
  * It needs 8 bytes x n_mat_max x n_pix of plan scratch.  3-D (cone): 0 =
- * voxel-driven gather with per-plane split tables in shared memory (default),
- * 1 = the direct voxel-driven gather (both deterministic and bitwise equal),
- * 2 = ray-driven scatter with global FP32 atomics.  All use the forward projector's per-ray weights and
- * are the exact transpose of mbir_project up to FP32 rounding.  MBIR_ERR_ARG
- * for another mode. */
+ * tile scatter (default): a CTA per 8 x 8 x 16-voxel tile runs over every
+ * view, stages the rays of the tile's detector box and adds each (ray, tile
+ * plane) sample's bilinear terms to 32-bit fixed-point shared-memory
+ * accumulators, flushed into exact 64-bit sums every vb views; each term is
+ * rounded to a grid of M max(2^-22, T 2^-30), M = max |weight x value| of
+ * the channel over the call, T = vb x the plan's bound on the rays of one view
+ * that reach one voxel (vb chosen so that T <= 256 where that bound allows),
+ * bitwise reproducible, a non-finite input makes its channel's image NaN;
+ * plans whose geometry gives no such bound (a source within the volume's
+ * reach) run mode 1 instead.  1 = voxel-driven gather (FP32 sums per view,
+ * Kahan-compensated across views; deterministic), 2 = ray-driven scatter with
+ * global FP32 atomics, 3 = the voxel gather with per-plane split tables in
+ * shared memory (bitwise equal to 1).  All use the forward projector's
+ * per-ray weights and are the exact transpose of mbir_project up to
+ * rounding.  MBIR_ERR_ARG for another mode (3 on a 2-D plan). */
 mbir_status mbir_plan_set_backprojector(mbir_plan *plan, int mode);
 /* Views handled by one CTA of the tile transpose (mode 0), 1..180: the
  * grid is (image tiles) x ceil(n_views / views_per_cta) CTAs.  The plan's
@@ -138,8 +148,8 @@ mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
  * 90/120/180 views per CTA (written to *views_per_cta if non-NULL), then the
  * forward projection of n_channels / 2 (at least 1) basis images by one
  * thread per ray and by the strip kernel with 32/64/128/256 bins (and
- * 256 / that many views) per CTA.  Cone-beam plans: the split-table and the
- * direct voxel gather (bitwise equal results), then the forward's per-lane
+ * 256 / that many views) per CTA.  Cone-beam plans: the tile scatter (where
+ * available), the direct voxel gather and the split-table gather, then the forward's per-lane
  * and warp-aligned marches (mbir_plan_set_projector modes 1 and 2; equal
  * results).  Synchronises; allocates and
  * frees temporary device buffers; not allowed while `stream` is capturing

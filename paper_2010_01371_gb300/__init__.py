@@ -78,9 +78,11 @@ class Plan:
         self.sino_shape = tuple(geom.sino_shape)
 
     def set_backprojector(self, mode: str):
-        """'tile' (default), 'gather' (deterministic) or 'atomic' (ray-driven
-        scatter with global atomics)."""
-        _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2}[mode])
+        """'tile' (default: fixed-point tile scatter, deterministic), 'gather'
+        (pixel / voxel gather, FP32, deterministic), 'atomic' (ray-driven
+        scatter with global atomics) or, for cone plans, 'split' (the voxel
+        gather with split tables, bitwise equal to 'gather')."""
+        _call(lib().mbir_plan_set_backprojector, self.h, {"tile": 0, "gather": 1, "atomic": 2, "split": 3}[mode])
 
     def set_tiling(self, views_per_cta: int):
         """Views per CTA of the 'tile' transpose (1..180)."""

@@ -217,7 +217,7 @@ struct mbir_plan {
     psps::DBuf<float4> ray;       // (f0, df, w, bits(axis,lo,hi))
     // 2-D per-view constants for the pixel-driven transpose
     psps::DBuf<float4> view;      // parallel: (cos, sin, -, -); fan: (sx, sy, beta + pi, -)
-    int back_mode = 0;            // 0 tile scatter (default), 1 pixel gather, 2 ray-driven atomics
+    int back_mode = 0;            // 0 tile scatter (default), 1 pixel / voxel gather, 2 ray-driven atomics, 3 split-table gather (3-D)
     int back_views = 60;          // views per CTA of the tile transpose
     int fwd_mode = 1;             // 0 tile sums, 1 one thread per ray (default), 2 shared-memory strips
     int strip_bins = 64;          // strip forward: bins per CTA (32, 64, 128 or 256; 256 / it views)
@@ -238,8 +238,14 @@ struct mbir_plan {
     // 2-D tile transpose: 64-bit fixed-point image sums ([n_mat_max][n_pix])
     psps::DBuf<long long> xfix;
     // bound on the rays of one view that add to one tile accumulator (0: none
-    // known; the CTA's candidate count bounds it then)
+    // known; 2-D: the CTA's candidate count bounds it then; 3-D: the tile
+    // transpose is replaced by the direct gather)
     int cell_rays = 0;
+    // 3-D tile transpose: the number of leading channels of the next calls
+    // that also accumulate each term's remainder (two words per voxel: terms
+    // held to 2^-12 of the fixed-point unit); set around a call by the
+    // gradient numerators' callers
+    int tile_fine = 0;
 };
 
 struct mbmd_spectrum {

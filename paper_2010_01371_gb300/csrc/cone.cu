@@ -34,7 +34,9 @@
 // must be a and the ray's sample split must put the voxel on one of its four
 // taps.  The ray-driven scatter with global FP32 atomics
 // remains as the alternative (mbir_plan_set_backprojector mode 2).
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -399,16 +401,34 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Weighted sinogram for the gather: ws[ray][c] = w_ray * sino[c][ray],
-// channels interleaved (C = 1, 2 or 4 floats per ray; channels past nc are 0).
+// Weighted sinogram for the transposes: ws[ray][c] = w_ray * sino[c][ray],
+// channels interleaved (C = 1, 2 or 4 floats per ray; channels past nc are
+// 0).  smax (optional, zeroed by the caller): per channel max_ray |ws| as
+// float bits (atomicMax on the bits orders non-negative floats; a NaN makes
+// it NaN bits, above every finite value).
 template <int C>
 __global__ void weigh_sino_kernel(const float2 *__restrict__ tb, const float *__restrict__ sino, int nc,
-                                  int64_t n_rays, float *__restrict__ ws) {
+                                  int64_t n_rays, float *__restrict__ ws, unsigned *__restrict__ smax) {
+    unsigned mx[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) mx[c] = 0u;
     for (int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ray < n_rays;
          ray += (int64_t)gridDim.x * blockDim.x) {
         const float w = tb[ray].x;
 #pragma unroll
-        for (int c = 0; c < C; ++c) ws[ray * C + c] = c < nc ? w * sino[(int64_t)c * n_rays + ray] : 0.f;
+        for (int c = 0; c < C; ++c) {
+            const float v = c < nc ? w * sino[(int64_t)c * n_rays + ray] : 0.f;
+            ws[ray * C + c] = v;
+            const float a = fabsf(v);
+            const unsigned bits = a != a ? 0x7fc00000u : __float_as_uint(a);
+            mx[c] = bits > mx[c] ? bits : mx[c];
+        }
+    }
+    if (!smax) return;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, mx[c]);
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(smax + c, m);
     }
 }
 
@@ -418,16 +438,19 @@ template <>
 struct Vec<1> {
     using T = float;
     __device__ static void get(const T &v, float (&o)[1]) { o[0] = v; }
+    __device__ static void put(T &v, const float (&o)[1]) { v = o[0]; }
 };
 template <>
 struct Vec<2> {
     using T = float2;
     __device__ static void get(const T &v, float (&o)[2]) { o[0] = v.x, o[1] = v.y; }
+    __device__ static void put(T &v, const float (&o)[2]) { v = make_float2(o[0], o[1]); }
 };
 template <>
 struct Vec<4> {
     using T = float4;
     __device__ static void get(const T &v, float (&o)[4]) { o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w; }
+    __device__ static void put(T &v, const float (&o)[4]) { v = make_float4(o[0], o[1], o[2], o[3]); }
 };
 
 // Detector cells whose centres lie in the bounding box of the projections of
@@ -833,6 +856,240 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
     }
 }
 
+// Ray-driven tile transpose with fixed-point shared-memory sums (mode 0,
+// the default).  A CTA owns a tile of kTX x kTY x kTZ voxels and runs over
+// every view.  For each view and each driving axis a of its rays it stages,
+// in chunks, the detector box that covers the tile's footprint (the gather's
+// box), and every pair (staged ray, tile plane of axis a) takes the forward's
+// sample split on that plane and adds the sample's bilinear terms, times the
+// ray's weighted value of each channel, to the tile's accumulators of the
+// taps that lie in the tile.  A voxel so receives exactly the terms of the
+// forward's weights (A^T), without the gather's per-voxel candidate search;
+// a sample whose taps straddle the tile's edge is taken by each tile it
+// reaches, for its own taps.
+//
+// The accumulators are 32-bit fixed point, [C][kTZ][kTY][kTX] with the x
+// index XOR-swizzled by y, so that a warp's lanes (eight planes x four rays)
+// fall in distinct banks for x- and y-driven rays.  Channel c uses the scale
+//   sc = min(2^22, 2^30 / T) / M_c,  M_c = max_i |w_i s_c,i|,
+// T = a bound on the terms one accumulator receives between two flushes: a
+// ray adds at most one term to a voxel and at most cell_rays rays of a view
+// reach one voxel (the plan's bound, from cone_setup), so with a flush every
+// vb views T = vb * cell_rays (vb chosen so that T <= 256 where the bound
+// allows: a grid of M_c 2^-22).  A ray's scaled value v = sc w s (rounded) is at
+// most min(2^22, 2^30 / T), each term round(w_bc v) (one FMA with the magic
+// number: exact rounding to nearest) at most that plus 1/2, and T of them
+// stay below 2^31.  Channels c < nfine (the gradient numerators, which the
+// cross-material preconditioners difference: there a grid of M_c 2^-22 shows
+// in the step) also add each term's remainder w v - round(w v), rounded to
+// 2^-11 units, to a second word: terms of at most 2^10 of those units, T of
+// them below 2^31.  At every flush each thread moves its own voxels' words
+// into 64-bit registers (exact integer sums in units of 2^-11 / sc) and
+// clears them; the image is sum / sc.  Integer sums are exact, so the result
+// is the same bit for bit whatever order the adds run in; its error against
+// exact arithmetic is at most half a unit 1 / sc per term (2^-12 units for
+// the fine channels) plus the final conversion's 2^-24 relative.  The 64-bit
+// sums hold up to 2^20 flushes.
+constexpr int kTX = 8, kTY = 8, kTZ = 16;     // 1024 voxels per CTA
+constexpr int kTVox = kTX * kTY * kTZ;
+constexpr int kTPlane = kTVox;                 // words per channel
+constexpr int kTThreads = 256;                 // four voxels per thread
+constexpr int kTCap = 512;                     // staged rays per chunk
+constexpr int kTMaxVB = 32;                    // views per flush at most
+constexpr float kFixMagic3 = 12582912.f;       // 1.5 * 2^23: x + magic rounds x (|x| <= 2^22) to an integer
+constexpr int kFixMagic3Bits = 0x4B400000;
+
+// Accumulator word of tile voxel (lx, ly, lz): x fastest, XOR-swizzled with
+// y so that a warp's lanes -- eight consecutive planes of four rays -- fall
+// in distinct banks for x- and y-driven rays.
+__device__ __forceinline__ int tile3_word(int lx, int ly, int lz) {
+    return (lz * kTY + ly) * kTX + (lx ^ (ly & (kTX - 1)));
+}
+
+// Fixed-point scale of one channel (see above) from M_c's float bits; 0 when
+// M_c is not finite, 1 when the channel is all zero.  The quotient is rounded
+// down so that M_c sc never exceeds the limit.
+__device__ __forceinline__ float tile3_scale(unsigned mbits, int bound) {
+    const float M = __uint_as_float(mbits);
+    if (!(M <= 3.0e38f)) return 0.f;
+    if (M == 0.f) return 1.f;
+    const float lim = fminf(4194304.f, 1073741824.f / (float)(bound > 1 ? bound : 1));
+    return fminf(__fdiv_rd(lim, M), 0x1p126f);
+}
+
+template <unsigned OFF>
+__device__ __forceinline__ void red_word(unsigned addr, int v) {
+    asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF) : "memory");
+}
+
+// The terms of one tap (byte address addr of channel 0's word) for every
+// channel: round(w v_c) to the coarse words, and for the first NF channels
+// the remainder w v_c - round(w v_c) on a grid 2^11 times finer to the low
+// words (LO bytes further on).
+template <int C, int NF, unsigned LO, int c = 0>
+__device__ __forceinline__ void tile3_tap(unsigned addr, float w, const float (&v)[C]) {
+    if constexpr (c < C) {
+        const float h = fmaf(w, v[c], kFixMagic3);   // magic + round(w v), exact
+        red_word<4u * c * kTPlane>(addr, __float_as_int(h) - kFixMagic3Bits);
+        if constexpr (c < NF) {
+            const float r = fmaf(w, v[c], kFixMagic3 - h);   // w v - round(w v), |r| <= 1/2
+            red_word<4u * c * kTPlane + LO>(addr, __float_as_int(fmaf(r, 2048.f, kFixMagic3)) - kFixMagic3Bits);
+        }
+        tile3_tap<C, NF, LO, c + 1>(addr, w, v);
+    }
+}
+
+// The pairs (staged ray k < m, tile plane p) of driving axis A: the sample's
+// split on plane a0 + p and its terms on the taps inside the tile (b in
+// [b0, b0 + eb), c in [c0, c0 + ec); planes p < np).  NP consecutive
+// threads take the NP planes (8, or 16 for z-driven rays) of one ray.
+template <int A, int C, int NF>
+__device__ __forceinline__ void tile3_scatter(int m, const float4 *s_ta, const typename Vec<C>::T *s_ws,
+                                              const int *s_ax, int a0, int np, float ca, int b0, int eb, int c0,
+                                              int ec, unsigned acc) {
+    constexpr int NP = A == 2 ? kTZ : (A == 0 ? kTX : kTY);
+    constexpr unsigned LO = 4u * C * kTPlane;   // byte offset of the low words
+    const int p = threadIdx.x % NP;
+    if (p >= np) return;
+    const float t = (float)(a0 + p) - ca;
+    for (int k = threadIdx.x / NP; k < m; k += kTThreads / NP) {
+        if (s_ax[k] != A) continue;
+        const float4 R = s_ta[k];
+        float gb, gc;
+        const int lb = joseph_split(fmaf(t, R.y, R.x), gb) - b0;
+        const int lc = joseph_split(fmaf(t, R.w, R.z), gc) - c0;
+        if (lb < -1 || lb >= eb || lc < -1 || lc >= ec) continue;
+        float v[C];
+        Vec<C>::get(s_ws[k], v);
+#pragma unroll
+        for (int dc = 0; dc < 2; ++dc) {
+            const int cc = lc + dc;
+            if (cc < 0 || cc >= ec) continue;
+            const float wc = dc ? gc : 1.f - gc;
+#pragma unroll
+            for (int db = 0; db < 2; ++db) {
+                const int bb = lb + db;
+                if (bb < 0 || bb >= eb) continue;
+                const float wbc = (db ? gb : 1.f - gb) * wc;
+                const int w = A == 0 ? tile3_word(p, bb, cc) : (A == 1 ? tile3_word(bb, p, cc) : tile3_word(bb, cc, p));
+                tile3_tap<C, NF, LO>(acc + 4u * (unsigned)w, wbc, v);
+            }
+        }
+    }
+}
+
+template <int C, int NF>
+__global__ void __launch_bounds__(kTThreads, 4)
+    back_cone_tile_kernel(mbir_geometry g, const float4 *__restrict__ vt, const float4 *__restrict__ ta,
+                          const float2 *__restrict__ tb, const int *__restrict__ view_axes,
+                          const typename Vec<C>::T *__restrict__ ws, const unsigned *__restrict__ smax, int vb,
+                          int T, int nc, float *__restrict__ x, int accumulate) {
+    __shared__ int acc[(C + NF) * kTPlane];   // C coarse planes, then the fine channels' low words
+    __shared__ float4 s_ta[kTCap];
+    __shared__ typename Vec<C>::T s_ws[kTCap];
+    __shared__ int s_ax[kTCap];
+    __shared__ int4 s_box[kTMaxVB * 3];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
+    const int ex = min(kTX, g.nx - x0), ey = min(kTY, g.ny - y0), ez = min(kTZ, g.nz - z0);
+    const float dx = (float)g.dx, dy = (float)g.dy, dz = (float)g.dz;
+    const float cx = 0.5f * (g.nx - 1), cy = 0.5f * (g.ny - 1), cz = 0.5f * (g.nz - 1);
+    const float tx0 = (x0 - cx) * dx, tx1 = (x0 + ex - 1 - cx) * dx;
+    const float ty0 = (y0 - cy) * dy, ty1 = (y0 + ey - 1 - cy) * dy;
+    const float tz0 = (z0 - cz) * dz, tz1 = (z0 + ez - 1 - cz) * dz;
+    const int *tbits = reinterpret_cast<const int *>(tb);
+    float sc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) sc[c] = tile3_scale(__ldg(smax + c), T);
+    for (int k = tid; k < (C + NF) * kTPlane; k += kTThreads) acc[k] = 0;
+    long long sum[kTVox / kTThreads][C];
+#pragma unroll
+    for (int r = 0; r < kTVox / kTThreads; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) sum[r][c] = 0;
+    const unsigned acc_addr = (unsigned)__cvta_generic_to_shared(acc);
+    for (int vb0 = 0; vb0 < g.n_views; vb0 += vb) {
+        const int nvb = min(vb, g.n_views - vb0);
+        // the detector boxes of the block's (view, axis) pairs, one lane each
+        if (tid < 32) {
+            for (int q = tid; q < 3 * nvb; q += 32) {
+                const int v = vb0 + q / 3, A = q % 3;
+                int4 b = make_int4(0, -1, 0, -1);
+                if ((__ldg(view_axes + v) >> A) & 1) {
+                    const float txs[2] = {A == 0 ? tx0 : tx0 - dx, A == 0 ? tx1 : tx1 + dx};
+                    const float tys[2] = {A == 1 ? ty0 : ty0 - dy, A == 1 ? ty1 : ty1 + dy};
+                    const float tzs[2] = {A == 2 ? tz0 : tz0 - dz, A == 2 ? tz1 : tz1 + dz};
+                    footprint_box<4>(g, __ldg(vt + v), txs, tys, tzs, b.x, b.y, b.z, b.w);
+                }
+                s_box[q] = b;
+            }
+        }
+        __syncthreads();   // boxes published; every flush of the previous block done
+        for (int q = 0; q < 3 * nvb; ++q) {
+            const int4 b = s_box[q];
+            if (b.y < b.x || b.w < b.z) continue;
+            const int v = vb0 + q / 3, A = q % 3;
+            const int sw = b.y - b.x + 1, n = sw * (b.w - b.z + 1);
+            const int64_t view0 = (int64_t)v * g.n_u * g.n_v;
+            for (int k0 = 0; k0 < n; k0 += kTCap) {
+                const int m = min(kTCap, n - k0);
+                for (int k = tid; k < m; k += kTThreads) {
+                    const int kk = k0 + k, row = kk / sw;
+                    const int64_t ray = view0 + (int64_t)(b.z + row) * g.n_u + b.x + (kk - row * sw);
+                    s_ta[k] = __ldg(ta + ray);
+                    float val[C];
+                    Vec<C>::get(__ldg(ws + ray), val);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) val[c] *= sc[c];
+                    Vec<C>::put(s_ws[k], val);
+                    s_ax[k] = __ldg(tbits + 2 * ray + 1) & 3;   // every ray: a view's empty rays may use another axis
+                }
+                __syncthreads();
+                if (A == 0)
+                    tile3_scatter<0, C, NF>(m, s_ta, s_ws, s_ax, x0, ex, cx, y0, ey, z0, ez, acc_addr);
+                else if (A == 1)
+                    tile3_scatter<1, C, NF>(m, s_ta, s_ws, s_ax, y0, ey, cy, x0, ex, z0, ez, acc_addr);
+                else
+                    tile3_scatter<2, C, NF>(m, s_ta, s_ws, s_ax, z0, ez, cz, x0, ex, y0, ey, acc_addr);
+                __syncthreads();
+            }
+        }
+        // flush this thread's voxels (no other thread reads or writes their
+        // words until the next block's first barrier)
+#pragma unroll
+        for (int r = 0; r < kTVox / kTThreads; ++r) {
+            const int j = tid + r * kTThreads;
+            const int w = tile3_word(j % kTX, (j / kTX) % kTY, j / (kTX * kTY));
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                // sums in units of 2^-11 / sc
+                long long u = (long long)acc[c * kTPlane + w] * 2048;
+                acc[c * kTPlane + w] = 0;
+                if (c < NF) {
+                    u += acc[(C + c) * kTPlane + w];
+                    acc[(C + c) * kTPlane + w] = 0;
+                }
+                sum[r][c] += u;
+            }
+        }
+    }
+    const int64_t npix = (int64_t)g.nx * g.ny * g.nz;
+#pragma unroll
+    for (int r = 0; r < kTVox / kTThreads; ++r) {
+        const int j = tid + r * kTThreads;
+        const int lx = j % kTX, ly = (j / kTX) % kTY, lz = j / (kTX * kTY);
+        if (lx >= ex || ly >= ey || lz >= ez) continue;
+        const int64_t o = ((int64_t)(z0 + lz) * g.ny + y0 + ly) * g.nx + x0 + lx;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            if (c >= nc) break;
+            const float v = sc[c] > 0.f ? __fdiv_rn(__ll2float_rn(sum[r][c]), sc[c]) * 0x1p-11f : __int_as_float(0x7fc00000);
+            float *dst = x + (int64_t)c * npix + o;
+            *dst = accumulate ? *dst + v : v;
+        }
+    }
+}
+
 }  // namespace
 
 int64_t cone_pack_floats(const mbir_geometry &g) { return pack3d_floats(g.nx, g.ny, g.nz); }
@@ -844,6 +1101,34 @@ mbir_status cone_setup(mbir_plan *p) {
     PSPS_TRY(p->view_axes.alloc(p->g.n_views));
     PSPS_TRY(p->view_axes.zero(0));
     PSPS_TRY(p->wsino.alloc((size_t)4 * p->n_rays));
+    PSPS_TRY(p->wmax.alloc(4));
+    {
+        // Rays of one view that reach one voxel j (any driving axis), for the
+        // fixed-point scale of the tile transpose.  A ray reaches j through its
+        // sample on j's plane, which then lies within one voxel of j's centre
+        // in the two interpolated axes, so inside the cube of half-side s
+        // (the largest voxel side) around j, whatever the ray's axis.  Its
+        // points are within R of the rotation axis and |z| <= Z, so at depth
+        // D >= D_min = sid - R from the source along the central ray.  On the
+        // flat detector u = sdd L / D and w = sdd z / D (L the lateral
+        // offset, |L| <= R); across the cube L, D and z change by at most
+        // 2 sqrt2 s, so its image spans at most
+        //   E_u = sdd (1 + R / D_min) 2 sqrt2 s / D_min in u,
+        //   E_v = sdd (1 + Z / D_min) 2 sqrt2 s / D_min in v,
+        // and holds at most floor(E / pitch) + 1 cell centres along each (one
+        // more for the FP32 set-up's rounding).
+        const mbir_geometry &g = p->g;
+        const double s = std::max(g.dx, std::max(g.dy, g.dz));
+        const double R = std::hypot((0.5 * g.nx + 1.0) * g.dx, (0.5 * g.ny + 1.0) * g.dy);
+        const double Z = (0.5 * g.nz + 1.0) * g.dz, D = g.sid - R;
+        p->cell_rays = 0;
+        if (D > 1e-6 * g.sid) {
+            const double side = 2.0 * std::sqrt(2.0) * s;
+            const double Eu = g.sdd * (1.0 + R / D) * side / D, Ev = g.sdd * (1.0 + Z / D) * side / D;
+            const double cells = (std::floor(Eu / g.du) + 2.0) * (std::floor(Ev / g.dv) + 2.0);
+            if (cells < 16384.0) p->cell_rays = (int)cells;
+        }
+    }
     setup_view3d_kernel<<<(unsigned)cdiv(p->g.n_views, 128), 128>>>(p->g, p->view.p);
     PSPS_LAUNCH_CHECK();
     setup_rays3d_kernel<<<(unsigned)cdiv(p->n_rays, kThreads), kThreads>>>(p->g, p->view.p, p->n_rays, p->ray.p,
@@ -904,9 +1189,19 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
         PSPS_LAUNCH_CHECK();
         return MBIR_OK;
     }
+    // mode 0 (default): fixed-point tile scatter (the direct gather where the
+    // plan has no bound on the rays reaching a voxel); 1: direct gather; 3:
+    // split-table gather (1 and 3 bitwise equal)
+    const int mode = p->back_mode == 0 && (p->cell_rays <= 0 || p->g.n_views > (1 << 20)) ? 1 : p->back_mode;
     const dim3 grd((unsigned)cdiv(p->g.nx, kGX), (unsigned)cdiv(p->g.ny, kGY), (unsigned)cdiv(p->g.nz, kGZ));
+    const dim3 grt((unsigned)cdiv(p->g.nx, kTX), (unsigned)cdiv(p->g.ny, kTY), (unsigned)cdiv(p->g.nz, kTZ));
     const int nthr = kGX * kGY * kGZ;
     const unsigned gw = (unsigned)(cdiv(p->n_rays, kThreads) < 65535 * 16 ? cdiv(p->n_rays, kThreads) : 65535 * 16);
+    // tile transpose: a flush every vb views, T = vb * cell_rays terms per
+    // accumulator between flushes (T <= 256, so a grid of M 2^-22, where the
+    // bound allows)
+    const int vb = mode == 0 ? std::max(1, std::min(kTMaxVB, 256 / p->cell_rays)) : 1;
+    const int T = mode == 0 ? vb * p->cell_rays : 0;
     for (int m0 = 0; m0 < n_mat;) {
         const int left = n_mat - m0;
         const float *sm = sino + (int64_t)m0 * p->n_rays;
@@ -914,38 +1209,43 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
         const int nc = left >= 4 ? 4 : left;                 // channels of this launch
         const int C = nc == 1 ? 1 : (nc == 2 ? 2 : 4);      // interleaved floats per ray
         float *w = p->wsino.p;
-        // mode 0 (default): split-table gather; mode 1: the direct gather
-        // (both deterministic and bitwise equal)
-        const bool split = p->back_mode == 0;
-        if (C == 4) {
-            weigh_sino_kernel<4><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
+        unsigned *smax = mode == 0 ? p->wmax.p : nullptr;
+        const int nfine = std::max(0, std::min(nc, p->tile_fine - m0));   // leading channels with low words
+        if (smax) PSPS_CUDA(cudaMemsetAsync(smax, 0, 4 * sizeof(unsigned), s));
+        auto run = [&](auto cst) -> mbir_status {
+            constexpr int CC = decltype(cst)::value;
+            using V = typename Vec<CC>::T;
+            weigh_sino_kernel<CC><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w, smax);
             PSPS_LAUNCH_CHECK();
-            if (split)
-                back_cone_split_kernel<4><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
-                                                               p->view_axes.p, (const float4 *)w, nc, xm, accumulate);
+            const V *wv = reinterpret_cast<const V *>(w);
+            if (mode == 0) {
+                // the fine channels' count rounded up to an instantiated one
+                // (more fine channels only add precision)
+                auto tile = [&](auto nf) {
+                    back_cone_tile_kernel<CC, decltype(nf)::value><<<grt, kTThreads, 0, s>>>(
+                        p->g, p->view.p, p->ray.p, p->ray3b.p, p->view_axes.p, wv, smax, vb, T, nc, xm, accumulate);
+                };
+                if (nfine == 0)
+                    tile(std::integral_constant<int, 0>{});
+                else if (nfine <= CC / 2)
+                    tile(std::integral_constant<int, CC / 2 ? CC / 2 : 1>{});
+                else
+                    tile(std::integral_constant<int, CC>{});
+            } else if (mode == 3)
+                back_cone_split_kernel<CC><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                                p->view_axes.p, wv, nc, xm, accumulate);
             else
-                back_cone_gather_kernel<4><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
-                                                                p->view_axes.p, (const float4 *)w, nc, xm, accumulate);
-        } else if (C == 2) {
-            weigh_sino_kernel<2><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
+                back_cone_gather_kernel<CC><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
+                                                                 p->view_axes.p, wv, nc, xm, accumulate);
             PSPS_LAUNCH_CHECK();
-            if (split)
-                back_cone_split_kernel<2><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
-                                                               p->view_axes.p, (const float2 *)w, nc, xm, accumulate);
-            else
-                back_cone_gather_kernel<2><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
-                                                                p->view_axes.p, (const float2 *)w, nc, xm, accumulate);
-        } else {
-            weigh_sino_kernel<1><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w);
-            PSPS_LAUNCH_CHECK();
-            if (split)
-                back_cone_split_kernel<1><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
-                                                               p->view_axes.p, w, nc, xm, accumulate);
-            else
-                back_cone_gather_kernel<1><<<grd, nthr, 0, s>>>(p->g, p->view.p, p->ray.p, p->ray3b.p,
-                                                                p->view_axes.p, w, nc, xm, accumulate);
-        }
-        PSPS_LAUNCH_CHECK();
+            return MBIR_OK;
+        };
+        if (C == 4)
+            PSPS_TRY(run(std::integral_constant<int, 4>{}));
+        else if (C == 2)
+            PSPS_TRY(run(std::integral_constant<int, 2>{}));
+        else
+            PSPS_TRY(run(std::integral_constant<int, 1>{}));
         m0 += nc;
     }
     return MBIR_OK;

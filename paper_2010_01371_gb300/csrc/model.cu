@@ -359,7 +359,12 @@ mbir_status data_term(mbir_plan *plan, const mbmd_spectrum *spec, const float *x
     }
     PSPS_TRY(launch_model_grad(spec_dev(spec), n_rays, l, y, curv ? sc.gam.p : nullptr, g, kap, sc.part.p, nb, s));
     if (objective) PSPS_TRY(reduce_partials(sc.part.p, nb, 1, objective, 0, s));
-    if (grad && plan) PSPS_TRY(backproject(plan, g, grad, nm, 0, s));
+    if (grad && plan) {
+        plan->tile_fine = nm;   // gradient numerators: terms to 2^-12 of the tile transpose's unit
+        const mbir_status r = backproject(plan, g, grad, nm, 0, s);
+        plan->tile_fine = 0;
+        PSPS_TRY(r);
+    }
     if (curv && plan) PSPS_TRY(backproject(plan, kap, curv, nm, 0, s));
     PSPS_CUDA(cudaStreamSynchronize(s));  // scratch is released on return
     return MBIR_OK;

@@ -466,8 +466,8 @@ struct HessOp {
         }
         return MBIR_OK;
     }
-    // precise: sum the transpose in FP32 with the deterministic pixel gather
-    // instead of the fixed-point tile kernel (2-D plans), for the build steps
+    // precise: sum the transpose in FP32 with the deterministic pixel / voxel
+    // gather instead of the fixed-point tile kernel, for the build steps
     // with few probes (M0 blocks, Fourier impulses), where each pixel's
     // response spans many decades and a grid of the launch-wide largest term
     // would dominate the error of its small values.
@@ -482,7 +482,7 @@ struct HessOp {
         fisher_mul_kernel<<<nblk(n_rays), kThreads, 0, s>>>(nm, nprobe, n_rays, F, l.p, u.p);
         PSPS_LAUNCH_CHECK();
         const int mode = plan->back_mode;
-        if (precise && plan->g.kind != MBIR_CONE3D && mode == 0) plan->back_mode = 1;
+        if (precise && mode == 0) plan->back_mode = 1;
         const mbir_status bs = backproject(plan, u.p, out, ch, 0, s);
         plan->back_mode = mode;
         PSPS_TRY(bs);

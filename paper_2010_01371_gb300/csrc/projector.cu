@@ -1334,7 +1334,8 @@ extern "C" mbir_status mbir_backproject(mbir_plan *p, const float *sino, float *
 }
 
 extern "C" mbir_status mbir_plan_set_backprojector(mbir_plan *p, int mode) {
-    if (!p || mode < 0 || mode > 2) return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument");
+    if (!p || mode < 0 || mode > (p->g.kind == MBIR_CONE3D ? 3 : 2))
+        return fail(MBIR_ERR_ARG, "mbir_plan_set_backprojector: bad argument (0..2; 3 for cone plans)");
     p->back_mode = mode;
     return MBIR_OK;
 }
@@ -1380,9 +1381,12 @@ mbir_status autotune_impl(mbir_plan *p, int n_channels, cudaStream_t s) {
     PSPS_CUDA(cudaMemsetAsync(img.p, 0, sizeof(float) * img.n, s));
     float ms = 0.f, best_ms = 3.0e38f;
     if (p->g.kind == MBIR_CONE3D) {
-        // the transpose's algorithm: split-table gather (0) or direct gather (1)
+        // the transpose's algorithm: fixed-point tile scatter (0, where the
+        // plan bounds the rays reaching a voxel), direct gather (1) or
+        // split-table gather (3)
         int best = p->back_mode;
-        for (int mode : {0, 1}) {
+        for (int mode : {0, 1, 3}) {
+            if (mode == 0 && p->cell_rays <= 0) continue;
             p->back_mode = mode;
             PSPS_TRY(time_calls([&] { return backproject(p, sino.p, img.p, n_channels, 0, s); }, s, ev.e0, ev.e1, 1,
                                 ms));

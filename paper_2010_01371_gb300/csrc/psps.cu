@@ -169,8 +169,15 @@ mbir_status project_or_copy(psps_state *st, const float *x, float *l, cudaStream
     return MBIR_OK;
 }
 
-mbir_status backproject_or_copy(psps_state *st, const float *s_, float *x, int ch, cudaStream_t s) {
-    if (st->plan) return backproject(st->plan, s_, x, ch, 0, s);
+// fine: leading channels whose terms the 3-D tile transpose keeps to 2^-12
+// of its fixed-point unit
+mbir_status backproject_or_copy(psps_state *st, const float *s_, float *x, int ch, cudaStream_t s, int fine = 0) {
+    if (st->plan) {
+        st->plan->tile_fine = fine;
+        const mbir_status r = backproject(st->plan, s_, x, ch, 0, s);
+        st->plan->tile_fine = 0;
+        return r;
+    }
     PSPS_CUDA(cudaMemcpyAsync(x, s_, sizeof(float) * ch * st->n_rays, cudaMemcpyDeviceToDevice, s));
     return MBIR_OK;
 }
@@ -207,7 +214,11 @@ mbir_status iterate(psps_state *st, bool reproject, cudaStream_t s) {
                                st->part_obj.p, st->nb_model, s));
     mark(st, PSPS_PROF_MODEL, 1, s);
     mark(st, PSPS_PROF_BACKPROJECT, 0, s);
-    PSPS_TRY(backproject_or_copy(st, st->gk.p, st->G.p, 2 * nm, s));
+    // the cross-material Fourier and wavelet preconditioners difference the
+    // materials' gradient numerators after a spatial filter, which shows a
+    // fixed-point grid of M 2^-22 in the step: keep those to 2^-12 of it
+    const bool fine = st->pc && (st->pc->kind == PSPS_PRECOND_BLOCK_FOURIER || st->pc->kind == PSPS_PRECOND_BLOCK_HAAR);
+    PSPS_TRY(backproject_or_copy(st, st->gk.p, st->G.p, 2 * nm, s, fine ? nm : 0));
     mark(st, PSPS_PROF_BACKPROJECT, 1, s);
     mark(st, PSPS_PROF_PRECOND, 0, s);
     if (st->has_pen) PSPS_TRY(penalty_call(st, st->x.p, nullptr, st->G.p, 1, 0, st->part_pen.p, s));

@@ -170,12 +170,13 @@ def test_cone_project_parity(psps, oracle_lib, name, nm):
 
 
 @pytest.mark.parametrize("name", list(cone_geoms()))
-@pytest.mark.parametrize("mode", ["tile", "gather", "atomic"])
+@pytest.mark.parametrize("mode", ["tile", "gather", "atomic", "split"])
 @pytest.mark.parametrize("nch", [1, 2, 3, 5])
 def test_cone_backproject_parity(psps, oracle_lib, name, mode, nch):
-    """3-D transposes: the voxel-driven gather with split tables (default,
-    mode 'tile'), the direct voxel-driven gather ('gather'; channel groups of
-    4 / 2 / 1) and the ray-driven atomic scatter; accumulate adds."""
+    """3-D transposes: the fixed-point tile scatter (default, 'tile'), the
+    direct voxel-driven gather ('gather'; channel groups of 4 / 2 / 1), the
+    ray-driven atomic scatter and the gather with split tables ('split');
+    accumulate adds."""
     g = cone_geoms()[name]
     s = np.random.default_rng(12).random((nch, g.n_rays))
     plan = psps.Plan(g)
@@ -221,11 +222,12 @@ def test_tile_transpose_nonfinite_input(psps):
 @pytest.mark.parametrize("name", list(cone_geoms()) + ["c5_64"])
 def test_cone_gather_deterministic(psps, name):
     """The 3-D gathers have no atomics: two runs are bitwise equal, and the
-    split-table gather (default) equals the direct gather bit for bit (same
-    candidates, weights and summation order), 1, 2 and 4 channels."""
+    split-table gather equals the direct gather bit for bit (same candidates,
+    weights and summation order), 1, 2 and 4 channels."""
     g = cone_geoms()[name] if name != "c5_64" else synth.config5(n=64, n_views=90, n_u=128, n_v=96,
                                                                      rays=False).geom
     plan = psps.Plan(g)
+    plan.set_backprojector("split")
     direct = psps.Plan(g)
     direct.set_backprojector("gather")
     for nch in [1, 2, 4]:
@@ -234,6 +236,51 @@ def test_cone_gather_deterministic(psps, name):
         b = to_host(psps.mbir_backproject(plan, s))
         assert np.array_equal(a, b)
         assert np.array_equal(a, to_host(psps.mbir_backproject(direct, s))), nch
+
+
+@pytest.mark.parametrize("name", list(cone_geoms()) + ["c5_64"])
+def test_cone_tile_fixed_point(psps, oracle_lib, name):
+    """The 3-D tile transpose sums in fixed point: two runs, and the
+    accumulate mode on a zero image, are bitwise equal.  Signed data (the
+    worst case: the sums cancel) spanning four decades across channels: the
+    relative L2 error against the oracle stays within the projector's 1e-5,
+    and the largest element-wise difference from the FP32 voxel gather (the
+    same weights) within 3e-6 of the largest |A^T s| -- each term carries at
+    most half a unit of M 2^-22 (M = max |w s|; about 1e-6 expected at the
+    largest of these sums' independent roundings)."""
+    import torch
+    g = cone_geoms()[name] if name != "c5_64" else synth.config5(n=64, n_views=90, n_u=128, n_v=96,
+                                                                     rays=False).geom
+    rng = np.random.default_rng(18)
+    plan = psps.Plan(g)
+    assert plan.tuning()["backproject_mode"] == 0
+    s = rng.standard_normal((5, g.n_rays)) * np.array([1.0, 1e-2, 1e2, 3.0, 0.5])[:, None]
+    a = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    b = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    assert np.array_equal(a, b)
+    z = torch.zeros((5,) + g.image_shape, device="cuda", dtype=torch.float32)
+    assert np.array_equal(a, to_host(psps.mbir_backproject(plan, to_dev(s), z, accumulate=True)))
+    want = oracle_lib.Projector(g).backproject(s)
+    gather = psps.Plan(g)
+    gather.set_backprojector("gather")
+    ref = to_host(psps.mbir_backproject(gather, to_dev(s)))
+    for c in range(5):
+        assert rel_l2(a[c], want[c]) < TOL, (c, rel_l2(a[c], want[c]))
+        err = float(np.abs(a[c] - ref[c]).max())
+        assert err <= 3e-6 * float(np.abs(ref[c]).max()), (c, err / float(np.abs(ref[c]).max()))
+
+
+def test_cone_tile_nonfinite_input(psps):
+    """A NaN in a channel makes that channel's image NaN (its fixed-point
+    scale cannot be formed); the other channels are unchanged."""
+    g = cone_geoms()["cone_ragged"]
+    s = np.random.default_rng(19).random((2, g.n_rays))
+    plan = psps.Plan(g)
+    ref = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    s[1, 11] = np.nan
+    got = to_host(psps.mbir_backproject(plan, to_dev(s)))
+    assert np.array_equal(got[0], ref[0])
+    assert np.isnan(got[1]).all()
 
 
 def test_cone_full_size_sampled(psps, oracle_lib):
@@ -286,12 +333,12 @@ def test_strip_forward_shapes(psps, oracle_lib, sb):
 
 
 def test_autotune_cone(psps, oracle_lib):
-    """Cone plans: the autotuner picks one of the two gathers (bitwise
-    equal) and the transpose stays exact."""
+    """Cone plans: the autotuner picks the tile scatter or one of the two
+    gathers, and the transpose stays exact."""
     g = cone_geoms()["cone_ragged"]
     plan = psps.Plan(g)
     plan.autotune(4)
-    assert plan.tuning()["backproject_mode"] in (0, 1)
+    assert plan.tuning()["backproject_mode"] in (0, 1, 3)
     s = np.random.default_rng(17).random((4, g.n_rays))
     assert rel_l2(to_host(psps.mbir_backproject(plan, to_dev(s))), oracle_lib.Projector(g).backproject(s)) < TOL
 
