@@ -47,6 +47,13 @@ DEVLS_BYTES = 80
 # workload (summaries under profiles/): DRAM bytes read + written per launch,
 # and the unit that binds it.  Remove an entry when its kernel changes.
 NCU_CAPTURES = {
+    # 128^3 capture of the same kernel (back_cone_tile_kernel<4, 0>), 340.4 MB
+    # per launch, scaled by the rays and voxels processed (8x each) to 256^3
+    ("c5_cone3d_256_block", "backproject"): {
+        "traffic": 8 * 340.4e6,
+        "binding": {"unit": "SM instruction issue (issue active, % of cycles)", "frac_of_peak": 0.792,
+                    "source": "profiles/back_cone_tile_c5_128.md"},
+    },
     ("c2_fan2d_512_haar", "backproject"): {
         "traffic": 16.12e6,
         "binding": {"unit": "SM instruction issue (issue active, % of cycles)", "frac_of_peak": 0.858,
