@@ -149,9 +149,9 @@ mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
  * forward projection of n_channels / 2 (at least 1) basis images by one
  * thread per ray and by the strip kernel with 32/64/128/256 bins (and
  * 256 / that many views) per CTA.  Cone-beam plans: the tile scatter (where
- * available), the direct voxel gather and the split-table gather, then the forward's per-lane
- * and warp-aligned marches (mbir_plan_set_projector modes 1 and 2; equal
- * results).  Synchronises; allocates and
+ * available), the direct voxel gather and the split-table gather, then the
+ * forward's per-lane and warp-aligned marches (mbir_plan_set_projector modes
+ * 1 and 2; equal results).  Synchronises; allocates and
  * frees temporary device buffers; not allowed while `stream` is capturing
  * (MBIR_ERR_ARG).  MBIR_ERR_ARG if n_channels is outside 1..n_mat_max; on
  * any error the plan keeps its previous choices. */
@@ -166,7 +166,8 @@ mbir_status mbir_plan_tuning(const mbir_plan *plan, int *fwd_mode, int *strip_bi
 /* Select the forward projector's algorithm (Eq. 1's A).  2-D: 0 = per-tile
  * partial sums through shared memory, combined with one FP32 atomic per
  * (tile, ray); 1 = one thread per ray with Kahan-compensated sums, gathering
- * from L1/L2 (deterministic); 2 = rays of a block of views and bins march
+ * from L1/L2, eight samples summed before each compensated add
+ * (deterministic); 2 = rays of a block of views and bins march
  * shared-memory strips of the image, every lane on the same driving index
  * (deterministic).  Cone beam: one thread per ray; 1 (and 0) = each lane
  * marches its own range, 2 = the lanes of a warp march the same plane index

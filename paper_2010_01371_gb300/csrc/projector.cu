@@ -291,10 +291,12 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_pair_kernel(const float4 *__r
     const int rel = __float_as_int(kSplitMagic) - 1;
     const float2 *row = (axis == 0 ? pc : pr) + (int64_t)lo * stride;
     float acc = 0.f, comp = 0.f, fi = (float)lo;
-    // Four samples per step: their neighbour-pair loads are issued before any
-    // is consumed, so a lane keeps four independent gathers in flight; the
-    // samples are then added in order, exactly as one at a time.
-    constexpr int U = 4;
+    // Eight samples per step: their neighbour-pair loads are issued before
+    // any is consumed, so a lane keeps eight independent gathers in flight;
+    // the eight samples are summed in order in FP32 and that partial sum is
+    // added to the Kahan-compensated total (error of a partial: 7 roundings
+    // of at most 8 terms, then compensated across partials).
+    constexpr int U = 8;
     int i = lo;
     for (; i + U - 1 <= hi; i += U, fi += (float)U, row += U * stride) {
         float2 ab[U];
@@ -309,15 +311,16 @@ __global__ void __launch_bounds__(kThreads) fwd_2d_pair_kernel(const float4 *__r
             f[u] = (h - (rn - kSplitMagic)) + 0.5f;
             ab[u] = __ldg(row + u * stride + (ok[u] ? k : 0));
         }
+        float part = 0.f;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (!ok[u]) continue;
-            const float v = fmaf(f[u], ab[u].y - ab[u].x, ab[u].x);
-            const float yk = __fsub_rn(v, comp);
-            const float t = __fadd_rn(acc, yk);
-            comp = __fsub_rn(__fsub_rn(t, acc), yk);
-            acc = t;
+            const float v = ok[u] ? fmaf(f[u], ab[u].y - ab[u].x, ab[u].x) : 0.f;
+            part = __fadd_rn(part, v);
         }
+        const float yk = __fsub_rn(part, comp);
+        const float t = __fadd_rn(acc, yk);
+        comp = __fsub_rn(__fsub_rn(t, acc), yk);
+        acc = t;
     }
     for (; i <= hi; ++i, fi += 1.f, row += stride) {
         const float h = fmaf(fi, r.y, f0h);
