@@ -705,8 +705,9 @@ def kernel_bench(args, prob):
         for mode in ["ray", "aligned"]:
             plan.set_projector(mode)
             out[f"project_{mode}_{nm}ch_ms"] = timec(lambda: p.mbir_project(plan, x1, l))
-        for mode in ["tile", "gather", "split"]:
-            plan.set_backprojector(mode)
+        for mode in ["tile", "tile8", "gather", "split"]:
+            plan.set_backprojector("tile" if mode == "tile8" else mode)
+            plan.set_cone_tile(8 if mode == "tile8" else 16)
             out[f"backproject_{mode}_{2 * nm}ch_ms"] = timec(lambda: p.mbir_backproject(plan, s4, img))
         print(json.dumps({"kernels": out, "workload": args.workload}), flush=True)
         return

@@ -149,7 +149,8 @@ mbir_status mbir_plan_set_tiling(mbir_plan *plan, int views_per_cta);
  * forward projection of n_channels / 2 (at least 1) basis images by one
  * thread per ray and by the strip kernel with 32/64/128/256 bins (and
  * 256 / that many views) per CTA.  Cone-beam plans: the tile scatter (where
- * available), the direct voxel gather and the split-table gather, then the
+ * available; 16- and 8-voxel-deep tiles), the direct voxel gather and the
+ * split-table gather, then the
  * forward's per-lane and warp-aligned marches (mbir_plan_set_projector modes
  * 1 and 2; equal results).  Synchronises; allocates and
  * frees temporary device buffers; not allowed while `stream` is capturing
@@ -159,10 +160,16 @@ mbir_status mbir_plan_autotune(mbir_plan *plan, int n_channels, mbir_stream stre
 /* Bins per CTA of the strip forward (mode 2): 32, 64, 128 or 256, with
  * 256 / bins views per CTA; MBIR_ERR_ARG otherwise.  Work split only. */
 mbir_status mbir_plan_set_strip_bins(mbir_plan *plan, int bins);
+/* Depth of the cone tile transpose's tiles (mode 0): 8 x 8 x 16 voxels
+ * (default; 256 threads, four voxels each) or 8 x 8 x 8 (two voxels per
+ * thread, five CTAs per SM).  Work split only: both give the same terms and
+ * the same fixed-point grid.  MBIR_ERR_ARG for a 2-D plan or another depth. */
+mbir_status mbir_plan_set_cone_tile(mbir_plan *plan, int depth);
 /* The plan's current choices (any pointer may be NULL): forward algorithm
- * (mbir_plan_set_projector's modes), strip bins per CTA, transpose mode and
- * tile-transpose views per CTA. */
-mbir_status mbir_plan_tuning(const mbir_plan *plan, int *fwd_mode, int *strip_bins, int *back_mode, int *back_views);
+ * (mbir_plan_set_projector's modes), strip bins per CTA, transpose mode,
+ * tile-transpose views per CTA (2-D) and cone tile depth (3-D). */
+mbir_status mbir_plan_tuning(const mbir_plan *plan, int *fwd_mode, int *strip_bins, int *back_mode, int *back_views,
+                             int *cone_tile);
 /* Select the forward projector's algorithm (Eq. 1's A).  2-D: 0 = per-tile
  * partial sums through shared memory, combined with one FP32 atomic per
  * (tile, ray); 1 = one thread per ray with Kahan-compensated sums, gathering

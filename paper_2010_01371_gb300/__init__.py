@@ -101,11 +101,16 @@ class Plan:
 
     def tuning(self) -> dict:
         """The plan's current choices (``mbir_plan_tuning``)."""
-        v = [ctypes.c_int() for _ in range(4)]
+        v = [ctypes.c_int() for _ in range(5)]
         _call(lib().mbir_plan_tuning, self.h, *[ctypes.byref(x) for x in v])
         names = {0: "tile", 1: "ray", 2: "strip"}
         return {"forward": names[v[0].value], "strip_bins": v[1].value, "backproject_mode": v[2].value,
-                "views_per_cta": v[3].value}
+                "views_per_cta": v[3].value, "cone_tile": v[4].value}
+
+    def set_cone_tile(self, depth: int):
+        """Depth (16 or 8 voxels) of the cone tile transpose's 8 x 8 x depth
+        tiles (cone plans only)."""
+        _call(lib().mbir_plan_set_cone_tile, self.h, int(depth))
 
     def set_projector(self, mode: str):
         """2-D: 'ray' (one thread per ray), 'strip' (shared-memory strips) or

@@ -40,7 +40,8 @@ SIGNATURES = [
     ("mbir_plan_set_tiling", c_int, [c_void_p, c_int]),
     ("mbir_plan_autotune", c_int, [c_void_p, c_int, c_void_p, P(c_int)]),
     ("mbir_plan_set_projector", c_int, [c_void_p, c_int]),
-    ("mbir_plan_tuning", c_int, [c_void_p, P(c_int), P(c_int), P(c_int), P(c_int)]),
+    ("mbir_plan_tuning", c_int, [c_void_p, P(c_int), P(c_int), P(c_int), P(c_int), P(c_int)]),
+    ("mbir_plan_set_cone_tile", c_int, [c_void_p, c_int]),
     ("mbir_plan_set_strip_bins", c_int, [c_void_p, c_int]),
     ("mbir_project", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("mbir_backproject", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),

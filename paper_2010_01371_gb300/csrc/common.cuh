@@ -246,6 +246,8 @@ struct mbir_plan {
     // held to 2^-12 of the fixed-point unit); set around a call by the
     // gradient numerators' callers
     int tile_fine = 0;
+    // 3-D tile transpose: tile depth (16 or 8 voxels; 8 x 8 across)
+    int cone_tile = 16;
 };
 
 struct mbmd_spectrum {

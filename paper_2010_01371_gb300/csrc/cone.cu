@@ -857,7 +857,8 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
 }
 
 // Ray-driven tile transpose with fixed-point shared-memory sums (mode 0,
-// the default).  A CTA owns a tile of kTX x kTY x kTZ voxels and runs over
+// the default).  A CTA owns a tile of 8 x 8 x TZ voxels (TZ = 16 or 8, chosen
+// per plan) and runs over
 // every view.  For each view and each driving axis a of its rays it stages,
 // in chunks, the detector box that covers the tile's footprint (the gather's
 // box), and every pair (staged ray, tile plane of axis a) takes the forward's
@@ -868,7 +869,7 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
 // a sample whose taps straddle the tile's edge is taken by each tile it
 // reaches, for its own taps.
 //
-// The accumulators are 32-bit fixed point, [C][kTZ][kTY][kTX] with the x
+// The accumulators are 32-bit fixed point, [C][TZ][kTY][kTX] with the x
 // index XOR-swizzled by y, so that a warp's lanes (eight planes x four rays)
 // fall in distinct banks for x- and y-driven rays.  Channel c uses the scale
 //   sc = min(2^22, 2^30 / T) / M_c,  M_c = max_i |w_i s_c,i|,
@@ -890,9 +891,13 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
 // exact arithmetic is at most half a unit 1 / sc per term (2^-12 units for
 // the fine channels) plus the final conversion's 2^-24 relative.  The 64-bit
 // sums hold up to 2^20 flushes.
-constexpr int kTX = 8, kTY = 8, kTZ = 16;     // 1024 voxels per CTA
-constexpr int kTVox = kTX * kTY * kTZ;
-constexpr int kTPlane = kTVox;                 // words per channel
+constexpr int kTX = 8, kTY = 8;               // tile width and height; depth TZ = 16 (default) or 8
+template <int TZ>
+struct Tile3 {
+    static constexpr int Vox = kTX * kTY * TZ;     // voxels per CTA
+    static constexpr int Plane = Vox;              // words per channel
+    static constexpr int PerThread = Vox / 256;    // voxels per thread
+};
 constexpr int kTThreads = 256;                 // four voxels per thread
 constexpr int kTCap = 512;                     // staged rays per chunk
 constexpr int kTMaxVB = 32;                    // views per flush at most
@@ -926,29 +931,30 @@ __device__ __forceinline__ void red_word(unsigned addr, int v) {
 // channel: round(w v_c) to the coarse words, and for the first NF channels
 // the remainder w v_c - round(w v_c) on a grid 2^11 times finer to the low
 // words (LO bytes further on).
-template <int C, int NF, unsigned LO, int c = 0>
+template <int C, int NF, unsigned LO, int PL, int c = 0>
 __device__ __forceinline__ void tile3_tap(unsigned addr, float w, const float (&v)[C]) {
     if constexpr (c < C) {
         const float h = fmaf(w, v[c], kFixMagic3);   // magic + round(w v), exact
-        red_word<4u * c * kTPlane>(addr, __float_as_int(h) - kFixMagic3Bits);
+        red_word<4u * c * PL>(addr, __float_as_int(h) - kFixMagic3Bits);
         if constexpr (c < NF) {
             const float r = fmaf(w, v[c], kFixMagic3 - h);   // w v - round(w v), |r| <= 1/2
-            red_word<4u * c * kTPlane + LO>(addr, __float_as_int(fmaf(r, 2048.f, kFixMagic3)) - kFixMagic3Bits);
+            red_word<4u * c * PL + LO>(addr, __float_as_int(fmaf(r, 2048.f, kFixMagic3)) - kFixMagic3Bits);
         }
-        tile3_tap<C, NF, LO, c + 1>(addr, w, v);
+        tile3_tap<C, NF, LO, PL, c + 1>(addr, w, v);
     }
 }
 
 // The pairs (staged ray k < m, tile plane p) of driving axis A: the sample's
 // split on plane a0 + p and its terms on the taps inside the tile (b in
 // [b0, b0 + eb), c in [c0, c0 + ec); planes p < np).  NP consecutive
-// threads take the NP planes (8, or 16 for z-driven rays) of one ray.
-template <int A, int C, int NF>
+// threads take the NP planes (8, or the depth for z-driven rays) of one ray.
+template <int A, int C, int NF, int TZ>
 __device__ __forceinline__ void tile3_scatter(int m, const float4 *s_ta, const typename Vec<C>::T *s_ws,
                                               const int *s_ax, int a0, int np, float ca, int b0, int eb, int c0,
                                               int ec, unsigned acc) {
-    constexpr int NP = A == 2 ? kTZ : (A == 0 ? kTX : kTY);
-    constexpr unsigned LO = 4u * C * kTPlane;   // byte offset of the low words
+    constexpr int NP = A == 2 ? TZ : (A == 0 ? kTX : kTY);
+    constexpr int PL = Tile3<TZ>::Plane;
+    constexpr unsigned LO = 4u * C * PL;        // byte offset of the low words
     const int p = threadIdx.x % NP;
     if (p >= np) return;
     const float t = (float)(a0 + p) - ca;
@@ -972,18 +978,19 @@ __device__ __forceinline__ void tile3_scatter(int m, const float4 *s_ta, const t
                 if (bb < 0 || bb >= eb) continue;
                 const float wbc = (db ? gb : 1.f - gb) * wc;
                 const int w = A == 0 ? tile3_word(p, bb, cc) : (A == 1 ? tile3_word(bb, p, cc) : tile3_word(bb, cc, p));
-                tile3_tap<C, NF, LO>(acc + 4u * (unsigned)w, wbc, v);
+                tile3_tap<C, NF, LO, PL>(acc + 4u * (unsigned)w, wbc, v);
             }
         }
     }
 }
 
-template <int C, int NF>
-__global__ void __launch_bounds__(kTThreads, 4)
+template <int C, int NF, int TZ>
+__global__ void __launch_bounds__(kTThreads, TZ == 16 ? 4 : 5)
     back_cone_tile_kernel(mbir_geometry g, const float4 *__restrict__ vt, const float4 *__restrict__ ta,
                           const float2 *__restrict__ tb, const int *__restrict__ view_axes,
                           const typename Vec<C>::T *__restrict__ ws, const unsigned *__restrict__ smax, int vb,
                           int T, int nc, float *__restrict__ x, int accumulate) {
+    constexpr int kTPlane = Tile3<TZ>::Plane, kTZ = TZ, kPer = Tile3<TZ>::PerThread;
     __shared__ int acc[(C + NF) * kTPlane];   // C coarse planes, then the fine channels' low words
     __shared__ float4 s_ta[kTCap];
     __shared__ typename Vec<C>::T s_ws[kTCap];
@@ -1002,9 +1009,9 @@ __global__ void __launch_bounds__(kTThreads, 4)
 #pragma unroll
     for (int c = 0; c < C; ++c) sc[c] = tile3_scale(__ldg(smax + c), T);
     for (int k = tid; k < (C + NF) * kTPlane; k += kTThreads) acc[k] = 0;
-    long long sum[kTVox / kTThreads][C];
+    long long sum[kPer][C];
 #pragma unroll
-    for (int r = 0; r < kTVox / kTThreads; ++r)
+    for (int r = 0; r < kPer; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) sum[r][c] = 0;
     const unsigned acc_addr = (unsigned)__cvta_generic_to_shared(acc);
@@ -1046,18 +1053,18 @@ __global__ void __launch_bounds__(kTThreads, 4)
                 }
                 __syncthreads();
                 if (A == 0)
-                    tile3_scatter<0, C, NF>(m, s_ta, s_ws, s_ax, x0, ex, cx, y0, ey, z0, ez, acc_addr);
+                    tile3_scatter<0, C, NF, TZ>(m, s_ta, s_ws, s_ax, x0, ex, cx, y0, ey, z0, ez, acc_addr);
                 else if (A == 1)
-                    tile3_scatter<1, C, NF>(m, s_ta, s_ws, s_ax, y0, ey, cy, x0, ex, z0, ez, acc_addr);
+                    tile3_scatter<1, C, NF, TZ>(m, s_ta, s_ws, s_ax, y0, ey, cy, x0, ex, z0, ez, acc_addr);
                 else
-                    tile3_scatter<2, C, NF>(m, s_ta, s_ws, s_ax, z0, ez, cz, x0, ex, y0, ey, acc_addr);
+                    tile3_scatter<2, C, NF, TZ>(m, s_ta, s_ws, s_ax, z0, ez, cz, x0, ex, y0, ey, acc_addr);
                 __syncthreads();
             }
         }
         // flush this thread's voxels (no other thread reads or writes their
         // words until the next block's first barrier)
 #pragma unroll
-        for (int r = 0; r < kTVox / kTThreads; ++r) {
+        for (int r = 0; r < kPer; ++r) {
             const int j = tid + r * kTThreads;
             const int w = tile3_word(j % kTX, (j / kTX) % kTY, j / (kTX * kTY));
 #pragma unroll
@@ -1075,7 +1082,7 @@ __global__ void __launch_bounds__(kTThreads, 4)
     }
     const int64_t npix = (int64_t)g.nx * g.ny * g.nz;
 #pragma unroll
-    for (int r = 0; r < kTVox / kTThreads; ++r) {
+    for (int r = 0; r < kPer; ++r) {
         const int j = tid + r * kTThreads;
         const int lx = j % kTX, ly = (j / kTX) % kTY, lz = j / (kTX * kTY);
         if (lx >= ex || ly >= ey || lz >= ez) continue;
@@ -1194,7 +1201,8 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
     // split-table gather (1 and 3 bitwise equal)
     const int mode = p->back_mode == 0 && (p->cell_rays <= 0 || p->g.n_views > (1 << 20)) ? 1 : p->back_mode;
     const dim3 grd((unsigned)cdiv(p->g.nx, kGX), (unsigned)cdiv(p->g.ny, kGY), (unsigned)cdiv(p->g.nz, kGZ));
-    const dim3 grt((unsigned)cdiv(p->g.nx, kTX), (unsigned)cdiv(p->g.ny, kTY), (unsigned)cdiv(p->g.nz, kTZ));
+    const int tz = p->cone_tile == 8 ? 8 : 16;   // tile depth of the tile transpose
+    const dim3 grt((unsigned)cdiv(p->g.nx, kTX), (unsigned)cdiv(p->g.ny, kTY), (unsigned)cdiv(p->g.nz, tz));
     const int nthr = kGX * kGY * kGZ;
     const unsigned gw = (unsigned)(cdiv(p->n_rays, kThreads) < 65535 * 16 ? cdiv(p->n_rays, kThreads) : 65535 * 16);
     // tile transpose: a flush every vb views, T = vb * cell_rays terms per
@@ -1222,8 +1230,13 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
                 // the fine channels' count rounded up to an instantiated one
                 // (more fine channels only add precision)
                 auto tile = [&](auto nf) {
-                    back_cone_tile_kernel<CC, decltype(nf)::value><<<grt, kTThreads, 0, s>>>(
-                        p->g, p->view.p, p->ray.p, p->ray3b.p, p->view_axes.p, wv, smax, vb, T, nc, xm, accumulate);
+                    constexpr int NF = decltype(nf)::value;
+                    if (tz == 8)
+                        back_cone_tile_kernel<CC, NF, 8><<<grt, kTThreads, 0, s>>>(
+                            p->g, p->view.p, p->ray.p, p->ray3b.p, p->view_axes.p, wv, smax, vb, T, nc, xm, accumulate);
+                    else
+                        back_cone_tile_kernel<CC, NF, 16><<<grt, kTThreads, 0, s>>>(
+                            p->g, p->view.p, p->ray.p, p->ray3b.p, p->view_axes.p, wv, smax, vb, T, nc, xm, accumulate);
                 };
                 if (nfine == 0)
                     tile(std::integral_constant<int, 0>{});

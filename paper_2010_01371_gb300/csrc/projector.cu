@@ -1387,15 +1387,19 @@ mbir_status autotune_impl(mbir_plan *p, int n_channels, cudaStream_t s) {
         // the transpose's algorithm: fixed-point tile scatter (0, where the
         // plan bounds the rays reaching a voxel), direct gather (1) or
         // split-table gather (3)
-        int best = p->back_mode;
-        for (int mode : {0, 1, 3}) {
+        // (the tile scatter with tiles 16 or 8 voxels deep)
+        int best = p->back_mode, best_tile = p->cone_tile;
+        for (int cand : {0, 100, 1, 3}) {
+            const int mode = cand == 100 ? 0 : cand;
             if (mode == 0 && p->cell_rays <= 0) continue;
             p->back_mode = mode;
+            p->cone_tile = cand == 100 ? 8 : 16;
             PSPS_TRY(time_calls([&] { return backproject(p, sino.p, img.p, n_channels, 0, s); }, s, ev.e0, ev.e1, 1,
                                 ms));
-            if (ms < best_ms) best_ms = ms, best = mode;
+            if (ms < best_ms) best_ms = ms, best = mode, best_tile = p->cone_tile;
         }
         p->back_mode = best;
+        p->cone_tile = best_tile;
         // the forward's march: each lane from its own range (1) or warp-aligned (2)
         best_ms = 3.0e38f;
         best = p->fwd_mode;
@@ -1443,9 +1447,11 @@ extern "C" mbir_status mbir_plan_autotune(mbir_plan *p, int n_channels, mbir_str
     PSPS_CUDA(cudaStreamIsCapturing(s, &cap));
     if (cap != cudaStreamCaptureStatusNone) return fail(MBIR_ERR_ARG, "mbir_plan_autotune: stream is capturing");
     const int back_mode = p->back_mode, back_views = p->back_views, fwd_mode = p->fwd_mode, sb = p->strip_bins;
+    const int cone_tile = p->cone_tile;
     const mbir_status st = autotune_impl(p, n_channels, s);
     if (st != MBIR_OK) {   // keep the plan as it was
         p->back_mode = back_mode, p->back_views = back_views, p->fwd_mode = fwd_mode, p->strip_bins = sb;
+        p->cone_tile = cone_tile;
         return st;
     }
     if (views_per_cta) *views_per_cta = p->back_views;
@@ -1459,13 +1465,21 @@ extern "C" mbir_status mbir_plan_set_strip_bins(mbir_plan *p, int bins) {
     return MBIR_OK;
 }
 
+extern "C" mbir_status mbir_plan_set_cone_tile(mbir_plan *p, int depth) {
+    if (!p || p->g.kind != MBIR_CONE3D || (depth != 8 && depth != 16))
+        return fail(MBIR_ERR_ARG, "mbir_plan_set_cone_tile: a cone plan and a depth of 8 or 16");
+    p->cone_tile = depth;
+    return MBIR_OK;
+}
+
 extern "C" mbir_status mbir_plan_tuning(const mbir_plan *p, int *fwd_mode, int *strip_bins, int *back_mode,
-                                        int *back_views) {
+                                        int *back_views, int *cone_tile) {
     if (!p) return fail(MBIR_ERR_ARG, "mbir_plan_tuning: null plan");
     if (fwd_mode) *fwd_mode = p->fwd_mode;
     if (strip_bins) *strip_bins = p->strip_bins;
     if (back_mode) *back_mode = p->back_mode;
     if (back_views) *back_views = p->back_views;
+    if (cone_tile) *cone_tile = p->cone_tile;
     return MBIR_OK;
 }
 

@@ -238,8 +238,9 @@ def test_cone_gather_deterministic(psps, name):
         assert np.array_equal(a, to_host(psps.mbir_backproject(direct, s))), nch
 
 
+@pytest.mark.parametrize("depth", [16, 8])
 @pytest.mark.parametrize("name", list(cone_geoms()) + ["c5_64"])
-def test_cone_tile_fixed_point(psps, oracle_lib, name):
+def test_cone_tile_fixed_point(psps, oracle_lib, name, depth):
     """The 3-D tile transpose sums in fixed point: two runs, and the
     accumulate mode on a zero image, are bitwise equal.  Signed data (the
     worst case: the sums cancel) spanning four decades across channels: the
@@ -253,7 +254,8 @@ def test_cone_tile_fixed_point(psps, oracle_lib, name):
                                                                      rays=False).geom
     rng = np.random.default_rng(18)
     plan = psps.Plan(g)
-    assert plan.tuning()["backproject_mode"] == 0
+    assert plan.tuning()["backproject_mode"] == 0 and plan.tuning()["cone_tile"] == 16
+    plan.set_cone_tile(depth)
     s = rng.standard_normal((5, g.n_rays)) * np.array([1.0, 1e-2, 1e2, 3.0, 0.5])[:, None]
     a = to_host(psps.mbir_backproject(plan, to_dev(s)))
     b = to_host(psps.mbir_backproject(plan, to_dev(s)))
@@ -338,7 +340,11 @@ def test_autotune_cone(psps, oracle_lib):
     g = cone_geoms()["cone_ragged"]
     plan = psps.Plan(g)
     plan.autotune(4)
-    assert plan.tuning()["backproject_mode"] in (0, 1, 3)
+    assert plan.tuning()["backproject_mode"] in (0, 1, 3) and plan.tuning()["cone_tile"] in (8, 16)
+    with pytest.raises(RuntimeError):
+        plan.set_cone_tile(12)
+    with pytest.raises(RuntimeError):
+        psps.Plan(small_geoms()["fan2d_ragged"]).set_cone_tile(8)
     s = np.random.default_rng(17).random((4, g.n_rays))
     assert rel_l2(to_host(psps.mbir_backproject(plan, to_dev(s))), oracle_lib.Projector(g).backproject(s)) < TOL
 
