@@ -401,37 +401,6 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Weighted sinogram for the transposes: ws[ray][c] = w_ray * sino[c][ray],
-// channels interleaved (C = 1, 2 or 4 floats per ray; channels past nc are
-// 0).  smax (optional, zeroed by the caller): per channel max_ray |ws| as
-// float bits (atomicMax on the bits orders non-negative floats; a NaN makes
-// it NaN bits, above every finite value).
-template <int C>
-__global__ void weigh_sino_kernel(const float2 *__restrict__ tb, const float *__restrict__ sino, int nc,
-                                  int64_t n_rays, float *__restrict__ ws, unsigned *__restrict__ smax) {
-    unsigned mx[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) mx[c] = 0u;
-    for (int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ray < n_rays;
-         ray += (int64_t)gridDim.x * blockDim.x) {
-        const float w = tb[ray].x;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const float v = c < nc ? w * sino[(int64_t)c * n_rays + ray] : 0.f;
-            ws[ray * C + c] = v;
-            const float a = fabsf(v);
-            const unsigned bits = a != a ? 0x7fc00000u : __float_as_uint(a);
-            mx[c] = bits > mx[c] ? bits : mx[c];
-        }
-    }
-    if (!smax) return;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const unsigned m = __reduce_max_sync(0xffffffffu, mx[c]);
-        if ((threadIdx.x & 31) == 0 && m) atomicMax(smax + c, m);
-    }
-}
-
 template <int C>
 struct Vec;
 template <>
@@ -452,6 +421,38 @@ struct Vec<4> {
     __device__ static void get(const T &v, float (&o)[4]) { o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w; }
     __device__ static void put(T &v, const float (&o)[4]) { v = make_float4(o[0], o[1], o[2], o[3]); }
 };
+
+// Weighted sinogram for the transposes: ws[ray][c] = w_ray * sino[c][ray],
+// channels interleaved (C = 1, 2 or 4 floats per ray, one vector store;
+// channels past nc are 0).  smax (optional, zeroed by the caller): per
+// channel max_ray |ws| as float bits (atomicMax on the bits orders
+// non-negative floats; a NaN makes it NaN bits, above every finite value).
+template <int C>
+__global__ void weigh_sino_kernel(const float2 *__restrict__ tb, const float *__restrict__ sino, int nc,
+                                  int64_t n_rays, typename Vec<C>::T *__restrict__ ws, unsigned *__restrict__ smax) {
+    unsigned mx[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) mx[c] = 0u;
+    for (int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ray < n_rays;
+         ray += (int64_t)gridDim.x * blockDim.x) {
+        const float w = tb[ray].x;
+        float v[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            v[c] = c < nc ? w * __ldg(sino + (int64_t)c * n_rays + ray) : 0.f;
+            const float a = fabsf(v[c]);
+            const unsigned bits = a != a ? 0x7fc00000u : __float_as_uint(a);
+            mx[c] = bits > mx[c] ? bits : mx[c];
+        }
+        Vec<C>::put(ws[ray], v);
+    }
+    if (!smax) return;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, mx[c]);
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(smax + c, m);
+    }
+}
 
 // Detector cells whose centres lie in the bounding box of the projections of
 // points (x, y, z) with x in {xs}, y in {ys}, z in {zs} (2 values each) for
@@ -1204,7 +1205,9 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
     const int tz = p->cone_tile == 8 ? 8 : 16;   // tile depth of the tile transpose
     const dim3 grt((unsigned)cdiv(p->g.nx, kTX), (unsigned)cdiv(p->g.ny, kTY), (unsigned)cdiv(p->g.nz, tz));
     const int nthr = kGX * kGY * kGZ;
-    const unsigned gw = (unsigned)(cdiv(p->n_rays, kThreads) < 65535 * 16 ? cdiv(p->n_rays, kThreads) : 65535 * 16);
+    // the weighting pass: a grid-stride loop over 2048 CTAs at most, so that
+    // its per-warp maxima meet in few same-address atomics
+    const unsigned gw = (unsigned)(cdiv(p->n_rays, kThreads) < 2048 ? cdiv(p->n_rays, kThreads) : 2048);
     // tile transpose: a flush every vb views, T = vb * cell_rays terms per
     // accumulator between flushes (T <= 256, so a grid of M 2^-22, where the
     // bound allows)
@@ -1223,7 +1226,7 @@ mbir_status backproject_cone(mbir_plan *p, const float *sino, float *x, int n_ma
         auto run = [&](auto cst) -> mbir_status {
             constexpr int CC = decltype(cst)::value;
             using V = typename Vec<CC>::T;
-            weigh_sino_kernel<CC><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, w, smax);
+            weigh_sino_kernel<CC><<<gw, kThreads, 0, s>>>(p->ray3b.p, sm, nc, p->n_rays, reinterpret_cast<V *>(w), smax);
             PSPS_LAUNCH_CHECK();
             const V *wv = reinterpret_cast<const V *>(w);
             if (mode == 0) {
