@@ -241,7 +241,10 @@ mbir_status mbmd_objective(mbir_plan *plan, const mbmd_spectrum *spec, const flo
 /* Gradient of the data term with respect to x (plan != NULL: the adjoint
  * A^T of the per-ray derivative, recomputing l = A x and exp(-Q l) instead of
  * storing them) or l (plan == NULL).  grad has the shape of x_or_l
- * (overwritten); objective (device, nullable) receives L. */
+ * (overwritten); objective (device, nullable) receives L.  On a cone plan
+ * whose transpose is the tile scatter, every gradient channel keeps its
+ * terms to 2^-12 of the fixed-point unit (the low words of
+ * mbir_plan_set_backprojector's mode 0). */
 mbir_status mbmd_gradient(mbir_plan *plan, const mbmd_spectrum *spec, const float *x_or_l, const float *y,
                           int64_t n_rays, float *grad, double *objective, mbir_stream stream);
 
@@ -416,8 +419,13 @@ mbir_status psps_state_destroy(psps_state *st);
  * PSPS_FLAG_LINESEARCH) and the update x += alpha p.  If objective_history
  * (HOST, length n_iter + 1) is non-NULL the call synchronises and writes
  * Phi before each iteration and after the last one (after an exact
- * re-projection).  Returns MBIR_ERR_NONFINITE if a reduction went non-finite,
- * MBIR_ERR_ARG for n_iter < 0. */
+ * re-projection).  On a cone plan whose transpose is the tile scatter, the
+ * cross-material Fourier and wavelet preconditioners (which difference the
+ * materials' gradient numerators after a spatial filter) get the gradient
+ * channels to 2^-12 of the fixed-point unit (low words), the other kinds
+ * the unit M 2^-22 of mbir_plan_set_backprojector's mode 0.  Returns
+ * MBIR_ERR_NONFINITE if a reduction went non-finite, MBIR_ERR_ARG for
+ * n_iter < 0. */
 mbir_status psps_step(psps_state *st, int n_iter, double *objective_history, mbir_stream stream);
 
 /* Replace the measured counts y of the state (n = n_chan * n_rays values,
