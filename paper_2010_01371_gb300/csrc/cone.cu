@@ -888,10 +888,11 @@ __global__ void __launch_bounds__(kGX * kGY * kGZ, 4)
 // them below 2^31.  At every flush each thread moves its own voxels' words
 // into 64-bit registers (exact integer sums in units of 2^-11 / sc) and
 // clears them; the image is sum / sc.  Integer sums are exact, so the result
-// is the same bit for bit whatever order the adds run in; its error against
-// exact arithmetic is at most half a unit 1 / sc per term (2^-12 units for
-// the fine channels) plus the final conversion's 2^-24 relative.  The 64-bit
-// sums hold up to 2^20 flushes.
+// is the same bit for bit whatever order the adds run in; its error is at
+// most half a unit 1 / sc per term (2^-12 units for the fine channels),
+// besides the FP32 roundings of the scaled value v and of the weight product
+// (2^-24 of each term, as in the FP32 gather) and the final conversion's
+// 2^-24 relative.  The 64-bit sums hold up to 2^20 flushes.
 constexpr int kTX = 8, kTY = 8;               // tile width and height; depth TZ = 16 (default) or 8
 template <int TZ>
 struct Tile3 {
